@@ -1,0 +1,320 @@
+"""Benchmark of the mode-space Langevin step on one GB300.
+
+Workload: 4096 independent 256-bp dsDNA chains, FP32 state, dt = 15.9 ps
+(dtau ~ 100, Table 2), equilibrium-sampled starts, zero shear, per-chain
+Philox streams.  A bench "step" is one Langevin step of the whole batch
+(inverse transform, force + noise, forward transform, mode update).
+
+Prints one JSON line (rank 0).  Metric: bead-timesteps/s (chains x beads x
+steps / s); simulated ns/s per chain is reported beside it.
+  --impl reference   time the FP64 CPU oracle on the host cores instead
+  --precision simt   time the plain FP32 CUDA-core path instead of tcgen05
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+C_CHAINS, M_BEADS, DT_PS = 4096, 256, 15.9
+WORKLOAD = "dsDNA 4096 chains x 256 bp, FP32 state, dt 15.9 ps, equilibrium starts, no shear"
+METRIC, UNIT = "bead-timesteps/s", "bead-steps/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="tc", choices=["tc", "simt"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ oracle (CPU)
+
+def cpu_oracle_rate(n_chains: int, n_steps: int, seed: int = 1):
+    """Time the FP64 oracle on a sample of the workload (all host threads)."""
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    import paper_1411_3487_gb300 as sfp_mod  # noqa: F401  (only for the time unit)
+    c_ps = 0.15912
+    try:
+        c_ps = sfp_mod.derive()["c_ps"]
+    except Exception:
+        pass
+    m = O.Model(M_BEADS, dtau=DT_PS / c_ps)
+    R = np.stack([m.equilibrium_start(seed, j) for j in range(n_chains)])
+    jobs = np.arange(n_chains)
+    m.run_modes(R, seed, jobs, 0, 1)                       # warm (page-in, thread pool)
+    t0 = time.perf_counter()
+    m.run_modes(R, seed, jobs, 0, n_steps)
+    dt = time.perf_counter() - t0
+    return n_chains * M_BEADS * n_steps / dt, dt, O.threads()
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    c_ps = 0.15912
+    m = O.Model(M_BEADS, dtau=DT_PS / c_ps)
+    sample = 32
+    R = np.stack([m.equilibrium_start(1, j) for j in range(sample)])
+    jobs = np.arange(sample)
+    for s in range(args.warmup):
+        R = m.run_modes(R, 1, jobs, s, 1)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        R = m.run_modes(R, 1, jobs, args.warmup + s, 1)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = sample * M_BEADS * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{sample} of {C_CHAINS} chains per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+                         "sample": f"{sample} chains x 256 beads x {args.steps} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = None
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.proc = subprocess.Popen([exe, f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                      "-i", str(index), "-lms", "100"],
+                                     stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        time.sleep(0.3)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_native(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import paper_1411_3487_gb300 as sfp
+    from paper_1411_3487_gb300 import build
+    build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    precision = sfp.SFP_FP32 if args.precision == "tc" else sfp.SFP_FP32_SIMT
+    # weak scaling: every rank owns its own 4096 chains (disjoint job ids)
+    chains = [{"n_beads": M_BEADS, "dt_ps": DT_PS, "job_id": rank * C_CHAINS + i} for i in range(C_CHAINS)]
+
+    def timed_steps(prec, steps, warmup, with_clocks):
+        b = sfp.Batch(chains, seed=1, precision=prec, stream=stream)
+        b.init_equilibrium(0)
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        for _ in range(warmup):
+            b.step(1)
+            flush.zero_()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        launches0 = b.info()["launches"]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local) if with_clocks else None
+        b.stage_timing(True)                  # per-stage CUDA events on the batch's stream
+        for e0, e1 in ev:
+            flush.zero_()                     # L2 flushed between timed steps
+            e0.record(stream)
+            b.step(1)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop() if clk else None
+        if world > 1:
+            dist.barrier()
+        launches = b.info()["launches"] - launches0
+        kern = b.stage_times()
+        b.stage_timing(False)
+        ms = [a.elapsed_time(c) for a, c in ev]
+        return b, ms, launches, clocks, kern
+
+    b, ms, launches, clocks, kern = timed_steps(precision, args.steps, args.warmup, True)
+    tot_ms = float(sum(ms))
+    if world > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    beads = C_CHAINS * M_BEADS
+    value = world * beads * args.steps / (tot_ms * 1e-3)
+    d = sfp.derive()
+    dtau = DT_PS / d["c_ps"]
+    ms_step = tot_ms / args.steps
+
+    pk, how = peaks()
+    roof = roofline(kern, pk, how, precision, sfp)
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = end_to_end(sfp, b, torch, min(args.steps, 50))
+
+    plain = None
+    if not args.no_plain and precision != sfp.SFP_FP32_SIMT:
+        b.close()
+        _, ms_p, _, _, _ = timed_steps(sfp.SFP_FP32_SIMT, min(args.steps, 100), 3, False)
+        plain = {"value": beads * len(ms_p) / (sum(ms_p) * 1e-3), "unit": UNIT,
+                 "ms_per_step": float(sum(ms_p) / len(ms_p)), "path": "plain FP32 CUDA-core path"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        n_c, n_s = 512, 128
+        rate, secs, cores = cpu_oracle_rate(n_c, n_s)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n_c} chains x 256 beads x {n_s} steps ({secs:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if precision == sfp.SFP_FP32_SIMT else "f32 (tf32x3 transforms)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "chains_per_gpu": C_CHAINS, "beads": M_BEADS, "dt_ps": DT_PS,
+                       "dtau": dtau, "precision": "SFP_FP32" if precision == sfp.SFP_FP32 else "SFP_FP32_SIMT",
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "sim_ns_per_s_per_chain": DT_PS * 1e-3 * args.steps / (tot_ms * 1e-3),
+            "roofline": roof, "kernels_us": kern, "cpu_baseline": cpu, "e2e": e2e,
+            "plain_path": plain, "clocks": clocks, "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def roofline(kern, pk, how, precision, sfp):
+    if not kern:
+        return None
+    M, rows = M_BEADS, 3 * C_CHAINS
+    if precision == sfp.SFP_FP32:
+        # forward transform: [DeltaH|Z] = phi^T [f|z], 2*rows x M x M, three TF32 passes
+        us = kern.get("forward_us")
+        flops = 3 * 2.0 * (2 * rows) * M * M
+        peak = pk.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
+        return {"bound": "tensor", "kernel": "tcgen05 forward transform (tf32x3)",
+                "achieved": flops / (us * 1e-6) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / (us * 1e-6) / 1e12 / peak, "traffic": None,
+                "peak_source": f"{how} bf16 x 1.1/2.25 (nominal tf32/bf16)"}
+    us = kern.get("forward_us")
+    flops = 2.0 * (2 * rows) * M * M
+    peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    return {"bound": "alu", "kernel": "FP32 CUDA-core forward transform",
+            "achieved": flops / (us * 1e-6) / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": flops / (us * 1e-6) / 1e12 / peak, "traffic": None,
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+
+
+def end_to_end(sfp, b, torch, steps):
+    """Per step: H2D of the FP64 mode state from pinned host memory (sfp_set_modes),
+    one sfp_step, D2H of the FP64 mode state (sfp_observe); wall-clock timed."""
+    n = 3 * C_CHAINS * M_BEADS
+    hin = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hout = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    a_in, a_out = hin.numpy(), hout.numpy()
+    a_in[:] = b.modes().ravel()
+    import ctypes as ct
+    L = sfp._lib.load()
+    for _ in range(3):
+        sfp._lib.check(L.sfp_set_modes(b._h, a_in.ctypes.data, n))
+        sfp._lib.check(L.sfp_step(b._h, 1))
+        sfp._lib.check(L.sfp_observe(b._h, sfp.SFP_OBS_MODES, a_out.ctypes.data, n * 8))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sfp._lib.check(L.sfp_set_modes(b._h, a_in.ctypes.data, n))
+        sfp._lib.check(L.sfp_step(b._h, 1))
+        sfp._lib.check(L.sfp_observe(b._h, sfp.SFP_OBS_MODES, a_out.ctypes.data, n * 8))
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": C_CHAINS * M_BEADS * steps / dt, "unit": UNIT, "h2d_bytes_per_step": n * 8,
+            "d2h_bytes_per_step": n * 8, "steps": steps, "api": "sfp_set_modes + sfp_step + sfp_observe"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_native(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * sfp.h -- C ABI of the GB300 mode-space Langevin integrator for the
+ * extensible bead-spring model of semiflexible polymers (Panja, Barkema,
+ * van Leeuwen, "Efficient simulation of semiflexible polymers",
+ * arXiv:1411.3487).
+ *
+ * One batch = many independent chains (no hydrodynamics, Sec. 1), each with
+ * its own length, step size, shear rate and noise key.  Every call returns
+ * SFP_OK (0) or a negative SFP_E* code; sfp_last_error() then holds a
+ * one-line message for the calling thread.
+ *
+ * Units at this boundary: nm, ps, 1/s.  Inside, the paper's scaled units
+ * (Sec. 3, Eqs. b3-b5): lengths in d = a(1-2 nu), time in xi/lambda, so that
+ * t = c tau with c = T* (1-2nu)^2 a^2 xi / kT (Eq. g2).
+ *
+ * Ownership: the caller owns every host buffer it passes and may reuse it as
+ * soon as the call returns.  A batch owns all device memory it allocates and
+ * frees it in sfp_destroy().  Device work is queued on the batch's stream;
+ * only sfp_observe, sfp_probe, sfp_save and the sfp_set_* calls synchronise it.
+ *
+ * Packed per-chain arrays: for chains c = 0..C-1 (in the order given to
+ * sfp_create) with M_c beads, chain c's block is [3][M_c] (axis-major, index
+ * contiguous) and starts at offset 3 * sum_{c' < c} M_{c'} elements.
+ */
+#ifndef SFP_H
+#define SFP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define SFP_OK          0
+#define SFP_EINVAL     -1   /* bad argument (see sfp_last_error) */
+#define SFP_ENOMEM     -2   /* device allocation failed or exceeds the HBM budget */
+#define SFP_ECUDA      -3   /* a CUDA runtime call failed */
+#define SFP_ETIMEDOUT  -4   /* a bounded device wait gave up */
+#define SFP_ENONFINITE -5   /* a chain's state became non-finite */
+#define SFP_ENOTSUP    -6   /* valid request this build does not support */
+
+/* ---- model parameters (Eqs. a1-a3, Sec. 2A, Sec. 7B) --------------------- */
+typedef struct sfp_params {
+    /* Stretching and bending stiffness lambda, kappa of Eq. a1 (pN/nm).
+     * If lambda <= 0 the dimensionless pair (T_star, nu) below is used. */
+    double lambda_pN_per_nm;
+    double kappa_pN_per_nm;
+    double a_nm;             /* mean bead spacing a = b d (Sec. 2; 0.33 nm for dsDNA) */
+    double xi_kg_per_s;      /* bead friction xi (Eq. g1: 1.91e-12 kg/s) */
+    double kT_pN_nm;         /* thermal energy (4.089 pN nm at 23 C, Sec. 7B) */
+    double T_star;           /* T* = kT / (lambda d^2), used when lambda <= 0 */
+    double nu;               /* nu = kappa / lambda, 0 < nu < 1/2 (Sec. 2) */
+    /* a^2 xi / kT in ps (Eq. factor).  > 0: used as given (52.0 is the
+     * printed value, which reproduces Table 2); 0: computed from a, xi, kT. */
+    double a2xi_over_kT_ps;
+} sfp_params;
+
+/* Fill the paper's dsDNA parameter set (Sec. 2A, Sec. 7B): T* = 0.034,
+ * nu = 0.35, a = 0.33 nm, xi = 1.91e-12 kg/s, kT = 4.089 pN nm, and the
+ * printed a^2 xi / kT = 52.0 ps.  Host only; never fails for p != NULL. */
+int sfp_params_dsdna(sfp_params *p);
+
+/* Derived constants (host only, no GPU needed):
+ * out[0] = T*, out[1] = nu, out[2] = c (ps per unit of scaled time, Eq. g2),
+ * out[3] = d (nm), out[4] = b = 1/(1-2nu) (Eq. a3), out[5] = l_p/a = b^2 nu/T*
+ * (Eq. a3), out[6] = lambda (pN/nm), out[7] = kappa (pN/nm).
+ * SFP_EINVAL if nu is outside (0, 1/2) (Sec. 2) or a value is non-positive. */
+int sfp_derive(const sfp_params *p, double out[8]);
+
+/* ---- chains --------------------------------------------------------------- */
+typedef struct sfp_chain_desc {
+    int32_t  n_beads;          /* N+1 beads = basepairs (Sec. 2A); 3..4096 */
+    int32_t  reserved;         /* must be 0 */
+    double   dt_ps;            /* step in ps; used when dtau <= 0 (Table 2) */
+    double   dtau;             /* step in scaled time; > 0 takes precedence */
+    double   shear_rate_per_s; /* gamma-dot of Eq. btum (flow v = gamma y x); 0 = none */
+    uint64_t job_id;           /* Philox key word of this chain's noise; < 2^32 */
+} sfp_chain_desc;
+
+/* Arithmetic of the step.
+ * SFP_FP32       FP32 state; transforms on the tensor cores (tcgen05) with
+ *                a three-pass TF32 hi/lo split, FP32 accumulate.
+ * SFP_FP64       FP64 throughout (CUDA cores).
+ * SFP_FP32_SIMT  FP32 throughout on the CUDA cores: the plain path. */
+enum { SFP_FP32 = 0, SFP_FP64 = 1, SFP_FP32_SIMT = 4 };
+
+typedef struct sfp_batch sfp_batch;   /* opaque */
+
+/* Create a batch of n_chains chains.  Chains are grouped internally by
+ * (n_beads, dtau); each group gets its own tables (Eqs. c8, c9, e9, d3, d6,
+ * f2).  The initial state is the straight ground-state rod along x with its
+ * centre of mass at the origin; call sfp_init_equilibrium or sfp_set_* next.
+ *   seed        Philox key word 0 (< 2^32); job_id is key word 1.
+ *   cuda_stream cudaStream_t to queue work on (NULL = legacy default stream).
+ *   hbm_budget_bytes  upper bound on device memory this batch may hold
+ *               (0 = no bound); exceeding it returns SFP_ENOMEM.
+ * On failure *out is set to NULL and nothing is leaked. */
+int sfp_create(const sfp_params *params, const sfp_chain_desc *chains, int32_t n_chains,
+               uint64_t seed, int32_t precision, void *cuda_stream,
+               size_t hbm_budget_bytes, sfp_batch **out);
+
+/* Replace every chain's conformation by an approximately equilibrated one
+ * (the paper leaves the start open): bond lengths from the Gaussian of the
+ * stretching energy about the straight-rod ground state of Eq. a2, tangents
+ * as a von Mises-Fisher chain with concentration nu l_{n-1} l_n / T*, centre
+ * of mass at the origin.  Philox counter (0, 0, k, 1).  Then runs
+ * burn_in_steps ordinary steps.  Resets step counters to 0 first. */
+int sfp_init_equilibrium(sfp_batch *b, int64_t burn_in_steps);
+
+/* Set the state from host FP64 arrays, packed per chain as [3][M_c].
+ * sfp_set_modes takes mode amplitudes R_p (p = 0..N, Eq. c1) in scaled
+ * units, with R_0 = sqrt(N+1) r_cm; sfp_set_positions takes absolute bead
+ * positions in nm.  Step counters are left unchanged.  Synchronous. */
+int sfp_set_modes(sfp_batch *b, const double *host_modes, size_t n_doubles);
+int sfp_set_positions(sfp_batch *b, const double *host_pos_nm, size_t n_doubles);
+
+/* Set every chain's step counter (the Philox counter of its next step). */
+int sfp_set_step(sfp_batch *b, int64_t step);
+
+/* Advance every chain by n_steps mode-space steps (Sec. 4):
+ *   r = phi R (Eq. c1); DeltaH from the bond forces (Eq. e11); bead noise
+ *   z ~ N(0,1) keyed by (seed, job_id, step, bead) and projected (Eq. c4);
+ *   R_p <- e^{-zeta_p dtau} R_p + h_p DeltaH_p + w_p Z_p (Eqs. d3, d6, f2);
+ *   shear adds gamma g_p R^y_p to R^x_p (Eq. btum); the centre of mass
+ *   (p = 0) is carried in FP64.
+ * Asynchronous on the batch's stream.  SFP_EINVAL for n_steps < 0. */
+int sfp_step(sfp_batch *b, int64_t n_steps);
+
+/* Observables, copied to host_out (synchronises the stream).
+ *   SFP_OBS_MODES      FP64 packed [3][M_c], scaled units, R_0 = sqrt(M) r_cm
+ *   SFP_OBS_POSITIONS  FP64 packed [3][M_c], absolute bead positions in nm
+ *   SFP_OBS_COM        FP64 [C][3] centre of mass in nm
+ *   SFP_OBS_STEP       int64 [C] step counters
+ *   SFP_OBS_SHAPE      FP64 [C][4] per chain: |L|^2 (L = r_N - r_0), |u_m|^2 of
+ *                      the middle bond m = ceil(N/2), |r_m - r_cm|^2 of the
+ *                      middle bead m = floor(N/2) (Sec. 5B, observables
+ *                      i-iii at this instant), all in nm^2, and the
+ *                      simulated time t = c tau in ps
+ * bytes must be at least the size of the requested array. */
+enum { SFP_OBS_MODES = 0, SFP_OBS_POSITIONS = 1, SFP_OBS_COM = 2, SFP_OBS_STEP = 3,
+       SFP_OBS_SHAPE = 4 };
+int sfp_observe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
+
+/* Intermediate arrays of the most recent step, FP64 packed [3][M_c] in scaled
+ * units, for checking each stage on its own:
+ *   SFP_PROBE_BEADS  r = phi R without the centre of mass (Eq. c1)
+ *   SFP_PROBE_FORCE  f_n = v_n - v_{n+1}, v_n = u_n (1/|u_n| - (1-2nu)),
+ *                    v_0 = v_{N+1} = 0, so that phi^T f = DeltaH (Eq. e11)
+ *   SFP_PROBE_NOISE  bead normals z of that step (Eq. b5, unit variance)
+ *   SFP_PROBE_DH     phi^T f = DeltaH_p (Eq. e11)
+ *   SFP_PROBE_ZMODE  phi^T z = Z_p (Eq. c4)
+ * SFP_EINVAL if no step has run since the batch was created or its state set. */
+enum { SFP_PROBE_BEADS = 0, SFP_PROBE_FORCE = 1, SFP_PROBE_NOISE = 2, SFP_PROBE_DH = 3,
+       SFP_PROBE_ZMODE = 4 };
+int sfp_probe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
+
+/* Checkpoint / resume.  sfp_save writes the whole dynamic state (modes,
+ * centre of mass, step counters) into host_buf; *needed receives the size
+ * (host_buf may be NULL to query it).  sfp_load restores it into a batch
+ * created with the same chains and precision.  Because the noise is
+ * counter-based, a resumed run continues the same trajectory bit for bit. */
+int sfp_save(sfp_batch *b, void *host_buf, size_t bytes, size_t *needed);
+int sfp_load(sfp_batch *b, const void *host_buf, size_t bytes);
+
+/* Number of chains, total beads, device bytes held, and kernel launches
+ * issued by sfp_step so far (out[0..3]). */
+int sfp_info(const sfp_batch *b, int64_t out[4]);
+
+/* Stage timing.  While enabled, every sfp_step records CUDA events on the
+ * batch's stream between its stage launches (inverse transform, force and
+ * noise, forward transform, mode update).  Enabling clears the totals.
+ * sfp_stage_times synchronises the stream and writes the summed device time
+ * in microseconds of [inverse, force+noise, forward, update, whole step]
+ * over *n_group_steps recorded group-steps (one per length group per step). */
+int sfp_stage_timing(sfp_batch *b, int32_t enable);
+int sfp_stage_times(sfp_batch *b, double out_us[5], int64_t *n_group_steps);
+
+/* Free every device buffer of the batch (synchronises its stream). NULL is a no-op. */
+int sfp_destroy(sfp_batch *b);
+
+/* Last error message of the calling thread ("" if none). */
+const char *sfp_last_error(void);
+
+/* Raw Philox4x32-10 words computed on the GPU for counter (step_lo, step_hi,
+ * i, tag) and key (seed, job), i = 0..count-1, into host_out[4*count].
+ * For checking the device generator bit for bit; synchronous. */
+int sfp_philox_words(uint32_t seed, uint32_t job, int64_t step, uint32_t tag,
+                     int32_t count, uint32_t *host_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFP_H */

@@ -1,0 +1,191 @@
+"""GB300 mode-space Langevin dynamics of the extensible bead-spring model of
+semiflexible polymers (Panja, Barkema, van Leeuwen, arXiv:1411.3487).
+
+The simulation runs in the CUDA library ``_build/libsfp.so`` behind the C ABI
+of ``include/sfp.h``; this package is its Python binding.  Host arrays are
+numpy; the CUDA stream may be a ``torch.cuda.Stream`` or a raw handle.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+
+import numpy as np
+
+from . import _lib
+from ._lib import (SFP_FP32, SFP_FP32_SIMT, SFP_FP64, SFP_OBS_COM, SFP_OBS_MODES,
+                   SFP_OBS_POSITIONS, SFP_OBS_SHAPE, SFP_OBS_STEP, SFP_PROBE_BEADS, SFP_PROBE_DH,
+                   SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_ZMODE, SfpChainDesc, SfpError,
+                   SfpParams)
+
+__all__ = ["Batch", "params_dsdna", "derive", "philox_words", "SfpError", "SFP_FP32",
+           "SFP_FP64", "SFP_FP32_SIMT"]
+
+
+def params_dsdna() -> SfpParams:
+    """The paper's dsDNA parameter set (Sec. 2A, Sec. 7B)."""
+    p = SfpParams()
+    _lib.check(_lib.load().sfp_params_dsdna(ct.byref(p)))
+    return p
+
+
+def derive(p: SfpParams | None = None) -> dict:
+    """Derived constants: T*, nu, c (ps per scaled time unit, Eq. g2), d (nm), b, l_p/a,
+    lambda, kappa (pN/nm)."""
+    p = p or params_dsdna()
+    out = (ct.c_double * 8)()
+    _lib.check(_lib.load().sfp_derive(ct.byref(p), out))
+    keys = ("Tstar", "nu", "c_ps", "d_nm", "b", "lp_over_a", "lambda_pN_per_nm", "kappa_pN_per_nm")
+    return dict(zip(keys, list(out)))
+
+
+def philox_words(seed: int, job: int, step: int, tag: int, count: int) -> np.ndarray:
+    """Raw Philox4x32-10 words computed on the GPU, shape [count, 4]."""
+    out = np.zeros((count, 4), dtype=np.uint32)
+    _lib.check(_lib.load().sfp_philox_words(seed, job, step, tag, count, out.ctypes.data))
+    return out
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+class Batch:
+    """A batch of independent chains advanced together on one GPU.
+
+    ``chains`` is a sequence of dicts with ``n_beads`` and one of ``dt_ps`` or
+    ``dtau``, optional ``shear_rate_per_s`` and ``job_id`` (default: index).
+    """
+
+    def __init__(self, chains, seed: int = 1, precision: int = SFP_FP32, params: SfpParams | None = None,
+                 stream=None, hbm_budget_bytes: int = 0):
+        L = _lib.load()
+        self.params = params or params_dsdna()
+        n = len(chains)
+        arr = (SfpChainDesc * n)()
+        self.n_beads = np.zeros(n, dtype=np.int64)
+        for i, c in enumerate(chains):
+            arr[i].n_beads = int(c["n_beads"])
+            arr[i].dt_ps = float(c.get("dt_ps", 0.0))
+            arr[i].dtau = float(c.get("dtau", 0.0))
+            arr[i].shear_rate_per_s = float(c.get("shear_rate_per_s", 0.0))
+            arr[i].job_id = int(c.get("job_id", i))
+            self.n_beads[i] = arr[i].n_beads
+        self.offsets = np.concatenate([[0], np.cumsum(3 * self.n_beads)])
+        self.n_chains = n
+        self.precision = precision
+        h = ct.c_void_p()
+        _lib.check(L.sfp_create(ct.byref(self.params), arr, n, seed, precision, _stream_handle(stream),
+                                hbm_budget_bytes, ct.byref(h)))
+        self._h = h
+
+    # -- lifecycle -----------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.check(_lib.load().sfp_destroy(self._h))
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- state ---------------------------------------------------------------
+    def init_equilibrium(self, burn_in_steps: int = 0) -> None:
+        _lib.check(_lib.load().sfp_init_equilibrium(self._h, burn_in_steps))
+
+    def _packed(self, a) -> np.ndarray:
+        if isinstance(a, (list, tuple)):
+            a = np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in a])
+        a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+        if a.size != self.offsets[-1]:
+            raise ValueError(f"expected {self.offsets[-1]} doubles, got {a.size}")
+        return a
+
+    def set_modes(self, modes) -> None:
+        a = self._packed(modes)
+        _lib.check(_lib.load().sfp_set_modes(self._h, a.ctypes.data, a.size))
+
+    def set_positions(self, pos_nm) -> None:
+        a = self._packed(pos_nm)
+        _lib.check(_lib.load().sfp_set_positions(self._h, a.ctypes.data, a.size))
+
+    def set_step(self, step: int) -> None:
+        _lib.check(_lib.load().sfp_set_step(self._h, step))
+
+    def step(self, n_steps: int = 1) -> None:
+        _lib.check(_lib.load().sfp_step(self._h, n_steps))
+
+    # -- outputs ---------------------------------------------------------------
+    def _unpack(self, flat: np.ndarray):
+        if np.all(self.n_beads == self.n_beads[0]):
+            return flat.reshape(self.n_chains, 3, int(self.n_beads[0]))
+        return [flat[self.offsets[i]:self.offsets[i + 1]].reshape(3, -1) for i in range(self.n_chains)]
+
+    def observe(self, what: int):
+        L = _lib.load()
+        if what in (SFP_OBS_MODES, SFP_OBS_POSITIONS):
+            out = np.zeros(int(self.offsets[-1]))
+            _lib.check(L.sfp_observe(self._h, what, out.ctypes.data, out.nbytes))
+            return self._unpack(out)
+        if what == SFP_OBS_COM:
+            out = np.zeros((self.n_chains, 3))
+        elif what == SFP_OBS_STEP:
+            out = np.zeros(self.n_chains, dtype=np.int64)
+        elif what == SFP_OBS_SHAPE:
+            out = np.zeros((self.n_chains, 4))
+        else:
+            raise ValueError(what)
+        _lib.check(L.sfp_observe(self._h, what, out.ctypes.data, out.nbytes))
+        return out
+
+    def modes(self):
+        return self.observe(SFP_OBS_MODES)
+
+    def positions_nm(self):
+        return self.observe(SFP_OBS_POSITIONS)
+
+    def probe(self, what: int):
+        out = np.zeros(int(self.offsets[-1]))
+        _lib.check(_lib.load().sfp_probe(self._h, what, out.ctypes.data, out.nbytes))
+        return self._unpack(out)
+
+    def save(self) -> bytes:
+        L = _lib.load()
+        need = ct.c_size_t()
+        _lib.check(L.sfp_save(self._h, None, 0, ct.byref(need)))
+        buf = ct.create_string_buffer(need.value)
+        _lib.check(L.sfp_save(self._h, buf, need.value, ct.byref(need)))
+        return buf.raw
+
+    def load(self, blob: bytes) -> None:
+        _lib.check(_lib.load().sfp_load(self._h, blob, len(blob)))
+
+    def stage_timing(self, enable: bool = True) -> None:
+        _lib.check(_lib.load().sfp_stage_timing(self._h, int(bool(enable))))
+
+    def stage_times(self) -> dict:
+        """Average device time per group-step of each stage, in microseconds."""
+        out = (ct.c_double * 5)()
+        n = ct.c_int64()
+        _lib.check(_lib.load().sfp_stage_times(self._h, out, ct.byref(n)))
+        k = max(1, n.value)
+        names = ("inverse_us", "force_noise_us", "forward_us", "update_us", "step_us")
+        d = {nm: out[i] / k for i, nm in enumerate(names)}
+        d["group_steps"] = n.value
+        return d
+
+    def info(self) -> dict:
+        out = (ct.c_int64 * 4)()
+        _lib.check(_lib.load().sfp_info(self._h, out))
+        return {"chains": out[0], "beads": out[1], "device_bytes": out[2], "launches": out[3]}

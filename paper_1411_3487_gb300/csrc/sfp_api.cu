@@ -1,0 +1,888 @@
+// sfp_api.cu -- host implementation of the C ABI declared in include/sfp.h.
+//
+// A batch holds one "group" per distinct (n_beads, dtau).  Each group owns
+// its FP64-derived tables (Eqs. c8, c9, e9, d3, d6, f2), its chains' state
+// R[c][3][M] (p = 0 slot kept at zero; the centre of mass lives in FP64
+// r_cm[c][3]), per-chain keys/shear/step counters, and scratch for the
+// unfused step: r (beads), f|z (force and noise), DeltaH|Z (mode space).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/sfp.h"
+#include "sfp_simt.cuh"
+#include "sfp_tc.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(SFP_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));      \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr uint64_t kMagic = 0x3148504653ull;   // "SFPH1"
+
+struct Derived {
+    double Tstar, nu, c_ps, d_nm, b, lp_over_a, lambda, kappa;
+};
+
+int derive(const sfp_params* p, Derived* d)
+{
+    if (!p) return fail(SFP_EINVAL, "params is NULL");
+    double Tstar, nu;
+    if (p->lambda_pN_per_nm > 0.0) {
+        if (!(p->kappa_pN_per_nm > 0.0)) return fail(SFP_EINVAL, "kappa must be > 0");
+        nu = p->kappa_pN_per_nm / p->lambda_pN_per_nm;
+        if (!(nu > 0.0 && nu < 0.5)) return fail(SFP_EINVAL, "nu = kappa/lambda = %g outside (0, 1/2)", nu);
+        if (!(p->a_nm > 0.0) || !(p->kT_pN_nm > 0.0))
+            return fail(SFP_EINVAL, "a and kT must be > 0 when lambda is given");
+        const double dd = p->a_nm * (1.0 - 2.0 * nu);
+        Tstar = p->kT_pN_nm / (p->lambda_pN_per_nm * dd * dd);
+    } else {
+        Tstar = p->T_star;
+        nu = p->nu;
+        if (!(nu > 0.0 && nu < 0.5)) return fail(SFP_EINVAL, "nu = %g outside (0, 1/2)", nu);
+        if (!(Tstar > 0.0)) return fail(SFP_EINVAL, "T_star must be > 0");
+    }
+    if (!(p->a_nm > 0.0)) return fail(SFP_EINVAL, "a_nm must be > 0");
+    double a2xi;
+    if (p->a2xi_over_kT_ps > 0.0) {
+        a2xi = p->a2xi_over_kT_ps;
+    } else {
+        if (!(p->xi_kg_per_s > 0.0) || !(p->kT_pN_nm > 0.0))
+            return fail(SFP_EINVAL, "xi and kT must be > 0 to compute a^2 xi / kT");
+        // (a nm)^2 * xi / (kT pN nm) in ps: 1e-18 m^2 * kg/s / 1e-21 J = 1e3 s -> 1e15 ps
+        a2xi = p->a_nm * p->a_nm * p->xi_kg_per_s / p->kT_pN_nm * 1e15;
+    }
+    const double b = 1.0 / (1.0 - 2.0 * nu);
+    d->Tstar = Tstar;
+    d->nu = nu;
+    d->c_ps = Tstar / (b * b) * a2xi;                       // Eq. g2
+    d->d_nm = p->a_nm / b;
+    d->b = b;
+    d->lp_over_a = b * b * nu / Tstar;                      // Eq. a3
+    d->lambda = (p->kT_pN_nm > 0.0) ? p->kT_pN_nm / (Tstar * d->d_nm * d->d_nm) : 0.0;
+    d->kappa = nu * d->lambda;
+    return SFP_OK;
+}
+
+// FP64 tables of one (M, dtau), the closed forms of Eqs. c8, c9, e9, d3, d6, f2
+// written for accuracy: 1 - cos t = 2 sin^2(t/2), 1 - e^{-x} = -expm1(-x).
+struct Tables {
+    std::vector<double> phi, phiT, dm, h, w, g;
+    double w0;
+};
+
+void make_tables(int M, double Tstar, double nu, double dtau, Tables* t)
+{
+    t->phi.assign((size_t)M * M, 0.0);
+    t->phiT.assign((size_t)M * M, 0.0);
+    for (int n = 0; n < M; ++n)
+        for (int p = 0; p < M; ++p) {
+            const double v = (p == 0) ? 1.0 / std::sqrt((double)M)
+                                      : std::sqrt(2.0 / M) * std::cos(kPi * p * (n + 0.5) / M);
+            t->phi[(size_t)n * M + p] = v;
+            t->phiT[(size_t)p * M + n] = v;
+        }
+    t->dm.assign(M, 0.0); t->h.assign(M, 0.0); t->w.assign(M, 0.0); t->g.assign(M, 0.0);
+    t->w0 = std::sqrt(2.0 * Tstar * dtau);
+    t->g[0] = dtau;
+    for (int p = 1; p < M; ++p) {
+        const double s2 = std::pow(std::sin(0.5 * kPi * p / M), 2);      // sin^2(theta/2)
+        const double zeta = 16.0 * nu * s2 * s2;                           // 4 nu (1 - cos)^2
+        const double gap = (1.0 - 2.0 * nu) * 4.0 * s2;                    // zeta^l - zeta
+        const double em = -std::expm1(-zeta * dtau);                       // 1 - e^{-zeta dtau}
+        t->dm[p] = em;
+        t->h[p] = std::exp(-zeta * dtau) * (-std::expm1(-gap * dtau)) / gap;
+        t->w[p] = std::sqrt(Tstar * (-std::expm1(-2.0 * zeta * dtau)) / zeta);
+        t->g[p] = em / zeta;
+    }
+}
+
+// Straight-rod ground state (tridiagonal l_n - nu (l_{n-1} + l_{n+1}) = 1) and the
+// Cholesky factor of I - nu A.
+void rod_tables(int M, double nu, std::vector<double>* l0, std::vector<double>* Ld,
+                std::vector<double>* Lo)
+{
+    const int N = M - 1;
+    l0->assign(N, 0.0); Ld->assign(N, 0.0); Lo->assign(N, 0.0);
+    std::vector<double> cp(N), dp(N);
+    cp[0] = -nu; dp[0] = 1.0;
+    for (int i = 1; i < N; ++i) {
+        const double den = 1.0 + nu * cp[i - 1];
+        cp[i] = -nu / den;
+        dp[i] = (1.0 + nu * dp[i - 1]) / den;
+    }
+    (*l0)[N - 1] = dp[N - 1];
+    for (int i = N - 2; i >= 0; --i) (*l0)[i] = dp[i] - cp[i] * (*l0)[i + 1];
+    (*Ld)[0] = 1.0;
+    for (int i = 1; i < N; ++i) {
+        (*Lo)[i] = -nu / (*Ld)[i - 1];
+        (*Ld)[i] = std::sqrt(1.0 - (*Lo)[i] * (*Lo)[i]);
+    }
+}
+
+}  // namespace
+
+int sfp::report(int code, const char* msg) { return fail(code, "%s", msg); }
+
+struct Group {
+    int M = 0;
+    double dtau = 0.0;
+    int C = 0;
+    std::vector<int> chains;      // indices into the batch's chain list
+    Tables tab;
+    // device
+    void* R = nullptr;            // [C][3][M] state (T)
+    double* com = nullptr;        // [C][3]
+    uint32_t* job = nullptr;      // [C]
+    double* shear = nullptr;      // [C] shear rate in 1/tau
+    int64_t* step = nullptr;      // [C]
+    void *phi = nullptr, *phiT = nullptr, *dm = nullptr, *h = nullptr, *w = nullptr, *g = nullptr;
+    double *phi_d = nullptr, *phiT_d = nullptr;   // FP64 copies for conversions
+    void* r = nullptr;            // [C][3][M]
+    void* fz = nullptr;           // [2][C][3][M]
+    void* yz = nullptr;           // [2][C][3][M]
+    double* stage = nullptr;      // [C][3][M] FP64 staging
+    double* stage2 = nullptr;     // [C][3][M] FP64 staging
+    sfp::TcPlan* tc = nullptr;    // tensor-core transform plan (SFP_FP32)
+};
+
+struct sfp_batch {
+    Derived dv{};
+    int precision = 0;
+    uint32_t seed = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0, held = 0;
+    int64_t launches = 0;
+    bool probed = false;
+    int C = 0;
+    int64_t total_beads = 0;
+    std::vector<sfp_chain_desc> desc;
+    std::vector<int64_t> off;      // packed offset (elements) of each chain
+    std::vector<int> group_of, slot_of;
+    std::vector<Group> groups;
+    std::vector<void*> allocs;
+    int* bad = nullptr;
+    // stage timing
+    bool timing = false;
+    std::vector<cudaEvent_t> events;   // pool, 5 per recorded group-step
+    size_t ev_used = 0;
+    double stage_us[5] = {0, 0, 0, 0, 0};
+    int64_t timed_group_steps = 0;
+};
+
+namespace {
+
+size_t esize(const sfp_batch* b) { return b->precision == SFP_FP64 ? sizeof(double) : sizeof(float); }
+
+int dalloc(sfp_batch* b, void** p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (b->budget && b->held + bytes > b->budget)
+        return fail(SFP_ENOMEM, "HBM budget of %zu bytes exceeded (%zu held, %zu requested)",
+                    b->budget, b->held, bytes);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(SFP_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    b->held += bytes;
+    b->allocs.push_back(*p);
+    return SFP_OK;
+}
+
+template <typename P> int dalloc_t(sfp_batch* b, P** p, size_t bytes)
+{
+    void* v = nullptr;
+    int rc = dalloc(b, &v, bytes);
+    *p = (P*)v;
+    return rc;
+}
+
+int upload_typed(sfp_batch* b, void* dst, const std::vector<double>& src)
+{
+    if (b->precision == SFP_FP64) {
+        CUDA_TRY(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    } else {
+        std::vector<float> f(src.begin(), src.end());
+        CUDA_TRY(cudaMemcpyAsync(dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice, b->stream));
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+    }
+    return SFP_OK;
+}
+
+unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename T>
+int launch_gemm(sfp_batch* b, const T* In, const T* B, T* Out, int J, int Nc, int K)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (Nc >= 128) {
+            dim3 grid(nblk(Nc, 128), nblk(J, 128));
+            sfp::k_gemm_nt<float, 128, 128, 8, 8, 8><<<grid, 256, 0, b->stream>>>(In, B, Out, J, Nc, K);
+        } else {
+            dim3 grid(nblk(Nc, 64), nblk(J, 64));
+            sfp::k_gemm_nt<float, 64, 64, 8, 4, 4><<<grid, 256, 0, b->stream>>>(In, B, Out, J, Nc, K);
+        }
+    } else {
+        dim3 grid(nblk(Nc, 64), nblk(J, 64));
+        sfp::k_gemm_nt<double, 64, 64, 8, 4, 4><<<grid, 256, 0, b->stream>>>(In, B, Out, J, Nc, K);
+    }
+    b->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return SFP_OK;
+}
+
+// Record one event of the current group-step (no-op unless timing is on).
+int mark(sfp_batch* b, int k)
+{
+    if (!b->timing) return SFP_OK;
+    const size_t idx = b->ev_used + k;
+    while (b->events.size() <= idx) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        b->events.push_back(e);
+    }
+    CUDA_TRY(cudaEventRecord(b->events[idx], b->stream));
+    if (k == 4) b->ev_used += 5;
+    return SFP_OK;
+}
+
+// Fold the recorded events into the per-stage totals (synchronises).
+int harvest(sfp_batch* b)
+{
+    if (b->ev_used == 0) return SFP_OK;
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    for (size_t i = 0; i < b->ev_used; i += 5) {
+        for (int k = 0; k < 4; ++k) {
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, b->events[i + k], b->events[i + k + 1]));
+            b->stage_us[k] += 1e3 * ms;
+        }
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, b->events[i], b->events[i + 4]));
+        b->stage_us[4] += 1e3 * ms;
+        b->timed_group_steps++;
+    }
+    b->ev_used = 0;
+    return SFP_OK;
+}
+
+template <typename T>
+int step_group(sfp_batch* b, Group& g)
+{
+    const int C = g.C, M = g.M;
+    const int64_t n = (int64_t)C * 3 * M;
+    T* R = (T*)g.R;
+    T* r = (T*)g.r;
+    T* fz = (T*)g.fz;
+    T* yz = (T*)g.yz;
+    int rc;
+    if ((rc = mark(b, 0))) return rc;
+    // a1: r = phi R  (inverse transform, Eq. c1)
+    if (g.tc) rc = sfp::tc_transform(g.tc, 0, (const float*)R, (float*)r, b->stream);
+    else rc = launch_gemm<T>(b, R, (const T*)g.phi, r, 3 * C, M, M);
+    if (rc) return rc;
+    if (g.tc) b->launches++;
+    if ((rc = mark(b, 1))) return rc;
+    // a2 + a3: residual bond force and bead noise
+    {
+        const T c12 = (T)(1.0 - 2.0 * b->dv.nu);
+        const int warps = 4;
+        dim3 grid(nblk(C, warps));
+        if constexpr (sizeof(T) == 4) {
+            if (M % 4 == 0)
+                sfp::k_force_noise<float, true><<<grid, 32 * warps, 0, b->stream>>>(
+                    r, fz, fz + n, C, M, c12, b->seed, g.job, g.step);
+            else
+                sfp::k_force_noise<float, false><<<grid, 32 * warps, 0, b->stream>>>(
+                    r, fz, fz + n, C, M, c12, b->seed, g.job, g.step);
+        } else {
+            sfp::k_force_noise<double, false><<<grid, 32 * warps, 0, b->stream>>>(
+                r, fz, fz + n, C, M, c12, b->seed, g.job, g.step);
+        }
+        b->launches++;
+        CUDA_TRY(cudaGetLastError());
+    }
+    if ((rc = mark(b, 2))) return rc;
+    // a4: [DeltaH | Z] = phi^T [f | z]  (forward transform, Eqs. c4, e11)
+    if (g.tc) rc = sfp::tc_transform(g.tc, 1, (const float*)fz, (float*)yz, b->stream);
+    else rc = launch_gemm<T>(b, fz, (const T*)g.phiT, yz, 6 * C, M, M);
+    if (rc) return rc;
+    if (g.tc) b->launches++;
+    if ((rc = mark(b, 3))) return rc;
+    // a5: mode update (Eqs. d3, d6, f2, btum)
+    sfp::k_mode_update<T><<<nblk((int64_t)C * M, 256), 256, 0, b->stream>>>(
+        R, yz, yz + n, g.com, g.step, (const T*)g.dm, (const T*)g.h, (const T*)g.w, (const T*)g.g,
+        g.shear, C, M, g.tab.w0, g.dtau, b->bad);
+    b->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return mark(b, 4);
+}
+
+int step_all(sfp_batch* b, int64_t n_steps)
+{
+    for (int64_t s = 0; s < n_steps; ++s) {
+        for (auto& g : b->groups) {
+            const int rc = (b->precision == SFP_FP64) ? step_group<double>(b, g) : step_group<float>(b, g);
+            if (rc) return rc;
+        }
+        if (b->timing && b->ev_used >= 4000) {
+            const int rc = harvest(b);
+            if (rc) return rc;
+        }
+    }
+    if (n_steps > 0) b->probed = true;
+    return SFP_OK;
+}
+
+// Modes (FP64, device, [C][3][M] incl. p = 0) -> state
+int load_modes_dev(sfp_batch* b, Group& g, const double* src)
+{
+    const int64_t n = (int64_t)g.C * 3 * g.M;
+    const double inv = 1.0 / std::sqrt((double)g.M);
+    if (b->precision == SFP_FP64)
+        sfp::k_load_modes<double><<<nblk(n, 256), 256, 0, b->stream>>>(src, (double*)g.R, g.com, g.C, g.M, inv);
+    else
+        sfp::k_load_modes<float><<<nblk(n, 256), 256, 0, b->stream>>>(src, (float*)g.R, g.com, g.C, g.M, inv);
+    CUDA_TRY(cudaGetLastError());
+    return SFP_OK;
+}
+
+int to_double(sfp_batch* b, const void* src, double* dst, int64_t n)
+{
+    if (b->precision == SFP_FP64)
+        CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
+    else {
+        sfp::k_to_double<float><<<nblk(n, 256), 256, 0, b->stream>>>((const float*)src, dst, n);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return SFP_OK;
+}
+
+// Gather host packed [3][M_c] blocks of one group into a contiguous host array.
+void gather_group(const sfp_batch* b, const Group& g, const double* packed, std::vector<double>& out)
+{
+    const size_t blk = (size_t)3 * g.M;
+    out.resize((size_t)g.C * blk);
+    for (int i = 0; i < g.C; ++i)
+        std::memcpy(out.data() + i * blk, packed + b->off[g.chains[i]], blk * sizeof(double));
+}
+
+void scatter_group(const sfp_batch* b, const Group& g, const std::vector<double>& in, double* packed)
+{
+    const size_t blk = (size_t)3 * g.M;
+    for (int i = 0; i < g.C; ++i)
+        std::memcpy(packed + b->off[g.chains[i]], in.data() + i * blk, blk * sizeof(double));
+}
+
+// CoM-relative bead positions (FP64, scaled) of a group into g.stage2
+int positions_dev(sfp_batch* b, Group& g)
+{
+    const int64_t n = (int64_t)g.C * 3 * g.M;
+    int rc = to_double(b, g.R, g.stage, n);
+    if (rc) return rc;
+    return launch_gemm<double>(b, g.stage, g.phi_d, g.stage2, 3 * g.C, g.M, g.M);
+}
+
+int destroy_impl(sfp_batch* b)
+{
+    if (!b) return SFP_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    for (auto& g : b->groups)
+        if (g.tc) sfp::tc_destroy(g.tc);
+    for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    for (void* p : b->allocs) cudaFree(p);
+    delete b;
+    return SFP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sfp_params_dsdna(sfp_params* p)
+{
+    if (!p) return fail(SFP_EINVAL, "params is NULL");
+    std::memset(p, 0, sizeof *p);
+    p->T_star = 0.034;
+    p->nu = 0.35;
+    p->a_nm = 0.33;
+    p->xi_kg_per_s = 1.91e-12;
+    p->kT_pN_nm = 4.089;
+    p->a2xi_over_kT_ps = 52.0;
+    return SFP_OK;
+}
+
+int sfp_derive(const sfp_params* p, double out[8])
+{
+    if (!out) return fail(SFP_EINVAL, "out is NULL");
+    Derived d;
+    const int rc = derive(p, &d);
+    if (rc) return rc;
+    out[0] = d.Tstar; out[1] = d.nu; out[2] = d.c_ps; out[3] = d.d_nm;
+    out[4] = d.b; out[5] = d.lp_over_a; out[6] = d.lambda; out[7] = d.kappa;
+    return SFP_OK;
+}
+
+const char* sfp_last_error(void) { return g_err.c_str(); }
+
+int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n_chains,
+               uint64_t seed, int32_t precision, void* cuda_stream, size_t hbm_budget_bytes,
+               sfp_batch** out)
+{
+    if (!out) return fail(SFP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!chains || n_chains <= 0) return fail(SFP_EINVAL, "need n_chains > 0 and a chain array");
+    if (seed >> 32) return fail(SFP_EINVAL, "seed must be < 2^32");
+    if (precision != SFP_FP32 && precision != SFP_FP64 && precision != SFP_FP32_SIMT)
+        return fail(SFP_EINVAL, "unknown precision %d", precision);
+    Derived dv;
+    int rc = derive(params, &dv);
+    if (rc) return rc;
+    sfp_batch* b = new sfp_batch();
+    b->dv = dv;
+    b->precision = precision;
+    b->seed = (uint32_t)seed;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->budget = hbm_budget_bytes;
+    b->C = n_chains;
+    b->desc.assign(chains, chains + n_chains);
+    b->off.resize(n_chains);
+    b->group_of.resize(n_chains);
+    b->slot_of.resize(n_chains);
+    std::map<std::pair<int, double>, int> gidx;
+    int64_t acc = 0;
+    for (int i = 0; i < n_chains; ++i) {
+        const sfp_chain_desc& d = chains[i];
+        if (d.n_beads < 3 || d.n_beads > 4096) { delete b; return fail(SFP_EINVAL, "chain %d: n_beads %d outside 3..4096", i, d.n_beads); }
+        if (d.reserved != 0) { delete b; return fail(SFP_EINVAL, "chain %d: reserved must be 0", i); }
+        if (d.job_id >> 32) { delete b; return fail(SFP_EINVAL, "chain %d: job_id must be < 2^32", i); }
+        const double dtau = d.dtau > 0.0 ? d.dtau : d.dt_ps / dv.c_ps;
+        if (!(dtau > 0.0) || !std::isfinite(dtau)) { delete b; return fail(SFP_EINVAL, "chain %d: step must be > 0", i); }
+        if (!std::isfinite(d.shear_rate_per_s)) { delete b; return fail(SFP_EINVAL, "chain %d: shear rate not finite", i); }
+        b->off[i] = acc;
+        acc += 3 * (int64_t)d.n_beads;
+        const auto key = std::make_pair((int)d.n_beads, dtau);
+        auto it = gidx.find(key);
+        int gi;
+        if (it == gidx.end()) {
+            gi = (int)b->groups.size();
+            gidx[key] = gi;
+            b->groups.emplace_back();
+            b->groups.back().M = d.n_beads;
+            b->groups.back().dtau = dtau;
+        } else {
+            gi = it->second;
+        }
+        b->group_of[i] = gi;
+        b->slot_of[i] = (int)b->groups[gi].chains.size();
+        b->groups[gi].chains.push_back(i);
+    }
+    b->total_beads = acc / 3;
+    const size_t es = (precision == SFP_FP64) ? 8 : 4;
+    if ((rc = dalloc_t(b, &b->bad, sizeof(int)))) { destroy_impl(b); return rc; }
+    for (auto& g : b->groups) {
+        const int M = g.M;
+        g.C = (int)g.chains.size();
+        const size_t n = (size_t)g.C * 3 * M;
+        make_tables(M, dv.Tstar, dv.nu, g.dtau, &g.tab);
+        if ((rc = dalloc(b, &g.R, n * es)) || (rc = dalloc_t(b, &g.com, (size_t)g.C * 3 * 8)) ||
+            (rc = dalloc_t(b, &g.job, (size_t)g.C * 4)) || (rc = dalloc_t(b, &g.shear, (size_t)g.C * 8)) ||
+            (rc = dalloc_t(b, &g.step, (size_t)g.C * 8)) || (rc = dalloc(b, &g.phi, (size_t)M * M * es)) ||
+            (rc = dalloc(b, &g.phiT, (size_t)M * M * es)) || (rc = dalloc(b, &g.dm, M * es)) ||
+            (rc = dalloc(b, &g.h, M * es)) || (rc = dalloc(b, &g.w, M * es)) || (rc = dalloc(b, &g.g, M * es)) ||
+            (rc = dalloc_t(b, &g.phi_d, (size_t)M * M * 8)) || (rc = dalloc_t(b, &g.phiT_d, (size_t)M * M * 8)) ||
+            (rc = dalloc(b, &g.r, n * es)) || (rc = dalloc(b, &g.fz, 2 * n * es)) ||
+            (rc = dalloc(b, &g.yz, 2 * n * es)) || (rc = dalloc_t(b, &g.stage, n * 8)) ||
+            (rc = dalloc_t(b, &g.stage2, n * 8))) {
+            destroy_impl(b);
+            return rc;
+        }
+        if ((rc = upload_typed(b, g.phi, g.tab.phi)) || (rc = upload_typed(b, g.phiT, g.tab.phiT)) ||
+            (rc = upload_typed(b, g.dm, g.tab.dm)) || (rc = upload_typed(b, g.h, g.tab.h)) ||
+            (rc = upload_typed(b, g.w, g.tab.w)) || (rc = upload_typed(b, g.g, g.tab.g))) {
+            destroy_impl(b);
+            return rc;
+        }
+        std::vector<uint32_t> jobs(g.C);
+        std::vector<double> sh(g.C);
+        std::vector<int64_t> st(g.C, 0);
+        for (int i = 0; i < g.C; ++i) {
+            const sfp_chain_desc& d = chains[g.chains[i]];
+            jobs[i] = (uint32_t)d.job_id;
+            sh[i] = d.shear_rate_per_s * dv.c_ps * 1e-12;   // 1/s -> 1/tau
+        }
+        // Straight ground-state rod along x, centre of mass at the origin.
+        std::vector<double> l0, Ld, Lo;
+        rod_tables(M, dv.nu, &l0, &Ld, &Lo);
+        std::vector<double> rod((size_t)3 * M, 0.0), Rrod((size_t)3 * M, 0.0);
+        for (int k = 1; k < M; ++k) rod[k] = rod[k - 1] + l0[k - 1];
+        double cm = 0.0;
+        for (int k = 0; k < M; ++k) cm += rod[k];
+        cm /= M;
+        for (int k = 0; k < M; ++k) rod[k] -= cm;
+        for (int p = 1; p < M; ++p) {
+            double s = 0.0;
+            for (int k = 0; k < M; ++k) s += rod[k] * g.tab.phi[(size_t)k * M + p];
+            Rrod[p] = s;
+        }
+        std::vector<double> init(n);
+        for (int i = 0; i < g.C; ++i) std::memcpy(init.data() + (size_t)i * 3 * M, Rrod.data(), 3 * M * sizeof(double));
+        cudaError_t e = cudaSuccess;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g.job, jobs.data(), g.C * 4, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g.shear, sh.data(), g.C * 8, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g.step, st.data(), g.C * 8, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g.phi_d, g.tab.phi.data(), (size_t)M * M * 8, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g.phiT_d, g.tab.phiT.data(), (size_t)M * M * 8, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g.stage, init.data(), n * 8, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->bad, 0, sizeof(int), b->stream);
+        if (e != cudaSuccess) { destroy_impl(b); return fail(SFP_ECUDA, "upload failed: %s", cudaGetErrorString(e)); }
+        if ((rc = load_modes_dev(b, g, g.stage))) { destroy_impl(b); return rc; }
+        e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) { destroy_impl(b); return fail(SFP_ECUDA, "create: %s", cudaGetErrorString(e)); }
+        if (precision == SFP_FP32) {
+            rc = sfp::tc_create(&g.tc, M, 3 * g.C, g.tab.phi.data(), g.tab.phiT.data(), b->stream);
+            if (rc) { destroy_impl(b); return rc; }
+        }
+    }
+    *out = b;
+    return SFP_OK;
+}
+
+int sfp_destroy(sfp_batch* b) { return destroy_impl(b); }
+
+int sfp_step(sfp_batch* b, int64_t n_steps)
+{
+    if (!b) return fail(SFP_EINVAL, "batch is NULL");
+    if (n_steps < 0) return fail(SFP_EINVAL, "n_steps < 0");
+    return step_all(b, n_steps);
+}
+
+int sfp_set_step(sfp_batch* b, int64_t step)
+{
+    if (!b) return fail(SFP_EINVAL, "batch is NULL");
+    if (step < 0) return fail(SFP_EINVAL, "step < 0");
+    for (auto& g : b->groups) {
+        std::vector<int64_t> st(g.C, step);
+        CUDA_TRY(cudaMemcpyAsync(g.step, st.data(), g.C * 8, cudaMemcpyHostToDevice, b->stream));
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+    }
+    return SFP_OK;
+}
+
+int sfp_set_modes(sfp_batch* b, const double* host, size_t n_doubles)
+{
+    if (!b || !host) return fail(SFP_EINVAL, "NULL argument");
+    if (n_doubles < (size_t)(3 * b->total_beads)) return fail(SFP_EINVAL, "need %lld doubles", (long long)(3 * b->total_beads));
+    std::vector<double> tmp;
+    for (auto& g : b->groups) {
+        gather_group(b, g, host, tmp);
+        CUDA_TRY(cudaMemcpyAsync(g.stage, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, b->stream));
+        int rc = load_modes_dev(b, g, g.stage);
+        if (rc) return rc;
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+    }
+    b->probed = false;
+    return SFP_OK;
+}
+
+int sfp_set_positions(sfp_batch* b, const double* host, size_t n_doubles)
+{
+    if (!b || !host) return fail(SFP_EINVAL, "NULL argument");
+    if (n_doubles < (size_t)(3 * b->total_beads)) return fail(SFP_EINVAL, "need %lld doubles", (long long)(3 * b->total_beads));
+    std::vector<double> tmp;
+    const double inv_d = 1.0 / b->dv.d_nm;
+    for (auto& g : b->groups) {
+        gather_group(b, g, host, tmp);
+        for (auto& x : tmp) x *= inv_d;
+        CUDA_TRY(cudaMemcpyAsync(g.stage2, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, b->stream));
+        int rc = launch_gemm<double>(b, g.stage2, g.phiT_d, g.stage, 3 * g.C, g.M, g.M);
+        if (rc) return rc;
+        if ((rc = load_modes_dev(b, g, g.stage))) return rc;
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+    }
+    b->probed = false;
+    return SFP_OK;
+}
+
+int sfp_init_equilibrium(sfp_batch* b, int64_t burn_in_steps)
+{
+    if (!b) return fail(SFP_EINVAL, "batch is NULL");
+    if (burn_in_steps < 0) return fail(SFP_EINVAL, "burn_in_steps < 0");
+    for (auto& g : b->groups) {
+        std::vector<double> l0, Ld, Lo;
+        rod_tables(g.M, b->dv.nu, &l0, &Ld, &Lo);
+        std::vector<double> all;
+        all.insert(all.end(), l0.begin(), l0.end());
+        all.insert(all.end(), Ld.begin(), Ld.end());
+        all.insert(all.end(), Lo.begin(), Lo.end());
+        const int N = g.M - 1;
+        // l0 | Ld | Lo live in the head of stage2's tail-free region: use yz scratch
+        double* tabs = nullptr;
+        double* xs = nullptr;
+        CUDA_TRY(cudaMalloc(&tabs, all.size() * 8));
+        cudaError_t e = cudaMalloc(&xs, (size_t)g.C * g.M * 8);
+        if (e != cudaSuccess) { cudaFree(tabs); return fail(SFP_ENOMEM, "init scratch: %s", cudaGetErrorString(e)); }
+        e = cudaMemcpyAsync(tabs, all.data(), all.size() * 8, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) {
+            sfp::k_equilibrium<<<nblk(g.C, 64), 64, 0, b->stream>>>(g.stage2, xs, tabs, tabs + N, tabs + 2 * N,
+                                                                   g.C, g.M, b->dv.Tstar, b->dv.nu, b->seed, g.job);
+            e = cudaGetLastError();
+        }
+        int rc = SFP_OK;
+        if (e == cudaSuccess) rc = launch_gemm<double>(b, g.stage2, g.phiT_d, g.stage, 3 * g.C, g.M, g.M);
+        if (e == cudaSuccess && !rc) rc = load_modes_dev(b, g, g.stage);
+        if (e == cudaSuccess && !rc) e = cudaMemsetAsync(g.com, 0, (size_t)g.C * 3 * 8, b->stream);
+        if (e == cudaSuccess && !rc) e = cudaMemsetAsync(g.step, 0, (size_t)g.C * 8, b->stream);
+        if (e == cudaSuccess && !rc) e = cudaStreamSynchronize(b->stream);
+        cudaFree(tabs);
+        cudaFree(xs);
+        if (rc) return rc;
+        if (e != cudaSuccess) return fail(SFP_ECUDA, "init_equilibrium: %s", cudaGetErrorString(e));
+    }
+    b->probed = false;
+    return step_all(b, burn_in_steps);
+}
+
+int sfp_observe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
+{
+    if (!b || !host_out) return fail(SFP_EINVAL, "NULL argument");
+    const size_t packed = (size_t)3 * b->total_beads * sizeof(double);
+    size_t need = 0;
+    switch (what) {
+        case SFP_OBS_MODES: case SFP_OBS_POSITIONS: need = packed; break;
+        case SFP_OBS_COM: need = (size_t)b->C * 3 * 8; break;
+        case SFP_OBS_STEP: need = (size_t)b->C * 8; break;
+        case SFP_OBS_SHAPE: need = (size_t)b->C * 4 * 8; break;
+        default: return fail(SFP_EINVAL, "unknown observable %d", what);
+    }
+    if (bytes < need) return fail(SFP_EINVAL, "buffer too small: need %zu bytes", need);
+    std::vector<double> tmp;
+    for (auto& g : b->groups) {
+        const int64_t n = (int64_t)g.C * 3 * g.M;
+        if (what == SFP_OBS_MODES) {
+            if (b->precision == SFP_FP64)
+                sfp::k_store_modes<double><<<nblk(n, 256), 256, 0, b->stream>>>((const double*)g.R, g.com, g.stage, g.C, g.M, std::sqrt((double)g.M));
+            else
+                sfp::k_store_modes<float><<<nblk(n, 256), 256, 0, b->stream>>>((const float*)g.R, g.com, g.stage, g.C, g.M, std::sqrt((double)g.M));
+            CUDA_TRY(cudaGetLastError());
+            tmp.resize(n);
+            CUDA_TRY(cudaMemcpyAsync(tmp.data(), g.stage, n * 8, cudaMemcpyDeviceToHost, b->stream));
+            CUDA_TRY(cudaStreamSynchronize(b->stream));
+            scatter_group(b, g, tmp, (double*)host_out);
+        } else if (what == SFP_OBS_POSITIONS || what == SFP_OBS_SHAPE) {
+            int rc = positions_dev(b, g);
+            if (rc) return rc;
+            if (what == SFP_OBS_SHAPE) {
+                std::vector<double> sh((size_t)g.C * 4);
+                sfp::k_shape<<<nblk(g.C, 128), 128, 0, b->stream>>>(g.stage2, g.C, g.M, g.stage, b->dv.d_nm * b->dv.d_nm);
+                CUDA_TRY(cudaGetLastError());
+                CUDA_TRY(cudaMemcpyAsync(sh.data(), g.stage, sh.size() * 8, cudaMemcpyDeviceToHost, b->stream));
+                std::vector<int64_t> st(g.C);
+                CUDA_TRY(cudaMemcpyAsync(st.data(), g.step, g.C * 8, cudaMemcpyDeviceToHost, b->stream));
+                CUDA_TRY(cudaStreamSynchronize(b->stream));
+                for (int i = 0; i < g.C; ++i) {
+                    double* o = (double*)host_out + 4 * (size_t)g.chains[i];
+                    o[0] = sh[4 * i]; o[1] = sh[4 * i + 1]; o[2] = sh[4 * i + 2];
+                    o[3] = (double)st[i] * g.dtau * b->dv.c_ps;
+                }
+            } else {
+                tmp.resize(n);
+                std::vector<double> cm((size_t)g.C * 3);
+                CUDA_TRY(cudaMemcpyAsync(tmp.data(), g.stage2, n * 8, cudaMemcpyDeviceToHost, b->stream));
+                CUDA_TRY(cudaMemcpyAsync(cm.data(), g.com, cm.size() * 8, cudaMemcpyDeviceToHost, b->stream));
+                CUDA_TRY(cudaStreamSynchronize(b->stream));
+                const double dnm = b->dv.d_nm;
+                for (int i = 0; i < g.C; ++i)
+                    for (int a = 0; a < 3; ++a)
+                        for (int k = 0; k < g.M; ++k) {
+                            double& x = tmp[((size_t)i * 3 + a) * g.M + k];
+                            x = (x + cm[3 * i + a]) * dnm;
+                        }
+                scatter_group(b, g, tmp, (double*)host_out);
+            }
+        } else if (what == SFP_OBS_COM) {
+            std::vector<double> cm((size_t)g.C * 3);
+            CUDA_TRY(cudaMemcpyAsync(cm.data(), g.com, cm.size() * 8, cudaMemcpyDeviceToHost, b->stream));
+            CUDA_TRY(cudaStreamSynchronize(b->stream));
+            for (int i = 0; i < g.C; ++i)
+                for (int a = 0; a < 3; ++a) ((double*)host_out)[3 * (size_t)g.chains[i] + a] = cm[3 * i + a] * b->dv.d_nm;
+        } else if (what == SFP_OBS_STEP) {
+            std::vector<int64_t> st(g.C);
+            CUDA_TRY(cudaMemcpyAsync(st.data(), g.step, g.C * 8, cudaMemcpyDeviceToHost, b->stream));
+            CUDA_TRY(cudaStreamSynchronize(b->stream));
+            for (int i = 0; i < g.C; ++i) ((int64_t*)host_out)[g.chains[i]] = st[i];
+        }
+    }
+    int bad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&bad, b->bad, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    if (bad) return fail(SFP_ENONFINITE, "a chain's state became non-finite");
+    return SFP_OK;
+}
+
+int sfp_probe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
+{
+    if (!b || !host_out) return fail(SFP_EINVAL, "NULL argument");
+    if (what < SFP_PROBE_BEADS || what > SFP_PROBE_ZMODE) return fail(SFP_EINVAL, "unknown probe %d", what);
+    if (!b->probed) return fail(SFP_EINVAL, "no step has run since the state was set");
+    const size_t need = (size_t)3 * b->total_beads * 8;
+    if (bytes < need) return fail(SFP_EINVAL, "buffer too small: need %zu bytes", need);
+    std::vector<double> tmp;
+    const size_t es = esize(b);
+    for (auto& g : b->groups) {
+        const int64_t n = (int64_t)g.C * 3 * g.M;
+        const char* src = nullptr;
+        switch (what) {
+            case SFP_PROBE_BEADS: src = (const char*)g.r; break;
+            case SFP_PROBE_FORCE: src = (const char*)g.fz; break;
+            case SFP_PROBE_NOISE: src = (const char*)g.fz + n * es; break;
+            case SFP_PROBE_DH: src = (const char*)g.yz; break;
+            case SFP_PROBE_ZMODE: src = (const char*)g.yz + n * es; break;
+        }
+        int rc = to_double(b, src, g.stage, n);
+        if (rc) return rc;
+        tmp.resize(n);
+        CUDA_TRY(cudaMemcpyAsync(tmp.data(), g.stage, n * 8, cudaMemcpyDeviceToHost, b->stream));
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+        scatter_group(b, g, tmp, (double*)host_out);
+    }
+    return SFP_OK;
+}
+
+int sfp_save(sfp_batch* b, void* host_buf, size_t bytes, size_t* needed)
+{
+    if (!b) return fail(SFP_EINVAL, "batch is NULL");
+    const size_t need = 4 * 8 + (size_t)3 * b->total_beads * 8 + (size_t)b->C * 3 * 8 + (size_t)b->C * 8;
+    if (needed) *needed = need;
+    if (!host_buf) return SFP_OK;
+    if (bytes < need) return fail(SFP_EINVAL, "buffer too small: need %zu bytes", need);
+    uint64_t* hdr = (uint64_t*)host_buf;
+    hdr[0] = kMagic; hdr[1] = (uint64_t)b->C; hdr[2] = (uint64_t)b->total_beads; hdr[3] = (uint64_t)b->precision;
+    double* modes = (double*)(hdr + 4);
+    double* com = modes + 3 * b->total_beads;
+    int64_t* st = (int64_t*)(com + 3 * (size_t)b->C);
+    std::vector<double> tmp;
+    for (auto& g : b->groups) {
+        const int64_t n = (int64_t)g.C * 3 * g.M;
+        int rc = to_double(b, g.R, g.stage, n);
+        if (rc) return rc;
+        tmp.resize(n);
+        std::vector<double> cm((size_t)g.C * 3);
+        std::vector<int64_t> s(g.C);
+        CUDA_TRY(cudaMemcpyAsync(tmp.data(), g.stage, n * 8, cudaMemcpyDeviceToHost, b->stream));
+        CUDA_TRY(cudaMemcpyAsync(cm.data(), g.com, cm.size() * 8, cudaMemcpyDeviceToHost, b->stream));
+        CUDA_TRY(cudaMemcpyAsync(s.data(), g.step, g.C * 8, cudaMemcpyDeviceToHost, b->stream));
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+        scatter_group(b, g, tmp, modes);
+        for (int i = 0; i < g.C; ++i) {
+            const int c = g.chains[i];
+            for (int a = 0; a < 3; ++a) com[3 * (size_t)c + a] = cm[3 * i + a];
+            st[c] = s[i];
+        }
+    }
+    return SFP_OK;
+}
+
+int sfp_load(sfp_batch* b, const void* host_buf, size_t bytes)
+{
+    if (!b || !host_buf) return fail(SFP_EINVAL, "NULL argument");
+    const size_t need = 4 * 8 + (size_t)3 * b->total_beads * 8 + (size_t)b->C * 3 * 8 + (size_t)b->C * 8;
+    if (bytes < need) return fail(SFP_EINVAL, "checkpoint too small: need %zu bytes", need);
+    const uint64_t* hdr = (const uint64_t*)host_buf;
+    if (hdr[0] != kMagic || hdr[1] != (uint64_t)b->C || hdr[2] != (uint64_t)b->total_beads ||
+        hdr[3] != (uint64_t)b->precision)
+        return fail(SFP_EINVAL, "checkpoint does not match this batch");
+    const double* modes = (const double*)(hdr + 4);
+    const double* com = modes + 3 * b->total_beads;
+    const int64_t* st = (const int64_t*)(com + 3 * (size_t)b->C);
+    std::vector<double> tmp;
+    for (auto& g : b->groups) {
+        gather_group(b, g, modes, tmp);
+        CUDA_TRY(cudaMemcpyAsync(g.stage, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, b->stream));
+        int rc = load_modes_dev(b, g, g.stage);
+        if (rc) return rc;
+        std::vector<double> cm((size_t)g.C * 3);
+        std::vector<int64_t> s(g.C);
+        for (int i = 0; i < g.C; ++i) {
+            const int c = g.chains[i];
+            for (int a = 0; a < 3; ++a) cm[3 * i + a] = com[3 * (size_t)c + a];
+            s[i] = st[c];
+        }
+        CUDA_TRY(cudaMemcpyAsync(g.com, cm.data(), cm.size() * 8, cudaMemcpyHostToDevice, b->stream));
+        CUDA_TRY(cudaMemcpyAsync(g.step, s.data(), g.C * 8, cudaMemcpyHostToDevice, b->stream));
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+    }
+    b->probed = false;
+    return SFP_OK;
+}
+
+int sfp_info(const sfp_batch* b, int64_t out[4])
+{
+    if (!b || !out) return fail(SFP_EINVAL, "NULL argument");
+    out[0] = b->C; out[1] = b->total_beads; out[2] = (int64_t)b->held; out[3] = b->launches;
+    return SFP_OK;
+}
+
+int sfp_stage_timing(sfp_batch* b, int32_t enable)
+{
+    if (!b) return fail(SFP_EINVAL, "batch is NULL");
+    int rc = harvest(b);
+    if (rc) return rc;
+    b->timing = enable != 0;
+    for (double& x : b->stage_us) x = 0.0;
+    b->timed_group_steps = 0;
+    return SFP_OK;
+}
+
+int sfp_stage_times(sfp_batch* b, double out_us[5], int64_t* n_group_steps)
+{
+    if (!b || !out_us) return fail(SFP_EINVAL, "NULL argument");
+    int rc = harvest(b);
+    if (rc) return rc;
+    for (int k = 0; k < 5; ++k) out_us[k] = b->stage_us[k];
+    if (n_group_steps) *n_group_steps = b->timed_group_steps;
+    return SFP_OK;
+}
+
+int sfp_philox_words(uint32_t seed, uint32_t job, int64_t step, uint32_t tag, int32_t count,
+                     uint32_t* host_out)
+{
+    if (!host_out || count <= 0) return fail(SFP_EINVAL, "need count > 0 and an output buffer");
+    uint32_t* d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, (size_t)count * 16));
+    sfp::k_philox_words<<<nblk(count, 128), 128>>>(seed, job, step, tag, count, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(host_out, d, (size_t)count * 16, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(SFP_ECUDA, "philox words: %s", cudaGetErrorString(e));
+    return SFP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// sfp_device.cuh -- device helpers shared by the kernels of the GB300 path:
+// the counter-based noise generator and the per-bead normals.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sfp {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64-bit multiplies with a Weyl-sequence key schedule.  Counter
+// (step_lo, step_hi, index, tag), key (seed, job_id).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Open-interval uniform from the top 23 bits: exact in FP32 and FP64, so the
+// FP32 and FP64 paths see bit-identical uniforms.
+__device__ __forceinline__ float u01f(uint32_t x)
+{
+    return (float)(x >> 9) * 1.1920928955078125e-07f + 5.9604644775390625e-08f;
+}
+__device__ __forceinline__ double u01d(uint32_t x)
+{
+    return (double)(x >> 9) * 1.1920928955078125e-07 + 5.9604644775390625e-08;
+}
+
+// Three N(0,1) draws for bead `n` at `step` (Box-Muller: words 0,1 -> x,y;
+// words 2,3 -> z, second value unused).
+template <typename T> struct Normals;
+template <> struct Normals<float> {
+    static __device__ __forceinline__ void draw(uint32_t seed, uint32_t job, int64_t step,
+                                                uint32_t n, uint32_t tag, float g[3])
+    {
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), n, tag), make_uint2(seed, job));
+        const float ra = sqrtf(-2.0f * logf(u01f(w.x)));
+        const float rb = sqrtf(-2.0f * logf(u01f(w.z)));
+        float sa, ca, sb, cb;
+        sincospif(2.0f * u01f(w.y), &sa, &ca);
+        sincospif(2.0f * u01f(w.w), &sb, &cb);
+        g[0] = ra * ca; g[1] = ra * sa; g[2] = rb * cb;
+    }
+};
+template <> struct Normals<double> {
+    static __device__ __forceinline__ void draw(uint32_t seed, uint32_t job, int64_t step,
+                                                uint32_t n, uint32_t tag, double g[3])
+    {
+        const uint4 w = philox4x32_10(
+            make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), n, tag), make_uint2(seed, job));
+        const double ra = sqrt(-2.0 * log(u01d(w.x)));
+        const double rb = sqrt(-2.0 * log(u01d(w.z)));
+        double sa, ca, sb, cb;
+        sincospi(2.0 * u01d(w.y), &sa, &ca);
+        sincospi(2.0 * u01d(w.w), &sb, &cb);
+        g[0] = ra * ca; g[1] = ra * sa; g[2] = rb * cb;
+    }
+};
+
+template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+
+}  // namespace sfp

@@ -1,0 +1,364 @@
+// sfp_simt.cuh -- CUDA-core kernels of the mode-space step (FP32 and FP64).
+//
+// Layout of every per-chain array: [chain][axis][index], index contiguous,
+// rows of length M (beads n or modes p).  A "row" j = 3*chain + axis.
+#pragma once
+#include "sfp_device.cuh"
+
+namespace sfp {
+
+// ---------------------------------------------------------------------------
+// Transform GEMM (NT):  Out[j][i] = sum_k In[j][k] * B[i][k]
+//   inverse (Eq. c1):  In = R (k = p), B = phi  stored [n][p]  -> Out = r
+//   forward (Eq. c4):  In = f|z (k = n), B = phi^T stored [p][n] -> Out = DeltaH|Z
+// Block tile BM rows x BN cols, K chunk BK; each thread owns TM x TN outputs.
+// Any J, Ncols, K (ragged tails are zero-filled).
+// ---------------------------------------------------------------------------
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_gemm_nt(const T* __restrict__ In, const T* __restrict__ B, T* __restrict__ Out,
+          int J, int Ncols, int K)
+{
+    constexpr int NT = (BM / TM) * (BN / TN);
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    const int j0 = blockIdx.y * BM, i0 = blockIdx.x * BN;
+    T acc[TM][TN];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) acc[a][b] = T(0);
+
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int e = tid; e < BM * BK; e += NT) {
+            const int row = e / BK, kk = e % BK;
+            const int gj = j0 + row, gk = k0 + kk;
+            As[kk][row] = (gj < J && gk < K) ? In[(size_t)gj * K + gk] : T(0);
+        }
+        for (int e = tid; e < BN * BK; e += NT) {
+            const int row = e / BK, kk = e % BK;
+            const int gi = i0 + row, gk = k0 + kk;
+            Bs[kk][row] = (gi < Ncols && gk < K) ? B[(size_t)gi * K + gk] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[TM], b[TN];
+#pragma unroll
+            for (int x = 0; x < TM; ++x) a[x] = As[kk][ty * TM + x];
+#pragma unroll
+            for (int y = 0; y < TN; ++y) b[y] = Bs[kk][tx * TN + y];
+#pragma unroll
+            for (int x = 0; x < TM; ++x)
+#pragma unroll
+                for (int y = 0; y < TN; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int x = 0; x < TM; ++x) {
+        const int gj = j0 + ty * TM + x;
+        if (gj >= J) continue;
+#pragma unroll
+        for (int y = 0; y < TN; ++y) {
+            const int gi = i0 + tx * TN + y;
+            if (gi < Ncols) Out[(size_t)gj * Ncols + gi] = acc[x][y];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Residual bond force + bead noise (Eqs. e4, e11, b5).
+// One warp per chain; each lane owns 4 consecutive beads per 128-bead chunk.
+//   u_n = r_n - r_{n-1} (n >= 1), v_n = u_n (1/|u_n| - (1 - 2nu)), v_0 = v_{N+1} = 0,
+//   f_n = v_n - v_{n+1}   so that  sum_n phi_{n,p} f_n = DeltaH_p  (Eq. e11).
+// Neighbour beads come from the adjacent lane by warp shuffle; the two chunk
+// edges come from the previous chunk (carried) and one halo load.
+// z[n] = three N(0,1) draws keyed by (seed, job, step, n, tag 0).
+// ---------------------------------------------------------------------------
+template <typename T, bool VEC4>
+__global__ void __launch_bounds__(128)
+k_force_noise(const T* __restrict__ r, T* __restrict__ f, T* __restrict__ z,
+              int C, int M, T c12nu, uint32_t seed, const uint32_t* __restrict__ job,
+              const int64_t* __restrict__ step)
+{
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= C) return;
+    const size_t base = (size_t)c * 3 * M;
+    const uint32_t jb = job[c];
+    const int64_t st = step[c];
+
+    T prev[3] = {T(0), T(0), T(0)};   // r of the bead before this chunk
+    for (int b0 = 0; b0 < M; b0 += 128) {
+        const int n0 = b0 + 4 * lane;
+        T x[3][4];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const T* ra = r + base + (size_t)a * M;
+            if (VEC4 && n0 + 3 < M) {
+                const float4 q = *reinterpret_cast<const float4*>(ra + n0);
+                x[a][0] = q.x; x[a][1] = q.y; x[a][2] = q.z; x[a][3] = q.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[a][i] = (n0 + i < M) ? ra[n0 + i] : T(0);
+            }
+        }
+        // r_{n0-1}: lane-1's last bead, or the carried bead for lane 0
+        T left[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const T up = __shfl_up_sync(0xffffffffu, x[a][3], 1);
+            left[a] = lane ? up : prev[a];
+        }
+        // v for the 4 owned beads
+        T v[3][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int n = n0 + i;
+            T u[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) u[a] = x[a][i] - (i ? x[a][i - 1] : left[a]);
+            const T l2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            const bool ok = (n >= 1) && (n < M);
+            const T s = ok ? rsqrt_t<T>(l2) - c12nu : T(0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) v[a][i] = u[a] * s;
+        }
+        // v_{n0+4}: next lane's first v; lane 31 computes it from a halo bead
+        T vnext[3];
+        {
+            T halo[3] = {T(0), T(0), T(0)};
+            const int nh = b0 + 128;
+            const bool has = (lane == 31) && (nh < M);
+            if (has) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) halo[a] = r[base + (size_t)a * M + nh];
+            }
+            T uh[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) uh[a] = halo[a] - x[a][3];
+            const T l2 = uh[0] * uh[0] + uh[1] * uh[1] + uh[2] * uh[2];
+            const T s = has ? rsqrt_t<T>(l2) - c12nu : T(0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const T dn = __shfl_down_sync(0xffffffffu, v[a][0], 1);
+                vnext[a] = (lane == 31) ? uh[a] * s : dn;
+            }
+        }
+        // carry r of the chunk's last bead to the next chunk
+#pragma unroll
+        for (int a = 0; a < 3; ++a) prev[a] = __shfl_sync(0xffffffffu, x[a][3], 31);
+
+        T fo[3][4], zo[3][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) fo[a][i] = v[a][i] - (i < 3 ? v[a][i + 1] : vnext[a]);
+            T g[3] = {T(0), T(0), T(0)};
+            if (n0 + i < M) Normals<T>::draw(seed, jb, st, (uint32_t)(n0 + i), 0u, g);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) zo[a][i] = g[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            T* fa = f + base + (size_t)a * M;
+            T* za = z + base + (size_t)a * M;
+            if (VEC4 && n0 + 3 < M) {
+                *reinterpret_cast<float4*>(fa + n0) = make_float4(fo[a][0], fo[a][1], fo[a][2], fo[a][3]);
+                *reinterpret_cast<float4*>(za + n0) = make_float4(zo[a][0], zo[a][1], zo[a][2], zo[a][3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (n0 + i < M) { fa[n0 + i] = fo[a][i]; za[n0 + i] = zo[a][i]; }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Mode update (Eqs. d3, d6, f2, btum), one thread per (chain, mode), all axes:
+//   p >= 1:  R += -dm_p R + h_p DeltaH_p + w_p Z_p ;  R^x += shear g_p R^y(old)
+//   p == 0:  r_cm (FP64) += w_0 Z_0 / sqrt(M) ; x_cm += shear dtau y_cm(old);
+//            the chain's step counter advances.
+// dm_p = 1 - e^{-zeta_p dtau}; written as an increment so FP32 keeps the
+// slow modes whose decay factor rounds to 1.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_mode_update(T* __restrict__ R, const T* __restrict__ DH, const T* __restrict__ ZM,
+              double* __restrict__ com, int64_t* __restrict__ step,
+              const T* __restrict__ dm, const T* __restrict__ h, const T* __restrict__ w,
+              const T* __restrict__ g, const double* __restrict__ shear,
+              int C, int M, double w0, double dtau, int* __restrict__ bad)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)C * M) return;
+    const int c = (int)(t / M), p = (int)(t % M);
+    const size_t b = (size_t)c * 3 * M + p;
+    const double sh = shear[c];
+    if (p == 0) {
+        const double inv = rsqrt((double)M);
+        const double ycm = com[3 * c + 1];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) com[3 * c + a] += w0 * (double)ZM[b + (size_t)a * M] * inv;
+        com[3 * c] += sh * dtau * ycm;
+        step[c] += 1;
+        return;
+    }
+    const T Rx = R[b], Ry = R[b + M], Rz = R[b + 2 * M];
+    const T d = dm[p], hh = h[p], ww = w[p];
+    T nx = Rx + fma(-d, Rx, fma(hh, DH[b], ww * ZM[b]));
+    const T ny = Ry + fma(-d, Ry, fma(hh, DH[b + M], ww * ZM[b + M]));
+    const T nz = Rz + fma(-d, Rz, fma(hh, DH[b + 2 * M], ww * ZM[b + 2 * M]));
+    nx += (T)sh * g[p] * Ry;
+    if (!(isfinite(nx) && isfinite(ny) && isfinite(nz))) atomicOr(bad, 1);
+    R[b] = nx; R[b + M] = ny; R[b + 2 * M] = nz;
+}
+
+// ---------------------------------------------------------------------------
+// Equilibrium start, one thread per chain, FP64 (Philox counter (0,0,k,1)):
+//   l = l0 + sqrt(T*) L^-T eps   with (I - nu A) = L L^T  (Ld diag, Lo sub-diag)
+//   t_1 uniform on the sphere, t_n ~ von Mises-Fisher(t_{n-1}, nu l_{n-1} l_n / T*)
+//   r_n = sum_{k<=n} l_k t_k, centroid removed.   out: pos[c][3][M], scratch x[c][M]
+// ---------------------------------------------------------------------------
+__global__ void k_equilibrium(double* __restrict__ pos, double* __restrict__ xs,
+                              const double* __restrict__ l0, const double* __restrict__ Ld,
+                              const double* __restrict__ Lo, int C, int M, double Tstar,
+                              double nu, uint32_t seed, const uint32_t* __restrict__ job)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const int N = M - 1;
+    const uint2 key = make_uint2(seed, job[c]);
+    double* x = xs + (size_t)c * M;
+    double* p = pos + (size_t)c * 3 * M;
+    // back substitution L^T x = eps, eps_i is the normal of bond i+1
+    for (int i = N - 1; i >= 0; --i) {
+        const uint4 wd = philox4x32_10(make_uint4(0u, 0u, (uint32_t)(i + 1), 1u), key);
+        double s, co;
+        sincospi(2.0 * u01d(wd.y), &s, &co);
+        const double eps = sqrt(-2.0 * log(u01d(wd.x))) * co;
+        const double nxt = (i + 1 < N) ? Lo[i + 1] * x[i + 1] : 0.0;
+        x[i] = (eps - nxt) / Ld[i];
+    }
+    double t[3];
+    {
+        const uint4 wd = philox4x32_10(make_uint4(0u, 0u, 0u, 1u), key);
+        const double ct = 2.0 * u01d(wd.x) - 1.0;
+        const double st = sqrt((1.0 - ct) * (1.0 + ct));
+        double sp, cp;
+        sincospi(2.0 * u01d(wd.y), &sp, &cp);
+        t[0] = st * cp; t[1] = st * sp; t[2] = ct;
+    }
+    const double sT = sqrt(Tstar);
+    double acc[3] = {0.0, 0.0, 0.0}, sum[3] = {0.0, 0.0, 0.0};
+    p[0] = p[M] = p[2 * M] = 0.0;
+    double lprev = 0.0;
+    for (int n = 1; n <= N; ++n) {
+        const double ln = l0[n - 1] + sT * x[n - 1];
+        if (n >= 2 && Tstar > 0.0) {
+            const uint4 wd = philox4x32_10(make_uint4(0u, 0u, (uint32_t)n, 1u), key);
+            const double kap = nu * lprev * ln / Tstar;
+            const double U = u01d(wd.z);
+            const double ct = 1.0 + log(U + (1.0 - U) * exp(-2.0 * kap)) / kap;
+            const double st = sqrt(fmax(0.0, (1.0 - ct) * (1.0 + ct)));
+            double sp, cp;
+            sincospi(2.0 * u01d(wd.w), &sp, &cp);
+            // orthonormal pair perpendicular to t (Duff et al., JCGT 2017)
+            const double sg = copysign(1.0, t[2]);
+            const double a = -1.0 / (sg + t[2]);
+            const double bb = t[0] * t[1] * a;
+            const double e1[3] = {1.0 + sg * t[0] * t[0] * a, sg * bb, -sg * t[0]};
+            const double e2[3] = {bb, sg + t[1] * t[1] * a, -t[1]};
+            double tn[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) tn[k] = ct * t[k] + st * (cp * e1[k] + sp * e2[k]);
+            const double nn = sqrt(tn[0] * tn[0] + tn[1] * tn[1] + tn[2] * tn[2]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) t[k] = tn[k] / nn;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            acc[k] += ln * t[k];
+            p[k * M + n] = acc[k];
+            sum[k] += acc[k];
+        }
+        lprev = ln;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double m = sum[k] / M;
+        for (int n = 0; n < M; ++n) p[k * M + n] -= m;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Small conversion kernels.
+// ---------------------------------------------------------------------------
+// modes (FP64, packed rows incl. p = 0) -> state R (T, p = 0 zeroed) + r_cm
+template <typename T>
+__global__ void k_load_modes(const double* __restrict__ src, T* __restrict__ R,
+                             double* __restrict__ com, int C, int M, double inv_sqrtM)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)C * 3 * M) return;
+    const int p = (int)(t % M);
+    const int64_t row = t / M;
+    if (p == 0) {
+        com[row] = src[t] * inv_sqrtM;
+        R[t] = T(0);
+    } else {
+        R[t] = (T)src[t];
+    }
+}
+
+// state -> modes (FP64, R_0 = sqrt(M) r_cm)
+template <typename T>
+__global__ void k_store_modes(const T* __restrict__ R, const double* __restrict__ com,
+                              double* __restrict__ dst, int C, int M, double sqrtM)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)C * 3 * M) return;
+    const int p = (int)(t % M);
+    dst[t] = (p == 0) ? com[t / M] * sqrtM : (double)R[t];
+}
+
+template <typename T>
+__global__ void k_to_double(const T* __restrict__ a, double* __restrict__ b, int64_t n)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) b[t] = (double)a[t];
+}
+
+// positions (FP64 scaled, CoM-relative) + CoM -> observables i-iii per chain
+__global__ void k_shape(const double* __restrict__ pos, int C, int M, double* __restrict__ out,
+                        double d2)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const int N = M - 1, mb = (N + 1) / 2, mm = N / 2;
+    const double* p = pos + (size_t)c * 3 * M;
+    double L2 = 0, u2 = 0, m2 = 0;
+    for (int a = 0; a < 3; ++a) {
+        const double L = p[a * M + N] - p[a * M];
+        const double u = p[a * M + mb] - p[a * M + mb - 1];
+        const double m = p[a * M + mm];
+        L2 += L * L; u2 += u * u; m2 += m * m;
+    }
+    out[4 * c + 0] = L2 * d2; out[4 * c + 1] = u2 * d2; out[4 * c + 2] = m2 * d2;
+}
+
+__global__ void k_philox_words(uint32_t seed, uint32_t job, int64_t step, uint32_t tag, int n,
+                               uint32_t* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 w = philox4x32_10(
+        make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)i, tag), make_uint2(seed, job));
+    out[4 * i] = w.x; out[4 * i + 1] = w.y; out[4 * i + 2] = w.z; out[4 * i + 3] = w.w;
+}
+
+}  // namespace sfp

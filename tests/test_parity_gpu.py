@@ -1,0 +1,253 @@
+"""Parity of the CUDA path with the FP64 oracle, through the C ABI.
+
+Same seeded inputs on both sides (oracle equilibrium starts, or neutral jittered
+rods from tests/inputs.py), same Philox noise keys.  Tolerances:
+  * Philox words: bit-exact.
+  * Trajectories (the mode state, p >= 1): per chain ||R_gpu - R_ref|| / ||R_ref||
+    <= 1e-5 for FP32 after up to 1000 steps; <= 1e-9 for FP64.
+  * Single stages after one step: see each test (FP32 rounding of the bead
+    positions dominates the force stage).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1411_3487_gb300 as sfp
+from inputs import jittered_rods
+from oracle import oracle as O
+from paper_1411_3487_gb300 import _lib, build
+
+pytestmark = pytest.mark.gpu
+
+TSTAR, NU = 0.034, 0.35
+TOL = {sfp.SFP_FP32_SIMT: 1e-5, sfp.SFP_FP32: 1e-5, sfp.SFP_FP64: 1e-9}
+SIMT = pytest.param(sfp.SFP_FP32_SIMT, id="simt")
+TC = pytest.param(sfp.SFP_FP32, id="tc")
+F64 = pytest.param(sfp.SFP_FP64, id="fp64")
+PRECISIONS = [SIMT, TC, F64]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+
+
+def rel_err(A, B):
+    """Per-chain relative L2 error over the internal modes p >= 1."""
+    A = np.asarray(A)[:, :, 1:]
+    B = np.asarray(B)[:, :, 1:]
+    return np.linalg.norm((A - B).reshape(len(A), -1), axis=1) / np.linalg.norm(B.reshape(len(B), -1), axis=1)
+
+
+def starts(M, C, seed=1, dtau=1.0):
+    m = O.Model(M, dtau=dtau)
+    return np.stack([m.equilibrium_start(seed, j) for j in range(C)])
+
+
+def make_batch(M, C, dtau, precision, seed=1, shear=0.0):
+    return sfp.Batch([{"n_beads": M, "dtau": dtau, "shear_rate_per_s": shear}] * C, seed=seed,
+                     precision=precision)
+
+
+def test_philox_bit_exact():
+    for seed, job, step, tag in ((0, 0, 0, 0), (1, 7, 123456789012, 0), (0xFFFFFFFF, 3, 2**40 + 5, 1)):
+        g = sfp.philox_words(seed, job, step, tag, 1000)
+        for i in (0, 1, 31, 500, 999):
+            ref = O.philox4x32_10([step & 0xFFFFFFFF, step >> 32, i, tag], [seed, job])
+            assert np.array_equal(g[i], ref)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("M,C,dtau", [(256, 37, 100.0), (64, 45, 10.0), (67, 5, 10.0), (512, 3, 100.0)])
+def test_each_stage_one_step(precision, M, C, dtau):
+    """a1 inverse transform, a2 force, a3 noise, a4 forward transform, a5 update."""
+    m = O.Model(M, dtau=dtau)
+    t = m.tables()
+    R0 = starts(M, C, dtau=dtau)
+    b = make_batch(M, C, dtau, precision)
+    b.set_modes(R0)
+    b.step(1)
+    fp64 = precision == sfp.SFP_FP64
+    # a1: CoM-relative bead positions r = phi R (p >= 1)
+    Rin = R0.copy()
+    Rin[:, :, 0] = 0
+    r_ref = np.stack([m.modes_to_beads(x) for x in Rin])
+    r_gpu = b.probe(sfp.SFP_PROBE_BEADS)
+    scale = np.abs(r_ref).max()
+    assert np.abs(r_gpu - r_ref).max() <= (1e-12 if fp64 else 2e-6) * scale
+    # a3: bead noise of step 0
+    z_ref = np.stack([O.bead_normals(1, j, 0, 0, M) for j in range(C)])
+    assert np.abs(b.probe(sfp.SFP_PROBE_NOISE) - z_ref).max() <= (1e-13 if fp64 else 4e-6)
+    # a2 + a4: DeltaH (Eq. e11) and the bead-space residual force f = phi DeltaH
+    dH_ref = np.stack([m.delta_H(x) for x in r_ref])
+    dH_gpu = b.probe(sfp.SFP_PROBE_DH)
+    f_gpu = b.probe(sfp.SFP_PROBE_FORCE)
+    f_ref = np.einsum("np,cap->can", t["phi"], dH_ref)
+    ftol = 1e-9 if fp64 else 2e-3
+    assert np.all(rel_err(dH_gpu, dH_ref) < ftol)
+    assert np.linalg.norm(f_gpu - f_ref) / np.linalg.norm(f_ref) < ftol
+    # a4: projected noise Z = phi^T z
+    Z_ref = np.einsum("np,can->cap", t["phi"], z_ref)
+    assert np.abs(b.probe(sfp.SFP_PROBE_ZMODE) - Z_ref).max() <= (1e-12 if fp64 else 2e-5)
+    # a5: the state after one step
+    R1 = m.run_modes(R0, 1, np.arange(C), 0, 1)
+    assert np.all(rel_err(b.modes(), R1) < TOL[precision])
+    assert np.all(b.observe(sfp.SFP_OBS_STEP) == 1)
+
+
+@pytest.mark.parametrize("precision", [SIMT, TC])
+def test_trajectory_256bp_fp32(precision):
+    """4096 x 256-bp workload, 32-chain subset: 1000 steps at dtau = 100 (15.9 ps)."""
+    M, C, dtau = 256, 32, 100.0
+    m = O.Model(M, dtau=dtau)
+    R = starts(M, C, dtau=dtau)
+    b = make_batch(M, C, dtau, precision)
+    b.set_modes(R)
+    done = 0
+    for mark in (1, 10, 100, 1000):
+        R = m.run_modes(R, 1, np.arange(C), done, mark - done)
+        b.step(mark - done)
+        done = mark
+        G = b.modes()
+        e = rel_err(G, R)
+        assert e.max() < TOL[precision], (mark, e.max())
+        # centre of mass (FP64 accumulator, FP32 noise projection)
+        dcm = np.abs(G[:, :, 0] - R[:, :, 0]).max() / math.sqrt(M)
+        assert dcm < 1e-5 * math.sqrt(6 * TSTAR * dtau * mark / M) + 1e-9
+
+
+def test_trajectory_64bp_fp64_full_config():
+    """Single 64-bp chain, FP64, dtau = 10 (1.59 ps), 2e4 steps, seed 1."""
+    M, dtau, n = 64, 10.0, 20000
+    m = O.Model(M, dtau=dtau)
+    R = starts(M, 1, dtau=dtau)
+    b = make_batch(M, 1, dtau, sfp.SFP_FP64)
+    b.set_modes(R)
+    b.step(n)
+    Rref = m.run_modes(R, 1, [0], 0, n)
+    assert rel_err(b.modes(), Rref).max() < TOL[sfp.SFP_FP64]
+    assert abs(b.modes()[0, 0, 0] - Rref[0, 0, 0]) < 1e-9
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("M,C", [(3, 4), (5, 1), (67, 5), (130, 45), (33, 300)])
+def test_ragged_and_tiny_shapes(precision, M, C):
+    dtau = 5.0
+    m = O.Model(M, dtau=dtau)
+    r0 = jittered_rods(C, M, seed=M)
+    R = np.stack([m.beads_to_modes(x) for x in r0])
+    b = make_batch(M, C, dtau, precision)
+    b.set_modes(R)
+    b.step(50)
+    Rref = m.run_modes(R, 1, np.arange(C), 0, 50)
+    assert rel_err(b.modes(), Rref).max() < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_uneven_batch_with_shear(precision):
+    """Lengths 64/128/256/512 with their Table 1 steps, mixed shear, one batch."""
+    lengths = [64, 128, 256, 512, 64, 256, 128, 512, 256]
+    dt = {64: 10.0, 128: 50.0, 256: 100.0, 512: 100.0}
+    rates = [0.0, 1.54e8, 0.0, 1e8, 5e7, 0.0, 0.0, 1.54e8, 1e6]
+    chains = [{"n_beads": M, "dtau": dt[M], "shear_rate_per_s": s, "job_id": 100 + i}
+              for i, (M, s) in enumerate(zip(lengths, rates))]
+    b = sfp.Batch(chains, seed=5, precision=precision)
+    c_ps = sfp.derive()["c_ps"]
+    starts_ = [O.Model(M, dtau=dt[M]).equilibrium_start(5, 100 + i) for i, M in enumerate(lengths)]
+    b.set_modes(starts_)
+    b.step(120)
+    G = b.modes()
+    for i, M in enumerate(lengths):
+        m = O.Model(M, dtau=dt[M])
+        ref = m.run_modes(starts_[i][None], 5, [100 + i], 0, 120, shear=rates[i] * c_ps * 1e-12)
+        assert rel_err(G[i][None], ref)[0] < TOL[precision], i
+
+
+@pytest.mark.parametrize("precision", [SIMT, F64])
+def test_init_equilibrium_matches_oracle_sampler(precision):
+    for M, C in ((64, 5), (256, 7), (512, 2)):
+        b = make_batch(M, C, 10.0, precision, seed=9)
+        b.init_equilibrium(0)
+        m = O.Model(M)
+        ref = np.stack([m.equilibrium_start(9, j) for j in range(C)])
+        G = b.modes()
+        assert rel_err(G, ref).max() < (1e-12 if precision == sfp.SFP_FP64 else 1e-6)
+        assert np.all(G[:, :, 0] == 0)
+        assert np.all(b.observe(sfp.SFP_OBS_STEP) == 0)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_checkpoint_resume_is_bit_exact(precision):
+    M, C = 128, 20
+    b = make_batch(M, C, 50.0, precision)
+    b.init_equilibrium(5)
+    blob = b.save()
+    b.step(30)
+    A = b.modes()
+    b.load(blob)
+    b.step(30)
+    assert np.array_equal(b.modes(), A)
+    assert np.all(b.observe(sfp.SFP_OBS_STEP) == 35)
+
+
+def test_positions_round_trip_and_shape_observables():
+    M, C = 256, 6
+    d = sfp.derive()
+    m = O.Model(M, dtau=100.0)
+    R = starts(M, C)
+    R[:, :, 0] = np.array([1.0, -2.0, 3.0]) * math.sqrt(M)         # off-origin centre of mass
+    pos_nm = np.stack([m.modes_to_beads(x) for x in R]) * d["d_nm"]
+    b = make_batch(M, C, 100.0, sfp.SFP_FP64)
+    b.set_positions(pos_nm)
+    assert rel_err(b.modes(), R).max() < 1e-12
+    assert np.abs(b.positions_nm() - pos_nm).max() < 1e-10
+    assert np.allclose(b.observe(sfp.SFP_OBS_COM), np.array([1.0, -2.0, 3.0]) * d["d_nm"])
+    shape = b.observe(sfp.SFP_OBS_SHAPE)
+    for c in range(C):
+        ref = m.observables(R[c])
+        assert shape[c, :3] == pytest.approx(ref[:3] * d["d_nm"] ** 2, rel=1e-10)
+
+
+@pytest.mark.parametrize("precision", [SIMT, TC])
+def test_full_size_256bp_sampled(precision):
+    """The 4096 x 256-bp workload at full size, in the benchmark's launch
+    configuration; six sampled chains recomputed by the oracle."""
+    M, C, dtau, n = 256, 4096, 100.0, 20
+    b = make_batch(M, C, dtau, precision)
+    b.init_equilibrium(0)
+    R0 = b.modes()
+    b.step(n)
+    G = b.modes()
+    m = O.Model(M, dtau=dtau)
+    pick = np.array([0, 1, 777, 2048, 4000, 4095])
+    ref = m.run_modes(R0[pick], 1, pick, 0, n)
+    assert rel_err(G[pick], ref).max() < TOL[precision]
+    # a law that holds at any size: centre-of-mass diffusion D = T*/(N+1)
+    dcm = (G[:, :, 0] - R0[:, :, 0]) / math.sqrt(M)
+    msd = np.mean(np.sum(dcm ** 2, axis=1))
+    assert msd == pytest.approx(6 * TSTAR * dtau * n / M, rel=4.5 * math.sqrt(2 / (3 * C)))
+
+
+def test_budget_and_errors():
+    with pytest.raises(sfp.SfpError) as e:
+        sfp.Batch([{"n_beads": 256, "dtau": 100.0}] * 64, hbm_budget_bytes=100_000,
+                  precision=sfp.SFP_FP32_SIMT)
+    assert e.value.code == _lib.SFP_ENOMEM
+    b = make_batch(64, 3, 10.0, sfp.SFP_FP32_SIMT)
+    with pytest.raises(sfp.SfpError):
+        b.probe(sfp.SFP_PROBE_DH)                 # no step yet
+    with pytest.raises(sfp.SfpError):
+        b.step(-1)
+
+
+def test_nonfinite_state_is_reported():
+    M, C = 64, 4
+    b = make_batch(M, C, 10.0, sfp.SFP_FP32_SIMT)
+    R = starts(M, C)
+    R[2, 1, 5] = np.nan
+    b.set_modes(R)
+    b.step(1)
+    with pytest.raises(sfp.SfpError) as e:
+        b.modes()
+    assert e.value.code == _lib.SFP_ENONFINITE
