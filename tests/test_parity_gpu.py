@@ -23,7 +23,7 @@ pytestmark = pytest.mark.gpu
 TSTAR, NU = 0.034, 0.35
 TOL = {sfp.SFP_FP32_SIMT: 1e-5, sfp.SFP_FP32: 1e-5, sfp.SFP_FP64: 1e-9}
 SIMT = pytest.param(sfp.SFP_FP32_SIMT, id="simt")
-TC = pytest.param(sfp.SFP_FP32, id="tc")
+TC = pytest.param(sfp.SFP_FP32, id="tcgen05")
 F64 = pytest.param(sfp.SFP_FP64, id="fp64")
 PRECISIONS = [SIMT, TC, F64]
 
