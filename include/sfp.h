@@ -189,6 +189,47 @@ const char *sfp_last_error(void);
 int sfp_philox_words(uint32_t seed, uint32_t job, int64_t step, uint32_t tag,
                      int32_t count, uint32_t *host_out);
 
+/* ---- allocation-free step -------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * must not allocate device memory: code running inside a host framework that
+ * owns every device buffer (its own pool, or a fixed budget enforced by an
+ * outside memory manager), and latency-critical loops where a cudaMalloc,
+ * which may synchronise the whole device, would stall other streams.
+ *
+ * sfp_step_noalloc advances n_chains chains that live in caller-owned device
+ * memory by n_steps steps of the plain FP32 CUDA-core path (the same kernels
+ * and the same arithmetic as sfp_step on an SFP_FP32_SIMT batch).  It calls
+ * no cudaMalloc, cudaFree or other allocating routine: its tables (phi,
+ * phi^T and the per-mode coefficients, rebuilt on the device on every call)
+ * and its scratch (bead positions, force and noise, mode-space force and
+ * noise, step counters) live in one file-scope device array of
+ * SFP_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU which loads the library
+ * holds until the process exits.
+ *   chain      n_beads, step (dtau, or dt_ps when dtau <= 0) and shear rate
+ *              shared by all chains; chain c uses Philox key
+ *              (seed, chain->job_id + c) and must keep job_id + c < 2^32.
+ *   step0      step counter of the first step (the Philox counter), the
+ *              same for every chain.
+ *   modes_dev  FP32 device array [n_chains][3][n_beads] of mode amplitudes
+ *              R_p in scaled units (in/out).  Entries p = 0 are ignored on
+ *              input and set to 0: the centre of mass is com_dev.
+ *   com_dev    FP64 device array [n_chains][3], centre of mass in scaled
+ *              units (in/out).
+ *   cuda_stream  the stream to queue the work on (NULL = legacy default).
+ * Scratch needed: 4 * (2 M^2 + 4 M + 15 n_chains M) bytes plus
+ * 24 * n_chains bytes (each piece rounded up to 256 bytes); a request that does
+ * not fit returns SFP_EINVAL with the limit in sfp_last_error().
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current), so make that first call
+ * before any stream capture.  Every call shares the one array, which keeps
+ * the previous call's contents; calls whose work overlaps on the GPU (two
+ * streams, or two host threads) race on it and must be serialised by the
+ * caller.  Asynchronous on cuda_stream; non-finite states are not reported. */
+#define SFP_NOALLOC_SCRATCH_BYTES (32u << 20)
+int sfp_step_noalloc(const sfp_params *params, const sfp_chain_desc *chain, int32_t n_chains,
+                     uint64_t seed, int64_t step0, float *modes_dev, double *com_dev,
+                     int64_t n_steps, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

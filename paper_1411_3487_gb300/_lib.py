@@ -23,7 +23,7 @@ EXPORTS = (
     "sfp_params_dsdna", "sfp_derive", "sfp_create", "sfp_init_equilibrium", "sfp_set_modes",
     "sfp_set_positions", "sfp_set_step", "sfp_step", "sfp_observe", "sfp_probe", "sfp_save",
     "sfp_load", "sfp_info", "sfp_destroy", "sfp_last_error", "sfp_philox_words",
-    "sfp_stage_timing", "sfp_stage_times",
+    "sfp_stage_timing", "sfp_stage_times", "sfp_step_noalloc",
 )
 
 
@@ -78,6 +78,8 @@ def load(path: str | None = None):
         L.sfp_philox_words.argtypes = [u32, u32, i64, u32, i32, vp]
         L.sfp_stage_timing.argtypes = [vp, i32]
         L.sfp_stage_times.argtypes = [vp, ct.POINTER(ct.c_double), ct.POINTER(i64)]
+        L.sfp_step_noalloc.argtypes = [ct.POINTER(SfpParams), ct.POINTER(SfpChainDesc), i32, u64, i64, vp, vp,
+                                       i64, vp]
         for name in EXPORTS:
             if name != "sfp_last_error":
                 getattr(L, name).restype = ct.c_int

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -420,6 +421,91 @@ int destroy_impl(sfp_batch* b)
     for (void* p : b->allocs) cudaFree(p);
     delete b;
     return SFP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free step: scratch and tables in one file-scope device array.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SFP_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 64;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up once per
+// device; the host-side name is only a stand-in and must never reach a kernel).
+int noalloc_scratch(unsigned char** out)
+{
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(SFP_ENOTSUP, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(SFP_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = (unsigned char*)g_noalloc_addr[dev];
+    return SFP_OK;
+}
+
+// Tables of Eqs. c8, c9, e9, d3, d6, f2 computed on the device in FP64, stored FP32.
+__global__ void k_noalloc_tables(float* phi, float* phiT, float* dm, float* h, float* w, float* g,
+                                 int M, double Tstar, double nu, double dtau)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < (int64_t)M * M) {
+        const int n = (int)(t / M), p = (int)(t % M);
+        const double v = (p == 0) ? rsqrt((double)M) : sqrt(2.0 / M) * cospi((double)p * (n + 0.5) / M);
+        phi[(size_t)n * M + p] = (float)v;
+        phiT[(size_t)p * M + n] = (float)v;
+    }
+    if (t < M) {
+        const int p = (int)t;
+        if (p == 0) {
+            dm[0] = 0.f; h[0] = 0.f; w[0] = (float)sqrt(2.0 * Tstar * dtau); g[0] = (float)dtau;
+        } else {
+            const double sn = sinpi(0.5 * p / M);
+            const double s2 = sn * sn;
+            const double zeta = 16.0 * nu * s2 * s2;
+            const double gap = (1.0 - 2.0 * nu) * 4.0 * s2;
+            const double em = -expm1(-zeta * dtau);
+            dm[p] = (float)em;
+            h[p] = (float)(exp(-zeta * dtau) * (-expm1(-gap * dtau)) / gap);
+            w[p] = (float)sqrt(Tstar * (-expm1(-2.0 * zeta * dtau)) / zeta);
+            g[p] = (float)(em / zeta);
+        }
+    }
+}
+
+// Per-call state: step counters, keys, shear, p = 0 entries cleared.
+__global__ void k_noalloc_prep(float* R, int64_t* step, uint32_t* job, double* shear, int* bad, int C, int M,
+                               int64_t step0, uint32_t job0, double shear_tau)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) *bad = 0;
+    if (c >= C) return;
+    step[c] = step0;
+    job[c] = job0 + (uint32_t)c;
+    shear[c] = shear_tau;
+    for (int a = 0; a < 3; ++a) R[((size_t)c * 3 + a) * M] = 0.f;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <typename T>
+cudaError_t gemm_on(cudaStream_t st, const T* In, const T* B, T* Out, int J, int Nc, int K)
+{
+    if (Nc >= 128) {
+        dim3 grid(nblk(Nc, 128), nblk(J, 128));
+        sfp::k_gemm_nt<T, 128, 128, 8, 8, 8><<<grid, 256, 0, st>>>(In, B, Out, J, Nc, K);
+    } else {
+        dim3 grid(nblk(Nc, 64), nblk(J, 64));
+        sfp::k_gemm_nt<T, 64, 64, 8, 4, 4><<<grid, 256, 0, st>>>(In, B, Out, J, Nc, K);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -882,6 +968,67 @@ int sfp_philox_words(uint32_t seed, uint32_t job, int64_t step, uint32_t tag, in
     if (e == cudaSuccess) e = cudaMemcpy(host_out, d, (size_t)count * 16, cudaMemcpyDeviceToHost);
     cudaFree(d);
     if (e != cudaSuccess) return fail(SFP_ECUDA, "philox words: %s", cudaGetErrorString(e));
+    return SFP_OK;
+}
+
+int sfp_step_noalloc(const sfp_params* params, const sfp_chain_desc* chain, int32_t n_chains,
+                     uint64_t seed, int64_t step0, float* modes_dev, double* com_dev, int64_t n_steps,
+                     void* cuda_stream)
+{
+    if (!chain || !modes_dev || !com_dev) return fail(SFP_EINVAL, "NULL argument");
+    if (n_chains <= 0 || n_steps < 0 || step0 < 0) return fail(SFP_EINVAL, "need n_chains > 0, n_steps >= 0, step0 >= 0");
+    if (seed >> 32) return fail(SFP_EINVAL, "seed must be < 2^32");
+    if (chain->job_id + (uint64_t)n_chains - 1 >= (1ull << 32)) return fail(SFP_EINVAL, "job_id + n_chains - 1 must be < 2^32");
+    if (chain->n_beads < 3 || chain->n_beads > 4096) return fail(SFP_EINVAL, "n_beads %d outside 3..4096", chain->n_beads);
+    Derived dv;
+    int rc = derive(params, &dv);
+    if (rc) return rc;
+    const double dtau = chain->dtau > 0.0 ? chain->dtau : chain->dt_ps / dv.c_ps;
+    if (!(dtau > 0.0) || !std::isfinite(dtau)) return fail(SFP_EINVAL, "step must be > 0");
+    if (!std::isfinite(chain->shear_rate_per_s)) return fail(SFP_EINVAL, "shear rate not finite");
+    const int M = chain->n_beads, C = n_chains;
+    const size_t fM = (size_t)M * sizeof(float), n = (size_t)C * 3 * M;
+    // carve the array: phi | phiT | dm h w g | r | f z | DeltaH Z | step | job | shear | flag
+    size_t off = 0;
+    auto take = [&off](size_t bytes) { const size_t o = off; off += align256(bytes); return o; };
+    const size_t o_phi = take(fM * M), o_phiT = take(fM * M), o_dm = take(fM), o_h = take(fM), o_w = take(fM),
+                 o_g = take(fM), o_r = take(n * 4), o_fz = take(2 * n * 4), o_yz = take(2 * n * 4),
+                 o_step = take((size_t)C * 8), o_job = take((size_t)C * 4), o_sh = take((size_t)C * 8),
+                 o_bad = take(sizeof(int));
+    if (off > (size_t)SFP_NOALLOC_SCRATCH_BYTES)
+        return fail(SFP_EINVAL, "%d chains x %d beads need %zu bytes of scratch; the static array holds %u",
+                    C, M, off, (unsigned)SFP_NOALLOC_SCRATCH_BYTES);
+    unsigned char* base = nullptr;
+    if ((rc = noalloc_scratch(&base))) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    float* phi = (float*)(base + o_phi);
+    float* phiT = (float*)(base + o_phiT);
+    float *dm = (float*)(base + o_dm), *h = (float*)(base + o_h), *w = (float*)(base + o_w), *g = (float*)(base + o_g);
+    float* r = (float*)(base + o_r);
+    float* fz = (float*)(base + o_fz);
+    float* yz = (float*)(base + o_yz);
+    int64_t* step = (int64_t*)(base + o_step);
+    uint32_t* job = (uint32_t*)(base + o_job);
+    double* shear = (double*)(base + o_sh);
+    k_noalloc_tables<<<nblk((int64_t)M * M, 256), 256, 0, st>>>(phi, phiT, dm, h, w, g, M, dv.Tstar, dv.nu, dtau);
+    k_noalloc_prep<<<nblk(C, 128), 128, 0, st>>>(modes_dev, step, job, shear, (int*)(base + o_bad), C, M, step0,
+                                                  (uint32_t)chain->job_id, chain->shear_rate_per_s * dv.c_ps * 1e-12);
+    CUDA_TRY(cudaGetLastError());
+    const float c12 = (float)(1.0 - 2.0 * dv.nu);
+    const double w0 = std::sqrt(2.0 * dv.Tstar * dtau);
+    int* bad = (int*)(base + o_bad);   // written by the update kernel, not reported here
+    for (int64_t s = 0; s < n_steps; ++s) {
+        CUDA_TRY(gemm_on<float>(st, modes_dev, phi, r, 3 * C, M, M));
+        if (M % 4 == 0)
+            sfp::k_force_noise<float, true><<<nblk(C, 4), 128, 0, st>>>(r, fz, fz + n, C, M, c12, (uint32_t)seed, job, step);
+        else
+            sfp::k_force_noise<float, false><<<nblk(C, 4), 128, 0, st>>>(r, fz, fz + n, C, M, c12, (uint32_t)seed, job, step);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(gemm_on<float>(st, fz, phiT, yz, 6 * C, M, M));
+        sfp::k_mode_update<float><<<nblk((int64_t)C * M, 256), 256, 0, st>>>(
+            modes_dev, yz, yz + n, com_dev, step, dm, h, w, g, shear, C, M, w0, dtau, bad);
+        CUDA_TRY(cudaGetLastError());
+    }
     return SFP_OK;
 }
 
