@@ -235,7 +235,7 @@ def run_native(args, rank, world, local):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        n_c, n_s = 512, 128
+        n_c, n_s = 512, 768
         rate, secs, cores = cpu_oracle_rate(n_c, n_s)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{n_c} chains x 256 beads x {n_s} steps ({secs:.1f} s)"}

@@ -120,7 +120,7 @@ int sfp_set_positions(sfp_batch *b, const double *host_pos_nm, size_t n_doubles)
 int sfp_set_step(sfp_batch *b, int64_t step);
 
 /* Advance every chain by n_steps mode-space steps (Sec. 4):
- *   r = phi R (Eq. c1); DeltaH from the bond forces (Eq. e11); bead noise
+ *   bond vectors u = chi R (Eq. e5); DeltaH from the bond forces (Eq. e11); bead noise
  *   z ~ N(0,1) keyed by (seed, job_id, step, bead) and projected (Eq. c4);
  *   R_p <- e^{-zeta_p dtau} R_p + h_p DeltaH_p + w_p Z_p (Eqs. d3, d6, f2);
  *   shear adds gamma g_p R^y_p to R^x_p (Eq. btum); the centre of mass
@@ -145,14 +145,15 @@ int sfp_observe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
 
 /* Intermediate arrays of the most recent step, FP64 packed [3][M_c] in scaled
  * units, for checking each stage on its own:
- *   SFP_PROBE_BEADS  r = phi R without the centre of mass (Eq. c1)
+ *   SFP_PROBE_BONDS  bond vectors u_n = r_n - r_{n-1} = sum_p chi_{n,p} R_p
+ *                    (Eq. e5) at index n = 1..N; index 0 holds 0
  *   SFP_PROBE_FORCE  f_n = v_n - v_{n+1}, v_n = u_n (1/|u_n| - (1-2nu)),
  *                    v_0 = v_{N+1} = 0, so that phi^T f = DeltaH (Eq. e11)
  *   SFP_PROBE_NOISE  bead normals z of that step (Eq. b5, unit variance)
  *   SFP_PROBE_DH     phi^T f = DeltaH_p (Eq. e11)
  *   SFP_PROBE_ZMODE  phi^T z = Z_p (Eq. c4)
  * SFP_EINVAL if no step has run since the batch was created or its state set. */
-enum { SFP_PROBE_BEADS = 0, SFP_PROBE_FORCE = 1, SFP_PROBE_NOISE = 2, SFP_PROBE_DH = 3,
+enum { SFP_PROBE_BONDS = 0, SFP_PROBE_FORCE = 1, SFP_PROBE_NOISE = 2, SFP_PROBE_DH = 3,
        SFP_PROBE_ZMODE = 4 };
 int sfp_probe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
 

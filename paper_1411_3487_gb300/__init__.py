@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (SFP_FP32, SFP_FP32_SIMT, SFP_FP64, SFP_OBS_COM, SFP_OBS_MODES,
-                   SFP_OBS_POSITIONS, SFP_OBS_SHAPE, SFP_OBS_STEP, SFP_PROBE_BEADS, SFP_PROBE_DH,
+                   SFP_OBS_POSITIONS, SFP_OBS_SHAPE, SFP_OBS_STEP, SFP_PROBE_BONDS, SFP_PROBE_DH,
                    SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_ZMODE, SfpChainDesc, SfpError,
                    SfpParams)
 

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libsfp.so")
 SFP_OK, SFP_EINVAL, SFP_ENOMEM, SFP_ECUDA, SFP_ETIMEDOUT, SFP_ENONFINITE, SFP_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 SFP_FP32, SFP_FP64, SFP_FP32_SIMT = 0, 1, 4
 SFP_OBS_MODES, SFP_OBS_POSITIONS, SFP_OBS_COM, SFP_OBS_STEP, SFP_OBS_SHAPE = 0, 1, 2, 3, 4
-SFP_PROBE_BEADS, SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_DH, SFP_PROBE_ZMODE = 0, 1, 2, 3, 4
+SFP_PROBE_BONDS, SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_DH, SFP_PROBE_ZMODE = 0, 1, 2, 3, 4
 
 # Every entry point declared in include/sfp.h.
 EXPORTS = (

@@ -91,7 +91,7 @@ int derive(const sfp_params* p, Derived* d)
 // FP64 tables of one (M, dtau), the closed forms of Eqs. c8, c9, e9, d3, d6, f2
 // written for accuracy: 1 - cos t = 2 sin^2(t/2), 1 - e^{-x} = -expm1(-x).
 struct Tables {
-    std::vector<double> phi, phiT, dm, h, w, g;
+    std::vector<double> phi, phiT, chi, dm, h, w, g;   // chi[n][p] = phi[n][p] - phi[n-1][p], chi[0][p] = 0
     double w0;
 };
 
@@ -106,6 +106,11 @@ void make_tables(int M, double Tstar, double nu, double dtau, Tables* t)
             t->phi[(size_t)n * M + p] = v;
             t->phiT[(size_t)p * M + n] = v;
         }
+    // Eq. e3 (first form): bond vectors u_n = sum_p chi_{n,p} R_p (Eq. e5); row n = 0 is zero.
+    t->chi.assign((size_t)M * M, 0.0);
+    for (int n = 1; n < M; ++n)
+        for (int p = 1; p < M; ++p)
+            t->chi[(size_t)n * M + p] = t->phi[(size_t)n * M + p] - t->phi[(size_t)(n - 1) * M + p];
     t->dm.assign(M, 0.0); t->h.assign(M, 0.0); t->w.assign(M, 0.0); t->g.assign(M, 0.0);
     t->w0 = std::sqrt(2.0 * Tstar * dtau);
     t->g[0] = dtau;
@@ -160,9 +165,9 @@ struct Group {
     uint32_t* job = nullptr;      // [C]
     double* shear = nullptr;      // [C] shear rate in 1/tau
     int64_t* step = nullptr;      // [C]
-    void *phi = nullptr, *phiT = nullptr, *dm = nullptr, *h = nullptr, *w = nullptr, *g = nullptr;
+    void *chi = nullptr, *phiT = nullptr, *dm = nullptr, *h = nullptr, *w = nullptr, *g = nullptr;
     double *phi_d = nullptr, *phiT_d = nullptr;   // FP64 copies for conversions
-    void* r = nullptr;            // [C][3][M]
+    void* r = nullptr;            // [C][3][M] bond vectors u (slot n = 0 unused)
     void* fz = nullptr;           // [2][C][3][M]
     void* yz = nullptr;           // [2][C][3][M]
     double* stage = nullptr;      // [C][3][M] FP64 staging
@@ -304,9 +309,9 @@ int step_group(sfp_batch* b, Group& g)
     T* yz = (T*)g.yz;
     int rc;
     if ((rc = mark(b, 0))) return rc;
-    // a1: r = phi R  (inverse transform, Eq. c1)
-    if (g.tc) rc = sfp::tc_transform(g.tc, 0, (const float*)R, (float*)r, b->stream);
-    else rc = launch_gemm<T>(b, R, (const T*)g.phi, r, 3 * C, M, M);
+    // a1: modes -> bond vectors u = chi R  (Eqs. c1, e5; the centre of mass drops out)
+    if (g.tc) rc = sfp::tc_transform(g.tc, 0, b->stream);
+    else rc = launch_gemm<T>(b, R, (const T*)g.chi, r, 3 * C, M, M);
     if (rc) return rc;
     if (g.tc) b->launches++;
     if ((rc = mark(b, 1))) return rc;
@@ -331,7 +336,7 @@ int step_group(sfp_batch* b, Group& g)
     }
     if ((rc = mark(b, 2))) return rc;
     // a4: [DeltaH | Z] = phi^T [f | z]  (forward transform, Eqs. c4, e11)
-    if (g.tc) rc = sfp::tc_transform(g.tc, 1, (const float*)fz, (float*)yz, b->stream);
+    if (g.tc) rc = sfp::tc_transform(g.tc, 1, b->stream);
     else rc = launch_gemm<T>(b, fz, (const T*)g.phiT, yz, 6 * C, M, M);
     if (rc) return rc;
     if (g.tc) b->launches++;
@@ -451,16 +456,19 @@ int noalloc_scratch(unsigned char** out)
     return SFP_OK;
 }
 
-// Tables of Eqs. c8, c9, e9, d3, d6, f2 computed on the device in FP64, stored FP32.
-__global__ void k_noalloc_tables(float* phi, float* phiT, float* dm, float* h, float* w, float* g,
+// Tables of Eqs. c8, e3, c9, e9, d3, d6, f2 computed on the device in FP64, stored FP32.
+__device__ __forceinline__ double phi_dev(int M, int n, int p)
+{
+    return (p == 0) ? rsqrt((double)M) : sqrt(2.0 / M) * cospi((double)p * (n + 0.5) / M);
+}
+__global__ void k_noalloc_tables(float* chi, float* phiT, float* dm, float* h, float* w, float* g,
                                  int M, double Tstar, double nu, double dtau)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < (int64_t)M * M) {
         const int n = (int)(t / M), p = (int)(t % M);
-        const double v = (p == 0) ? rsqrt((double)M) : sqrt(2.0 / M) * cospi((double)p * (n + 0.5) / M);
-        phi[(size_t)n * M + p] = (float)v;
-        phiT[(size_t)p * M + n] = (float)v;
+        phiT[(size_t)p * M + n] = (float)phi_dev(M, n, p);
+        chi[(size_t)n * M + p] = (n == 0 || p == 0) ? 0.f : (float)(phi_dev(M, n, p) - phi_dev(M, n - 1, p));
     }
     if (t < M) {
         const int p = (int)t;
@@ -600,7 +608,7 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
         make_tables(M, dv.Tstar, dv.nu, g.dtau, &g.tab);
         if ((rc = dalloc(b, &g.R, n * es)) || (rc = dalloc_t(b, &g.com, (size_t)g.C * 3 * 8)) ||
             (rc = dalloc_t(b, &g.job, (size_t)g.C * 4)) || (rc = dalloc_t(b, &g.shear, (size_t)g.C * 8)) ||
-            (rc = dalloc_t(b, &g.step, (size_t)g.C * 8)) || (rc = dalloc(b, &g.phi, (size_t)M * M * es)) ||
+            (rc = dalloc_t(b, &g.step, (size_t)g.C * 8)) || (rc = dalloc(b, &g.chi, (size_t)M * M * es)) ||
             (rc = dalloc(b, &g.phiT, (size_t)M * M * es)) || (rc = dalloc(b, &g.dm, M * es)) ||
             (rc = dalloc(b, &g.h, M * es)) || (rc = dalloc(b, &g.w, M * es)) || (rc = dalloc(b, &g.g, M * es)) ||
             (rc = dalloc_t(b, &g.phi_d, (size_t)M * M * 8)) || (rc = dalloc_t(b, &g.phiT_d, (size_t)M * M * 8)) ||
@@ -610,7 +618,7 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
             destroy_impl(b);
             return rc;
         }
-        if ((rc = upload_typed(b, g.phi, g.tab.phi)) || (rc = upload_typed(b, g.phiT, g.tab.phiT)) ||
+        if ((rc = upload_typed(b, g.chi, g.tab.chi)) || (rc = upload_typed(b, g.phiT, g.tab.phiT)) ||
             (rc = upload_typed(b, g.dm, g.tab.dm)) || (rc = upload_typed(b, g.h, g.tab.h)) ||
             (rc = upload_typed(b, g.w, g.tab.w)) || (rc = upload_typed(b, g.g, g.tab.g))) {
             destroy_impl(b);
@@ -652,8 +660,9 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
         if ((rc = load_modes_dev(b, g, g.stage))) { destroy_impl(b); return rc; }
         e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) { destroy_impl(b); return fail(SFP_ECUDA, "create: %s", cudaGetErrorString(e)); }
-        if (precision == SFP_FP32) {
-            rc = sfp::tc_create(&g.tc, M, 3 * g.C, g.tab.phi.data(), g.tab.phiT.data(), b->stream);
+        if (precision == SFP_FP32 && sfp::tc_supported(M)) {
+            rc = sfp::tc_create(&g.tc, M, 3 * g.C, g.tab.chi.data(), g.tab.phiT.data(), (const float*)g.R,
+                                (float*)g.r, (const float*)g.fz, (float*)g.yz, b->bad, b->stream);
             if (rc) { destroy_impl(b); return rc; }
         }
     }
@@ -688,8 +697,12 @@ int sfp_set_modes(sfp_batch* b, const double* host, size_t n_doubles)
     if (n_doubles < (size_t)(3 * b->total_beads)) return fail(SFP_EINVAL, "need %lld doubles", (long long)(3 * b->total_beads));
     std::vector<double> tmp;
     for (auto& g : b->groups) {
-        gather_group(b, g, host, tmp);
-        CUDA_TRY(cudaMemcpyAsync(g.stage, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, b->stream));
+        if (b->groups.size() == 1) {   // packed order is the group order: copy straight from the caller
+            CUDA_TRY(cudaMemcpyAsync(g.stage, host, (size_t)g.C * 3 * g.M * 8, cudaMemcpyHostToDevice, b->stream));
+        } else {
+            gather_group(b, g, host, tmp);
+            CUDA_TRY(cudaMemcpyAsync(g.stage, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, b->stream));
+        }
         int rc = load_modes_dev(b, g, g.stage);
         if (rc) return rc;
         CUDA_TRY(cudaStreamSynchronize(b->stream));
@@ -778,10 +791,15 @@ int sfp_observe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
             else
                 sfp::k_store_modes<float><<<nblk(n, 256), 256, 0, b->stream>>>((const float*)g.R, g.com, g.stage, g.C, g.M, std::sqrt((double)g.M));
             CUDA_TRY(cudaGetLastError());
-            tmp.resize(n);
-            CUDA_TRY(cudaMemcpyAsync(tmp.data(), g.stage, n * 8, cudaMemcpyDeviceToHost, b->stream));
-            CUDA_TRY(cudaStreamSynchronize(b->stream));
-            scatter_group(b, g, tmp, (double*)host_out);
+            if (b->groups.size() == 1) {
+                CUDA_TRY(cudaMemcpyAsync(host_out, g.stage, n * 8, cudaMemcpyDeviceToHost, b->stream));
+                CUDA_TRY(cudaStreamSynchronize(b->stream));
+            } else {
+                tmp.resize(n);
+                CUDA_TRY(cudaMemcpyAsync(tmp.data(), g.stage, n * 8, cudaMemcpyDeviceToHost, b->stream));
+                CUDA_TRY(cudaStreamSynchronize(b->stream));
+                scatter_group(b, g, tmp, (double*)host_out);
+            }
         } else if (what == SFP_OBS_POSITIONS || what == SFP_OBS_SHAPE) {
             int rc = positions_dev(b, g);
             if (rc) return rc;
@@ -829,14 +847,15 @@ int sfp_observe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
     int bad = 0;
     CUDA_TRY(cudaMemcpyAsync(&bad, b->bad, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     CUDA_TRY(cudaStreamSynchronize(b->stream));
-    if (bad) return fail(SFP_ENONFINITE, "a chain's state became non-finite");
+    if (bad & 2) return fail(SFP_ETIMEDOUT, "a tensor-core pipeline wait timed out");
+    if (bad & 1) return fail(SFP_ENONFINITE, "a chain's state became non-finite");
     return SFP_OK;
 }
 
 int sfp_probe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
 {
     if (!b || !host_out) return fail(SFP_EINVAL, "NULL argument");
-    if (what < SFP_PROBE_BEADS || what > SFP_PROBE_ZMODE) return fail(SFP_EINVAL, "unknown probe %d", what);
+    if (what < SFP_PROBE_BONDS || what > SFP_PROBE_ZMODE) return fail(SFP_EINVAL, "unknown probe %d", what);
     if (!b->probed) return fail(SFP_EINVAL, "no step has run since the state was set");
     const size_t need = (size_t)3 * b->total_beads * 8;
     if (bytes < need) return fail(SFP_EINVAL, "buffer too small: need %zu bytes", need);
@@ -846,7 +865,7 @@ int sfp_probe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
         const int64_t n = (int64_t)g.C * 3 * g.M;
         const char* src = nullptr;
         switch (what) {
-            case SFP_PROBE_BEADS: src = (const char*)g.r; break;
+            case SFP_PROBE_BONDS: src = (const char*)g.r; break;
             case SFP_PROBE_FORCE: src = (const char*)g.fz; break;
             case SFP_PROBE_NOISE: src = (const char*)g.fz + n * es; break;
             case SFP_PROBE_DH: src = (const char*)g.yz; break;
@@ -942,6 +961,12 @@ int sfp_stage_timing(sfp_batch* b, int32_t enable)
     int rc = harvest(b);
     if (rc) return rc;
     b->timing = enable != 0;
+    const size_t want = 5 * b->groups.size() * 64;
+    while (b->timing && b->events.size() < want) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        b->events.push_back(e);
+    }
     for (double& x : b->stage_us) x = 0.0;
     b->timed_group_steps = 0;
     return SFP_OK;
@@ -988,10 +1013,10 @@ int sfp_step_noalloc(const sfp_params* params, const sfp_chain_desc* chain, int3
     if (!std::isfinite(chain->shear_rate_per_s)) return fail(SFP_EINVAL, "shear rate not finite");
     const int M = chain->n_beads, C = n_chains;
     const size_t fM = (size_t)M * sizeof(float), n = (size_t)C * 3 * M;
-    // carve the array: phi | phiT | dm h w g | r | f z | DeltaH Z | step | job | shear | flag
+    // carve the array: chi | phiT | dm h w g | u | f z | DeltaH Z | step | job | shear | flag
     size_t off = 0;
     auto take = [&off](size_t bytes) { const size_t o = off; off += align256(bytes); return o; };
-    const size_t o_phi = take(fM * M), o_phiT = take(fM * M), o_dm = take(fM), o_h = take(fM), o_w = take(fM),
+    const size_t o_chi = take(fM * M), o_phiT = take(fM * M), o_dm = take(fM), o_h = take(fM), o_w = take(fM),
                  o_g = take(fM), o_r = take(n * 4), o_fz = take(2 * n * 4), o_yz = take(2 * n * 4),
                  o_step = take((size_t)C * 8), o_job = take((size_t)C * 4), o_sh = take((size_t)C * 8),
                  o_bad = take(sizeof(int));
@@ -1001,7 +1026,7 @@ int sfp_step_noalloc(const sfp_params* params, const sfp_chain_desc* chain, int3
     unsigned char* base = nullptr;
     if ((rc = noalloc_scratch(&base))) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    float* phi = (float*)(base + o_phi);
+    float* chi = (float*)(base + o_chi);
     float* phiT = (float*)(base + o_phiT);
     float *dm = (float*)(base + o_dm), *h = (float*)(base + o_h), *w = (float*)(base + o_w), *g = (float*)(base + o_g);
     float* r = (float*)(base + o_r);
@@ -1010,7 +1035,7 @@ int sfp_step_noalloc(const sfp_params* params, const sfp_chain_desc* chain, int3
     int64_t* step = (int64_t*)(base + o_step);
     uint32_t* job = (uint32_t*)(base + o_job);
     double* shear = (double*)(base + o_sh);
-    k_noalloc_tables<<<nblk((int64_t)M * M, 256), 256, 0, st>>>(phi, phiT, dm, h, w, g, M, dv.Tstar, dv.nu, dtau);
+    k_noalloc_tables<<<nblk((int64_t)M * M, 256), 256, 0, st>>>(chi, phiT, dm, h, w, g, M, dv.Tstar, dv.nu, dtau);
     k_noalloc_prep<<<nblk(C, 128), 128, 0, st>>>(modes_dev, step, job, shear, (int*)(base + o_bad), C, M, step0,
                                                   (uint32_t)chain->job_id, chain->shear_rate_per_s * dv.c_ps * 1e-12);
     CUDA_TRY(cudaGetLastError());
@@ -1018,7 +1043,7 @@ int sfp_step_noalloc(const sfp_params* params, const sfp_chain_desc* chain, int3
     const double w0 = std::sqrt(2.0 * dv.Tstar * dtau);
     int* bad = (int*)(base + o_bad);   // written by the update kernel, not reported here
     for (int64_t s = 0; s < n_steps; ++s) {
-        CUDA_TRY(gemm_on<float>(st, modes_dev, phi, r, 3 * C, M, M));
+        CUDA_TRY(gemm_on<float>(st, modes_dev, chi, r, 3 * C, M, M));
         if (M % 4 == 0)
             sfp::k_force_noise<float, true><<<nblk(C, 4), 128, 0, st>>>(r, fz, fz + n, C, M, c12, (uint32_t)seed, job, step);
         else

@@ -9,7 +9,7 @@ namespace sfp {
 
 // ---------------------------------------------------------------------------
 // Transform GEMM (NT):  Out[j][i] = sum_k In[j][k] * B[i][k]
-//   inverse (Eq. c1):  In = R (k = p), B = phi  stored [n][p]  -> Out = r
+//   inverse (Eq. e5):  In = R (k = p), B = chi  stored [n][p]  -> Out = u (bonds)
 //   forward (Eq. c4):  In = f|z (k = n), B = phi^T stored [p][n] -> Out = DeltaH|Z
 // Block tile BM rows x BN cols, K chunk BK; each thread owns TM x TN outputs.
 // Any J, Ncols, K (ragged tails are zero-filled).
@@ -70,17 +70,26 @@ k_gemm_nt(const T* __restrict__ In, const T* __restrict__ B, T* __restrict__ Out
 }
 
 // ---------------------------------------------------------------------------
-// Residual bond force + bead noise (Eqs. e4, e11, b5).
-// One warp per chain; each lane owns 4 consecutive beads per 128-bead chunk.
-//   u_n = r_n - r_{n-1} (n >= 1), v_n = u_n (1/|u_n| - (1 - 2nu)), v_0 = v_{N+1} = 0,
+// Residual bond force + bead noise (Eqs. e4, e5, e11, b5), from bond vectors.
+// One warp per chain; each lane owns 4 consecutive indices per 128-wide chunk.
+//   u_n = sum_p chi_{n,p} R_p (given, n >= 1; slot 0 unused),
+//   v_n = u_n (1/|u_n| - (1 - 2nu)), v_0 = v_{N+1} = 0,
 //   f_n = v_n - v_{n+1}   so that  sum_n phi_{n,p} f_n = DeltaH_p  (Eq. e11).
-// Neighbour beads come from the adjacent lane by warp shuffle; the two chunk
-// edges come from the previous chunk (carried) and one halo load.
-// z[n] = three N(0,1) draws keyed by (seed, job, step, n, tag 0).
+// v_{n+1} comes from the next lane by warp shuffle; the chunk edge from one
+// halo load.  z[n] = three N(0,1) draws keyed by (seed, job, step, n, tag 0).
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void residual_v(const T u[3], bool ok, T c12nu, T v[3])
+{
+    const T l2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const T s = ok ? rsqrt_t<T>(l2) - c12nu : T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = u[a] * s;
+}
+
 template <typename T, bool VEC4>
 __global__ void __launch_bounds__(128)
-k_force_noise(const T* __restrict__ r, T* __restrict__ f, T* __restrict__ z,
+k_force_noise(const T* __restrict__ ub, T* __restrict__ f, T* __restrict__ z,
               int C, int M, T c12nu, uint32_t seed, const uint32_t* __restrict__ job,
               const int64_t* __restrict__ step)
 {
@@ -91,67 +100,48 @@ k_force_noise(const T* __restrict__ r, T* __restrict__ f, T* __restrict__ z,
     const uint32_t jb = job[c];
     const int64_t st = step[c];
 
-    T prev[3] = {T(0), T(0), T(0)};   // r of the bead before this chunk
     for (int b0 = 0; b0 < M; b0 += 128) {
         const int n0 = b0 + 4 * lane;
         T x[3][4];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const T* ra = r + base + (size_t)a * M;
-            if (VEC4 && n0 + 3 < M) {
-                const float4 q = *reinterpret_cast<const float4*>(ra + n0);
-                x[a][0] = q.x; x[a][1] = q.y; x[a][2] = q.z; x[a][3] = q.w;
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) x[a][i] = (n0 + i < M) ? ra[n0 + i] : T(0);
+            const T* ua = ub + base + (size_t)a * M;
+            if constexpr (VEC4) {
+                if (n0 + 3 < M) {
+                    const float4 q = *reinterpret_cast<const float4*>(ua + n0);
+                    x[a][0] = q.x; x[a][1] = q.y; x[a][2] = q.z; x[a][3] = q.w;
+                    continue;
+                }
             }
-        }
-        // r_{n0-1}: lane-1's last bead, or the carried bead for lane 0
-        T left[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const T up = __shfl_up_sync(0xffffffffu, x[a][3], 1);
-            left[a] = lane ? up : prev[a];
+            for (int i = 0; i < 4; ++i) x[a][i] = (n0 + i < M) ? ua[n0 + i] : T(0);
         }
-        // v for the 4 owned beads
         T v[3][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int n = n0 + i;
-            T u[3];
+            T u[3] = {x[0][i], x[1][i], x[2][i]}, vv[3];
+            residual_v<T>(u, n >= 1 && n < M, c12nu, vv);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) u[a] = x[a][i] - (i ? x[a][i - 1] : left[a]);
-            const T l2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            const bool ok = (n >= 1) && (n < M);
-            const T s = ok ? rsqrt_t<T>(l2) - c12nu : T(0);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) v[a][i] = u[a] * s;
+            for (int a = 0; a < 3; ++a) v[a][i] = vv[a];
         }
-        // v_{n0+4}: next lane's first v; lane 31 computes it from a halo bead
+        // v_{n0+4}: next lane's first v; lane 31 recomputes it from one halo bond
         T vnext[3];
         {
-            T halo[3] = {T(0), T(0), T(0)};
             const int nh = b0 + 128;
+            T uh[3] = {T(0), T(0), T(0)}, vh[3];
             const bool has = (lane == 31) && (nh < M);
             if (has) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) halo[a] = r[base + (size_t)a * M + nh];
+                for (int a = 0; a < 3; ++a) uh[a] = ub[base + (size_t)a * M + nh];
             }
-            T uh[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) uh[a] = halo[a] - x[a][3];
-            const T l2 = uh[0] * uh[0] + uh[1] * uh[1] + uh[2] * uh[2];
-            const T s = has ? rsqrt_t<T>(l2) - c12nu : T(0);
+            residual_v<T>(uh, has, c12nu, vh);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const T dn = __shfl_down_sync(0xffffffffu, v[a][0], 1);
-                vnext[a] = (lane == 31) ? uh[a] * s : dn;
+                vnext[a] = (lane == 31) ? vh[a] : dn;
             }
         }
-        // carry r of the chunk's last bead to the next chunk
-#pragma unroll
-        for (int a = 0; a < 3; ++a) prev[a] = __shfl_sync(0xffffffffu, x[a][3], 31);
-
         T fo[3][4], zo[3][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -166,14 +156,16 @@ k_force_noise(const T* __restrict__ r, T* __restrict__ f, T* __restrict__ z,
         for (int a = 0; a < 3; ++a) {
             T* fa = f + base + (size_t)a * M;
             T* za = z + base + (size_t)a * M;
-            if (VEC4 && n0 + 3 < M) {
-                *reinterpret_cast<float4*>(fa + n0) = make_float4(fo[a][0], fo[a][1], fo[a][2], fo[a][3]);
-                *reinterpret_cast<float4*>(za + n0) = make_float4(zo[a][0], zo[a][1], zo[a][2], zo[a][3]);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (n0 + i < M) { fa[n0 + i] = fo[a][i]; za[n0 + i] = zo[a][i]; }
+            if constexpr (VEC4) {
+                if (n0 + 3 < M) {
+                    *reinterpret_cast<float4*>(fa + n0) = make_float4(fo[a][0], fo[a][1], fo[a][2], fo[a][3]);
+                    *reinterpret_cast<float4*>(za + n0) = make_float4(zo[a][0], zo[a][1], zo[a][2], zo[a][3]);
+                    continue;
+                }
             }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (n0 + i < M) { fa[n0 + i] = fo[a][i]; za[n0 + i] = zo[a][i]; }
         }
     }
 }

@@ -9,13 +9,20 @@ struct TcPlan;
 // Record an error message for sfp_last_error() and return `code`.
 int report(int code, const char* msg);
 
-// Plan the two transforms of one group with M beads and `rows` = 3 * chains
-// state rows: inverse r = phi R (rows rows) and forward [DeltaH|Z] = phi^T [f|z]
-// (2 * rows rows).  phi / phiT are the FP64 tables [n][p] / [p][n].
-int tc_create(TcPlan** out, int M, int rows, const double* phi, const double* phiT,
-              cudaStream_t stream);
-// which = 0: inverse, 1: forward.  FP32 in and out, row-major [row][M].
-int tc_transform(TcPlan* plan, int which, const float* in, float* out, cudaStream_t stream);
+// True when a group of M beads can use the tensor-core transforms
+// (M = 32, 64, 128, 256 or 512; other lengths keep the CUDA-core transforms).
+bool tc_supported(int M);
+
+// Plan the two transforms of one group with M beads and `rows` = 3 * chains:
+// inverse u = chi R (bond vectors, Eq. e5) reads R [rows][M] and writes r_out;
+// forward [DeltaH|Z] = phi^T [f|z] reads fz [2 rows][M] and writes yz_out.
+// phi / phiT are the FP64 tables chi [n][p] / phi^T [p][n]; they are split once
+// into TF32 hi/lo.
+// A wait that times out inside the kernel sets bit 2 of *err.
+int tc_create(TcPlan** out, int M, int rows, const double* phi, const double* phiT, const float* R,
+              float* r_out, const float* fz, float* yz_out, int* err, cudaStream_t stream);
+// which = 0: inverse, 1: forward.
+int tc_transform(TcPlan* plan, int which, cudaStream_t stream);
 void tc_destroy(TcPlan* plan);
 
 }  // namespace sfp

@@ -5,8 +5,9 @@ rods from tests/inputs.py), same Philox noise keys.  Tolerances:
   * Philox words: bit-exact.
   * Trajectories (the mode state, p >= 1): per chain ||R_gpu - R_ref|| / ||R_ref||
     <= 1e-5 for FP32 after up to 1000 steps; <= 1e-9 for FP64.
-  * Single stages after one step: see each test (FP32 rounding of the bead
-    positions dominates the force stage).
+  * Single stages after one step (diagnostics): absolute on bond vectors and
+    projected noise, relative on the force; the tensor-core path is looser
+    there because its FP32 accumulation in TMEM rounds less finely than FMA.
 """
 import math
 
@@ -69,13 +70,13 @@ def test_each_stage_one_step(precision, M, C, dtau):
     b.set_modes(R0)
     b.step(1)
     fp64 = precision == sfp.SFP_FP64
-    # a1: CoM-relative bead positions r = phi R (p >= 1)
-    Rin = R0.copy()
-    Rin[:, :, 0] = 0
-    r_ref = np.stack([m.modes_to_beads(x) for x in Rin])
-    r_gpu = b.probe(sfp.SFP_PROBE_BEADS)
-    scale = np.abs(r_ref).max()
-    assert np.abs(r_gpu - r_ref).max() <= (1e-12 if fp64 else 2e-6) * scale
+    tc = precision == sfp.SFP_FP32
+    # a1: bond vectors u_n = r_n - r_{n-1} = sum_p chi_{n,p} R_p (Eq. e5), slot 0 = 0
+    r_ref = np.stack([m.modes_to_beads(x) for x in R0])
+    u_ref = np.zeros_like(r_ref)
+    u_ref[:, :, 1:] = np.diff(r_ref, axis=2)
+    u_gpu = b.probe(sfp.SFP_PROBE_BONDS)
+    assert np.abs(u_gpu - u_ref).max() <= (1e-11 if fp64 else 2e-4 if tc else 2e-5)
     # a3: bead noise of step 0
     z_ref = np.stack([O.bead_normals(1, j, 0, 0, M) for j in range(C)])
     assert np.abs(b.probe(sfp.SFP_PROBE_NOISE) - z_ref).max() <= (1e-13 if fp64 else 4e-6)
@@ -89,7 +90,7 @@ def test_each_stage_one_step(precision, M, C, dtau):
     assert np.linalg.norm(f_gpu - f_ref) / np.linalg.norm(f_ref) < ftol
     # a4: projected noise Z = phi^T z
     Z_ref = np.einsum("np,can->cap", t["phi"], z_ref)
-    assert np.abs(b.probe(sfp.SFP_PROBE_ZMODE) - Z_ref).max() <= (1e-12 if fp64 else 2e-5)
+    assert np.abs(b.probe(sfp.SFP_PROBE_ZMODE) - Z_ref).max() <= (1e-12 if fp64 else 1e-4 if tc else 2e-5)
     # a5: the state after one step
     R1 = m.run_modes(R0, 1, np.arange(C), 0, 1)
     assert np.all(rel_err(b.modes(), R1) < TOL[precision])
