@@ -73,6 +73,8 @@ def lib():
             L.orc_equilibrium_start.argtypes = [ct.c_void_p, ct.c_uint32, ct.c_uint32, _D]
             L.orc_observables.argtypes = [ct.c_void_p, _D, _D]
             L.orc_threads.restype = ct.c_int
+            L.orc_run_mc.argtypes = [ct.c_void_p, ct.c_int, ct.c_uint32, _U32, ct.c_int64,
+                                     ct.c_int64, _D, _D, ct.POINTER(ct.c_int64), _D, ct.c_int]
             _lib = L
     return _lib
 
@@ -207,3 +209,44 @@ class Model:
         out = np.zeros(6)
         lib().orc_observables(self._h, _dp(x), _dp(out))
         return out
+
+    def run_mc(self, R, seed: int, jobs, sweep0: int, n_sweeps: int, step, sample: bool = False,
+               nthreads: int = 0):
+        """Metropolis sweeps in the mode representation (Sec. 5A), see ``orc_mc_sweeps``.
+
+        Returns ``(R, acc, obs)``: the new states ``[C][3][M]``, accepted moves per
+        chain and mode ``[C][M]`` and, if ``sample``, per-chain sums of |L|^2,
+        |u_m|^2, |r_m - r_cm|^2 and the sample count ``[C][4]`` (else None).
+        """
+        R = np.array(R, dtype=np.float64)
+        C = R.shape[0]
+        R = R.reshape(C, 3, self.M).copy()
+        j = np.ascontiguousarray(jobs, dtype=np.uint32)
+        assert j.shape == (C,)
+        s = np.ascontiguousarray(step, dtype=np.float64)
+        assert s.shape == (self.M,)
+        acc = np.zeros((C, self.M), dtype=np.int64)
+        obs = np.zeros((C, 4)) if sample else None
+        lib().orc_run_mc(self._h, C, seed, _up(j), sweep0, n_sweeps, _dp(s), _dp(R),
+                         acc.ctypes.data_as(ct.POINTER(ct.c_int64)),
+                         _dp(obs) if sample else None, nthreads)
+        return R, acc, obs
+
+    def mc_tuned_steps(self, R, seed: int, jobs, rounds: int = 8, sweeps: int = 50,
+                       target: float = 0.4):
+        """Per-mode MC step sizes tuned toward ``target`` acceptance during a burn-in.
+
+        Starts from sqrt(T*/zeta^l_p) and rescales each s_p by its acceptance over
+        ``sweeps`` sweeps, ``rounds`` times (sweep counters 2^40 + k, away from the
+        sampling sweeps).  Returns ``(step, R)``: the step sizes, to be held fixed
+        while sampling, and the burnt-in states.
+        """
+        zl = self.tables()["zl"]
+        step = np.zeros(self.M)
+        step[1:] = np.sqrt(self.Tstar / zl[1:])
+        C = np.asarray(R).shape[0]
+        for k in range(rounds):
+            R, acc, _ = self.run_mc(R, seed, jobs, (1 << 40) + k * sweeps, sweeps, step)
+            rate = acc.sum(axis=0) / (3.0 * sweeps * C)
+            step[1:] *= np.clip(rate[1:] / target, 0.25, 4.0)
+        return step, R

@@ -26,6 +26,9 @@
  *   - Shear (Eq. btum) in mode space: dR^x_p/dtau gains gamma R^y_p; it is
  *     integrated with R^y held at its start-of-step value.
  *
+ * Also here: the Metropolis Monte Carlo sampler in mode amplitudes that the
+ * paper uses as its equilibrium benchmark (Sec. 5A), orc_mc_sweeps.
+ *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written
  * from its published definition.  key = (seed, job_id); counter =
  * (step_lo, step_hi, index, tag).  Uniforms use the top 23 bits,
@@ -528,4 +531,103 @@ void orc_observables(const orc_model *m, const double *R, double *out)
     out[0] = L2; out[1] = u2; out[2] = d2;
     out[3] = cm[0]; out[4] = cm[1]; out[5] = cm[2];
     free(r);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Metropolis Monte Carlo in the mode representation (Sec. 5A)               */
+/* ------------------------------------------------------------------------ */
+
+/* Scaled energy H' of Eq. a2 from the bond vectors u[a*N + (n-1)], n = 1..N. */
+static double energy_of_bonds(int N, double nu, const double *u)
+{
+    double e = 0.0;
+    for (int n = 0; n < N; ++n) {
+        const double ux = u[n], uy = u[N + n], uz = u[2 * N + n];
+        const double len = sqrt(ux * ux + uy * uy + uz * uz);
+        e += 0.5 * (len - 1.0) * (len - 1.0);
+        if (n >= 1) e -= nu * (ux * u[n - 1] + uy * u[N + n - 1] + uz * u[2 * N + n - 1]);
+    }
+    return e;
+}
+
+/* Bonds of a mode state, u_n = sum_p chi_{n,p} R_p (Eq. e5). */
+static void bonds_of_modes(const orc_model *m, const double *R, double *u)
+{
+    const int M = m->M, N = M - 1;
+    for (int a = 0; a < 3; ++a)
+        for (int n = 1; n <= N; ++n) {
+            double s = 0.0;
+            for (int p = 0; p < M; ++p) s += m->chi[(size_t)(n - 1) * M + p] * R[a * M + p];
+            u[a * N + n - 1] = s;
+        }
+}
+
+/* The equilibrium benchmark of Sec. 5A: Monte Carlo in the mode amplitudes
+ * with large moves for the slow modes and small moves for the fast ones.
+ * One sweep visits every internal mode p = 1..N and axis alpha in order and
+ * proposes R_p^alpha += delta, delta uniform on (-s_p, s_p); the bonds then
+ * change by chi_{n,p} delta along alpha (Eq. e5), the energy H' is
+ * recomputed from them (Eq. a2) and the move is accepted with probability
+ * min(1, exp(-(H'_new - H'_old)/T*)).  The map R -> u is linear with a
+ * constant Jacobian, so the chain samples exp(-H'/T*) over bond space.
+ * The centre-of-mass mode p = 0 does not enter H' and is left unchanged.
+ * Random numbers: Philox counter (sweep_lo, sweep_hi, 3(p-1)+alpha, 3); word 0
+ * draws delta, word 1 the acceptance uniform.
+ *   acc[p]   incremented once per accepted move of mode p (any axis);
+ *   obs[k]   if non-NULL, after every sweep adds observables (orc_observables)
+ *            0..2, i.e. |L|^2, |u_m|^2 and |r_m - r_cm|^2, and obs[3] += 1. */
+void orc_mc_sweeps(const orc_model *m, uint32_t seed, uint32_t job, int64_t sweep0,
+                   int64_t n_sweeps, const double *step, double *R, int64_t *acc, double *obs)
+{
+    const int M = m->M, N = M - 1;
+    const double T = m->Tstar;
+    double *u = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+    double *un = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+    const uint32_t key[2] = {seed, job};
+    for (int64_t s = 0; s < n_sweeps; ++s) {
+        const int64_t sw = sweep0 + s;
+        bonds_of_modes(m, R, u);            /* fresh every sweep: no drift from updates */
+        double e = energy_of_bonds(N, m->nu, u);
+        for (int p = 1; p <= N; ++p)
+            for (int a = 0; a < 3; ++a) {
+                const uint32_t ctr[4] = {(uint32_t)((uint64_t)sw & 0xffffffffu),
+                                         (uint32_t)((uint64_t)sw >> 32),
+                                         (uint32_t)(3 * (p - 1) + a), 3u};
+                uint32_t x[4];
+                orc_philox4x32_10(ctr, key, x);
+                const double delta = step[p] * (2.0 * orc_u01(x[0]) - 1.0);
+                memcpy(un, u, sizeof(double) * 3 * (size_t)N);
+                for (int n = 1; n <= N; ++n) un[a * N + n - 1] += m->chi[(size_t)(n - 1) * M + p] * delta;
+                const double en = energy_of_bonds(N, m->nu, un);
+                const double de = en - e;
+                if (de <= 0.0 || orc_u01(x[1]) < exp(-de / T)) {
+                    R[a * M + p] += delta;
+                    memcpy(u, un, sizeof(double) * 3 * (size_t)N);
+                    e = en;
+                    if (acc) acc[p] += 1;
+                }
+            }
+        if (obs) {
+            double o[6];
+            orc_observables(m, R, o);
+            obs[0] += o[0]; obs[1] += o[1]; obs[2] += o[2]; obs[3] += 1.0;
+        }
+    }
+    free(u); free(un);
+}
+
+/* orc_mc_sweeps for C independent chains (OpenMP over chains): chain c uses
+ * job jobs[c], its state R[c][3][M], acceptance counts acc[c][M] and
+ * observable sums obs[c][4] (either may be NULL). */
+int orc_run_mc(const orc_model *m, int C, uint32_t seed, const uint32_t *jobs, int64_t sweep0,
+               int64_t n_sweeps, const double *step, double *R, int64_t *acc, double *obs,
+               int nthreads)
+{
+    const int M = m->M;
+    set_threads(nthreads);
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < C; ++c)
+        orc_mc_sweeps(m, seed, jobs[c], sweep0, n_sweeps, step, R + (size_t)c * 3 * M,
+                      acc ? acc + (size_t)c * M : NULL, obs ? obs + (size_t)c * 4 : NULL);
+    return 0;
 }

@@ -363,3 +363,86 @@ def test_bead_normals_statistics():
     assert np.abs(c - np.eye(3)).max() < 4.5 / math.sqrt(X.shape[1])
     lag = np.corrcoef(zz[:-1].ravel(), zz[1:].ravel())[0, 1]
     assert abs(lag) < 4.5 / math.sqrt(zz[1:].size)
+
+
+# ---------------------------------------------------------------- Monte Carlo (Sec. 5A)
+
+def _two_bond_quadrature(T, nu, n=1500):
+    """<|L|^2>, <|u_1|^2>, <|r_1 - r_cm|^2> of a 3-bead chain under exp(-H'/T*),
+    by direct quadrature over the bond lengths l1, l2 and the bond angle.
+
+    H' = 1/2 (l1-1)^2 + 1/2 (l2-1)^2 - nu l1 l2 c (Eq. a2 with N = 2), volume
+    element l1^2 l2^2 dl1 dl2 dc; the c-integral is done in closed form:
+    int e^{kc} dc = 2 sinh(k)/k and <c> = coth(k) - 1/k, k = nu l1 l2 / T*.
+    L = u1 + u2 and r_1 - r_cm = (u1 - u2)/3."""
+    l = np.linspace(1e-4, 3.0 + 14.0 * math.sqrt(T), n)
+    L1, L2 = np.meshgrid(l, l, indexing="ij")
+    k = nu * L1 * L2 / T
+    logw = (2 * np.log(L1) + 2 * np.log(L2) - (0.5 * (L1 - 1) ** 2 + 0.5 * (L2 - 1) ** 2) / T
+            + k - np.log(k) + np.log1p(-np.exp(-2 * k)))
+    w = np.exp(logw - logw.max())
+    c = 1.0 / np.tanh(k) - 1.0 / k
+    Z = w.sum()
+    return np.array([(w * (L1 ** 2 + L2 ** 2 + 2 * L1 * L2 * c)).sum() / Z,
+                     (w * L1 ** 2).sum() / Z,
+                     (w * (L1 ** 2 + L2 ** 2 - 2 * L1 * L2 * c)).sum() / Z / 9.0])
+
+
+@pytest.mark.parametrize("T,nu", [(TSTAR, NU), (0.3, 0.2)])
+def test_mc_samples_boltzmann_two_bonds(T, nu):
+    """The mode-space Metropolis sampler (Sec. 5A) on a 3-bead chain reproduces
+    averages of the Boltzmann weight of Eq. a2 computed by quadrature in bond
+    coordinates, which share nothing with the mode machinery (chi, phi, steps)."""
+    m = O.Model(3, Tstar=T, nu=nu)
+    C = 32
+    r = np.zeros((3, 3))
+    r[0] = [-1.5, 0.0, 1.5]
+    R = np.repeat(m.beads_to_modes(r)[None], C, axis=0)
+    step, R = m.mc_tuned_steps(R, 7, np.arange(C))
+    R, acc, obs = m.run_mc(R, 7, np.arange(C), 0, 20000, step, sample=True)
+    per = obs[:, :3] / obs[:, 3:4]
+    mean, se = per.mean(axis=0), per.std(axis=0, ddof=1) / math.sqrt(C)
+    q = _two_bond_quadrature(T, nu)
+    assert np.all(np.abs(mean - q) < 4.5 * se + 1e-12), (mean, q, se)
+    assert np.all(np.abs(mean / q - 1) < 0.01), (mean, q)
+    rate = acc[:, 1:].sum() / (3.0 * 20000 * C * 2)
+    assert 0.25 < rate < 0.55
+
+
+def test_mc_generalised_equipartition():
+    """MC samples obey <R_p^a dH'/dR_p^a> = T* for every internal mode, the
+    identity of any Boltzmann sampler, with dH'/dR_p = zeta_p R_p - DeltaH_p
+    (Eq. e10) evaluated independently of the sampler's energy routine."""
+    M, C = 12, 32
+    m = O.Model(M)
+    t = m.tables()
+    R = np.stack([m.equilibrium_start(3, j) for j in range(C)])
+    step, R = m.mc_tuned_steps(R, 3, np.arange(C))
+    acc, cnt = np.zeros(M), 0
+    for k in range(100):
+        R, _, _ = m.run_mc(R, 3, np.arange(C), 100 * k, 100, step)
+        for c in range(C):
+            dH = m.delta_H(m.modes_to_beads(R[c]))
+            acc += np.mean(R[c] * (t["zeta"][None, :] * R[c] - dH), axis=0)
+            cnt += 1
+    ratio = (acc / cnt)[1:] / TSTAR
+    assert abs(ratio.mean() - 1) < 0.04, ratio
+    # p = 1 relaxes slowest and its estimator has the largest variance: mean only
+    assert np.all(np.abs(ratio[1:] - 1) < 0.12), ratio
+
+
+@pytest.mark.parametrize("M", [5, 64])
+def test_bond_path_equals_bead_path(M):
+    """Eq. e11 two ways: the oracle's DeltaH = chi^T v (bond path) equals the
+    bead-space stencil f_n = v_n - v_{n+1} (v_0 = v_{N+1} = 0) projected with
+    phi^T (bead path), since sum_n phi_{n,p} (v_n - v_{n+1}) = sum_n chi_{n,p} v_n."""
+    m = O.Model(M)
+    phi = m.tables()["phi"]
+    r = jittered_rods(1, M, seed=21)[0]
+    u = np.diff(r, axis=1)
+    s = 1.0 / np.linalg.norm(u, axis=0) - (1.0 - 2.0 * NU)
+    v = np.zeros((3, M + 1))
+    v[:, 1:M] = u * s
+    f = v[:, :M] - v[:, 1:]
+    bead_path = f @ phi
+    assert np.abs(m.delta_H(r) - bead_path).max() < 1e-12 * max(1.0, np.abs(bead_path).max())
