@@ -176,7 +176,9 @@ def run_native(args, rank, world, local):
     stream = torch.cuda.current_stream()
     precision = sfp.SFP_FP32 if args.precision == "tc" else sfp.SFP_FP32_SIMT
     # weak scaling: every rank owns its own 4096 chains (disjoint job ids)
-    chains = [{"n_beads": M_BEADS, "dt_ps": DT_PS, "job_id": rank * C_CHAINS + i} for i in range(C_CHAINS)]
+    from paper_1411_3487_gb300 import shard
+    chains = [{"n_beads": M_BEADS, "dt_ps": DT_PS, "job_id": j}
+              for j in shard.job_range(rank, world, world * C_CHAINS)]
 
     def timed_steps(prec, steps, warmup, with_clocks):
         b = sfp.Batch(chains, seed=1, precision=prec, stream=stream)

@@ -138,10 +138,31 @@ int sfp_step(sfp_batch *b, int64_t n_steps);
  *                      middle bead m = floor(N/2) (Sec. 5B, observables
  *                      i-iii at this instant), all in nm^2, and the
  *                      simulated time t = c tau in ps
+ * Accumulators of sfp_set_sampling (SFP_EINVAL before its first call):
+ *   SFP_OBS_ACCUM      FP64 [C][4] per chain: sums over samples of the three
+ *                      SFP_OBS_SHAPE quantities (nm^2) and the sample count;
+ *                      their ratio is the equilibrium value Q(0) of the
+ *                      paper's observables i-iii (Sec. 5B)
+ *   SFP_OBS_MODE_POWER FP64 packed [3][M_c]: sums over samples of (R_p^alpha)^2
+ *                      in scaled units (R_0 = sqrt(M) r_cm)
+ *   SFP_OBS_COM_MSD    FP64 [C][4][2] per chain and lag of 1, 10, 100, 1000
+ *                      sampling intervals: sum of |r_cm(t) - r_cm(t - lag)|^2
+ *                      (nm^2, FP64 centre of mass, non-overlapping windows) and
+ *                      the number of windows; ratio / (6 t_lag) estimates the
+ *                      diffusion coefficient kT/((N+1) xi) of Sec. 7B
  * bytes must be at least the size of the requested array. */
 enum { SFP_OBS_MODES = 0, SFP_OBS_POSITIONS = 1, SFP_OBS_COM = 2, SFP_OBS_STEP = 3,
-       SFP_OBS_SHAPE = 4 };
+       SFP_OBS_SHAPE = 4, SFP_OBS_ACCUM = 5, SFP_OBS_MODE_POWER = 6, SFP_OBS_COM_MSD = 7 };
 int sfp_observe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
+
+/* Observable sampling (Sec. 5B).  every_steps > 0 clears the accumulators of
+ * SFP_OBS_ACCUM, SFP_OBS_MODE_POWER and SFP_OBS_COM_MSD, takes sample 0 of the
+ * current state at once, and from then on one sample after every every_steps
+ * steps of sfp_step (a small kernel on the batch's stream; the first call
+ * allocates about 8 (3 M + 16) bytes per chain).  every_steps = 0 stops
+ * sampling and keeps the sums readable.  Accumulators are not part of a
+ * checkpoint (sfp_save).  SFP_EINVAL for every_steps < 0. */
+int sfp_set_sampling(sfp_batch *b, int32_t every_steps);
 
 /* Intermediate arrays of the most recent step, FP64 packed [3][M_c] in scaled
  * units, for checking each stage on its own:

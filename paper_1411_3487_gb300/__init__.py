@@ -12,8 +12,9 @@ import ctypes as ct
 import numpy as np
 
 from . import _lib
-from ._lib import (SFP_FP32, SFP_FP32_SIMT, SFP_FP64, SFP_OBS_COM, SFP_OBS_MODES,
-                   SFP_OBS_POSITIONS, SFP_OBS_SHAPE, SFP_OBS_STEP, SFP_PROBE_BONDS, SFP_PROBE_DH,
+from ._lib import (SFP_FP32, SFP_FP32_SIMT, SFP_FP64, SFP_OBS_ACCUM, SFP_OBS_COM,
+                   SFP_OBS_COM_MSD, SFP_OBS_MODE_POWER, SFP_OBS_MODES, SFP_OBS_POSITIONS,
+                   SFP_OBS_SHAPE, SFP_OBS_STEP, SFP_PROBE_BONDS, SFP_PROBE_DH,
                    SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_ZMODE, SfpChainDesc, SfpError,
                    SfpParams)
 
@@ -132,9 +133,13 @@ class Batch:
             return flat.reshape(self.n_chains, 3, int(self.n_beads[0]))
         return [flat[self.offsets[i]:self.offsets[i + 1]].reshape(3, -1) for i in range(self.n_chains)]
 
+    def set_sampling(self, every_steps: int) -> None:
+        """Sample observables i-iii, mode power and CoM windows every ``every_steps`` steps."""
+        _lib.check(_lib.load().sfp_set_sampling(self._h, int(every_steps)))
+
     def observe(self, what: int):
         L = _lib.load()
-        if what in (SFP_OBS_MODES, SFP_OBS_POSITIONS):
+        if what in (SFP_OBS_MODES, SFP_OBS_POSITIONS, SFP_OBS_MODE_POWER):
             out = np.zeros(int(self.offsets[-1]))
             _lib.check(L.sfp_observe(self._h, what, out.ctypes.data, out.nbytes))
             return self._unpack(out)
@@ -142,8 +147,10 @@ class Batch:
             out = np.zeros((self.n_chains, 3))
         elif what == SFP_OBS_STEP:
             out = np.zeros(self.n_chains, dtype=np.int64)
-        elif what == SFP_OBS_SHAPE:
+        elif what in (SFP_OBS_SHAPE, SFP_OBS_ACCUM):
             out = np.zeros((self.n_chains, 4))
+        elif what == SFP_OBS_COM_MSD:
+            out = np.zeros((self.n_chains, 4, 2))
         else:
             raise ValueError(what)
         _lib.check(L.sfp_observe(self._h, what, out.ctypes.data, out.nbytes))

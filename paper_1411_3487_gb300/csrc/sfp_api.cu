@@ -173,6 +173,12 @@ struct Group {
     double* stage = nullptr;      // [C][3][M] FP64 staging
     double* stage2 = nullptr;     // [C][3][M] FP64 staging
     sfp::TcPlan* tc = nullptr;    // tensor-core transform plan (SFP_FP32)
+    // observable sampling (allocated by the first sfp_set_sampling)
+    double* obs_tab = nullptr;    // [3][M] rows: phi_N - phi_0, chi_m, phi_m' (p >= 1)
+    double* acc_shape = nullptr;  // [C][4]
+    double* acc_pow = nullptr;    // [C][3][M]
+    double* msd_snap = nullptr;   // [C][4][3]
+    double* msd_acc = nullptr;    // [C][4][2]
 };
 
 struct sfp_batch {
@@ -197,6 +203,11 @@ struct sfp_batch {
     size_t ev_used = 0;
     double stage_us[5] = {0, 0, 0, 0, 0};
     int64_t timed_group_steps = 0;
+    // observable sampling
+    int32_t sample_every = 0;      // 0 = off
+    int64_t since_sample = 0;      // steps since the last sample
+    int64_t n_samples = 0;         // samples taken since sampling was (re)enabled
+    bool sampled = false;          // accumulators exist
 };
 
 namespace {
@@ -350,11 +361,38 @@ int step_group(sfp_batch* b, Group& g)
     return mark(b, 4);
 }
 
+// One sample of observables i-iii, the mode power and the centre-of-mass
+// windows for every chain (sample index b->n_samples).
+int sample_all(sfp_batch* b)
+{
+    const int4 lags = make_int4(1, 10, 100, 1000);
+    for (auto& g : b->groups) {
+        const unsigned grid = nblk(g.C, 4);
+        if (b->precision == SFP_FP64)
+            sfp::k_sample<double><<<grid, 128, 0, b->stream>>>((const double*)g.R, g.com, g.obs_tab, g.C, g.M,
+                                                               g.acc_shape, g.acc_pow, g.msd_snap, g.msd_acc,
+                                                               b->n_samples, lags);
+        else
+            sfp::k_sample<float><<<grid, 128, 0, b->stream>>>((const float*)g.R, g.com, g.obs_tab, g.C, g.M,
+                                                              g.acc_shape, g.acc_pow, g.msd_snap, g.msd_acc,
+                                                              b->n_samples, lags);
+        b->launches++;
+        CUDA_TRY(cudaGetLastError());
+    }
+    b->n_samples++;
+    b->since_sample = 0;
+    return SFP_OK;
+}
+
 int step_all(sfp_batch* b, int64_t n_steps)
 {
     for (int64_t s = 0; s < n_steps; ++s) {
         for (auto& g : b->groups) {
             const int rc = (b->precision == SFP_FP64) ? step_group<double>(b, g) : step_group<float>(b, g);
+            if (rc) return rc;
+        }
+        if (b->sample_every > 0 && ++b->since_sample == b->sample_every) {
+            const int rc = sample_all(b);
             if (rc) return rc;
         }
         if (b->timing && b->ev_used >= 4000) {
@@ -779,8 +817,13 @@ int sfp_observe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
         case SFP_OBS_COM: need = (size_t)b->C * 3 * 8; break;
         case SFP_OBS_STEP: need = (size_t)b->C * 8; break;
         case SFP_OBS_SHAPE: need = (size_t)b->C * 4 * 8; break;
+        case SFP_OBS_ACCUM: need = (size_t)b->C * 4 * 8; break;
+        case SFP_OBS_MODE_POWER: need = packed; break;
+        case SFP_OBS_COM_MSD: need = (size_t)b->C * 8 * 8; break;
         default: return fail(SFP_EINVAL, "unknown observable %d", what);
     }
+    if ((what == SFP_OBS_ACCUM || what == SFP_OBS_MODE_POWER || what == SFP_OBS_COM_MSD) && !b->sampled)
+        return fail(SFP_EINVAL, "observable %d needs sfp_set_sampling first", what);
     if (bytes < need) return fail(SFP_EINVAL, "buffer too small: need %zu bytes", need);
     std::vector<double> tmp;
     for (auto& g : b->groups) {
@@ -837,6 +880,24 @@ int sfp_observe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
             CUDA_TRY(cudaStreamSynchronize(b->stream));
             for (int i = 0; i < g.C; ++i)
                 for (int a = 0; a < 3; ++a) ((double*)host_out)[3 * (size_t)g.chains[i] + a] = cm[3 * i + a] * b->dv.d_nm;
+        } else if (what == SFP_OBS_ACCUM || what == SFP_OBS_COM_MSD) {
+            const int w = what == SFP_OBS_ACCUM ? 4 : 8;
+            std::vector<double> a((size_t)g.C * w);
+            CUDA_TRY(cudaMemcpyAsync(a.data(), what == SFP_OBS_ACCUM ? g.acc_shape : g.msd_acc, a.size() * 8,
+                                     cudaMemcpyDeviceToHost, b->stream));
+            CUDA_TRY(cudaStreamSynchronize(b->stream));
+            const double d2 = b->dv.d_nm * b->dv.d_nm;
+            for (int i = 0; i < g.C; ++i)
+                for (int k = 0; k < w; ++k) {
+                    // sums in nm^2; counts as they are
+                    const bool is_count = (what == SFP_OBS_ACCUM) ? k == 3 : (k & 1) == 1;
+                    ((double*)host_out)[(size_t)w * g.chains[i] + k] = a[(size_t)w * i + k] * (is_count ? 1.0 : d2);
+                }
+        } else if (what == SFP_OBS_MODE_POWER) {
+            tmp.resize(n);
+            CUDA_TRY(cudaMemcpyAsync(tmp.data(), g.acc_pow, n * 8, cudaMemcpyDeviceToHost, b->stream));
+            CUDA_TRY(cudaStreamSynchronize(b->stream));
+            scatter_group(b, g, tmp, (double*)host_out);
         } else if (what == SFP_OBS_STEP) {
             std::vector<int64_t> st(g.C);
             CUDA_TRY(cudaMemcpyAsync(st.data(), g.step, g.C * 8, cudaMemcpyDeviceToHost, b->stream));
@@ -980,6 +1041,48 @@ int sfp_stage_times(sfp_batch* b, double out_us[5], int64_t* n_group_steps)
     for (int k = 0; k < 5; ++k) out_us[k] = b->stage_us[k];
     if (n_group_steps) *n_group_steps = b->timed_group_steps;
     return SFP_OK;
+}
+
+int sfp_set_sampling(sfp_batch* b, int32_t every_steps)
+{
+    if (!b) return fail(SFP_EINVAL, "batch is NULL");
+    if (every_steps < 0) return fail(SFP_EINVAL, "every_steps < 0");
+    if (every_steps == 0) {
+        b->sample_every = 0;
+        return SFP_OK;
+    }
+    int rc;
+    for (auto& g : b->groups) {
+        const int M = g.M, N = M - 1;
+        if (!g.obs_tab) {
+            if ((rc = dalloc_t(b, &g.obs_tab, (size_t)3 * M * 8)) ||
+                (rc = dalloc_t(b, &g.acc_shape, (size_t)g.C * 4 * 8)) ||
+                (rc = dalloc_t(b, &g.acc_pow, (size_t)g.C * 3 * M * 8)) ||
+                (rc = dalloc_t(b, &g.msd_snap, (size_t)g.C * 12 * 8)) ||
+                (rc = dalloc_t(b, &g.msd_acc, (size_t)g.C * 8 * 8)))
+                return rc;
+            // coefficient rows of L = r_N - r_0, u_m = r_m - r_{m-1} (m = ceil(N/2)) and
+            // r_m' - r_cm (m' = floor(N/2)) in terms of R_p (Eq. c1); p = 0 drops out of all three
+            std::vector<double> t((size_t)3 * M, 0.0);
+            const int mb = (N + 1) / 2, mm = N / 2;
+            const auto& phi = g.tab.phi;
+            for (int p = 1; p < M; ++p) {
+                t[p] = phi[(size_t)N * M + p] - phi[p];
+                t[M + p] = phi[(size_t)mb * M + p] - phi[(size_t)(mb - 1) * M + p];
+                t[2 * M + p] = phi[(size_t)mm * M + p];
+            }
+            CUDA_TRY(cudaMemcpyAsync(g.obs_tab, t.data(), t.size() * 8, cudaMemcpyHostToDevice, b->stream));
+            CUDA_TRY(cudaStreamSynchronize(b->stream));
+        }
+        CUDA_TRY(cudaMemsetAsync(g.acc_shape, 0, (size_t)g.C * 4 * 8, b->stream));
+        CUDA_TRY(cudaMemsetAsync(g.acc_pow, 0, (size_t)g.C * 3 * M * 8, b->stream));
+        CUDA_TRY(cudaMemsetAsync(g.msd_snap, 0, (size_t)g.C * 12 * 8, b->stream));
+        CUDA_TRY(cudaMemsetAsync(g.msd_acc, 0, (size_t)g.C * 8 * 8, b->stream));
+    }
+    b->sampled = true;
+    b->sample_every = every_steps;
+    b->n_samples = 0;
+    return sample_all(b);
 }
 
 int sfp_philox_words(uint32_t seed, uint32_t job, int64_t step, uint32_t tag, int32_t count,

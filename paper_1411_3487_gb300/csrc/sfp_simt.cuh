@@ -354,3 +354,75 @@ __global__ void k_philox_words(uint32_t seed, uint32_t job, int64_t step, uint32
 }
 
 }  // namespace sfp
+
+namespace sfp {
+
+// ---------------------------------------------------------------------------
+// Observable sampling (Sec. 5B, observables i-iii), one warp per chain, read
+// from the mode state only:
+//   L     = r_N - r_0       = sum_p (phi_{N,p} - phi_{0,p}) R_p
+//   u_m   (middle bond)     = sum_p chi_{m,p} R_p,          m = ceil(N/2)
+//   r_m - r_cm (middle bead)= sum_{p>=1} phi_{m',p} R_p,   m' = floor(N/2)
+// tab = [3][M] FP64 coefficient rows for these three sums.  Per chain, adds
+// |L|^2, |u_m|^2, |r_m - r_cm|^2 and 1 to shape[c][0..3] and (R_p^a)^2 to
+// power[c][a][p] (R_0 = sqrt(M) r_cm).  Centre-of-mass displacement over
+// non-overlapping windows of lag[i] samples (sample index k): when k is a
+// multiple of lag[i], adds |r_cm - snap_i|^2 and 1 to msd[c][i][0..1] (from
+// the second window edge on) and sets snap_i = r_cm.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128)
+k_sample(const T* __restrict__ R, const double* __restrict__ com, const double* __restrict__ tab,
+         int C, int M, double* __restrict__ shape, double* __restrict__ power,
+         double* __restrict__ snap, double* __restrict__ msd, int64_t k, int4 lag)
+{
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= C) return;
+    const T* Rc = R + (size_t)c * 3 * M;
+    double* pw = power + (size_t)c * 3 * M;
+    double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const double sqM = sqrt((double)M);
+    for (int p = lane; p < M; p += 32) {
+        const double cl = tab[p], cu = tab[M + p], cd = tab[2 * M + p];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double x = (p == 0) ? 0.0 : (double)Rc[(size_t)a * M + p];
+            s[a] += cl * x;
+            s[3 + a] += cu * x;
+            s[6 + a] += cd * x;
+            const double xp = (p == 0) ? sqM * com[3 * c + a] : x;
+            pw[(size_t)a * M + p] += xp * xp;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
+    if (lane != 0) return;
+    double* sh = shape + 4 * (size_t)c;
+    sh[0] += s[0] * s[0] + s[1] * s[1] + s[2] * s[2];
+    sh[1] += s[3] * s[3] + s[4] * s[4] + s[5] * s[5];
+    sh[2] += s[6] * s[6] + s[7] * s[7] + s[8] * s[8];
+    sh[3] += 1.0;
+    const int lags[4] = {lag.x, lag.y, lag.z, lag.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (lags[i] <= 0 || k % lags[i] != 0) continue;
+        double* sn = snap + ((size_t)c * 4 + i) * 3;
+        if (k > 0) {
+            double d2 = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double d = com[3 * c + a] - sn[a];
+                d2 += d * d;
+            }
+            msd[((size_t)c * 4 + i) * 2] += d2;
+            msd[((size_t)c * 4 + i) * 2 + 1] += 1.0;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sn[a] = com[3 * c + a];
+    }
+}
+
+}  // namespace sfp

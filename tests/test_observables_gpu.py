@@ -1,0 +1,115 @@
+"""Observable accumulators of the CUDA path (Sec. 5B) against the oracle, and
+the paper's own acceptance test: equilibrium observables at the largest step
+of Table 1 within 5% of the Monte Carlo benchmark (Sec. 5A)."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1411_3487_gb300 as sfp
+from oracle import oracle as O
+from paper_1411_3487_gb300 import build
+
+pytestmark = pytest.mark.gpu
+
+TSTAR = 0.034
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+
+
+def d_nm():
+    return sfp.derive()["d_nm"]
+
+
+@pytest.mark.parametrize("precision,tol", [(sfp.SFP_FP32, 2e-5), (sfp.SFP_FP32_SIMT, 2e-5),
+                                           (sfp.SFP_FP64, 1e-9)], ids=["tcgen05", "simt", "fp64"])
+def test_sampled_sums_match_oracle(precision, tol):
+    """Sums of |L|^2, |u_m|^2, |r_m - r_cm|^2, (R_p)^2 and the centre-of-mass
+    windows over samples every 5 steps, GPU vs the oracle's trajectory."""
+    M, C, dtau, every, nsamp = 64, 37, 10.0, 5, 41
+    m = O.Model(M, dtau=dtau)
+    R = np.stack([m.equilibrium_start(1, j) for j in range(C)])
+    b = sfp.Batch([{"n_beads": M, "dtau": dtau}] * C, seed=1, precision=precision)
+    b.set_modes(R)
+    b.set_sampling(every)
+    b.step(every * (nsamp - 1))
+    shape = np.zeros((C, 4))
+    power = np.zeros((C, 3, M))
+    msd = np.zeros((C, 4, 2))
+    snap = np.zeros((C, 4, 3))
+    for k in range(nsamp):
+        if k:
+            R = m.run_modes(R, 1, np.arange(C), every * (k - 1), every)
+        for c in range(C):
+            o = m.observables(R[c])
+            shape[c] += [o[0], o[1], o[2], 1.0]
+            power[c] += R[c] ** 2
+            for i, lag in enumerate((1, 10, 100, 1000)):
+                if k % lag == 0:
+                    if k:
+                        msd[c, i] += [np.sum((o[3:6] - snap[c, i]) ** 2), 1.0]
+                    snap[c, i] = o[3:6]
+    d2 = d_nm() ** 2
+    g_shape = b.observe(sfp.SFP_OBS_ACCUM)
+    assert np.all(g_shape[:, 3] == nsamp)
+    assert np.abs(g_shape[:, :3] / (shape[:, :3] * d2) - 1).max() < tol
+    g_pow = b.observe(sfp.SFP_OBS_MODE_POWER)
+    assert np.abs(g_pow[:, :, 1:] - power[:, :, 1:]).max() < 10 * tol * power[:, :, 1:].max()
+    g_msd = b.observe(sfp.SFP_OBS_COM_MSD)
+    assert np.array_equal(g_msd[:, :, 1], msd[:, :, 1])
+    assert np.abs(g_msd[:, :2, 0] - msd[:, :2, 0] * d2).max() < 1e-5 * (msd[:, :2, 0] * d2).max()
+
+
+def test_com_diffusion_is_free_draining():
+    """Centre-of-mass MSD at lags of 1, 10 and 100 steps equals 6 D t with
+    D = kT/((N+1) xi) (Sec. 7B): in scaled units 6 T* t/(N+1), exactly, for any
+    step size, because the internal forces cancel in the p = 0 mode."""
+    M, C, dtau = 256, 2048, 100.0
+    b = sfp.Batch([{"n_beads": M, "dtau": dtau}] * C, seed=3, precision=sfp.SFP_FP32)
+    b.init_equilibrium(0)
+    b.set_sampling(1)
+    b.step(1000)
+    msd = b.observe(sfp.SFP_OBS_COM_MSD)
+    d2 = d_nm() ** 2
+    for i, lag in enumerate((1, 10, 100)):
+        n = msd[:, i, 1].sum()
+        est = msd[:, i, 0].sum() / n / d2
+        exact = 6 * TSTAR * lag * dtau / M
+        # |dr|^2 / (2 D t) is chi-square with 3 dof per window: sd = sqrt(2/3) / sqrt(n)
+        assert abs(est / exact - 1) < 5 * math.sqrt(2.0 / 3.0 / n), (lag, est, exact)
+
+
+def test_equilibrium_observables_within_5pct_of_monte_carlo():
+    """The paper's criterion for its step sizes (Sec. 5B, Table 1): at the
+    largest step for 64 bp (dtau = 10, i.e. 1.59 ps) the equilibrium values of
+    <|L|^2>, <|u_m|^2> and <|r_m - r_cm|^2> from the dynamics lie within 5% of
+    the Monte Carlo benchmark in mode space (Sec. 5A).  GPU: 4096 chains,
+    tensor-core path, 2e4 steps of relaxation, then 2e4 steps sampled every 100.
+    Monte Carlo: the oracle's sampler, 64 chains x 2e4 sweeps after tuning."""
+    M, dtau = 64, 10.0
+    m = O.Model(M, dtau=dtau)
+    Cm = 64
+    R = np.stack([m.equilibrium_start(9, j) for j in range(Cm)])
+    step, R = m.mc_tuned_steps(R, 9, np.arange(Cm))
+    R, _, _ = m.run_mc(R, 9, np.arange(Cm), 0, 4000, step)
+    R, _, obs = m.run_mc(R, 9, np.arange(Cm), 4000, 20000, step, sample=True)
+    mc_per = obs[:, :3] / obs[:, 3:4]
+    mc = mc_per.mean(axis=0)
+    mc_se = mc_per.std(axis=0, ddof=1) / math.sqrt(Cm)
+
+    C = 4096
+    b = sfp.Batch([{"n_beads": M, "dtau": dtau}] * C, seed=9, precision=sfp.SFP_FP32)
+    b.init_equilibrium(0)
+    b.step(20000)
+    b.set_sampling(100)
+    b.step(20000)
+    acc = b.observe(sfp.SFP_OBS_ACCUM)
+    per = acc[:, :3] / acc[:, 3:4] / d_nm() ** 2
+    gpu = per.mean(axis=0)
+    gpu_se = per.std(axis=0, ddof=1) / math.sqrt(C)
+    ratio = gpu / mc
+    print("MC", mc, "+-", mc_se, "GPU", gpu, "+-", gpu_se, "ratio", ratio)
+    assert np.all(np.abs(ratio - 1) < 0.05), ratio
