@@ -9,6 +9,7 @@ Prints one JSON line (rank 0).  Metric: bead-timesteps/s (chains x beads x
 steps / s); simulated ns/s per chain is reported beside it.
   --impl reference   time the FP64 CPU oracle on the host cores instead
   --precision simt   time the plain FP32 CUDA-core path instead of tcgen05
+  --path staged      time the per-stage tcgen05 kernels instead of the fused step
 """
 from __future__ import annotations
 
@@ -38,6 +39,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="tc", choices=["tc", "simt"])
+    ap.add_argument("--path", default="fused", choices=["fused", "staged"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     return ap.parse_args()
@@ -180,8 +182,13 @@ def run_native(args, rank, world, local):
     chains = [{"n_beads": M_BEADS, "dt_ps": DT_PS, "job_id": j}
               for j in shard.job_range(rank, world, world * C_CHAINS)]
 
-    def timed_steps(prec, steps, warmup, with_clocks):
+    path = sfp.SFP_PATH_FUSED if args.path == "fused" else sfp.SFP_PATH_STAGED
+    if precision == sfp.SFP_FP32_SIMT:
+        path = sfp.SFP_PATH_STAGED
+
+    def timed_steps(prec, pth, steps, warmup, with_clocks):
         b = sfp.Batch(chains, seed=1, precision=prec, stream=stream)
+        b.set_path(pth)
         b.init_equilibrium(0)
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
         for _ in range(warmup):
@@ -210,7 +217,7 @@ def run_native(args, rank, world, local):
         ms = [a.elapsed_time(c) for a, c in ev]
         return b, ms, launches, clocks, kern
 
-    b, ms, launches, clocks, kern = timed_steps(precision, args.steps, args.warmup, True)
+    b, ms, launches, clocks, kern = timed_steps(precision, path, args.steps, args.warmup, True)
     tot_ms = float(sum(ms))
     if world > 1:
         t = torch.tensor([tot_ms], device="cuda")
@@ -223,17 +230,22 @@ def run_native(args, rank, world, local):
     ms_step = tot_ms / args.steps
 
     pk, how = peaks()
-    roof = roofline(kern, pk, how, precision, sfp)
+    roof = roofline(kern, pk, how, precision, path, sfp)
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = end_to_end(sfp, b, torch, min(args.steps, 50))
 
-    plain = None
+    plain = staged = None
     if not args.no_plain and precision != sfp.SFP_FP32_SIMT:
         b.close()
-        _, ms_p, _, _, _ = timed_steps(sfp.SFP_FP32_SIMT, min(args.steps, 100), 3, False)
+        _, ms_p, _, _, _ = timed_steps(sfp.SFP_FP32_SIMT, sfp.SFP_PATH_STAGED, min(args.steps, 100), 3, False)
         plain = {"value": beads * len(ms_p) / (sum(ms_p) * 1e-3), "unit": UNIT,
                  "ms_per_step": float(sum(ms_p) / len(ms_p)), "path": "plain FP32 CUDA-core path"}
+        if path == sfp.SFP_PATH_FUSED:
+            _, ms_s, _, _, k_s = timed_steps(sfp.SFP_FP32, sfp.SFP_PATH_STAGED, min(args.steps, 100), 3, False)
+            staged = {"value": beads * len(ms_s) / (sum(ms_s) * 1e-3), "unit": UNIT,
+                      "ms_per_step": float(sum(ms_s) / len(ms_s)), "kernels_us": k_s,
+                      "path": "tcgen05 transforms, one kernel per stage"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -251,35 +263,50 @@ def run_native(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "chains_per_gpu": C_CHAINS, "beads": M_BEADS, "dt_ps": DT_PS,
                        "dtau": dtau, "precision": "SFP_FP32" if precision == sfp.SFP_FP32 else "SFP_FP32_SIMT",
+                       "path": "fused" if (path == sfp.SFP_PATH_FUSED and precision == sfp.SFP_FP32) else "staged",
                        "l2": "flushed between timed steps (256 MB write)"},
             "sim_ns_per_s_per_chain": DT_PS * 1e-3 * args.steps / (tot_ms * 1e-3),
             "roofline": roof, "kernels_us": kern, "cpu_baseline": cpu, "e2e": e2e,
-            "plain_path": plain, "clocks": clocks, "gpu_launches": launches,
+            "plain_path": plain, "staged_path": staged, "clocks": clocks, "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def roofline(kern, pk, how, precision, sfp):
+def roofline(kern, pk, how, precision, path, sfp):
+    """Roofline of the dominant kernel from its live CUDA-event time.
+
+    Algorithmic work of the transforms: 18 M flops per bead-step (inverse
+    2 M x 3 rows, forward 2 M x 6 rows per chain); the SFP_FP32 kernels execute
+    each product as three TF32 MMAs (hi/lo split), so the tensor pipe does
+    54 M TF32 flops per bead-step, compared with the TF32 dense peak."""
     if not kern:
         return None
-    M, rows = M_BEADS, 3 * C_CHAINS
+    M, beads = M_BEADS, C_CHAINS * M_BEADS
+    tf32_peak = pk.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
+    src = f"{how} bf16 x 1.1/2.25 (nominal tf32/bf16 dense ratio)"
+    if precision == sfp.SFP_FP32 and path == sfp.SFP_PATH_FUSED:
+        us = kern.get("inverse_us")          # the fused kernel is recorded as the first stage
+        flops = 3 * 18.0 * M * beads
+        return {"bound": "tensor", "kernel": "k_fused_step<256> (whole step, tf32x3)",
+                "achieved": flops / (us * 1e-6) / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
+                "frac": flops / (us * 1e-6) / 1e12 / tf32_peak, "traffic": None, "kernel_us": us,
+                "peak_source": src}
     if precision == sfp.SFP_FP32:
         # forward transform: [DeltaH|Z] = phi^T [f|z], 2*rows x M x M, three TF32 passes
         us = kern.get("forward_us")
-        flops = 3 * 2.0 * (2 * rows) * M * M
-        peak = pk.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
-        return {"bound": "tensor", "kernel": "tcgen05 forward transform (tf32x3)",
-                "achieved": flops / (us * 1e-6) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "frac": flops / (us * 1e-6) / 1e12 / peak, "traffic": None,
-                "peak_source": f"{how} bf16 x 1.1/2.25 (nominal tf32/bf16)"}
+        flops = 3 * 2.0 * (6 * C_CHAINS) * M * M
+        return {"bound": "tensor", "kernel": "k_tc_gemm<256> forward transform (tf32x3)",
+                "achieved": flops / (us * 1e-6) / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
+                "frac": flops / (us * 1e-6) / 1e12 / tf32_peak, "traffic": None, "kernel_us": us,
+                "peak_source": src}
     us = kern.get("forward_us")
-    flops = 2.0 * (2 * rows) * M * M
+    flops = 2.0 * (6 * C_CHAINS) * M * M
     peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     return {"bound": "alu", "kernel": "FP32 CUDA-core forward transform",
             "achieved": flops / (us * 1e-6) / 1e12, "peak": peak, "unit": "TFLOP/s",
-            "frac": flops / (us * 1e-6) / 1e12 / peak, "traffic": None,
+            "frac": flops / (us * 1e-6) / 1e12 / peak, "traffic": None, "kernel_us": us,
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
 
 

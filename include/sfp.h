@@ -155,6 +155,18 @@ enum { SFP_OBS_MODES = 0, SFP_OBS_POSITIONS = 1, SFP_OBS_COM = 2, SFP_OBS_STEP =
        SFP_OBS_SHAPE = 4, SFP_OBS_ACCUM = 5, SFP_OBS_MODE_POWER = 6, SFP_OBS_COM_MSD = 7 };
 int sfp_observe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
 
+/* Kernel path of the SFP_FP32 step (other precisions ignore it).
+ *   SFP_PATH_FUSED   (default) chains of 64, 128 or 256 beads take one kernel
+ *                    per step and group: inverse transform, bond force, noise,
+ *                    forward transform and mode update in one launch with the
+ *                    intermediates kept on chip (TMEM and shared memory);
+ *                    other lengths take the staged path.
+ *   SFP_PATH_STAGED  one kernel per stage; keeps the intermediate arrays, so
+ *                    sfp_probe works after the step.
+ * Both give the same trajectory within FP32 rounding.  SFP_EINVAL otherwise. */
+enum { SFP_PATH_FUSED = 0, SFP_PATH_STAGED = 1 };
+int sfp_set_path(sfp_batch *b, int32_t path);
+
 /* Observable sampling (Sec. 5B).  every_steps > 0 clears the accumulators of
  * SFP_OBS_ACCUM, SFP_OBS_MODE_POWER and SFP_OBS_COM_MSD, takes sample 0 of the
  * current state at once, and from then on one sample after every every_steps
@@ -173,7 +185,8 @@ int sfp_set_sampling(sfp_batch *b, int32_t every_steps);
  *   SFP_PROBE_NOISE  bead normals z of that step (Eq. b5, unit variance)
  *   SFP_PROBE_DH     phi^T f = DeltaH_p (Eq. e11)
  *   SFP_PROBE_ZMODE  phi^T z = Z_p (Eq. c4)
- * SFP_EINVAL if no step has run since the batch was created or its state set. */
+ * SFP_EINVAL if no step has run since the batch was created or its state set,
+ * or if the last step ran on SFP_PATH_FUSED (set SFP_PATH_STAGED first). */
 enum { SFP_PROBE_BONDS = 0, SFP_PROBE_FORCE = 1, SFP_PROBE_NOISE = 2, SFP_PROBE_DH = 3,
        SFP_PROBE_ZMODE = 4 };
 int sfp_probe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
@@ -195,7 +208,9 @@ int sfp_info(const sfp_batch *b, int64_t out[4]);
  * noise, forward transform, mode update).  Enabling clears the totals.
  * sfp_stage_times synchronises the stream and writes the summed device time
  * in microseconds of [inverse, force+noise, forward, update, whole step]
- * over *n_group_steps recorded group-steps (one per length group per step). */
+ * over *n_group_steps recorded group-steps (one per length group per step).
+ * A fused step (SFP_PATH_FUSED) is one kernel: its whole time is counted in
+ * the first entry and in the whole-step entry. */
 int sfp_stage_timing(sfp_batch *b, int32_t enable);
 int sfp_stage_times(sfp_batch *b, double out_us[5], int64_t *n_group_steps);
 

@@ -14,7 +14,7 @@ import numpy as np
 from . import _lib
 from ._lib import (SFP_FP32, SFP_FP32_SIMT, SFP_FP64, SFP_OBS_ACCUM, SFP_OBS_COM,
                    SFP_OBS_COM_MSD, SFP_OBS_MODE_POWER, SFP_OBS_MODES, SFP_OBS_POSITIONS,
-                   SFP_OBS_SHAPE, SFP_OBS_STEP, SFP_PROBE_BONDS, SFP_PROBE_DH,
+                   SFP_OBS_SHAPE, SFP_OBS_STEP, SFP_PATH_FUSED, SFP_PATH_STAGED, SFP_PROBE_BONDS, SFP_PROBE_DH,
                    SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_ZMODE, SfpChainDesc, SfpError,
                    SfpParams)
 
@@ -132,6 +132,10 @@ class Batch:
         if np.all(self.n_beads == self.n_beads[0]):
             return flat.reshape(self.n_chains, 3, int(self.n_beads[0]))
         return [flat[self.offsets[i]:self.offsets[i + 1]].reshape(3, -1) for i in range(self.n_chains)]
+
+    def set_path(self, path: int) -> None:
+        """SFP_PATH_FUSED (one kernel per step) or SFP_PATH_STAGED (one per stage, probes kept)."""
+        _lib.check(_lib.load().sfp_set_path(self._h, int(path)))
 
     def set_sampling(self, every_steps: int) -> None:
         """Sample observables i-iii, mode power and CoM windows every ``every_steps`` steps."""

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/sfp.h"
+#include "sfp_fused.h"
 #include "sfp_simt.cuh"
 #include "sfp_tc.h"
 
@@ -173,6 +174,8 @@ struct Group {
     double* stage = nullptr;      // [C][3][M] FP64 staging
     double* stage2 = nullptr;     // [C][3][M] FP64 staging
     sfp::TcPlan* tc = nullptr;    // tensor-core transform plan (SFP_FP32)
+    sfp::FusedPlan* fused = nullptr;   // one-kernel step (SFP_FP32, M = 64, 128, 256)
+    bool last_fused = false;      // the most recent step of this group ran fused
     // observable sampling (allocated by the first sfp_set_sampling)
     double* obs_tab = nullptr;    // [3][M] rows: phi_N - phi_0, chi_m, phi_m' (p >= 1)
     double* acc_shape = nullptr;  // [C][4]
@@ -189,6 +192,7 @@ struct sfp_batch {
     size_t budget = 0, held = 0;
     int64_t launches = 0;
     bool probed = false;
+    int32_t path = SFP_PATH_FUSED;
     int C = 0;
     int64_t total_beads = 0;
     std::vector<sfp_chain_desc> desc;
@@ -200,6 +204,7 @@ struct sfp_batch {
     // stage timing
     bool timing = false;
     std::vector<cudaEvent_t> events;   // pool, 5 per recorded group-step
+    std::vector<char> ev_fused;        // per recorded group-step: events 0 and 4 only
     size_t ev_used = 0;
     double stage_us[5] = {0, 0, 0, 0, 0};
     int64_t timed_group_steps = 0;
@@ -275,9 +280,15 @@ int launch_gemm(sfp_batch* b, const T* In, const T* B, T* Out, int J, int Nc, in
 }
 
 // Record one event of the current group-step (no-op unless timing is on).
-int mark(sfp_batch* b, int k)
+// A fused step records only events 0 and 4.
+int mark(sfp_batch* b, int k, bool fused = false)
 {
     if (!b->timing) return SFP_OK;
+    if (k == 4) {
+        const size_t gs = b->ev_used / 5;
+        if (b->ev_fused.size() <= gs) b->ev_fused.resize(gs + 1);
+        b->ev_fused[gs] = fused;
+    }
     const size_t idx = b->ev_used + k;
     while (b->events.size() <= idx) {
         cudaEvent_t e;
@@ -295,23 +306,56 @@ int harvest(sfp_batch* b)
     if (b->ev_used == 0) return SFP_OK;
     CUDA_TRY(cudaStreamSynchronize(b->stream));
     for (size_t i = 0; i < b->ev_used; i += 5) {
-        for (int k = 0; k < 4; ++k) {
-            float ms = 0.f;
-            CUDA_TRY(cudaEventElapsedTime(&ms, b->events[i + k], b->events[i + k + 1]));
-            b->stage_us[k] += 1e3 * ms;
-        }
+        const bool fused = i / 5 < b->ev_fused.size() && b->ev_fused[i / 5];
         float ms = 0.f;
         CUDA_TRY(cudaEventElapsedTime(&ms, b->events[i], b->events[i + 4]));
         b->stage_us[4] += 1e3 * ms;
+        if (fused) {
+            b->stage_us[0] += 1e3 * ms;
+        } else {
+            for (int k = 0; k < 4; ++k) {
+                float mk = 0.f;
+                CUDA_TRY(cudaEventElapsedTime(&mk, b->events[i + k], b->events[i + k + 1]));
+                b->stage_us[k] += 1e3 * mk;
+            }
+        }
         b->timed_group_steps++;
     }
     b->ev_used = 0;
     return SFP_OK;
 }
 
+// One step of a group through the fused kernel (stage timing: all of it is
+// recorded as the first stage).
+int step_group_fused(sfp_batch* b, Group& g)
+{
+    int rc;
+    if ((rc = mark(b, 0))) return rc;
+    sfp::FusedArgs a;
+    a.R = (float*)g.R;
+    a.com = g.com;
+    a.step = g.step;
+    a.job = g.job;
+    a.shear = g.shear;
+    a.dm = (const float*)g.dm;
+    a.g = (const float*)g.g;
+    a.err = b->bad;
+    a.C = g.C;
+    a.c12nu = (float)(1.0 - 2.0 * b->dv.nu);
+    a.seed = b->seed;
+    a.inv_sqrtM = 1.0 / std::sqrt((double)g.M);
+    a.dtau = g.dtau;
+    if ((rc = sfp::fused_step(g.fused, a, b->stream))) return rc;
+    b->launches++;
+    g.last_fused = true;
+    return mark(b, 4, true);
+}
+
 template <typename T>
 int step_group(sfp_batch* b, Group& g)
 {
+    if (g.fused && b->path == SFP_PATH_FUSED) return step_group_fused(b, g);
+    g.last_fused = false;
     const int C = g.C, M = g.M;
     const int64_t n = (int64_t)C * 3 * M;
     T* R = (T*)g.R;
@@ -458,8 +502,10 @@ int destroy_impl(sfp_batch* b)
     if (!b) return SFP_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
     else cudaDeviceSynchronize();
-    for (auto& g : b->groups)
+    for (auto& g : b->groups) {
         if (g.tc) sfp::tc_destroy(g.tc);
+        if (g.fused) sfp::fused_destroy(g.fused);
+    }
     for (cudaEvent_t e : b->events) cudaEventDestroy(e);
     for (void* p : b->allocs) cudaFree(p);
     delete b;
@@ -703,6 +749,13 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
                                 (float*)g.r, (const float*)g.fz, (float*)g.yz, b->bad, b->stream);
             if (rc) { destroy_impl(b); return rc; }
         }
+        if (precision == SFP_FP32 && sfp::fused_supported(M)) {
+            std::vector<double> w = g.tab.w;
+            w[0] = g.tab.w0;
+            rc = sfp::fused_create(&g.fused, M, g.C, g.tab.chi.data(), g.tab.phi.data(), g.tab.h.data(), w.data(),
+                                   (float*)g.R, b->stream);
+            if (rc) { destroy_impl(b); return rc; }
+        }
     }
     *out = b;
     return SFP_OK;
@@ -918,6 +971,8 @@ int sfp_probe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
     if (!b || !host_out) return fail(SFP_EINVAL, "NULL argument");
     if (what < SFP_PROBE_BONDS || what > SFP_PROBE_ZMODE) return fail(SFP_EINVAL, "unknown probe %d", what);
     if (!b->probed) return fail(SFP_EINVAL, "no step has run since the state was set");
+    for (const auto& g : b->groups)
+        if (g.last_fused) return fail(SFP_EINVAL, "the last step ran fused; probes need SFP_PATH_STAGED");
     const size_t need = (size_t)3 * b->total_beads * 8;
     if (bytes < need) return fail(SFP_EINVAL, "buffer too small: need %zu bytes", need);
     std::vector<double> tmp;
@@ -1040,6 +1095,14 @@ int sfp_stage_times(sfp_batch* b, double out_us[5], int64_t* n_group_steps)
     if (rc) return rc;
     for (int k = 0; k < 5; ++k) out_us[k] = b->stage_us[k];
     if (n_group_steps) *n_group_steps = b->timed_group_steps;
+    return SFP_OK;
+}
+
+int sfp_set_path(sfp_batch* b, int32_t path)
+{
+    if (!b) return fail(SFP_EINVAL, "batch is NULL");
+    if (path != SFP_PATH_FUSED && path != SFP_PATH_STAGED) return fail(SFP_EINVAL, "unknown path %d", path);
+    b->path = path;
     return SFP_OK;
 }
 

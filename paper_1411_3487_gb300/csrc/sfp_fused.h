@@ -1,0 +1,41 @@
+// sfp_fused.h -- the fused mode-space step (one kernel per step and length
+// group) of the SFP_FP32 path.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sfp {
+
+struct FusedPlan;
+
+// Device pointers and scalars of one length group, read by every launch.
+struct FusedArgs {
+    float* R;               // [C][3][M] mode amplitudes, p = 0 slots held at 0
+    double* com;            // [C][3] centre of mass (scaled units)
+    int64_t* step;          // [C] Philox step counters
+    const uint32_t* job;    // [C] Philox key word 1
+    const double* shear;    // [C] shear rate in 1/tau
+    const float* dm;        // [M] 1 - e^{-zeta_p dtau}
+    const float* g;         // [M] shear weights (g_0 = dtau)
+    int* err;               // bit 0: non-finite state, bit 1: a pipeline wait timed out
+    int C;
+    float c12nu;            // 1 - 2 nu
+    uint32_t seed;
+    double inv_sqrtM;
+    double dtau;
+};
+
+// True when a group of M beads can take the fused step (M = 64, 128 or 256).
+bool fused_supported(int M);
+
+// Tables of one group: chi [n][p] (row n = 0 and column p = 0 zero), phi [n][p],
+// and the per-mode weights h_p (Eq. f2), w_p (Eq. d6; w[0] = sqrt(2 T* dtau)).
+// The forward table F = [h_p chi_{n,p} ; w_p phi_{n,p}] (2M rows p, M columns n)
+// and chi are split once into TF32 hi / lo.  R is the group's state array.
+int fused_create(FusedPlan** out, int M, int C, const double* chi, const double* phi, const double* h,
+                 const double* w, float* R, cudaStream_t stream);
+// One step of every chain of the group.
+int fused_step(FusedPlan* plan, const FusedArgs& args, cudaStream_t stream);
+void fused_destroy(FusedPlan* plan);
+
+}  // namespace sfp

@@ -23,10 +23,13 @@ pytestmark = pytest.mark.gpu
 
 TSTAR, NU = 0.034, 0.35
 TOL = {sfp.SFP_FP32_SIMT: 1e-5, sfp.SFP_FP32: 1e-5, sfp.SFP_FP64: 1e-9}
-SIMT = pytest.param(sfp.SFP_FP32_SIMT, id="simt")
-TC = pytest.param(sfp.SFP_FP32, id="tcgen05")
-F64 = pytest.param(sfp.SFP_FP64, id="fp64")
-PRECISIONS = [SIMT, TC, F64]
+# A "precision" parameter is (precision, kernel path): the SFP_FP32 path runs
+# fused (one kernel per step, M = 64/128/256) by default, or staged.
+SIMT = pytest.param((sfp.SFP_FP32_SIMT, sfp.SFP_PATH_STAGED), id="simt")
+TC = pytest.param((sfp.SFP_FP32, sfp.SFP_PATH_FUSED), id="tcgen05")
+TCS = pytest.param((sfp.SFP_FP32, sfp.SFP_PATH_STAGED), id="tcgen05_staged")
+F64 = pytest.param((sfp.SFP_FP64, sfp.SFP_PATH_STAGED), id="fp64")
+PRECISIONS = [SIMT, TC, TCS, F64]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -47,8 +50,11 @@ def starts(M, C, seed=1, dtau=1.0):
 
 
 def make_batch(M, C, dtau, precision, seed=1, shear=0.0):
-    return sfp.Batch([{"n_beads": M, "dtau": dtau, "shear_rate_per_s": shear}] * C, seed=seed,
-                     precision=precision)
+    precision, path = precision if isinstance(precision, tuple) else (precision, sfp.SFP_PATH_FUSED)
+    b = sfp.Batch([{"n_beads": M, "dtau": dtau, "shear_rate_per_s": shear}] * C, seed=seed,
+                  precision=precision)
+    b.set_path(path)
+    return b
 
 
 def test_philox_bit_exact():
@@ -59,14 +65,15 @@ def test_philox_bit_exact():
             assert np.array_equal(g[i], ref)
 
 
-@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("precision", [SIMT, TCS, F64])
 @pytest.mark.parametrize("M,C,dtau", [(256, 37, 100.0), (64, 45, 10.0), (67, 5, 10.0), (512, 3, 100.0)])
 def test_each_stage_one_step(precision, M, C, dtau):
     """a1 inverse transform, a2 force, a3 noise, a4 forward transform, a5 update."""
+    precision, _ = precision
     m = O.Model(M, dtau=dtau)
     t = m.tables()
     R0 = starts(M, C, dtau=dtau)
-    b = make_batch(M, C, dtau, precision)
+    b = make_batch(M, C, dtau, (precision, sfp.SFP_PATH_STAGED))
     b.set_modes(R0)
     b.step(1)
     fp64 = precision == sfp.SFP_FP64
@@ -97,7 +104,7 @@ def test_each_stage_one_step(precision, M, C, dtau):
     assert np.all(b.observe(sfp.SFP_OBS_STEP) == 1)
 
 
-@pytest.mark.parametrize("precision", [SIMT, TC])
+@pytest.mark.parametrize("precision", [SIMT, TC, TCS])
 def test_trajectory_256bp_fp32(precision):
     """4096 x 256-bp workload, 32-chain subset: 1000 steps at dtau = 100 (15.9 ps)."""
     M, C, dtau = 256, 32, 100.0
@@ -112,7 +119,7 @@ def test_trajectory_256bp_fp32(precision):
         done = mark
         G = b.modes()
         e = rel_err(G, R)
-        assert e.max() < TOL[precision], (mark, e.max())
+        assert e.max() < TOL[precision[0]], (mark, e.max())
         # centre of mass (FP64 accumulator, FP32 noise projection)
         dcm = np.abs(G[:, :, 0] - R[:, :, 0]).max() / math.sqrt(M)
         assert dcm < 1e-5 * math.sqrt(6 * TSTAR * dtau * mark / M) + 1e-9
@@ -132,7 +139,8 @@ def test_trajectory_64bp_fp64_full_config():
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
-@pytest.mark.parametrize("M,C", [(3, 4), (5, 1), (67, 5), (130, 45), (33, 300)])
+@pytest.mark.parametrize("M,C", [(3, 4), (5, 1), (67, 5), (130, 45), (33, 300), (64, 43), (128, 85),
+                                 (256, 84)])
 def test_ragged_and_tiny_shapes(precision, M, C):
     dtau = 5.0
     m = O.Model(M, dtau=dtau)
@@ -142,7 +150,7 @@ def test_ragged_and_tiny_shapes(precision, M, C):
     b.set_modes(R)
     b.step(50)
     Rref = m.run_modes(R, 1, np.arange(C), 0, 50)
-    assert rel_err(b.modes(), Rref).max() < TOL[precision]
+    assert rel_err(b.modes(), Rref).max() < TOL[precision[0]]
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
@@ -153,7 +161,8 @@ def test_uneven_batch_with_shear(precision):
     rates = [0.0, 1.54e8, 0.0, 1e8, 5e7, 0.0, 0.0, 1.54e8, 1e6]
     chains = [{"n_beads": M, "dtau": dt[M], "shear_rate_per_s": s, "job_id": 100 + i}
               for i, (M, s) in enumerate(zip(lengths, rates))]
-    b = sfp.Batch(chains, seed=5, precision=precision)
+    b = sfp.Batch(chains, seed=5, precision=precision[0])
+    b.set_path(precision[1])
     c_ps = sfp.derive()["c_ps"]
     starts_ = [O.Model(M, dtau=dt[M]).equilibrium_start(5, 100 + i) for i, M in enumerate(lengths)]
     b.set_modes(starts_)
@@ -162,7 +171,7 @@ def test_uneven_batch_with_shear(precision):
     for i, M in enumerate(lengths):
         m = O.Model(M, dtau=dt[M])
         ref = m.run_modes(starts_[i][None], 5, [100 + i], 0, 120, shear=rates[i] * c_ps * 1e-12)
-        assert rel_err(G[i][None], ref)[0] < TOL[precision], i
+        assert rel_err(G[i][None], ref)[0] < TOL[precision[0]], i
 
 
 @pytest.mark.parametrize("precision", [SIMT, F64])
@@ -173,7 +182,7 @@ def test_init_equilibrium_matches_oracle_sampler(precision):
         m = O.Model(M)
         ref = np.stack([m.equilibrium_start(9, j) for j in range(C)])
         G = b.modes()
-        assert rel_err(G, ref).max() < (1e-12 if precision == sfp.SFP_FP64 else 1e-6)
+        assert rel_err(G, ref).max() < (1e-12 if precision[0] == sfp.SFP_FP64 else 1e-6)
         assert np.all(G[:, :, 0] == 0)
         assert np.all(b.observe(sfp.SFP_OBS_STEP) == 0)
 
@@ -210,7 +219,7 @@ def test_positions_round_trip_and_shape_observables():
         assert shape[c, :3] == pytest.approx(ref[:3] * d["d_nm"] ** 2, rel=1e-10)
 
 
-@pytest.mark.parametrize("precision", [SIMT, TC])
+@pytest.mark.parametrize("precision", [SIMT, TC, TCS])
 def test_full_size_256bp_sampled(precision):
     """The 4096 x 256-bp workload at full size, in the benchmark's launch
     configuration; six sampled chains recomputed by the oracle."""
@@ -223,7 +232,7 @@ def test_full_size_256bp_sampled(precision):
     m = O.Model(M, dtau=dtau)
     pick = np.array([0, 1, 777, 2048, 4000, 4095])
     ref = m.run_modes(R0[pick], 1, pick, 0, n)
-    assert rel_err(G[pick], ref).max() < TOL[precision]
+    assert rel_err(G[pick], ref).max() < TOL[precision[0]]
     # a law that holds at any size: centre-of-mass diffusion D = T*/(N+1)
     dcm = (G[:, :, 0] - R0[:, :, 0]) / math.sqrt(M)
     msd = np.mean(np.sum(dcm ** 2, axis=1))
@@ -242,9 +251,10 @@ def test_budget_and_errors():
         b.step(-1)
 
 
-def test_nonfinite_state_is_reported():
+@pytest.mark.parametrize("precision", [SIMT, TC])
+def test_nonfinite_state_is_reported(precision):
     M, C = 64, 4
-    b = make_batch(M, C, 10.0, sfp.SFP_FP32_SIMT)
+    b = make_batch(M, C, 10.0, precision)
     R = starts(M, C)
     R[2, 1, 5] = np.nan
     b.set_modes(R)
@@ -252,3 +262,23 @@ def test_nonfinite_state_is_reported():
     with pytest.raises(sfp.SfpError) as e:
         b.modes()
     assert e.value.code == _lib.SFP_ENONFINITE
+
+
+def test_fused_and_staged_paths_agree():
+    """The one-kernel step and the per-stage kernels compute the same step
+    (Eq. e11 as chi^T v in the fused kernel, as phi^T f in the staged one), so
+    their trajectories agree to FP32 rounding; probes refuse a fused step."""
+    M, C, dtau = 128, 90, 50.0
+    R = starts(M, C, dtau=dtau)
+    out = []
+    for path in (sfp.SFP_PATH_FUSED, sfp.SFP_PATH_STAGED):
+        b = make_batch(M, C, dtau, (sfp.SFP_FP32, path))
+        b.set_modes(R)
+        b.step(200)
+        out.append(b.modes())
+        if path == sfp.SFP_PATH_FUSED:
+            with pytest.raises(sfp.SfpError):
+                b.probe(sfp.SFP_PROBE_DH)
+    assert rel_err(out[0], out[1]).max() < 1e-5
+    dcm = np.abs(out[0][:, :, 0] - out[1][:, :, 0]).max() / math.sqrt(M)
+    assert dcm < 1e-5 * math.sqrt(6 * TSTAR * dtau * 200 / M)
