@@ -205,6 +205,7 @@ struct sfp_batch {
     bool timing = false;
     std::vector<cudaEvent_t> events;   // pool, 5 per recorded group-step
     std::vector<char> ev_fused;        // per recorded group-step: events 0 and 4 only
+    std::vector<int64_t> ev_steps;     // per recorded group-step: steps it covered
     size_t ev_used = 0;
     double stage_us[5] = {0, 0, 0, 0, 0};
     int64_t timed_group_steps = 0;
@@ -281,13 +282,15 @@ int launch_gemm(sfp_batch* b, const T* In, const T* B, T* Out, int J, int Nc, in
 
 // Record one event of the current group-step (no-op unless timing is on).
 // A fused step records only events 0 and 4.
-int mark(sfp_batch* b, int k, bool fused = false)
+int mark(sfp_batch* b, int k, bool fused = false, int64_t steps = 1)
 {
     if (!b->timing) return SFP_OK;
     if (k == 4) {
         const size_t gs = b->ev_used / 5;
         if (b->ev_fused.size() <= gs) b->ev_fused.resize(gs + 1);
+        if (b->ev_steps.size() <= gs) b->ev_steps.resize(gs + 1);
         b->ev_fused[gs] = fused;
+        b->ev_steps[gs] = steps;
     }
     const size_t idx = b->ev_used + k;
     while (b->events.size() <= idx) {
@@ -319,15 +322,15 @@ int harvest(sfp_batch* b)
                 b->stage_us[k] += 1e3 * mk;
             }
         }
-        b->timed_group_steps++;
+        b->timed_group_steps += (i / 5 < b->ev_steps.size()) ? b->ev_steps[i / 5] : 1;
     }
     b->ev_used = 0;
     return SFP_OK;
 }
 
-// One step of a group through the fused kernel (stage timing: all of it is
-// recorded as the first stage).
-int step_group_fused(sfp_batch* b, Group& g)
+// n_steps steps of a group in one launch of the fused kernel (stage timing:
+// all of it is recorded as the first stage).
+int step_group_fused(sfp_batch* b, Group& g, int64_t n_steps)
 {
     int rc;
     if ((rc = mark(b, 0))) return rc;
@@ -345,16 +348,16 @@ int step_group_fused(sfp_batch* b, Group& g)
     a.seed = b->seed;
     a.inv_sqrtM = 1.0 / std::sqrt((double)g.M);
     a.dtau = g.dtau;
+    a.n_steps = (int)n_steps;
     if ((rc = sfp::fused_step(g.fused, a, b->stream))) return rc;
     b->launches++;
     g.last_fused = true;
-    return mark(b, 4, true);
+    return mark(b, 4, true, n_steps);
 }
 
 template <typename T>
 int step_group(sfp_batch* b, Group& g)
 {
-    if (g.fused && b->path == SFP_PATH_FUSED) return step_group_fused(b, g);
     g.last_fused = false;
     const int C = g.C, M = g.M;
     const int64_t n = (int64_t)C * 3 * M;
@@ -428,14 +431,27 @@ int sample_all(sfp_batch* b)
     return SFP_OK;
 }
 
+constexpr int64_t kMaxFusedSteps = 1024;   // steps per fused launch
+
 int step_all(sfp_batch* b, int64_t n_steps)
 {
-    for (int64_t s = 0; s < n_steps; ++s) {
+    for (int64_t s = 0; s < n_steps;) {
+        // steps up to the next observable sample: one launch per fused group,
+        // one launch per stage and step for the others
+        int64_t chunk = std::min<int64_t>(n_steps - s, kMaxFusedSteps);
+        if (b->sample_every > 0) chunk = std::min<int64_t>(chunk, b->sample_every - b->since_sample);
         for (auto& g : b->groups) {
-            const int rc = (b->precision == SFP_FP64) ? step_group<double>(b, g) : step_group<float>(b, g);
+            int rc = SFP_OK;
+            if (g.fused && b->path == SFP_PATH_FUSED) {
+                rc = step_group_fused(b, g, chunk);
+            } else {
+                for (int64_t k = 0; k < chunk && rc == SFP_OK; ++k)
+                    rc = (b->precision == SFP_FP64) ? step_group<double>(b, g) : step_group<float>(b, g);
+            }
             if (rc) return rc;
         }
-        if (b->sample_every > 0 && ++b->since_sample == b->sample_every) {
+        s += chunk;
+        if (b->sample_every > 0 && (b->since_sample += chunk) == b->sample_every) {
             const int rc = sample_all(b);
             if (rc) return rc;
         }

@@ -1,5 +1,5 @@
-// sfp_fused.cu -- one kernel per mode-space step (Sec. 4) for tiles of 42
-// chains of the SFP_FP32 path, M = 64, 128 or 256 beads.
+// sfp_fused.cu -- mode-space steps (Sec. 4) for tiles of 42 chains of the
+// SFP_FP32 path, M = 64, 128 or 256 beads, n_steps per launch.
 //
 // A tile's 126 chain-axis rows j = 3c + alpha (2 padding rows) are the 128
 // TMEM lanes; bead / mode indices are TMEM columns.  Per step and tile:
@@ -31,6 +31,9 @@
 // noise half of the forward contraction does not depend on the state, so its
 // Philox / Box-Muller work overlaps the inverse MMAs; only the force blocks
 // wait for the bond vectors.
+// Chains never interact, so a CTA runs all n_steps of its tile without any
+// grid-wide synchronisation: TMEM stays allocated, the tables stream again
+// from L2, and the state goes through global memory (L2) between steps.
 // Every mbarrier wait is bounded (1 s); after a timeout the CTA raises bit 1
 // of the error word, skips all further work but still passes every barrier,
 // frees its TMEM and returns.
@@ -110,7 +113,8 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     uint64_t* u_done = bars + 12;       // all inverse MMAs done            (commit)
     uint64_t* inc_done = bars + 13;     // all forward MMAs done            (commit)
     uint64_t* r_full = bars + 14;       // R tile reloaded for the epilogue (1 + tx)
-    uint32_t* tmem_slot = (uint32_t*)(bars + 15);
+    uint64_t* epi_done = bars + 15;     // epilogue stored R, stages free   (1)
+    uint32_t* tmem_slot = (uint32_t*)(bars + 16);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -127,6 +131,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         mbar_init(u_done, 1);
         mbar_init(inc_done, 1);
         mbar_init(r_full, 1);
+        mbar_init(epi_done, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmR)) : "memory");
@@ -161,10 +166,15 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     if (warp == 0) {
         // ---------------- TMA producer
         if (lane == 0) {
+          bool ok = true;
+          for (int sp = 0; sp < a.n_steps && ok; ++sp) {
+            // the previous step's epilogue used the stage memory and stored R
+            if (sp > 0 && !mbar_wait(epi_done, (sp - 1) & 1, a.err, abort_flag)) break;
             for (int blk = 0; blk < NBLK; ++blk) {
-                const int s = blk % ST;
-                const uint32_t ph = (blk / ST) & 1;
-                if (!mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag)) break;
+                const int gb = sp * NBLK + blk;
+                const int s = gb % ST;
+                const uint32_t ph = (gb / ST) & 1;
+                if (!mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag)) { ok = false; break; }
                 uint8_t* st = stage0 + s * S::kStage;
                 uint8_t* bh = st + 2 * S::kA;
                 uint8_t* bl = bh + S::kB;
@@ -185,19 +195,24 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             }
             // every stage is free once the forward MMAs are done: reload the R tile
             // (KB column blocks of 128 rows x 32) there for the epilogue
-            if (mbar_wait(inc_done, 0, a.err, abort_flag)) {
+            if (ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag)) {
                 mbar_expect_tx(r_full, KB * S::kA);
                 for (int k = 0; k < KB; ++k) tma_load_2d(stage0 + k * S::kA, &tmR, r_full, k * kKB, row0);
+            } else {
+                ok = false;
             }
+          }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_tf32(kRows, NB);
             bool ok = true;
+            for (int sp = 0; sp < a.n_steps; ++sp) {
             for (int blk = 0; blk < NBLK; ++blk) {
-                const int s = blk % ST;
-                const uint32_t ph = (blk / ST) & 1;
+                const int gb = sp * NBLK + blk;
+                const int s = gb % ST;
+                const uint32_t ph = (gb / ST) & 1;
                 ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
                 ok = ok && mbar_wait(&ready[s], ph, a.err, abort_flag);
                 if (ok) {
@@ -219,6 +234,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 if (blk == 2 * KB - 2) mma_commit(u_done);
             }
             mma_commit(inc_done);
+            }
         }
     } else {
         // ---------------- compute warps 2..17
@@ -232,6 +248,15 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         // every force / noise block; values are computed into registers first and
         // written once the stage is free, so the arithmetic overlaps earlier MMAs.
 
+        const int grp = cw >> 2;                      // 4 groups of 4 warps (one per lane quarter)
+        const int row = 32 * q + lane;
+        const int crow = row / 3, ax = row - 3 * (row / 3);
+        const bool live = row < 3 * Ct;
+        float* col0 = U;                              // D_inc[j][0] per row (epilogue)
+        bool finite = true;
+#pragma unroll 1
+        for (int sp = 0; sp < a.n_steps; ++sp) {
+        const int g0 = sp * NBLK;                     // global index of this step's first block
         // (1) per bead block nb: split the R tile of inverse block nb into TF32
         //     hi / lo (in place), and write noise block nb (Eq. b5)
 #pragma unroll 1
@@ -242,10 +267,10 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             for (int i = 0; i < kPer; ++i) {
                 const int c = cw + kComputeWarps * i;
                 zz[i][0] = zz[i][1] = zz[i][2] = 0.f;
-                if (c < Ct) Normals<float>::draw(a.seed, s_job[c], s_step[c], (uint32_t)n, 0u, zz[i]);
+                if (c < Ct) Normals<float>::draw(a.seed, s_job[c], s_step[c] + sp, (uint32_t)n, 0u, zz[i]);
             }
             {
-                const int blk = 2 * nb, s = blk % ST;
+                const int blk = g0 + 2 * nb, s = blk % ST;
                 const uint32_t ph = (blk / ST) & 1;
                 ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
                 if (ok) {
@@ -268,7 +293,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 mbar_arrive(&ready[s]);
             }
             {
-                const int blk = 2 * nb + 1, s = blk % ST;
+                const int blk = g0 + 2 * nb + 1, s = blk % ST;
                 const uint32_t ph = (blk / ST) & 1;
                 ok = ok && mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
                 if (ok) {
@@ -290,7 +315,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         }
 
         // (2) per bead block nb: bond vectors from D_u -> residual force v (Eq. e11)
-        ok = ok && mbar_wait(u_done, 0, a.err, abort_flag);
+        ok = ok && mbar_wait(u_done, sp & 1, a.err, abort_flag);
         fence_after();
 #pragma unroll 1
         for (int nb = 0; nb < KB; ++nb) {
@@ -326,7 +351,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             }
             named_bar(1, kCompute);   // U is free for the next bead block
             {
-                const int blk = 2 * KB + nb, s = blk % ST;
+                const int blk = g0 + 2 * KB + nb, s = blk % ST;
                 const uint32_t ph = (blk / ST) & 1;
                 ok = ok && mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
                 if (ok) {
@@ -350,15 +375,9 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         // (3) epilogue: R += -dm R + D_inc (+ shear) on the R tile that the producer
         // reloaded into the stage memory (KB blocks of [128 rows][32], swizzled),
         // in place, 16 columns at a time; then TMA-stored back (126 rows).
-        ok = ok && mbar_wait(inc_done, 0, a.err, abort_flag);
-        ok = ok && mbar_wait(r_full, 0, a.err, abort_flag);
+        ok = ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag);
+        ok = ok && mbar_wait(r_full, sp & 1, a.err, abort_flag);
         fence_after();
-        const int grp = cw >> 2;                      // 4 groups of 4 warps (one per lane quarter)
-        const int row = 32 * q + lane;
-        const int c = row / 3, ax = row - 3 * (row / 3);
-        const bool live = row < 3 * Ct;
-        float* col0 = U;                              // D_inc[j][0] per row
-        bool finite = true;
 #pragma unroll 1
         for (int k = grp; k < NB / 16; k += kComputeWarps / 4) {
             const int p0 = 16 * k;
@@ -374,7 +393,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             float ry[16];
             if (has_shear) {
                 // start-of-step R^y of this chain (row 3c+1), read before anyone writes
-                const int ry_row = min(3 * c + 1, kRows - 1);
+                const int ry_row = min(3 * crow + 1, kRows - 1);
 #pragma unroll
                 for (int k4 = 0; k4 < 4; ++k4) {
                     const float4 x = *reinterpret_cast<const float4*>(blk + swz(ry_row, kin + 4 * k4));
@@ -386,7 +405,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 #pragma unroll
             for (int i = 0; i < 16; ++i) o[i] = r[i] + fmaf(-s_dm[p0 + i], r[i], d[i]);
             if (has_shear && live && ax == 0) {
-                const float sh = (float)s_shear[c];
+                const float sh = (float)s_shear[crow];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) o[i] += sh * s_g[p0 + i] * ry[i];
             }
@@ -406,21 +425,26 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         }
         fence_proxy_async();
         named_bar(1, kCompute);   // tile and col0 complete
-        if (ct == 0 && ok) {
-            for (int k = 0; k < KB; ++k) tma_store_2d(&tmRst, stage0 + k * S::kA, k * kKB, row0);
-            tma_store_commit();
+        if (ct == 0) {
+            if (ok) {
+                for (int k = 0; k < KB; ++k) tma_store_2d(&tmRst, stage0 + k * S::kA, k * kKB, row0);
+                tma_store_commit();
+                tma_store_wait();   // R is in global memory and the stages are free again
+            }
+            mbar_arrive(epi_done);
         }
         if (ok && grp == 0 && live && ax == 0) {
-            // centre of mass in FP64 (p = 0 of Eq. d3 with zeta_0 = 0) and the step counter
-            double* cm = a.com + 3 * (size_t)(c0 + c);
+            // centre of mass in FP64 (p = 0 of Eq. d3 with zeta_0 = 0)
+            double* cm = a.com + 3 * (size_t)(c0 + crow);
             const double ycm = cm[1];
-            cm[0] += (double)col0[row] * a.inv_sqrtM + s_shear[c] * a.dtau * ycm;
+            cm[0] += (double)col0[row] * a.inv_sqrtM + s_shear[crow] * a.dtau * ycm;
             cm[1] += (double)col0[row + 1] * a.inv_sqrtM;
             cm[2] += (double)col0[row + 2] * a.inv_sqrtM;
-            a.step[c0 + c] = s_step[c] + 1;
         }
+        named_bar(1, kCompute);   // col0 read before the next step reuses U
+        }   // steps
+        if (ok && grp == 0 && live && ax == 0) a.step[c0 + crow] = s_step[crow] + a.n_steps;
         if (!finite) atomicOr(a.err, 1);
-        if (ct == 0 && ok) tma_store_wait();   // shared memory stays valid until the stores are done
     }
     fence_before();
     __syncthreads();

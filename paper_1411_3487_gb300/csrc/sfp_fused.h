@@ -23,6 +23,7 @@ struct FusedArgs {
     uint32_t seed;
     double inv_sqrtM;
     double dtau;
+    int n_steps;            // steps per launch (>= 1)
 };
 
 // True when a group of M beads can take the fused step (M = 64, 128 or 256).
@@ -34,7 +35,7 @@ bool fused_supported(int M);
 // and chi are split once into TF32 hi / lo.  R is the group's state array.
 int fused_create(FusedPlan** out, int M, int C, const double* chi, const double* phi, const double* h,
                  const double* w, float* R, cudaStream_t stream);
-// One step of every chain of the group.
+// args.n_steps steps of every chain of the group, in one launch.
 int fused_step(FusedPlan* plan, const FusedArgs& args, cudaStream_t stream);
 void fused_destroy(FusedPlan* plan);
 

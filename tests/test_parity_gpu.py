@@ -282,3 +282,25 @@ def test_fused_and_staged_paths_agree():
     assert rel_err(out[0], out[1]).max() < 1e-5
     dcm = np.abs(out[0][:, :, 0] - out[1][:, :, 0]).max() / math.sqrt(M)
     assert dcm < 1e-5 * math.sqrt(6 * TSTAR * dtau * 200 / M)
+
+
+@pytest.mark.parametrize("M,C", [(256, 50), (64, 100)])
+def test_fused_multi_step_launch_is_bit_exact(M, C):
+    """sfp_step(n) runs n steps in one fused launch; chains are independent, so
+    it must reproduce n launches of one step bit for bit (and the oracle)."""
+    dtau = 50.0
+    R = starts(M, C, dtau=dtau)
+    out = []
+    for split in (False, True):
+        b = make_batch(M, C, dtau, (sfp.SFP_FP32, sfp.SFP_PATH_FUSED))
+        b.set_modes(R)
+        if split:
+            for _ in range(37):
+                b.step(1)
+        else:
+            b.step(37)
+        out.append(b.modes())
+        assert np.all(b.observe(sfp.SFP_OBS_STEP) == 37)
+    assert np.array_equal(out[0], out[1])
+    ref = O.Model(M, dtau=dtau).run_modes(R, 1, np.arange(C), 0, 37)
+    assert rel_err(out[0], ref).max() < TOL[sfp.SFP_FP32]
