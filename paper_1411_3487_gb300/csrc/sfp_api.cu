@@ -349,6 +349,7 @@ int step_group_fused(sfp_batch* b, Group& g, int64_t n_steps)
     a.inv_sqrtM = 1.0 / std::sqrt((double)g.M);
     a.dtau = g.dtau;
     a.n_steps = (int)n_steps;
+    a.cpt = sfp::fused_tile(g.fused);
     if ((rc = sfp::fused_step(g.fused, a, b->stream))) return rc;
     b->launches++;
     g.last_fused = true;

@@ -1,8 +1,10 @@
 // sfp_fused.cu -- mode-space steps (Sec. 4) for tiles of 42 chains of the
 // SFP_FP32 path, M = 64, 128 or 256 beads, n_steps per launch.
 //
-// A tile's 126 chain-axis rows j = 3c + alpha (2 padding rows) are the 128
-// TMEM lanes; bead / mode indices are TMEM columns.  Per step and tile:
+// A tile's chain-axis rows j = 3c + alpha (up to 42 chains, 126 rows; the
+// rest padding) are the 128 TMEM lanes; bead / mode indices are TMEM
+// columns.  Fewer chains per tile give more CTAs on small batches: the MMA
+// time of a tile is fixed by its 128 rows, the noise and force work is not.  Per step and tile:
 //   inverse  (Eq. e5)   D_u[j][n]   = sum_p R[j][p] chi[n][p]            (bonds)
 //   force    (Eq. e11)  v_n = u_n (1/|u_n| - (1 - 2 nu)),  v_0 = 0
 //   noise    (Eq. b5)   z_n ~ N(0,1), Philox keyed by (seed, job, step, n)
@@ -39,6 +41,7 @@
 // frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <algorithm>
 #include <cstdint>
 #include <vector>
 
@@ -53,7 +56,7 @@ namespace {
 using namespace ptx;
 
 constexpr int kRows = 128;                   // UMMA M = TMEM lanes
-constexpr int kChains = 42;                  // chains per tile (126 rows)
+constexpr int kChains = 42;                  // most chains per tile (126 of 128 rows)
 constexpr int kKB = 32;                      // K block: 32 FP32 = one 128-byte swizzle row
 constexpr int kComputeWarps = 16;
 constexpr int kCompute = 32 * kComputeWarps;  // 512 threads
@@ -118,8 +121,8 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c0 = blockIdx.x * kChains;
-    const int Ct = min(kChains, a.C - c0);
+    const int c0 = blockIdx.x * a.cpt;
+    const int Ct = min(a.cpt, a.C - c0);
     const int row0 = 3 * c0;
 
     if (threadIdx.x == 0) {
@@ -302,12 +305,11 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 #pragma unroll
                     for (int i = 0; i < kPer; ++i) {
                         const int c = cw + kComputeWarps * i;
-                        if (c < kChains) {
+                        if (c < a.cpt) {
 #pragma unroll
                             for (int x = 0; x < 3; ++x) put_hi_lo(ah, al, 3 * c + x, lane, zz[i][x]);
                         }
                     }
-                    if (cw < kRows - 3 * kChains) put_hi_lo(ah, al, 3 * kChains + cw, lane, 0.f);
                     fence_proxy_async();
                 }
                 mbar_arrive(&ready[s]);
@@ -339,7 +341,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             for (int i = 0; i < kPer; ++i) {
                 const int c = cw + kComputeWarps * i;
                 float u[3] = {0.f, 0.f, 0.f};
-                if (c < kChains) {
+                if (c < a.cpt) {
 #pragma unroll
                     for (int x = 0; x < 3; ++x)
                         u[x] = *reinterpret_cast<const float*>((const uint8_t*)U + swz(3 * c + x, lane));
@@ -360,12 +362,11 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 #pragma unroll
                     for (int i = 0; i < kPer; ++i) {
                         const int c = cw + kComputeWarps * i;
-                        if (c < kChains) {
+                        if (c < a.cpt) {
 #pragma unroll
                             for (int x = 0; x < 3; ++x) put_hi_lo(ah, al, 3 * c + x, lane, vv[i][x]);
                         }
                     }
-                    if (cw < kRows - 3 * kChains) put_hi_lo(ah, al, 3 * kChains + cw, lane, 0.f);
                     fence_proxy_async();
                 }
                 mbar_arrive(&ready[s]);
@@ -457,8 +458,9 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 }  // namespace
 
 struct FusedPlan {
-    int M = 0, C = 0;
+    int M = 0, C = 0, cpt = kChains;
     float* tab[4] = {nullptr, nullptr, nullptr, nullptr};   // chi_hi, chi_lo, F_hi, F_lo
+    float* R = nullptr;
     CUtensorMap tmR, tmRst, tmChiH, tmChiL, tmFH, tmFL;
 };
 
@@ -478,6 +480,12 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
     FusedPlan* p = new FusedPlan();
     p->M = M;
     p->C = C;
+    p->R = R;
+    // one wave: chains per tile = ceil(C / SMs), at most 42 (fused_set_tile changes it)
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 148;
+    p->cpt = std::max(1, std::min(kChains, (C + sms - 1) / sms));
     const size_t mm = (size_t)M * M;
     // chi [n][p] (row n = 0 and column p = 0 are zero) and F [2M][M]:
     // F[p][n] = h_p chi[n][p] (Eq. f2 weight on DeltaH = chi^T v, Eq. e11),
@@ -511,8 +519,8 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
         }
     }
     int rc;
-    // the store box is 126 rows: a tile must not write the next tile's first chain
-    if ((rc = make_map_2d(&p->tmR, R, 3 * C, M, kRows)) || (rc = make_map_2d(&p->tmRst, R, 3 * C, M, 3 * kChains)) ||
+    // the store box is the tile's 3 cpt rows: a tile must not write the next tile's chains
+    if ((rc = make_map_2d(&p->tmR, R, 3 * C, M, kRows)) || (rc = make_map_2d(&p->tmRst, R, 3 * C, M, 3 * p->cpt)) ||
         (rc = make_map_2d(&p->tmChiH, p->tab[0], M, M, M)) ||
         (rc = make_map_2d(&p->tmChiL, p->tab[1], M, M, M)) || (rc = make_map_2d(&p->tmFH, p->tab[2], 2 * M, M, M)) ||
         (rc = make_map_2d(&p->tmFL, p->tab[3], 2 * M, M, M))) {
@@ -530,7 +538,8 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
 
 int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
 {
-    const dim3 grid((unsigned)((p->C + kChains - 1) / kChains));
+    if (args.cpt != p->cpt) return report(SFP_EINVAL, "fused step: chains per tile differ from the plan's");
+    const dim3 grid((unsigned)((p->C + p->cpt - 1) / p->cpt));
     switch (p->M) {
         case 256:
             k_fused_step<256><<<grid, kThreads, FSmem<256>::kBytes, stream>>>(p->tmR, p->tmRst, p->tmChiH, p->tmChiL, p->tmFH, p->tmFL, args);
@@ -546,6 +555,19 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return report(SFP_ECUDA, cudaGetErrorString(e));
+    return SFP_OK;
+}
+
+int fused_tile(const FusedPlan* p) { return p->cpt; }
+
+int fused_set_tile(FusedPlan* p, int cpt)
+{
+    if (cpt < 1 || cpt > kChains) return report(SFP_EINVAL, "chains per tile must be 1..42");
+    CUtensorMap m;
+    const int rc = make_map_2d(&m, p->R, 3 * p->C, p->M, 3 * cpt);
+    if (rc) return rc;
+    p->tmRst = m;
+    p->cpt = cpt;
     return SFP_OK;
 }
 

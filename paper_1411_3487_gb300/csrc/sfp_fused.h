@@ -24,6 +24,7 @@ struct FusedArgs {
     double inv_sqrtM;
     double dtau;
     int n_steps;            // steps per launch (>= 1)
+    int cpt;                // chains per tile (1..42), as in the plan (fused_tile)
 };
 
 // True when a group of M beads can take the fused step (M = 64, 128 or 256).
@@ -37,6 +38,9 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
                  const double* w, float* R, cudaStream_t stream);
 // args.n_steps steps of every chain of the group, in one launch.
 int fused_step(FusedPlan* plan, const FusedArgs& args, cudaStream_t stream);
+// Chains per tile of the plan, and a new value (1..42; rebuilds the store map).
+int fused_tile(const FusedPlan* plan);
+int fused_set_tile(FusedPlan* plan, int cpt);
 void fused_destroy(FusedPlan* plan);
 
 }  // namespace sfp
