@@ -226,6 +226,75 @@ const char *sfp_last_error(void);
 int sfp_philox_words(uint32_t seed, uint32_t job, int64_t step, uint32_t tag,
                      int32_t count, uint32_t *host_out);
 
+/* ---- serving: continuous batching of simulation jobs -----------------------
+ * A server accepts jobs at any time (from any thread), keeps every running
+ * chain's mode state on the GPU, and advances all running jobs together:
+ * jobs of one (length, step size) share a pool of slots that one sfp_step call
+ * per quantum advances, so a job that arrives while others run joins their
+ * next launch.  Pools are created as jobs need them while the HBM budget
+ * allows, and idle pools of other shapes are released to make room; a job
+ * that does not fit waits.  Each job starts from the equilibrium sampler of
+ * sfp_init_equilibrium keyed by (seed, job_id), with its own step counter
+ * from 0, so its result does not depend on the slot it ran in or on the other
+ * jobs (noise keyed by (seed, job_id, step, bead)).  A job stops exactly
+ * after its n_steps steps even inside a quantum.  One worker thread per
+ * server issues all GPU work on the server's own stream. */
+typedef struct sfp_server sfp_server;   /* opaque */
+
+typedef struct sfp_server_config {
+    uint64_t seed;               /* Philox key word 0 (< 2^32) */
+    int32_t  precision;          /* SFP_FP32, SFP_FP32_SIMT or SFP_FP64 */
+    int32_t  slots_per_pool;     /* chains per pool (one pool per allocation) */
+    int32_t  quantum_steps;      /* steps per round of the request loop */
+    int32_t  keep_results;       /* 1: keep each job's final modes for sfp_server_result_modes */
+    size_t   hbm_budget_bytes;   /* device memory all pools together may hold (0 = no bound) */
+} sfp_server_config;
+
+typedef struct sfp_job {
+    int32_t  n_beads;            /* N+1 beads (Sec. 2A); 3..4096 */
+    int32_t  reserved;           /* must be 0 */
+    double   dt_ps;              /* step in ps; used when dtau <= 0 */
+    double   dtau;               /* step in scaled time; > 0 takes precedence */
+    double   shear_rate_per_s;   /* gamma-dot of Eq. btum; 0 = none */
+    int64_t  n_steps;            /* steps to run (>= 0) */
+    uint64_t job_id;             /* Philox key word 1 of this job; < 2^32 */
+} sfp_job;
+
+typedef struct sfp_job_result {
+    uint64_t ticket;             /* as returned by sfp_server_submit */
+    uint64_t job_id;
+    int32_t  n_beads;
+    int32_t  status;             /* SFP_OK or a negative SFP_E* code */
+    int64_t  n_steps;
+    double   submit_s, admit_s, finish_s;   /* server clock (s since sfp_server_create) */
+    double   com_nm[3];          /* final centre of mass (nm) */
+} sfp_job_result;
+
+/* Defaults: seed 1, SFP_FP32, 512 slots per pool, quantum 64 steps, results
+ * kept, no budget bound.  Host only. */
+int sfp_server_config_default(sfp_server_config *cfg);
+/* Start a server (and its worker thread) on the current CUDA device. */
+int sfp_server_create(const sfp_params *params, const sfp_server_config *cfg, sfp_server **out);
+/* Queue a job; thread-safe; never blocks on the GPU.  *ticket numbers jobs
+ * from 0 in submission order.  SFP_EINVAL for a malformed job. */
+int sfp_server_submit(sfp_server *s, const sfp_job *job, uint64_t *ticket);
+/* Move up to max_results finished jobs into out (oldest first); *n_out gets
+ * the count.  Non-blocking.  Returns the worker's error code if it stopped. */
+int sfp_server_poll(sfp_server *s, sfp_job_result *out, int32_t max_results, int32_t *n_out);
+/* Final mode amplitudes of a finished job, FP64 [3][n_beads] in scaled units
+ * (R_0 = sqrt(n_beads) r_cm), when keep_results = 1. */
+int sfp_server_result_modes(sfp_server *s, uint64_t ticket, double *host_modes, size_t n_doubles);
+/* Block until no job is waiting or running, or timeout_s passes (SFP_ETIMEDOUT). */
+int sfp_server_wait_idle(sfp_server *s, double timeout_s);
+/* out[0..9]: jobs submitted, finished, waiting, running; device bytes held;
+ * p50, p99 and max latency (finish - submit, s); server clock (s); bead-steps
+ * of the finished jobs. */
+int sfp_server_stats(sfp_server *s, double out[10]);
+/* Stop the worker (running jobs are abandoned), free every pool. NULL is a no-op. */
+int sfp_server_destroy(sfp_server *s);
+/* Last error message of the calling thread for sfp_server_* calls. */
+const char *sfp_server_last_error(void);
+
 /* ---- allocation-free step -------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that
  * must not allocate device memory: code running inside a host framework that

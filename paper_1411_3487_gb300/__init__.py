@@ -18,7 +18,7 @@ from ._lib import (SFP_FP32, SFP_FP32_SIMT, SFP_FP64, SFP_OBS_ACCUM, SFP_OBS_COM
                    SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_ZMODE, SfpChainDesc, SfpError,
                    SfpParams)
 
-__all__ = ["Batch", "params_dsdna", "derive", "philox_words", "SfpError", "SFP_FP32",
+__all__ = ["Batch", "Server", "params_dsdna", "derive", "philox_words", "SfpError", "SFP_FP32",
            "SFP_FP64", "SFP_FP32_SIMT"]
 
 
@@ -200,3 +200,81 @@ class Batch:
         out = (ct.c_int64 * 4)()
         _lib.check(_lib.load().sfp_info(self._h, out))
         return {"chains": out[0], "beads": out[1], "device_bytes": out[2], "launches": out[3]}
+
+
+class Server:
+    """Continuous-batching request loop (``sfp_server_*``): submit jobs at any
+    time, poll finished ones.  A job is a dict with ``n_beads``, ``n_steps``,
+    one of ``dt_ps`` / ``dtau``, optional ``shear_rate_per_s`` and ``job_id``."""
+
+    def __init__(self, params: SfpParams | None = None, seed: int = 1, precision: int = SFP_FP32,
+                 slots_per_pool: int = 512, quantum_steps: int = 64, keep_results: bool = True,
+                 hbm_budget_bytes: int = 0):
+        L = _lib.load()
+        cfg = _lib.SfpServerConfig()
+        _lib.check_server(L.sfp_server_config_default(ct.byref(cfg)))
+        cfg.seed, cfg.precision, cfg.slots_per_pool = seed, precision, slots_per_pool
+        cfg.quantum_steps, cfg.keep_results, cfg.hbm_budget_bytes = quantum_steps, int(keep_results), hbm_budget_bytes
+        self.params = params or params_dsdna()
+        h = ct.c_void_p()
+        _lib.check_server(L.sfp_server_create(ct.byref(self.params), ct.byref(cfg), ct.byref(h)))
+        self._h = h
+        self._beads = {}
+
+    def submit(self, job: dict) -> int:
+        j = _lib.SfpJob()
+        j.n_beads = int(job["n_beads"])
+        j.dt_ps = float(job.get("dt_ps", 0.0))
+        j.dtau = float(job.get("dtau", 0.0))
+        j.shear_rate_per_s = float(job.get("shear_rate_per_s", 0.0))
+        j.n_steps = int(job["n_steps"])
+        j.job_id = int(job.get("job_id", 0))
+        t = ct.c_uint64()
+        _lib.check_server(_lib.load().sfp_server_submit(self._h, ct.byref(j), ct.byref(t)))
+        self._beads[t.value] = j.n_beads
+        return t.value
+
+    def poll(self, max_results: int = 1024) -> list:
+        arr = (_lib.SfpJobResult * max_results)()
+        n = ct.c_int32()
+        _lib.check_server(_lib.load().sfp_server_poll(self._h, arr, max_results, ct.byref(n)))
+        out = []
+        for r in arr[:n.value]:
+            out.append({"ticket": r.ticket, "job_id": r.job_id, "n_beads": r.n_beads, "status": r.status,
+                        "n_steps": r.n_steps, "submit_s": r.submit_s, "admit_s": r.admit_s,
+                        "finish_s": r.finish_s, "latency_s": r.finish_s - r.submit_s,
+                        "com_nm": list(r.com_nm)})
+        return out
+
+    def modes(self, ticket: int) -> np.ndarray:
+        M = self._beads[ticket]
+        out = np.zeros((3, M))
+        _lib.check_server(_lib.load().sfp_server_result_modes(self._h, ticket, out.ctypes.data, out.size))
+        return out
+
+    def wait_idle(self, timeout_s: float = 600.0) -> None:
+        _lib.check_server(_lib.load().sfp_server_wait_idle(self._h, float(timeout_s)))
+
+    def stats(self) -> dict:
+        out = (ct.c_double * 10)()
+        _lib.check_server(_lib.load().sfp_server_stats(self._h, out))
+        keys = ("submitted", "finished", "waiting", "running", "device_bytes", "p50_s", "p99_s", "max_s",
+                "clock_s", "bead_steps")
+        return dict(zip(keys, list(out)))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.load().sfp_server_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -26,7 +26,9 @@ EXPORTS = (
     "sfp_set_positions", "sfp_set_step", "sfp_step", "sfp_observe", "sfp_probe", "sfp_save",
     "sfp_load", "sfp_info", "sfp_destroy", "sfp_last_error", "sfp_philox_words",
     "sfp_stage_timing", "sfp_stage_times", "sfp_step_noalloc", "sfp_set_sampling",
-    "sfp_set_path",
+    "sfp_set_path", "sfp_server_config_default", "sfp_server_create", "sfp_server_submit",
+    "sfp_server_poll", "sfp_server_result_modes", "sfp_server_wait_idle", "sfp_server_stats",
+    "sfp_server_destroy", "sfp_server_last_error",
 )
 
 
@@ -39,6 +41,23 @@ class SfpParams(ct.Structure):
 class SfpChainDesc(ct.Structure):
     _fields_ = [("n_beads", ct.c_int32), ("reserved", ct.c_int32), ("dt_ps", ct.c_double),
                 ("dtau", ct.c_double), ("shear_rate_per_s", ct.c_double), ("job_id", ct.c_uint64)]
+
+
+class SfpServerConfig(ct.Structure):
+    _fields_ = [("seed", ct.c_uint64), ("precision", ct.c_int32), ("slots_per_pool", ct.c_int32),
+                ("quantum_steps", ct.c_int32), ("keep_results", ct.c_int32), ("hbm_budget_bytes", ct.c_size_t)]
+
+
+class SfpJob(ct.Structure):
+    _fields_ = [("n_beads", ct.c_int32), ("reserved", ct.c_int32), ("dt_ps", ct.c_double),
+                ("dtau", ct.c_double), ("shear_rate_per_s", ct.c_double), ("n_steps", ct.c_int64),
+                ("job_id", ct.c_uint64)]
+
+
+class SfpJobResult(ct.Structure):
+    _fields_ = [("ticket", ct.c_uint64), ("job_id", ct.c_uint64), ("n_beads", ct.c_int32),
+                ("status", ct.c_int32), ("n_steps", ct.c_int64), ("submit_s", ct.c_double),
+                ("admit_s", ct.c_double), ("finish_s", ct.c_double), ("com_nm", ct.c_double * 3)]
 
 
 class SfpError(RuntimeError):
@@ -83,10 +102,19 @@ def load(path: str | None = None):
         L.sfp_stage_times.argtypes = [vp, ct.POINTER(ct.c_double), ct.POINTER(i64)]
         L.sfp_set_sampling.argtypes = [vp, i32]
         L.sfp_set_path.argtypes = [vp, i32]
+        L.sfp_server_config_default.argtypes = [ct.POINTER(SfpServerConfig)]
+        L.sfp_server_create.argtypes = [ct.POINTER(SfpParams), ct.POINTER(SfpServerConfig), ct.POINTER(vp)]
+        L.sfp_server_submit.argtypes = [vp, ct.POINTER(SfpJob), ct.POINTER(u64)]
+        L.sfp_server_poll.argtypes = [vp, ct.POINTER(SfpJobResult), i32, ct.POINTER(i32)]
+        L.sfp_server_result_modes.argtypes = [vp, u64, vp, sz]
+        L.sfp_server_wait_idle.argtypes = [vp, ct.c_double]
+        L.sfp_server_stats.argtypes = [vp, ct.POINTER(ct.c_double)]
+        L.sfp_server_destroy.argtypes = [vp]
+        L.sfp_server_last_error.restype = ct.c_char_p
         L.sfp_step_noalloc.argtypes = [ct.POINTER(SfpParams), ct.POINTER(SfpChainDesc), i32, u64, i64, vp, vp,
                                        i64, vp]
         for name in EXPORTS:
-            if name != "sfp_last_error":
+            if name not in ("sfp_last_error", "sfp_server_last_error"):
                 getattr(L, name).restype = ct.c_int
         _lib = L
         return _lib
@@ -95,3 +123,8 @@ def load(path: str | None = None):
 def check(rc: int) -> None:
     if rc != SFP_OK:
         raise SfpError(rc, load().sfp_last_error().decode())
+
+
+def check_server(rc: int) -> None:
+    if rc != SFP_OK:
+        raise SfpError(rc, load().sfp_server_last_error().decode())

@@ -17,6 +17,7 @@
 
 #include "../../include/sfp.h"
 #include "sfp_fused.h"
+#include "sfp_internal.h"
 #include "sfp_simt.cuh"
 #include "sfp_tc.h"
 
@@ -166,6 +167,14 @@ struct Group {
     uint32_t* job = nullptr;      // [C]
     double* shear = nullptr;      // [C] shear rate in 1/tau
     int64_t* step = nullptr;      // [C]
+    int64_t* stop = nullptr;      // [C] a chain advances only while step < stop
+    bool limited = false;         // some stop < INT64_MAX (serving pools)
+    double* rod = nullptr;        // [3N] ground-state bonds and Cholesky factor (slot starts)
+    int32_t* slot_idx = nullptr;  // [C] staging for slot starts / reads
+    uint32_t* slot_job = nullptr;
+    int64_t* slot_stop = nullptr;
+    double* slot_shear = nullptr;
+    double* gather = nullptr;     // [kGather][3][M] + [kGather][3] + [kGather] FP64 / i64
     void *chi = nullptr, *phiT = nullptr, *dm = nullptr, *h = nullptr, *w = nullptr, *g = nullptr;
     double *phi_d = nullptr, *phiT_d = nullptr;   // FP64 copies for conversions
     void* r = nullptr;            // [C][3][M] bond vectors u (slot n = 0 unused)
@@ -338,6 +347,7 @@ int step_group_fused(sfp_batch* b, Group& g, int64_t n_steps)
     a.R = (float*)g.R;
     a.com = g.com;
     a.step = g.step;
+    a.stop = g.limited ? g.stop : nullptr;
     a.job = g.job;
     a.shear = g.shear;
     a.dm = (const float*)g.dm;
@@ -403,9 +413,14 @@ int step_group(sfp_batch* b, Group& g)
     // a5: mode update (Eqs. d3, d6, f2, btum)
     sfp::k_mode_update<T><<<nblk((int64_t)C * M, 256), 256, 0, b->stream>>>(
         R, yz, yz + n, g.com, g.step, (const T*)g.dm, (const T*)g.h, (const T*)g.w, (const T*)g.g,
-        g.shear, C, M, g.tab.w0, g.dtau, b->bad);
+        g.shear, C, M, g.tab.w0, g.dtau, b->bad, g.limited ? g.stop : nullptr);
     b->launches++;
     CUDA_TRY(cudaGetLastError());
+    if (g.limited) {
+        sfp::k_advance_steps<<<nblk(C, 256), 256, 0, b->stream>>>(g.step, g.stop, C);
+        b->launches++;
+        CUDA_TRY(cudaGetLastError());
+    }
     return mark(b, 4);
 }
 
@@ -709,7 +724,8 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
         make_tables(M, dv.Tstar, dv.nu, g.dtau, &g.tab);
         if ((rc = dalloc(b, &g.R, n * es)) || (rc = dalloc_t(b, &g.com, (size_t)g.C * 3 * 8)) ||
             (rc = dalloc_t(b, &g.job, (size_t)g.C * 4)) || (rc = dalloc_t(b, &g.shear, (size_t)g.C * 8)) ||
-            (rc = dalloc_t(b, &g.step, (size_t)g.C * 8)) || (rc = dalloc(b, &g.chi, (size_t)M * M * es)) ||
+            (rc = dalloc_t(b, &g.step, (size_t)g.C * 8)) || (rc = dalloc_t(b, &g.stop, (size_t)g.C * 8)) ||
+            (rc = dalloc(b, &g.chi, (size_t)M * M * es)) ||
             (rc = dalloc(b, &g.phiT, (size_t)M * M * es)) || (rc = dalloc(b, &g.dm, M * es)) ||
             (rc = dalloc(b, &g.h, M * es)) || (rc = dalloc(b, &g.w, M * es)) || (rc = dalloc(b, &g.g, M * es)) ||
             (rc = dalloc_t(b, &g.phi_d, (size_t)M * M * 8)) || (rc = dalloc_t(b, &g.phiT_d, (size_t)M * M * 8)) ||
@@ -727,7 +743,7 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
         }
         std::vector<uint32_t> jobs(g.C);
         std::vector<double> sh(g.C);
-        std::vector<int64_t> st(g.C, 0);
+        std::vector<int64_t> st(g.C, 0), nostop(g.C, INT64_MAX);
         for (int i = 0; i < g.C; ++i) {
             const sfp_chain_desc& d = chains[g.chains[i]];
             jobs[i] = (uint32_t)d.job_id;
@@ -753,6 +769,7 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
         if (e == cudaSuccess) e = cudaMemcpyAsync(g.job, jobs.data(), g.C * 4, cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(g.shear, sh.data(), g.C * 8, cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(g.step, st.data(), g.C * 8, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g.stop, nostop.data(), g.C * 8, cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(g.phi_d, g.tab.phi.data(), (size_t)M * M * 8, cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(g.phiT_d, g.tab.phiT.data(), (size_t)M * M * 8, cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(g.stage, init.data(), n * 8, cudaMemcpyHostToDevice, b->stream);
@@ -772,6 +789,12 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
             rc = sfp::fused_create(&g.fused, M, g.C, g.tab.chi.data(), g.tab.phi.data(), g.tab.h.data(), w.data(),
                                    (float*)g.R, b->stream);
             if (rc) { destroy_impl(b); return rc; }
+        }
+        b->held += sfp::tc_bytes(g.tc) + sfp::fused_bytes(g.fused);
+        if (b->budget && b->held > b->budget) {
+            const size_t held = b->held;
+            destroy_impl(b);
+            return fail(SFP_ENOMEM, "HBM budget of %zu bytes exceeded (%zu needed)", hbm_budget_bytes, held);
         }
     }
     *out = b;
@@ -1241,3 +1264,127 @@ int sfp_step_noalloc(const sfp_params* params, const sfp_chain_desc* chain, int3
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Slot access for the serving loop (sfp_server.cu); single-group batches.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kGather = 256;   // slots read back per launch
+
+int slot_buffers(sfp_batch* b, Group& g)
+{
+    if (g.slot_idx) return SFP_OK;
+    int rc;
+    const int N = g.M - 1;
+    if ((rc = dalloc_t(b, &g.rod, (size_t)3 * N * 8)) || (rc = dalloc_t(b, &g.slot_idx, (size_t)g.C * 4)) ||
+        (rc = dalloc_t(b, &g.slot_job, (size_t)g.C * 4)) || (rc = dalloc_t(b, &g.slot_stop, (size_t)g.C * 8)) ||
+        (rc = dalloc_t(b, &g.slot_shear, (size_t)g.C * 8)) ||
+        (rc = dalloc_t(b, &g.gather, (size_t)kGather * (3 * g.M + 4) * 8)))
+        return rc;
+    std::vector<double> l0, Ld, Lo;
+    rod_tables(g.M, b->dv.nu, &l0, &Ld, &Lo);
+    std::vector<double> all;
+    all.insert(all.end(), l0.begin(), l0.end());
+    all.insert(all.end(), Ld.begin(), Ld.end());
+    all.insert(all.end(), Lo.begin(), Lo.end());
+    CUDA_TRY(cudaMemcpyAsync(g.rod, all.data(), all.size() * 8, cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    return SFP_OK;
+}
+}  // namespace
+
+int sfp::internal_idle_all(sfp_batch* b)
+{
+    if (!b || b->groups.size() != 1) return fail(SFP_EINVAL, "serving pools hold one length group");
+    Group& g = b->groups[0];
+    const int rc = slot_buffers(b, g);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemsetAsync(g.stop, 0, (size_t)g.C * 8, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    g.limited = true;
+    return SFP_OK;
+}
+
+int sfp::internal_slots_start(sfp_batch* b, const int32_t* slots, const uint32_t* jobs, const int64_t* stops,
+                              const double* shear_per_s, int32_t n)
+{
+    if (!b || b->groups.size() != 1) return fail(SFP_EINVAL, "serving pools hold one length group");
+    if (n <= 0) return SFP_OK;
+    Group& g = b->groups[0];
+    if (n > g.C) return fail(SFP_EINVAL, "more slots than the pool holds");
+    for (int i = 0; i < n; ++i)
+        if (slots[i] < 0 || slots[i] >= g.C) return fail(SFP_EINVAL, "slot %d out of range", slots[i]);
+    int rc = slot_buffers(b, g);
+    if (rc) return rc;
+    std::vector<double> sh(n);
+    for (int i = 0; i < n; ++i) sh[i] = shear_per_s[i] * b->dv.c_ps * 1e-12;   // 1/s -> 1/tau
+    CUDA_TRY(cudaMemcpyAsync(g.slot_idx, slots, (size_t)n * 4, cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(cudaMemcpyAsync(g.slot_job, jobs, (size_t)n * 4, cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(cudaMemcpyAsync(g.slot_stop, stops, (size_t)n * 8, cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(cudaMemcpyAsync(g.slot_shear, sh.data(), (size_t)n * 8, cudaMemcpyHostToDevice, b->stream));
+    const int N = g.M - 1;
+    const size_t smem = (size_t)4 * g.M * 8;
+    if (b->precision == SFP_FP64) {
+        if (smem > 48 * 1024)
+            CUDA_TRY(cudaFuncSetAttribute(sfp::k_init_slots<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        sfp::k_init_slots<double><<<n, 128, smem, b->stream>>>((double*)g.R, g.com, g.step, g.stop, g.job, g.shear,
+            g.slot_idx, g.slot_job, g.slot_stop, g.slot_shear, g.phi_d, g.rod, g.rod + N, g.rod + 2 * N,
+            g.M, b->dv.Tstar, b->dv.nu, b->seed);
+    } else {
+        if (smem > 48 * 1024)
+            CUDA_TRY(cudaFuncSetAttribute(sfp::k_init_slots<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        sfp::k_init_slots<float><<<n, 128, smem, b->stream>>>((float*)g.R, g.com, g.step, g.stop, g.job, g.shear,
+            g.slot_idx, g.slot_job, g.slot_stop, g.slot_shear, g.phi_d, g.rod, g.rod + N, g.rod + 2 * N,
+            g.M, b->dv.Tstar, b->dv.nu, b->seed);
+    }
+    CUDA_TRY(cudaGetLastError());
+    g.limited = true;
+    b->probed = false;
+    return SFP_OK;
+}
+
+int sfp::internal_slots_read(sfp_batch* b, const int32_t* slots, int32_t n, double* modes, double* com_nm,
+                             int64_t* steps)
+{
+    if (!b || b->groups.size() != 1) return fail(SFP_EINVAL, "serving pools hold one length group");
+    Group& g = b->groups[0];
+    int rc = slot_buffers(b, g);
+    if (rc) return rc;
+    const int M = g.M;
+    for (int i0 = 0; i0 < n; i0 += kGather) {
+        const int k = std::min(kGather, n - i0);
+        for (int i = 0; i < k; ++i)
+            if (slots[i0 + i] < 0 || slots[i0 + i] >= g.C) return fail(SFP_EINVAL, "slot out of range");
+        double* out = g.gather;
+        double* cm = out + (size_t)kGather * 3 * M;
+        int64_t* st = (int64_t*)(cm + (size_t)kGather * 3);
+        CUDA_TRY(cudaMemcpyAsync(g.slot_idx, slots + i0, (size_t)k * 4, cudaMemcpyHostToDevice, b->stream));
+        if (b->precision == SFP_FP64)
+            sfp::k_gather_slots<double><<<k, 128, 0, b->stream>>>((const double*)g.R, g.com, g.step, g.slot_idx, k, M, out, cm, st);
+        else
+            sfp::k_gather_slots<float><<<k, 128, 0, b->stream>>>((const float*)g.R, g.com, g.step, g.slot_idx, k, M, out, cm, st);
+        CUDA_TRY(cudaGetLastError());
+        if (modes) CUDA_TRY(cudaMemcpyAsync(modes + (size_t)i0 * 3 * M, out, (size_t)k * 3 * M * 8, cudaMemcpyDeviceToHost, b->stream));
+        std::vector<double> c3((size_t)k * 3);
+        CUDA_TRY(cudaMemcpyAsync(c3.data(), cm, c3.size() * 8, cudaMemcpyDeviceToHost, b->stream));
+        if (steps) CUDA_TRY(cudaMemcpyAsync(steps + i0, st, (size_t)k * 8, cudaMemcpyDeviceToHost, b->stream));
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+        if (com_nm)
+            for (size_t i = 0; i < c3.size(); ++i) com_nm[(size_t)i0 * 3 + i] = c3[i] * b->dv.d_nm;
+    }
+    int bad = 0;
+    CUDA_TRY(cudaMemcpy(&bad, b->bad, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bad & 2) return fail(SFP_ETIMEDOUT, "a tensor-core pipeline wait timed out");
+    if (bad & 1) return fail(SFP_ENONFINITE, "a chain's state became non-finite");
+    return SFP_OK;
+}
+
+int sfp::internal_shape(const sfp_batch* b, int32_t* M, double* dtau, int32_t* C, size_t* bytes)
+{
+    if (!b || b->groups.empty()) return fail(SFP_EINVAL, "empty batch");
+    if (M) *M = b->groups[0].M;
+    if (dtau) *dtau = b->groups[0].dtau;
+    if (C) *C = b->groups[0].C;
+    if (bytes) *bytes = b->held;
+    return SFP_OK;
+}

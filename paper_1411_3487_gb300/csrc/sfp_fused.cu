@@ -110,6 +110,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     float* s_dm = (float*)(misc + 1024);
     float* s_g = (float*)(misc + 2048);
     uint64_t* bars = (uint64_t*)(misc + 3072);
+    int64_t* s_stop = (int64_t*)(misc + 3328);
     uint64_t* full = bars;              // TMA bytes landed                 (1 + tx)
     uint64_t* ready = bars + 4;         // A operand prepared by threads    (256)
     uint64_t* empty = bars + 8;         // MMAs done with the stage         (commit)
@@ -148,6 +149,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         const bool live = i < Ct;
         s_job[i] = live ? a.job[c0 + i] : 0u;
         s_step[i] = live ? a.step[c0 + i] : 0;
+        s_stop[i] = (live && a.stop) ? a.stop[c0 + i] : INT64_MAX;
         s_shear[i] = live ? a.shear[c0 + i] : 0.0;
     }
     for (int p = threadIdx.x; p < NB; p += kThreads) {
@@ -402,10 +404,12 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 }
                 named_bar(2 + grp, 128);
             }
+            // a chain whose step counter has reached its stop step stays as it is
+            const bool adv = live && s_step[crow] + sp < s_stop[crow];
             float o[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) o[i] = r[i] + fmaf(-s_dm[p0 + i], r[i], d[i]);
-            if (has_shear && live && ax == 0) {
+            for (int i = 0; i < 16; ++i) o[i] = adv ? r[i] + fmaf(-s_dm[p0 + i], r[i], d[i]) : r[i];
+            if (has_shear && adv && ax == 0) {
                 const float sh = (float)s_shear[crow];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) o[i] += sh * s_g[p0 + i] * ry[i];
@@ -434,7 +438,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             }
             mbar_arrive(epi_done);
         }
-        if (ok && grp == 0 && live && ax == 0) {
+        if (ok && grp == 0 && live && ax == 0 && s_step[crow] + sp < s_stop[crow]) {
             // centre of mass in FP64 (p = 0 of Eq. d3 with zeta_0 = 0)
             double* cm = a.com + 3 * (size_t)(c0 + crow);
             const double ycm = cm[1];
@@ -444,7 +448,8 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         }
         named_bar(1, kCompute);   // col0 read before the next step reuses U
         }   // steps
-        if (ok && grp == 0 && live && ax == 0) a.step[c0 + crow] = s_step[crow] + a.n_steps;
+        if (ok && grp == 0 && live && ax == 0)
+            a.step[c0 + crow] = max(s_step[crow], min(s_step[crow] + (int64_t)a.n_steps, s_stop[crow]));
         if (!finite) atomicOr(a.err, 1);
     }
     fence_before();
@@ -559,6 +564,8 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
 }
 
 int fused_tile(const FusedPlan* p) { return p->cpt; }
+
+size_t fused_bytes(const FusedPlan* p) { return p ? (size_t)6 * p->M * p->M * sizeof(float) : 0; }
 
 int fused_set_tile(FusedPlan* p, int cpt)
 {

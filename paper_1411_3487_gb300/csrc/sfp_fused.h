@@ -13,6 +13,7 @@ struct FusedArgs {
     float* R;               // [C][3][M] mode amplitudes, p = 0 slots held at 0
     double* com;            // [C][3] centre of mass (scaled units)
     int64_t* step;          // [C] Philox step counters
+    const int64_t* stop;    // [C] a chain advances only while step < stop (NULL: no limit)
     const uint32_t* job;    // [C] Philox key word 1
     const double* shear;    // [C] shear rate in 1/tau
     const float* dm;        // [M] 1 - e^{-zeta_p dtau}
@@ -40,6 +41,8 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
 int fused_step(FusedPlan* plan, const FusedArgs& args, cudaStream_t stream);
 // Chains per tile of the plan, and a new value (1..42; rebuilds the store map).
 int fused_tile(const FusedPlan* plan);
+// Device bytes the plan's tables hold.
+size_t fused_bytes(const FusedPlan* plan);
 int fused_set_tile(FusedPlan* plan, int cpt);
 void fused_destroy(FusedPlan* plan);
 

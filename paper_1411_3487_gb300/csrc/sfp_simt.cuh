@@ -178,17 +178,22 @@ k_force_noise(const T* __restrict__ ub, T* __restrict__ f, T* __restrict__ z,
 // dm_p = 1 - e^{-zeta_p dtau}; written as an increment so FP32 keeps the
 // slow modes whose decay factor rounds to 1.
 // ---------------------------------------------------------------------------
+// With stop != NULL a chain advances only while step < stop, and the step
+// counters are advanced afterwards by k_advance_steps (so that no thread of
+// this kernel reads a counter that another one changes).
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_mode_update(T* __restrict__ R, const T* __restrict__ DH, const T* __restrict__ ZM,
               double* __restrict__ com, int64_t* __restrict__ step,
               const T* __restrict__ dm, const T* __restrict__ h, const T* __restrict__ w,
               const T* __restrict__ g, const double* __restrict__ shear,
-              int C, int M, double w0, double dtau, int* __restrict__ bad)
+              int C, int M, double w0, double dtau, int* __restrict__ bad,
+              const int64_t* __restrict__ stop = nullptr)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)C * M) return;
     const int c = (int)(t / M), p = (int)(t % M);
+    if (stop && step[c] >= stop[c]) return;
     const size_t b = (size_t)c * 3 * M + p;
     const double sh = shear[c];
     if (p == 0) {
@@ -197,7 +202,7 @@ k_mode_update(T* __restrict__ R, const T* __restrict__ DH, const T* __restrict__
 #pragma unroll
         for (int a = 0; a < 3; ++a) com[3 * c + a] += w0 * (double)ZM[b + (size_t)a * M] * inv;
         com[3 * c] += sh * dtau * ycm;
-        step[c] += 1;
+        if (!stop) step[c] += 1;
         return;
     }
     const T Rx = R[b], Ry = R[b + M], Rz = R[b + 2 * M];
@@ -210,23 +215,28 @@ k_mode_update(T* __restrict__ R, const T* __restrict__ DH, const T* __restrict__
     R[b] = nx; R[b + M] = ny; R[b + 2 * M] = nz;
 }
 
+// step[c] += 1 for chains still below their stop step (after k_mode_update).
+__global__ void k_advance_steps(int64_t* __restrict__ step, const int64_t* __restrict__ stop, int C)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < C && step[c] < stop[c]) step[c] += 1;
+}
+
 // ---------------------------------------------------------------------------
 // Equilibrium start, one thread per chain, FP64 (Philox counter (0,0,k,1)):
 //   l = l0 + sqrt(T*) L^-T eps   with (I - nu A) = L L^T  (Ld diag, Lo sub-diag)
 //   t_1 uniform on the sphere, t_n ~ von Mises-Fisher(t_{n-1}, nu l_{n-1} l_n / T*)
 //   r_n = sum_{k<=n} l_k t_k, centroid removed.   out: pos[c][3][M], scratch x[c][M]
 // ---------------------------------------------------------------------------
-__global__ void k_equilibrium(double* __restrict__ pos, double* __restrict__ xs,
-                              const double* __restrict__ l0, const double* __restrict__ Ld,
-                              const double* __restrict__ Lo, int C, int M, double Tstar,
-                              double nu, uint32_t seed, const uint32_t* __restrict__ job)
+// One chain's equilibrium start (positions p[3][M], scratch x[M]); p and x may
+// be global or shared memory.
+__device__ void sample_start(double* __restrict__ p, double* __restrict__ x,
+                             const double* __restrict__ l0, const double* __restrict__ Ld,
+                             const double* __restrict__ Lo, int M, double Tstar, double nu,
+                             uint32_t seed, uint32_t job)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
     const int N = M - 1;
-    const uint2 key = make_uint2(seed, job[c]);
-    double* x = xs + (size_t)c * M;
-    double* p = pos + (size_t)c * 3 * M;
+    const uint2 key = make_uint2(seed, job);
     // back substitution L^T x = eps, eps_i is the normal of bond i+1
     for (int i = N - 1; i >= 0; --i) {
         const uint4 wd = philox4x32_10(make_uint4(0u, 0u, (uint32_t)(i + 1), 1u), key);
@@ -285,6 +295,76 @@ __global__ void k_equilibrium(double* __restrict__ pos, double* __restrict__ xs,
         const double m = sum[k] / M;
         for (int n = 0; n < M; ++n) p[k * M + n] -= m;
     }
+}
+
+__global__ void k_equilibrium(double* __restrict__ pos, double* __restrict__ xs,
+                              const double* __restrict__ l0, const double* __restrict__ Ld,
+                              const double* __restrict__ Lo, int C, int M, double Tstar,
+                              double nu, uint32_t seed, const uint32_t* __restrict__ job)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    sample_start(pos + (size_t)c * 3 * M, xs + (size_t)c * M, l0, Ld, Lo, M, Tstar, nu, seed, job[c]);
+}
+
+// Serving: start n chains in the slots slot[i] with job key jobv[i], stop step
+// stopv[i] and shear rate shv[i] (1/tau).  One block per slot: thread 0 draws the
+// equilibrium start into shared memory (3M + M doubles), then the block projects it
+// onto the modes R_p = sum_n phi_{n,p} r_n (Eq. c1, p >= 1; phi FP64 [n][p]); the
+// centre of mass is at the origin and the step counter 0.
+template <typename T>
+__global__ void k_init_slots(T* __restrict__ R, double* __restrict__ com, int64_t* __restrict__ step,
+                             int64_t* __restrict__ stop, uint32_t* __restrict__ job, double* __restrict__ shear,
+                             const int32_t* __restrict__ slot, const uint32_t* __restrict__ jobv,
+                             const int64_t* __restrict__ stopv, const double* __restrict__ shv,
+                             const double* __restrict__ phi, const double* __restrict__ l0,
+                             const double* __restrict__ Ld, const double* __restrict__ Lo,
+                             int M, double Tstar, double nu, uint32_t seed)
+{
+    extern __shared__ double sh_pos[];
+    double* xs = sh_pos + 3 * M;
+    const int i = blockIdx.x;
+    const int c = slot[i];
+    if (threadIdx.x == 0) sample_start(sh_pos, xs, l0, Ld, Lo, M, Tstar, nu, seed, jobv[i]);
+    __syncthreads();
+    T* Rc = R + (size_t)c * 3 * M;
+    for (int p = threadIdx.x; p < M; p += blockDim.x) {
+        double s[3] = {0.0, 0.0, 0.0};
+        if (p > 0)
+            for (int n = 0; n < M; ++n) {
+                const double f = phi[(size_t)n * M + p];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) s[a] += f * sh_pos[a * M + n];
+            }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Rc[(size_t)a * M + p] = (T)s[a];
+    }
+    if (threadIdx.x == 0) {
+        com[3 * c] = com[3 * c + 1] = com[3 * c + 2] = 0.0;
+        step[c] = 0;
+        stop[c] = stopv[i];
+        job[c] = jobv[i];
+        shear[c] = shv[i];
+    }
+}
+
+// Serving: copy the state of slots slot[i] to out[i][3][M] (FP64, R_0 = sqrt(M) r_cm),
+// their centres of mass to cm[i][3] and step counters to st[i].
+template <typename T>
+__global__ void k_gather_slots(const T* __restrict__ R, const double* __restrict__ com,
+                               const int64_t* __restrict__ step, const int32_t* __restrict__ slot, int n, int M,
+                               double* __restrict__ out, double* __restrict__ cm, int64_t* __restrict__ st)
+{
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    const int c = slot[i];
+    const double sq = sqrt((double)M);
+    for (int e = threadIdx.x; e < 3 * M; e += blockDim.x) {
+        const int a = e / M, p = e % M;
+        out[(size_t)i * 3 * M + e] = (p == 0) ? com[3 * c + a] * sq : (double)R[(size_t)c * 3 * M + e];
+    }
+    if (threadIdx.x < 3) cm[3 * i + threadIdx.x] = com[3 * c + threadIdx.x];
+    if (threadIdx.x == 0) st[i] = step[c];
 }
 
 // ---------------------------------------------------------------------------

@@ -275,6 +275,8 @@ int tc_transform(TcPlan* p, int which, cudaStream_t stream)
     return SFP_OK;
 }
 
+size_t tc_bytes(const TcPlan* p) { return p ? (size_t)4 * p->M * p->M * sizeof(float) : 0; }
+
 void tc_destroy(TcPlan* p)
 {
     if (!p) return;

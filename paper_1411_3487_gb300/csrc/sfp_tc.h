@@ -1,5 +1,6 @@
 // sfp_tc.h -- tensor-core (tcgen05) mode transforms used by the SFP_FP32 path.
 #pragma once
+#include <cstddef>
 #include <cuda_runtime.h>
 
 namespace sfp {
@@ -23,6 +24,8 @@ int tc_create(TcPlan** out, int M, int rows, const double* phi, const double* ph
               float* r_out, const float* fz, float* yz_out, int* err, cudaStream_t stream);
 // which = 0: inverse, 1: forward.
 int tc_transform(TcPlan* plan, int which, cudaStream_t stream);
+// Device bytes the plan's tables hold.
+size_t tc_bytes(const TcPlan* plan);
 void tc_destroy(TcPlan* plan);
 
 }  // namespace sfp
