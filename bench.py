@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="tc", choices=["tc", "simt"])
     ap.add_argument("--path", default="fused", choices=["fused", "staged"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "serving"])
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-budget-mb", type=float, default=40e3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     return ap.parse_args()
@@ -377,11 +381,70 @@ def end_to_end(sfp, b, torch, steps):
             "d2h_bytes_per_step": n * 8, "steps": steps, "api": "sfp_set_modes + sfp_step + sfp_observe"}
 
 
+def run_serving(args, rank):
+    """Continuous-batching serving: Poisson arrivals of jobs with lengths
+    uniform over 64/128/256/512 bp at their Table 2 steps, 10^U(3,5) steps,
+    shear 0 with probability 1/2 else U[1e6, 1e8] 1/s; p50/p99 latency from
+    submission to the result being on the host."""
+    if rank != 0:
+        return
+    import torch
+    sys.path.insert(0, ROOT)
+    import paper_1411_3487_gb300 as sfp
+    from paper_1411_3487_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    dt_ps = {64: 1.59, 128: 7.96, 256: 15.9, 512: 15.9}
+    rng = np.random.default_rng(1)
+    budget = int(args.serve_budget_mb * (1 << 20))
+    srv = sfp.Server(slots_per_pool=1024, quantum_steps=64, keep_results=False, hbm_budget_bytes=budget)
+    clk = ClockSampler(0)
+    t0 = time.perf_counter()
+    t_next, k, offered = 0.0, 0, 0.0
+    while t_next < args.serve_seconds:
+        wait = t0 + t_next - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        M = int(rng.choice([64, 128, 256, 512]))
+        n = int(round(10 ** rng.uniform(3, 5)))
+        shear = 0.0 if rng.random() < 0.5 else float(rng.uniform(1e6, 1e8))
+        srv.submit({"n_beads": M, "dt_ps": dt_ps[M], "n_steps": n, "shear_rate_per_s": shear, "job_id": k})
+        offered += M * n
+        k += 1
+        t_next += rng.exponential(1.0 / args.serve_rate)
+    arrivals_s = time.perf_counter() - t0
+    srv.wait_idle(3600)
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    res = srv.poll(k + 16)
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r["latency_s"] for r in res])
+    bad = sum(1 for r in res if r["status"] != 0)
+    line = {
+        "metric": "p50/p99 request latency", "unit": "s", "higher_is_better": False,
+        "value": float(np.percentile(lat, 50)), "p50_s": float(np.percentile(lat, 50)),
+        "p99_s": float(np.percentile(lat, 99)), "max_s": float(lat.max()), "jobs": k, "failed": bad,
+        "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": "serving: Poisson arrivals, 64/128/256/512 bp at Table 2 steps, "
+                               "10^U(3,5) steps, half sheared U[1e6,1e8]/s",
+                   "rate_jobs_per_s": args.serve_rate, "arrival_window_s": args.serve_seconds,
+                   "hbm_budget_bytes": budget, "slots_per_pool": 1024, "quantum_steps": 64,
+                   "precision": "SFP_FP32"},
+        "served_bead_steps_per_s": st["bead_steps"] / wall, "offered_bead_steps_per_s": offered / arrivals_s,
+        "wall_s": wall, "peak_device_bytes_at_end": st["device_bytes"], "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "serving":
+        run_serving(args, rank)
         return
     run_native(args, rank, world, local)
 

@@ -232,8 +232,10 @@ int sfp_philox_words(uint32_t seed, uint32_t job, int64_t step, uint32_t tag,
  * jobs of one (length, step size) share a pool of slots that one sfp_step call
  * per quantum advances, so a job that arrives while others run joins their
  * next launch.  Pools are created as jobs need them while the HBM budget
- * allows, and idle pools of other shapes are released to make room; a job
- * that does not fit waits.  Each job starts from the equilibrium sampler of
+ * allows (a pool that does not fit is retried with half as many slots), and
+ * idle pools of other shapes are released to make room; a job that does not
+ * fit waits for running jobs to finish, and finishes with status SFP_ENOMEM
+ * if even a one-slot pool cannot fit while nothing runs.  Each job starts from the equilibrium sampler of
  * sfp_init_equilibrium keyed by (seed, job_id), with its own step counter
  * from 0, so its result does not depend on the slot it ran in or on the other
  * jobs (noise keyed by (seed, job_id, step, bead)).  A job stops exactly

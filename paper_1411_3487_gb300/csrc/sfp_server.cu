@@ -112,11 +112,10 @@ int srv_fail(int code, const std::string& msg)
     return code;
 }
 
-// Create a pool of cfg.slots_per_pool slots for (M, dtau) within the remaining
-// budget; SFP_ENOMEM when it does not fit.
-int make_pool(sfp_server* s, int M, double dtau, std::unique_ptr<Pool>* out)
+// Create a pool of cap slots for (M, dtau) within the remaining budget;
+// SFP_ENOMEM when it does not fit.
+int make_pool(sfp_server* s, int M, double dtau, int cap, std::unique_ptr<Pool>* out)
 {
-    const int cap = s->cfg.slots_per_pool;
     std::vector<sfp_chain_desc> d(cap);
     for (int i = 0; i < cap; ++i) {
         d[i] = sfp_chain_desc{};
@@ -187,24 +186,45 @@ int admit(sfp_server* s)
             }
         if (!pool && !budget_full) {
             std::unique_ptr<Pool> np;
-            int rc = make_pool(s, j->desc.n_beads, j->dtau, &np);
+            int cap = s->cfg.slots_per_pool;
+            int rc = make_pool(s, j->desc.n_beads, j->dtau, cap, &np);
             while (rc == SFP_ENOMEM) {
-                // evict an idle pool (no running and no just-admitted slots) and retry
+                // evict an idle pool (no running and no just-admitted slots) and retry;
+                // with none left, try a pool of half as many slots
                 size_t victim = s->pools.size();
                 for (size_t k = 0; k < s->pools.size(); ++k)
                     if (s->pools[k]->active == 0) {
                         victim = k;
                         break;
                     }
-                if (victim == s->pools.size()) break;
-                drop_pool(s, victim);
-                rc = make_pool(s, j->desc.n_beads, j->dtau, &np);
+                if (victim < s->pools.size()) {
+                    drop_pool(s, victim);
+                } else if (cap > 1) {
+                    cap = std::max(1, cap / 2);
+                } else {
+                    break;
+                }
+                rc = make_pool(s, j->desc.n_beads, j->dtau, cap, &np);
             }
             if (rc == SFP_OK) {
                 s->pools.push_back(std::move(np));
                 pool = s->pools.back().get();
                 slot = 0;
             } else if (rc == SFP_ENOMEM) {
+                bool running = false;
+                for (auto& p : s->pools) running = running || p->active > 0;
+                if (!running) {
+                    // nothing will free memory: this job can never fit the budget
+                    std::lock_guard<std::mutex> lk(s->mu);
+                    j->status = SFP_ENOMEM;
+                    j->t_admit = j->t_finish = s->now();
+                    s->done.push_back(j);
+                    s->latencies.push_back(j->t_finish - j->t_submit);
+                    s->n_pending--;
+                    s->n_finished++;
+                    s->cv_done.notify_all();
+                    continue;
+                }
                 budget_full = true;
             } else {
                 return srv_fail(rc, std::string("pool creation failed: ") + sfp_last_error());

@@ -125,3 +125,18 @@ def test_malformed_jobs_are_refused():
         for bad in (job(2, 10, 1), job(64, -1, 1), job(64, 10, 1 << 32)):
             with pytest.raises(sfp.SfpError):
                 s.submit(bad)
+
+
+def test_pools_shrink_to_fit_and_impossible_jobs_fail():
+    """Pools that do not fit the budget are retried smaller; a job that cannot
+    fit even a one-slot pool while nothing runs fails with SFP_ENOMEM."""
+    with sfp.Server(slots_per_pool=4096, quantum_steps=32, hbm_budget_bytes=24 << 20) as s:
+        t = s.submit(job(512, 40, 9))
+        s.wait_idle(60)
+        r = s.poll()
+        assert r[0]["status"] == 0 and s.stats()["device_bytes"] <= 24 << 20
+        assert rel(s.modes(t), oracle_run(512, 9, 40, 0.0)) < 1e-5
+    with sfp.Server(hbm_budget_bytes=64 << 10) as s:
+        s.submit(job(512, 10, 1))
+        s.wait_idle(60)
+        assert s.poll()[0]["status"] == sfp._lib.SFP_ENOMEM
