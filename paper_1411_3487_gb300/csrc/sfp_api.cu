@@ -289,6 +289,34 @@ int launch_gemm(sfp_batch* b, const T* In, const T* B, T* Out, int J, int Nc, in
     return SFP_OK;
 }
 
+// Launch the staged force + noise kernel (one thread per bead, chains on
+// grid y) and the mode update (4 modes per thread when M % 4 == 0).
+unsigned chains_y(int C) { return (unsigned)std::min(C, 65535); }
+
+template <typename T>
+cudaError_t launch_force_noise(cudaStream_t st, const T* u, T* f, T* z, int C, int M, T c12nu, uint32_t seed,
+                               const uint32_t* job, const int64_t* step)
+{
+    const dim3 grid(nblk(M, 128), chains_y(C));
+    sfp::k_force_noise<T><<<grid, 128, 0, st>>>(u, f, z, C, M, c12nu, seed, job, step);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mode_update(cudaStream_t st, T* R, const T* DH, const T* ZM, double* com, int64_t* step,
+                               const T* dm, const T* h, const T* w, const T* g, const double* shear, int C, int M,
+                               double w0, double dtau, int* bad, const int64_t* stop)
+{
+    if (sizeof(T) == 4 && M % 4 == 0) {
+        const dim3 grid(nblk(M / 4, 128), chains_y(C));
+        sfp::k_mode_update<T, 4><<<grid, 128, 0, st>>>(R, DH, ZM, com, step, dm, h, w, g, shear, C, M, w0, dtau, bad, stop);
+    } else {
+        const dim3 grid(nblk(M, 128), chains_y(C));
+        sfp::k_mode_update<T, 1><<<grid, 128, 0, st>>>(R, DH, ZM, com, step, dm, h, w, g, shear, C, M, w0, dtau, bad, stop);
+    }
+    return cudaGetLastError();
+}
+
 // Record one event of the current group-step (no-op unless timing is on).
 // A fused step records only events 0 and 4.
 int mark(sfp_batch* b, int k, bool fused = false, int64_t steps = 1)
@@ -387,21 +415,8 @@ int step_group(sfp_batch* b, Group& g)
     // a2 + a3: residual bond force and bead noise
     {
         const T c12 = (T)(1.0 - 2.0 * b->dv.nu);
-        const int warps = 4;
-        dim3 grid(nblk(C, warps));
-        if constexpr (sizeof(T) == 4) {
-            if (M % 4 == 0)
-                sfp::k_force_noise<float, true><<<grid, 32 * warps, 0, b->stream>>>(
-                    r, fz, fz + n, C, M, c12, b->seed, g.job, g.step);
-            else
-                sfp::k_force_noise<float, false><<<grid, 32 * warps, 0, b->stream>>>(
-                    r, fz, fz + n, C, M, c12, b->seed, g.job, g.step);
-        } else {
-            sfp::k_force_noise<double, false><<<grid, 32 * warps, 0, b->stream>>>(
-                r, fz, fz + n, C, M, c12, b->seed, g.job, g.step);
-        }
+        CUDA_TRY(launch_force_noise<T>(b->stream, r, fz, fz + n, C, M, c12, b->seed, g.job, g.step));
         b->launches++;
-        CUDA_TRY(cudaGetLastError());
     }
     if ((rc = mark(b, 2))) return rc;
     // a4: [DeltaH | Z] = phi^T [f | z]  (forward transform, Eqs. c4, e11)
@@ -411,11 +426,10 @@ int step_group(sfp_batch* b, Group& g)
     if (g.tc) b->launches++;
     if ((rc = mark(b, 3))) return rc;
     // a5: mode update (Eqs. d3, d6, f2, btum)
-    sfp::k_mode_update<T><<<nblk((int64_t)C * M, 256), 256, 0, b->stream>>>(
-        R, yz, yz + n, g.com, g.step, (const T*)g.dm, (const T*)g.h, (const T*)g.w, (const T*)g.g,
-        g.shear, C, M, g.tab.w0, g.dtau, b->bad, g.limited ? g.stop : nullptr);
+    CUDA_TRY(launch_mode_update<T>(b->stream, R, yz, yz + n, g.com, g.step, (const T*)g.dm, (const T*)g.h,
+                                   (const T*)g.w, (const T*)g.g, g.shear, C, M, g.tab.w0, g.dtau, b->bad,
+                                   g.limited ? g.stop : nullptr));
     b->launches++;
-    CUDA_TRY(cudaGetLastError());
     if (g.limited) {
         sfp::k_advance_steps<<<nblk(C, 256), 256, 0, b->stream>>>(g.step, g.stop, C);
         b->launches++;
@@ -1250,15 +1264,10 @@ int sfp_step_noalloc(const sfp_params* params, const sfp_chain_desc* chain, int3
     int* bad = (int*)(base + o_bad);   // written by the update kernel, not reported here
     for (int64_t s = 0; s < n_steps; ++s) {
         CUDA_TRY(gemm_on<float>(st, modes_dev, chi, r, 3 * C, M, M));
-        if (M % 4 == 0)
-            sfp::k_force_noise<float, true><<<nblk(C, 4), 128, 0, st>>>(r, fz, fz + n, C, M, c12, (uint32_t)seed, job, step);
-        else
-            sfp::k_force_noise<float, false><<<nblk(C, 4), 128, 0, st>>>(r, fz, fz + n, C, M, c12, (uint32_t)seed, job, step);
-        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(launch_force_noise<float>(st, r, fz, fz + n, C, M, c12, (uint32_t)seed, job, step));
         CUDA_TRY(gemm_on<float>(st, fz, phiT, yz, 6 * C, M, M));
-        sfp::k_mode_update<float><<<nblk((int64_t)C * M, 256), 256, 0, st>>>(
-            modes_dev, yz, yz + n, com_dev, step, dm, h, w, g, shear, C, M, w0, dtau, bad);
-        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(launch_mode_update<float>(st, modes_dev, yz, yz + n, com_dev, step, dm, h, w, g, shear, C, M, w0,
+                                           dtau, bad, nullptr));
     }
     return SFP_OK;
 }

@@ -87,85 +87,37 @@ __device__ __forceinline__ void residual_v(const T u[3], bool ok, T c12nu, T v[3
     for (int a = 0; a < 3; ++a) v[a] = u[a] * s;
 }
 
-template <typename T, bool VEC4>
+// One thread per bead n of chain blockIdx.y (grid-stride over chains): the
+// thread evaluates v_n and v_{n+1} from its own two bond loads (the second is
+// the neighbour's, served by L1), so there is no halo exchange; then draws its
+// bead's three normals.  Threads of a warp touch consecutive beads, so every
+// load and store is coalesced; many warps per chain keep enough Philox chains
+// in flight to hide their latency.
+template <typename T>
 __global__ void __launch_bounds__(128)
 k_force_noise(const T* __restrict__ ub, T* __restrict__ f, T* __restrict__ z,
               int C, int M, T c12nu, uint32_t seed, const uint32_t* __restrict__ job,
               const int64_t* __restrict__ step)
 {
-    const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (c >= C) return;
-    const size_t base = (size_t)c * 3 * M;
-    const uint32_t jb = job[c];
-    const int64_t st = step[c];
-
-    for (int b0 = 0; b0 < M; b0 += 128) {
-        const int n0 = b0 + 4 * lane;
-        T x[3][4];
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= M) return;
+    for (int c = blockIdx.y; c < C; c += gridDim.y) {
+        const size_t base = (size_t)c * 3 * M;
+        T u[3], w[3], v0[3], v1[3];
+        const bool has1 = n + 1 < M;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const T* ua = ub + base + (size_t)a * M;
-            if constexpr (VEC4) {
-                if (n0 + 3 < M) {
-                    const float4 q = *reinterpret_cast<const float4*>(ua + n0);
-                    x[a][0] = q.x; x[a][1] = q.y; x[a][2] = q.z; x[a][3] = q.w;
-                    continue;
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) x[a][i] = (n0 + i < M) ? ua[n0 + i] : T(0);
+            u[a] = n >= 1 ? ub[base + (size_t)a * M + n] : T(0);
+            w[a] = has1 ? ub[base + (size_t)a * M + n + 1] : T(0);
         }
-        T v[3][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int n = n0 + i;
-            T u[3] = {x[0][i], x[1][i], x[2][i]}, vv[3];
-            residual_v<T>(u, n >= 1 && n < M, c12nu, vv);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) v[a][i] = vv[a];
-        }
-        // v_{n0+4}: next lane's first v; lane 31 recomputes it from one halo bond
-        T vnext[3];
-        {
-            const int nh = b0 + 128;
-            T uh[3] = {T(0), T(0), T(0)}, vh[3];
-            const bool has = (lane == 31) && (nh < M);
-            if (has) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) uh[a] = ub[base + (size_t)a * M + nh];
-            }
-            residual_v<T>(uh, has, c12nu, vh);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const T dn = __shfl_down_sync(0xffffffffu, v[a][0], 1);
-                vnext[a] = (lane == 31) ? vh[a] : dn;
-            }
-        }
-        T fo[3][4], zo[3][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) fo[a][i] = v[a][i] - (i < 3 ? v[a][i + 1] : vnext[a]);
-            T g[3] = {T(0), T(0), T(0)};
-            if (n0 + i < M) Normals<T>::draw(seed, jb, st, (uint32_t)(n0 + i), 0u, g);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) zo[a][i] = g[a];
-        }
+        residual_v<T>(u, n >= 1, c12nu, v0);
+        residual_v<T>(w, has1, c12nu, v1);
+        T g[3];
+        Normals<T>::draw(seed, job[c], step[c], (uint32_t)n, 0u, g);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            T* fa = f + base + (size_t)a * M;
-            T* za = z + base + (size_t)a * M;
-            if constexpr (VEC4) {
-                if (n0 + 3 < M) {
-                    *reinterpret_cast<float4*>(fa + n0) = make_float4(fo[a][0], fo[a][1], fo[a][2], fo[a][3]);
-                    *reinterpret_cast<float4*>(za + n0) = make_float4(zo[a][0], zo[a][1], zo[a][2], zo[a][3]);
-                    continue;
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (n0 + i < M) { fa[n0 + i] = fo[a][i]; za[n0 + i] = zo[a][i]; }
+            f[base + (size_t)a * M + n] = v0[a] - v1[a];
+            z[base + (size_t)a * M + n] = g[a];
         }
     }
 }
@@ -178,41 +130,86 @@ k_force_noise(const T* __restrict__ ub, T* __restrict__ f, T* __restrict__ z,
 // dm_p = 1 - e^{-zeta_p dtau}; written as an increment so FP32 keeps the
 // slow modes whose decay factor rounds to 1.
 // ---------------------------------------------------------------------------
-// With stop != NULL a chain advances only while step < stop, and the step
-// counters are advanced afterwards by k_advance_steps (so that no thread of
-// this kernel reads a counter that another one changes).
-template <typename T>
-__global__ void __launch_bounds__(256)
+// V consecutive modes per thread (V = 4: float4 loads and stores, needs
+// M % 4 == 0), chains along grid y (grid-stride).  With stop != NULL a chain
+// advances only while step < stop, and the step counters are advanced
+// afterwards by k_advance_steps (so that no thread of this kernel reads a
+// counter that another one changes).
+template <typename T, int V>
+__device__ __forceinline__ void load_v(const T* p, T (&x)[V])
+{
+    if constexpr (V == 4 && sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) x[i] = p[i];
+    }
+}
+template <typename T, int V>
+__device__ __forceinline__ void store_v(T* p, const T (&x)[V])
+{
+    if constexpr (V == 4 && sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < V; ++i) p[i] = x[i];
+    }
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(128)
 k_mode_update(T* __restrict__ R, const T* __restrict__ DH, const T* __restrict__ ZM,
               double* __restrict__ com, int64_t* __restrict__ step,
               const T* __restrict__ dm, const T* __restrict__ h, const T* __restrict__ w,
               const T* __restrict__ g, const double* __restrict__ shear,
               int C, int M, double w0, double dtau, int* __restrict__ bad,
-              const int64_t* __restrict__ stop = nullptr)
+              const int64_t* __restrict__ stop)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)C * M) return;
-    const int c = (int)(t / M), p = (int)(t % M);
-    if (stop && step[c] >= stop[c]) return;
-    const size_t b = (size_t)c * 3 * M + p;
-    const double sh = shear[c];
-    if (p == 0) {
-        const double inv = rsqrt((double)M);
-        const double ycm = com[3 * c + 1];
+    const int p0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (p0 >= M) return;
+    T d[V], hh[V], ww[V], gg[V];
+    load_v<T, V>(dm + p0, d);
+    load_v<T, V>(h + p0, hh);
+    load_v<T, V>(w + p0, ww);
+    load_v<T, V>(g + p0, gg);
+    for (int c = blockIdx.y; c < C; c += gridDim.y) {
+        if (stop && step[c] >= stop[c]) continue;
+        const size_t b = (size_t)c * 3 * M + p0;
+        const double sh = shear[c];
+        T r[3][V], y[3][V], zz[3][V];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) com[3 * c + a] += w0 * (double)ZM[b + (size_t)a * M] * inv;
-        com[3 * c] += sh * dtau * ycm;
-        if (!stop) step[c] += 1;
-        return;
+        for (int a = 0; a < 3; ++a) {
+            load_v<T, V>(R + b + (size_t)a * M, r[a]);
+            load_v<T, V>(DH + b + (size_t)a * M, y[a]);
+            load_v<T, V>(ZM + b + (size_t)a * M, zz[a]);
+        }
+        T o[3][V];
+        bool fin = true;
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) o[a][i] = r[a][i] + fma(-d[i], r[a][i], fma(hh[i], y[a][i], ww[i] * zz[a][i]));
+            o[0][i] += (T)sh * gg[i] * r[1][i];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) fin = fin && isfinite(o[a][i]);
+        }
+        if (p0 == 0) {
+            // p = 0: the centre of mass in FP64 (zeta_0 = 0, Eq. d6 limit w_0)
+            const double inv = rsqrt((double)M);
+            const double ycm = com[3 * c + 1];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                com[3 * c + a] += w0 * (double)zz[a][0] * inv;
+                o[a][0] = r[a][0];
+            }
+            com[3 * c] += sh * dtau * ycm;
+            if (!stop) step[c] += 1;
+        }
+        if (!fin) atomicOr(bad, 1);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) store_v<T, V>(R + b + (size_t)a * M, o[a]);
     }
-    const T Rx = R[b], Ry = R[b + M], Rz = R[b + 2 * M];
-    const T d = dm[p], hh = h[p], ww = w[p];
-    T nx = Rx + fma(-d, Rx, fma(hh, DH[b], ww * ZM[b]));
-    const T ny = Ry + fma(-d, Ry, fma(hh, DH[b + M], ww * ZM[b + M]));
-    const T nz = Rz + fma(-d, Rz, fma(hh, DH[b + 2 * M], ww * ZM[b + 2 * M]));
-    nx += (T)sh * g[p] * Ry;
-    if (!(isfinite(nx) && isfinite(ny) && isfinite(nz))) atomicOr(bad, 1);
-    R[b] = nx; R[b + M] = ny; R[b + 2 * M] = nz;
 }
 
 // step[c] += 1 for chains still below their stop step (after k_mode_update).
