@@ -167,6 +167,21 @@ int sfp_observe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
 enum { SFP_PATH_FUSED = 0, SFP_PATH_STAGED = 1 };
 int sfp_set_path(sfp_batch *b, int32_t path);
 
+/* Integrator of sfp_step.
+ *   SFP_INTEGRATOR_MODES  the mode-space step of Sec. 4 (default).
+ *   SFP_INTEGRATOR_EULER  the default bead-position Euler scheme of Sec. 3A
+ *                         (Eqs. b3-b5): r_n += dtau (F_n + gamma y_n x)
+ *                         + sqrt(2 T* dtau) z_n with the full force of Eq. a2,
+ *                         stable only for small dtau (about 0.1, Sec. 3A), with
+ *                         the same bead noise z_n as the mode-space step.  It
+ *                         runs on the bond vectors (FP32 keeps the small
+ *                         increments) and the FP64 centre of mass; each
+ *                         sfp_step call converts modes -> bonds -> modes once.
+ *                         Up to 4096 beads; probes are not kept.
+ * SFP_EINVAL for an unknown value. */
+enum { SFP_INTEGRATOR_MODES = 0, SFP_INTEGRATOR_EULER = 1 };
+int sfp_set_integrator(sfp_batch *b, int32_t integrator);
+
 /* Observable sampling (Sec. 5B).  every_steps > 0 clears the accumulators of
  * SFP_OBS_ACCUM, SFP_OBS_MODE_POWER and SFP_OBS_COM_MSD, takes sample 0 of the
  * current state at once, and from then on one sample after every every_steps

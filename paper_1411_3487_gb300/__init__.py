@@ -14,7 +14,8 @@ import numpy as np
 from . import _lib
 from ._lib import (SFP_FP32, SFP_FP32_SIMT, SFP_FP64, SFP_OBS_ACCUM, SFP_OBS_COM,
                    SFP_OBS_COM_MSD, SFP_OBS_MODE_POWER, SFP_OBS_MODES, SFP_OBS_POSITIONS,
-                   SFP_OBS_SHAPE, SFP_OBS_STEP, SFP_PATH_FUSED, SFP_PATH_STAGED, SFP_PROBE_BONDS, SFP_PROBE_DH,
+                   SFP_INTEGRATOR_EULER, SFP_INTEGRATOR_MODES, SFP_OBS_SHAPE, SFP_OBS_STEP,
+                   SFP_PATH_FUSED, SFP_PATH_STAGED, SFP_PROBE_BONDS, SFP_PROBE_DH,
                    SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_ZMODE, SfpChainDesc, SfpError,
                    SfpParams)
 
@@ -136,6 +137,10 @@ class Batch:
     def set_path(self, path: int) -> None:
         """SFP_PATH_FUSED (one kernel per step) or SFP_PATH_STAGED (one per stage, probes kept)."""
         _lib.check(_lib.load().sfp_set_path(self._h, int(path)))
+
+    def set_integrator(self, integrator: int) -> None:
+        """SFP_INTEGRATOR_MODES (Sec. 4) or SFP_INTEGRATOR_EULER (bead-position Euler, Sec. 3A)."""
+        _lib.check(_lib.load().sfp_set_integrator(self._h, int(integrator)))
 
     def set_sampling(self, every_steps: int) -> None:
         """Sample observables i-iii, mode power and CoM windows every ``every_steps`` steps."""

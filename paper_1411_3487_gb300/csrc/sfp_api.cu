@@ -175,6 +175,7 @@ struct Group {
     int64_t* slot_stop = nullptr;
     double* slot_shear = nullptr;
     double* gather = nullptr;     // [kGather][3][M] + [kGather][3] + [kGather] FP64 / i64
+    void* psiT = nullptr;         // [p][k] = sum_{n >= k} phi_{n,p} (bonds -> modes; Euler path)
     void *chi = nullptr, *phiT = nullptr, *dm = nullptr, *h = nullptr, *w = nullptr, *g = nullptr;
     double *phi_d = nullptr, *phiT_d = nullptr;   // FP64 copies for conversions
     void* r = nullptr;            // [C][3][M] bond vectors u (slot n = 0 unused)
@@ -202,6 +203,7 @@ struct sfp_batch {
     int64_t launches = 0;
     bool probed = false;
     int32_t path = SFP_PATH_FUSED;
+    int32_t integrator = SFP_INTEGRATOR_MODES;
     int C = 0;
     int64_t total_beads = 0;
     std::vector<sfp_chain_desc> desc;
@@ -461,6 +463,50 @@ int sample_all(sfp_batch* b)
     return SFP_OK;
 }
 
+// n_steps of the default bead-position Euler scheme (Eqs. b3-b5) for a group:
+// bonds u = chi R (Eq. e5), k_euler_bonds on the bonds and the FP64 centre of
+// mass, then back to modes R_p = sum_n phi_{n,p} r_n = sum_k psi_{k,p} u_k with
+// psi_{k,p} = sum_{n >= k} phi_{n,p} (p >= 1; constant shifts drop out).
+template <typename T>
+int step_group_euler(sfp_batch* b, Group& g, int64_t n_steps)
+{
+    const int C = g.C, M = g.M;
+    int rc;
+    if (!g.psiT) {
+        std::vector<double> psi((size_t)M * M, 0.0);
+        for (int p = 1; p < M; ++p) {
+            double acc = 0.0;
+            for (int k = M - 1; k >= 1; --k) {
+                acc += g.tab.phi[(size_t)k * M + p];
+                psi[(size_t)p * M + k] = acc;
+            }
+        }
+        if ((rc = dalloc(b, &g.psiT, (size_t)M * M * sizeof(T))) || (rc = upload_typed(b, g.psiT, psi))) return rc;
+    }
+    if ((rc = mark(b, 0))) return rc;
+    if (g.tc) {
+        if ((rc = sfp::tc_transform(g.tc, 0, b->stream))) return rc;
+    } else if ((rc = launch_gemm<T>(b, (const T*)g.R, (const T*)g.chi, (T*)g.r, 3 * C, M, M))) {
+        return rc;
+    }
+    const int threads = std::min(1024, (M + 31) / 32 * 32);
+    if ((M + threads - 1) / threads > 4) return fail(SFP_ENOTSUP, "the Euler path supports up to 4096 beads");
+    const size_t smem = (size_t)(6 * M + 3) * sizeof(T);
+    if (smem > 48 * 1024)
+        CUDA_TRY(cudaFuncSetAttribute(sfp::k_euler_bonds<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int64_t s0 = 0; s0 < n_steps; s0 += 1024) {
+        const int k = (int)std::min<int64_t>(1024, n_steps - s0);
+        sfp::k_euler_bonds<T><<<C, threads, smem, b->stream>>>((T*)g.r, g.com, g.step, g.job, g.shear, C, M,
+                                                                (T)g.dtau, (T)std::sqrt(2.0 * b->dv.Tstar * g.dtau),
+                                                                (T)b->dv.nu, b->seed, k, b->bad);
+        CUDA_TRY(cudaGetLastError());
+        b->launches++;
+    }
+    if ((rc = launch_gemm<T>(b, (const T*)g.r, (const T*)g.psiT, (T*)g.R, 3 * C, M, M))) return rc;
+    g.last_fused = true;   // no stage arrays to probe
+    return mark(b, 4, true, n_steps);
+}
+
 constexpr int64_t kMaxFusedSteps = 1024;   // steps per fused launch
 
 int step_all(sfp_batch* b, int64_t n_steps)
@@ -472,7 +518,10 @@ int step_all(sfp_batch* b, int64_t n_steps)
         if (b->sample_every > 0) chunk = std::min<int64_t>(chunk, b->sample_every - b->since_sample);
         for (auto& g : b->groups) {
             int rc = SFP_OK;
-            if (g.fused && b->path == SFP_PATH_FUSED) {
+            if (b->integrator == SFP_INTEGRATOR_EULER) {
+                rc = (b->precision == SFP_FP64) ? step_group_euler<double>(b, g, chunk)
+                                                : step_group_euler<float>(b, g, chunk);
+            } else if (g.fused && b->path == SFP_PATH_FUSED) {
                 rc = step_group_fused(b, g, chunk);
             } else {
                 for (int64_t k = 0; k < chunk && rc == SFP_OK; ++k)
@@ -1157,6 +1206,17 @@ int sfp_set_path(sfp_batch* b, int32_t path)
     if (!b) return fail(SFP_EINVAL, "batch is NULL");
     if (path != SFP_PATH_FUSED && path != SFP_PATH_STAGED) return fail(SFP_EINVAL, "unknown path %d", path);
     b->path = path;
+    return SFP_OK;
+}
+
+int sfp_set_integrator(sfp_batch* b, int32_t integrator)
+{
+    if (!b) return fail(SFP_EINVAL, "batch is NULL");
+    if (integrator != SFP_INTEGRATOR_MODES && integrator != SFP_INTEGRATOR_EULER)
+        return fail(SFP_EINVAL, "unknown integrator %d", integrator);
+    for (const auto& g : b->groups)
+        if (g.limited) return fail(SFP_ENOTSUP, "serving pools step in mode space only");
+    b->integrator = integrator;
     return SFP_OK;
 }
 

@@ -503,3 +503,124 @@ k_sample(const T* __restrict__ R, const double* __restrict__ com, const double* 
 }
 
 }  // namespace sfp
+
+namespace sfp {
+
+// ---------------------------------------------------------------------------
+// Default bead-position Euler scheme (Sec. 3A, Eqs. b3-b5), integrated on the
+// bond vectors u_n = r_n - r_{n-1} (n = 1..N; slot 0 unused) with the centre
+// of mass in FP64, one block per chain, n_steps steps per launch:
+//   e_n = (|u_n| - 1) u_n/|u_n| - nu (u_{n-1} + u_{n+1}),  u_0 = u_{N+1} = 0
+//   bead force F_n = e_{n+1} - e_n (e_0 = e_{N+1} = 0), so the bond update is
+//   u_n += dtau (e_{n+1} - 2 e_n + e_{n-1}) + a (z_n - z_{n-1}) [+ dtau g u_n^y x]
+//   r_cm += a sum_n z_n / M [+ dtau g y_cm x],   a = sqrt(2 T* dtau)
+// with z_n the bead normals of the mode-space path (same Philox stream).
+// Shared memory: 6 M + 3 values of T (bonds, then noise; e with two zero ends).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_euler_bonds(T* __restrict__ U, double* __restrict__ com, int64_t* __restrict__ step,
+                              const uint32_t* __restrict__ job, const double* __restrict__ shear,
+                              int C, int M, T dtau, T amp, T nu, uint32_t seed, int n_steps,
+                              int* __restrict__ bad)
+{
+    extern __shared__ unsigned char euler_smem[];
+    T* su = reinterpret_cast<T*>(euler_smem);   // [3][M] bonds, later noise
+    T* se = su + 3 * M;                          // [3][M+1] e_0 .. e_N (e_0 = 0 stays)
+    __shared__ double red[3][32];
+    const int c = blockIdx.x;
+    if (c >= C) return;
+    const int N = M - 1;
+    T* Uc = U + (size_t)c * 3 * M;
+    const uint32_t jb = job[c];
+    const double sh = shear[c];
+    int64_t st = step[c];
+    bool fin = true;
+    for (int s = 0; s < n_steps; ++s, ++st) {
+        for (int i = threadIdx.x; i < 3 * M; i += blockDim.x) su[i] = Uc[i];
+        __syncthreads();
+        // e_n for bonds n = 1..N; e_0 and e_{N+1} are zero
+        for (int n = threadIdx.x; n <= N + 1; n += blockDim.x) {
+            T e[3] = {T(0), T(0), T(0)};
+            if (n >= 1 && n <= N) {
+                T u[3], um[3], up[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    u[a] = su[a * M + n];
+                    um[a] = n >= 2 ? su[a * M + n - 1] : T(0);
+                    up[a] = n + 1 <= N ? su[a * M + n + 1] : T(0);
+                }
+                const T len = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                const T f = (len - T(1)) / len;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) e[a] = f * u[a] - nu * (um[a] + up[a]);
+            }
+            if (n <= N) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) se[a * (M + 1) + n] = e[a];
+            } else {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) se[a * (M + 1) + n] = T(0);
+            }
+        }
+        // bonds stay in registers of the thread that updates them
+        __syncthreads();
+        T unew[3][4];   // up to 4 bonds per thread (M <= 4 blockDim)
+        int k = 0;
+        for (int n = threadIdx.x; n < M; n += blockDim.x, ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) unew[a][k] = su[a * M + n];
+        __syncthreads();
+        // bead noise of this step into su (the bonds are in registers now)
+        double zs[3] = {0.0, 0.0, 0.0};
+        for (int n = threadIdx.x; n < M; n += blockDim.x) {
+            T g[3];
+            Normals<T>::draw(seed, jb, st, (uint32_t)n, 0u, g);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                su[a * M + n] = g[a];
+                zs[a] += (double)g[a];
+            }
+        }
+        // block sum of the noise (centre of mass)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double v = zs[a];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = v;
+        }
+        __syncthreads();
+        k = 0;
+        for (int n = threadIdx.x; n < M; n += blockDim.x, ++k) {
+            if (n == 0) continue;
+            T o[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const T lap = se[a * (M + 1) + n + 1] - T(2) * se[a * (M + 1) + n] + se[a * (M + 1) + n - 1];
+                o[a] = unew[a][k] + dtau * lap + amp * (su[a * M + n] - su[a * M + n - 1]);
+            }
+            o[0] += dtau * (T)sh * unew[1][k];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                fin = fin && isfinite(o[a]);
+                Uc[a * M + n] = o[a];
+            }
+        }
+        if (threadIdx.x == 0) {
+            double tot[3] = {0.0, 0.0, 0.0};
+            for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) tot[a] += red[a][w];
+            double* cm = com + 3 * (size_t)c;
+            const double ycm = cm[1];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) cm[a] += (double)amp * tot[a] / (double)M;
+            cm[0] += (double)dtau * sh * ycm;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) step[c] = st;
+    if (!fin) atomicOr(bad, 1);
+}
+
+}  // namespace sfp
