@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="tc", choices=["tc", "simt"])
     ap.add_argument("--path", default="fused", choices=["fused", "staged"])
-    ap.add_argument("--workload", default="batch", choices=["batch", "serving"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "serving", "precision"])
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-mb", type=float, default=40e3)
@@ -437,6 +437,37 @@ def run_serving(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_precision(args, rank):
+    """Error per observable against the FP64 oracle at 16384 x 512 bp (dt 15.9 ps),
+    for each GPU precision, with the step time of each (16384 x 512 bp)."""
+    if rank != 0:
+        return
+    import torch
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import paper_1411_3487_gb300 as sfp
+    from paper_1411_3487_gb300 import build
+    from oracle import oracle as O
+    from precision_case import errors
+    build.build()
+    torch.cuda.set_device(0)
+    out = {}
+    for name, prec in (("tf32x3_tcgen05", sfp.SFP_FP32), ("fp32_cuda_cores", sfp.SFP_FP32_SIMT),
+                       ("fp64", sfp.SFP_FP64)):
+        e = errors(sfp, O, prec, steps=2000, every=20, sub=32)
+        b = sfp.Batch([{"n_beads": 512, "dtau": 100.0}] * 16384, seed=1, precision=prec)
+        b.init_equilibrium(0)
+        b.step(3)
+        b.stage_timing(True)
+        b.step(20)
+        e["step_us"] = b.stage_times()["step_us"]
+        b.close()
+        out[name] = e
+    print(json.dumps({"metric": "error per observable vs FP64 oracle", "workload":
+                      "16384 chains x 512 bp, dt 15.9 ps, equilibrium starts; oracle on 32 chains, 2000 steps, "
+                      "sums sampled every 20 steps", "errors": out}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -445,6 +476,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args, rank)
+        return
+    if args.workload == "precision":
+        run_precision(args, rank)
         return
     run_native(args, rank, world, local)
 

@@ -1,0 +1,32 @@
+"""Error per observable against the FP64 oracle at the 16384 x 512-bp size
+(NEXT-3 precision row): TF32 hi/lo tensor-core transforms (SFP_FP32), plain
+FP32 (SFP_FP32_SIMT) and FP64."""
+import pytest
+
+import paper_1411_3487_gb300 as sfp
+from oracle import oracle as O
+from paper_1411_3487_gb300 import build
+from precision_case import errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+
+
+# Bounds: the trajectory norm, |L|^2, the total mode power and the FP64
+# centre of mass are set by the slow modes, where FP32 state keeps ~1e-6; the
+# middle-bond and middle-bead observables are local sums u = chi R over modes
+# whose slow amplitudes reach ~1e4 at 512 bp, so FP32 rounding of the state
+# shows there at ~1e-5 (measured 1.1e-5 and 1.3e-5 with the TF32 split).
+@pytest.mark.parametrize("precision,tol,tol_local", [(sfp.SFP_FP32, 1e-5, 1e-4), (sfp.SFP_FP32_SIMT, 1e-5, 1e-4),
+                                                     (sfp.SFP_FP64, 1e-9, 1e-9)], ids=["tf32x3", "fp32", "fp64"])
+def test_error_per_observable_16384x512(precision, tol, tol_local):
+    e = errors(sfp, O, precision, steps=400, every=20, sub=8)
+    print(precision, e)
+    for k in ("L2", "mode_power", "com_msd_lag1", "com_msd_lag10", "trajectory"):
+        assert e[k] < tol, (k, e[k])
+    for k in ("u_mid2", "r_mid2"):
+        assert e[k] < tol_local, (k, e[k])
