@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="tc", choices=["tc", "simt"])
     ap.add_argument("--path", default="fused", choices=["fused", "staged"])
-    ap.add_argument("--workload", default="batch", choices=["batch", "serving", "precision"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "serving", "precision", "uneven"])
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-mb", type=float, default=40e3)
@@ -468,6 +468,49 @@ def run_precision(args, rank):
                       "sums sampled every 20 steps", "errors": out}), flush=True)
 
 
+def run_uneven(args, rank):
+    """8192 chains with lengths uniform over 64/128/256/512 bp at their Table 1
+    steps (FP32, equilibrium starts): bead-steps/s of runs of 1000 steps per
+    call, one launch per fused group per call, groups on their own streams; as
+    created, after the chains-per-tile autotuner, and with graph replay."""
+    if rank != 0:
+        return
+    import torch
+    sys.path.insert(0, ROOT)
+    import paper_1411_3487_gb300 as sfp
+    from paper_1411_3487_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    dt = {64: 10.0, 128: 50.0, 256: 100.0, 512: 100.0}
+    rng = np.random.default_rng(1)
+    lengths = rng.choice([64, 128, 256, 512], size=8192)
+    chains = [{"n_beads": int(M), "dtau": dt[int(M)], "job_id": i} for i, M in enumerate(lengths)]
+    beads = int(lengths.sum())
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name in ("as_created", "autotuned", "autotuned_graph"):
+        b = sfp.Batch(chains, seed=1, stream=stream)
+        b.init_equilibrium(0)
+        tiles = b.autotune(20) if name != "as_created" else None
+        if name == "autotuned_graph":
+            b.set_graph(True)
+        b.step(200)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps // 100 or 1):
+            b.step(1000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        n = 1000 * (args.steps // 100 or 1)
+        ms = e0.elapsed_time(e1)
+        res[name] = {"value": beads * n / (ms * 1e-3), "ms_per_step": ms / n, "chains_per_tile": tiles}
+        b.close()
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "8192 chains, lengths uniform over "
+                      "64/128/256/512 bp, dtau 10/50/100/100, FP32, 1000 steps per call (state stays in L2)",
+                      "beads": beads, "results": res}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -479,6 +522,9 @@ def main():
         return
     if args.workload == "precision":
         run_precision(args, rank)
+        return
+    if args.workload == "uneven":
+        run_uneven(args, rank)
         return
     run_native(args, rank, world, local)
 

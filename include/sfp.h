@@ -167,6 +167,22 @@ int sfp_observe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
 enum { SFP_PATH_FUSED = 0, SFP_PATH_STAGED = 1 };
 int sfp_set_path(sfp_batch *b, int32_t path);
 
+/* Launch plan of sfp_step.
+ * sfp_set_graph(b, 1): each chunk of steps (up to 1024, or 64 when a group
+ * takes the staged kernels; chunks end at observable samples) is captured
+ * once into a CUDA graph on an internal stream and replayed on the batch's
+ * stream; off with stage timing and for the Euler integrator.  A batch of
+ * several length groups runs each group on its own stream, forked from and
+ * joined back into the batch's stream, so the groups share the GPU.
+ * sfp_autotune(b, trial_steps, out): chooses the chains per tile of every
+ * fused group (1..42) by timing candidates for trial_steps steps, alone and
+ * together; the state, noise counters and trajectory are restored after every
+ * trial (it allocates a temporary copy of the state outside the HBM budget).
+ * out, if not NULL, receives each group's choice (0 for staged groups), in
+ * order of first appearance of each (n_beads, dtau) in the chain list. */
+int sfp_set_graph(sfp_batch *b, int32_t enable);
+int sfp_autotune(sfp_batch *b, int32_t trial_steps, int32_t *chains_per_tile);
+
 /* Integrator of sfp_step.
  *   SFP_INTEGRATOR_MODES  the mode-space step of Sec. 4 (default).
  *   SFP_INTEGRATOR_EULER  the default bead-position Euler scheme of Sec. 3A

@@ -138,6 +138,16 @@ class Batch:
         """SFP_PATH_FUSED (one kernel per step) or SFP_PATH_STAGED (one per stage, probes kept)."""
         _lib.check(_lib.load().sfp_set_path(self._h, int(path)))
 
+    def set_graph(self, enable: bool = True) -> None:
+        """Replay each chunk of steps from a captured CUDA graph."""
+        _lib.check(_lib.load().sfp_set_graph(self._h, int(bool(enable))))
+
+    def autotune(self, trial_steps: int = 20) -> list:
+        """Choose chains per tile of the fused groups by timing; returns them per group."""
+        out = (ct.c_int32 * self.n_chains)()          # at most one group per chain
+        _lib.check(_lib.load().sfp_autotune(self._h, int(trial_steps), out))
+        return list(out[:len({(int(n), 0) for n in self.n_beads})])
+
     def set_integrator(self, integrator: int) -> None:
         """SFP_INTEGRATOR_MODES (Sec. 4) or SFP_INTEGRATOR_EULER (bead-position Euler, Sec. 3A)."""
         _lib.check(_lib.load().sfp_set_integrator(self._h, int(integrator)))

@@ -27,7 +27,7 @@ EXPORTS = (
     "sfp_set_positions", "sfp_set_step", "sfp_step", "sfp_observe", "sfp_probe", "sfp_save",
     "sfp_load", "sfp_info", "sfp_destroy", "sfp_last_error", "sfp_philox_words",
     "sfp_stage_timing", "sfp_stage_times", "sfp_step_noalloc", "sfp_set_sampling",
-    "sfp_set_path", "sfp_set_integrator", "sfp_server_config_default", "sfp_server_create", "sfp_server_submit",
+    "sfp_set_path", "sfp_set_integrator", "sfp_set_graph", "sfp_autotune", "sfp_server_config_default", "sfp_server_create", "sfp_server_submit",
     "sfp_server_poll", "sfp_server_result_modes", "sfp_server_wait_idle", "sfp_server_stats",
     "sfp_server_destroy", "sfp_server_last_error",
 )
@@ -104,6 +104,8 @@ def load(path: str | None = None):
         L.sfp_set_sampling.argtypes = [vp, i32]
         L.sfp_set_path.argtypes = [vp, i32]
         L.sfp_set_integrator.argtypes = [vp, i32]
+        L.sfp_set_graph.argtypes = [vp, i32]
+        L.sfp_autotune.argtypes = [vp, i32, vp]
         L.sfp_server_config_default.argtypes = [ct.POINTER(SfpServerConfig)]
         L.sfp_server_create.argtypes = [ct.POINTER(SfpParams), ct.POINTER(SfpServerConfig), ct.POINTER(vp)]
         L.sfp_server_submit.argtypes = [vp, ct.POINTER(SfpJob), ct.POINTER(u64)]

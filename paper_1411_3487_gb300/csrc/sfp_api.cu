@@ -186,6 +186,8 @@ struct Group {
     sfp::TcPlan* tc = nullptr;    // tensor-core transform plan (SFP_FP32)
     sfp::FusedPlan* fused = nullptr;   // one-kernel step (SFP_FP32, M = 64, 128, 256)
     bool last_fused = false;      // the most recent step of this group ran fused
+    cudaStream_t gs = nullptr;    // this group's stream (batches of several groups)
+    cudaEvent_t join = nullptr;
     // observable sampling (allocated by the first sfp_set_sampling)
     double* obs_tab = nullptr;    // [3][M] rows: phi_N - phi_0, chi_m, phi_m' (p >= 1)
     double* acc_shape = nullptr;  // [C][4]
@@ -204,6 +206,14 @@ struct sfp_batch {
     bool probed = false;
     int32_t path = SFP_PATH_FUSED;
     int32_t integrator = SFP_INTEGRATOR_MODES;
+    // concurrency across length groups and graph replay of step chunks
+    cudaStream_t cur = nullptr;        // stream the step path launches on (b->stream or a group's)
+    cudaStream_t cap = nullptr;        // capture stream (graphs)
+    cudaEvent_t fork = nullptr;
+    bool use_graph = false;
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_chunk = 0;
+    int64_t graph_launches = 0;        // kernels in one replay
     int C = 0;
     int64_t total_beads = 0;
     std::vector<sfp_chain_desc> desc;
@@ -277,14 +287,14 @@ int launch_gemm(sfp_batch* b, const T* In, const T* B, T* Out, int J, int Nc, in
     if constexpr (sizeof(T) == 4) {
         if (Nc >= 128) {
             dim3 grid(nblk(Nc, 128), nblk(J, 128));
-            sfp::k_gemm_nt<float, 128, 128, 8, 8, 8><<<grid, 256, 0, b->stream>>>(In, B, Out, J, Nc, K);
+            sfp::k_gemm_nt<float, 128, 128, 8, 8, 8><<<grid, 256, 0, b->cur>>>(In, B, Out, J, Nc, K);
         } else {
             dim3 grid(nblk(Nc, 64), nblk(J, 64));
-            sfp::k_gemm_nt<float, 64, 64, 8, 4, 4><<<grid, 256, 0, b->stream>>>(In, B, Out, J, Nc, K);
+            sfp::k_gemm_nt<float, 64, 64, 8, 4, 4><<<grid, 256, 0, b->cur>>>(In, B, Out, J, Nc, K);
         }
     } else {
         dim3 grid(nblk(Nc, 64), nblk(J, 64));
-        sfp::k_gemm_nt<double, 64, 64, 8, 4, 4><<<grid, 256, 0, b->stream>>>(In, B, Out, J, Nc, K);
+        sfp::k_gemm_nt<double, 64, 64, 8, 4, 4><<<grid, 256, 0, b->cur>>>(In, B, Out, J, Nc, K);
     }
     b->launches++;
     CUDA_TRY(cudaGetLastError());
@@ -337,7 +347,7 @@ int mark(sfp_batch* b, int k, bool fused = false, int64_t steps = 1)
         CUDA_TRY(cudaEventCreate(&e));
         b->events.push_back(e);
     }
-    CUDA_TRY(cudaEventRecord(b->events[idx], b->stream));
+    CUDA_TRY(cudaEventRecord(b->events[idx], b->cur));
     if (k == 4) b->ev_used += 5;
     return SFP_OK;
 }
@@ -390,7 +400,7 @@ int step_group_fused(sfp_batch* b, Group& g, int64_t n_steps)
     a.dtau = g.dtau;
     a.n_steps = (int)n_steps;
     a.cpt = sfp::fused_tile(g.fused);
-    if ((rc = sfp::fused_step(g.fused, a, b->stream))) return rc;
+    if ((rc = sfp::fused_step(g.fused, a, b->cur))) return rc;
     b->launches++;
     g.last_fused = true;
     return mark(b, 4, true, n_steps);
@@ -409,7 +419,7 @@ int step_group(sfp_batch* b, Group& g)
     int rc;
     if ((rc = mark(b, 0))) return rc;
     // a1: modes -> bond vectors u = chi R  (Eqs. c1, e5; the centre of mass drops out)
-    if (g.tc) rc = sfp::tc_transform(g.tc, 0, b->stream);
+    if (g.tc) rc = sfp::tc_transform(g.tc, 0, b->cur);
     else rc = launch_gemm<T>(b, R, (const T*)g.chi, r, 3 * C, M, M);
     if (rc) return rc;
     if (g.tc) b->launches++;
@@ -417,23 +427,23 @@ int step_group(sfp_batch* b, Group& g)
     // a2 + a3: residual bond force and bead noise
     {
         const T c12 = (T)(1.0 - 2.0 * b->dv.nu);
-        CUDA_TRY(launch_force_noise<T>(b->stream, r, fz, fz + n, C, M, c12, b->seed, g.job, g.step));
+        CUDA_TRY(launch_force_noise<T>(b->cur, r, fz, fz + n, C, M, c12, b->seed, g.job, g.step));
         b->launches++;
     }
     if ((rc = mark(b, 2))) return rc;
     // a4: [DeltaH | Z] = phi^T [f | z]  (forward transform, Eqs. c4, e11)
-    if (g.tc) rc = sfp::tc_transform(g.tc, 1, b->stream);
+    if (g.tc) rc = sfp::tc_transform(g.tc, 1, b->cur);
     else rc = launch_gemm<T>(b, fz, (const T*)g.phiT, yz, 6 * C, M, M);
     if (rc) return rc;
     if (g.tc) b->launches++;
     if ((rc = mark(b, 3))) return rc;
     // a5: mode update (Eqs. d3, d6, f2, btum)
-    CUDA_TRY(launch_mode_update<T>(b->stream, R, yz, yz + n, g.com, g.step, (const T*)g.dm, (const T*)g.h,
+    CUDA_TRY(launch_mode_update<T>(b->cur, R, yz, yz + n, g.com, g.step, (const T*)g.dm, (const T*)g.h,
                                    (const T*)g.w, (const T*)g.g, g.shear, C, M, g.tab.w0, g.dtau, b->bad,
                                    g.limited ? g.stop : nullptr));
     b->launches++;
     if (g.limited) {
-        sfp::k_advance_steps<<<nblk(C, 256), 256, 0, b->stream>>>(g.step, g.stop, C);
+        sfp::k_advance_steps<<<nblk(C, 256), 256, 0, b->cur>>>(g.step, g.stop, C);
         b->launches++;
         CUDA_TRY(cudaGetLastError());
     }
@@ -485,7 +495,7 @@ int step_group_euler(sfp_batch* b, Group& g, int64_t n_steps)
     }
     if ((rc = mark(b, 0))) return rc;
     if (g.tc) {
-        if ((rc = sfp::tc_transform(g.tc, 0, b->stream))) return rc;
+        if ((rc = sfp::tc_transform(g.tc, 0, b->cur))) return rc;
     } else if ((rc = launch_gemm<T>(b, (const T*)g.R, (const T*)g.chi, (T*)g.r, 3 * C, M, M))) {
         return rc;
     }
@@ -496,7 +506,7 @@ int step_group_euler(sfp_batch* b, Group& g, int64_t n_steps)
         CUDA_TRY(cudaFuncSetAttribute(sfp::k_euler_bonds<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int64_t s0 = 0; s0 < n_steps; s0 += 1024) {
         const int k = (int)std::min<int64_t>(1024, n_steps - s0);
-        sfp::k_euler_bonds<T><<<C, threads, smem, b->stream>>>((T*)g.r, g.com, g.step, g.job, g.shear, C, M,
+        sfp::k_euler_bonds<T><<<C, threads, smem, b->cur>>>((T*)g.r, g.com, g.step, g.job, g.shear, C, M,
                                                                 (T)g.dtau, (T)std::sqrt(2.0 * b->dv.Tstar * g.dtau),
                                                                 (T)b->dv.nu, b->seed, k, b->bad);
         CUDA_TRY(cudaGetLastError());
@@ -509,26 +519,92 @@ int step_group_euler(sfp_batch* b, Group& g, int64_t n_steps)
 
 constexpr int64_t kMaxFusedSteps = 1024;   // steps per fused launch
 
+// The launches of one chunk of steps for every group.  With several groups
+// (and no stage timing) each group runs on its own stream, forked from and
+// joined back into `base`, so groups of different lengths share the GPU.
+int issue_chunk(sfp_batch* b, int64_t chunk, cudaStream_t base)
+{
+    const bool conc = b->groups.size() > 1 && !b->timing;
+    if (conc) {
+        CUDA_TRY(cudaEventRecord(b->fork, base));
+        for (auto& g : b->groups) CUDA_TRY(cudaStreamWaitEvent(g.gs, b->fork, 0));
+    }
+    int rc = SFP_OK;
+    for (auto& g : b->groups) {
+        b->cur = conc ? g.gs : base;
+        if (b->integrator == SFP_INTEGRATOR_EULER) {
+            rc = (b->precision == SFP_FP64) ? step_group_euler<double>(b, g, chunk)
+                                            : step_group_euler<float>(b, g, chunk);
+        } else if (g.fused && b->path == SFP_PATH_FUSED) {
+            rc = step_group_fused(b, g, chunk);
+        } else {
+            for (int64_t k = 0; k < chunk && rc == SFP_OK; ++k)
+                rc = (b->precision == SFP_FP64) ? step_group<double>(b, g) : step_group<float>(b, g);
+        }
+        if (rc) break;
+    }
+    if (conc) {
+        for (auto& g : b->groups) {
+            const cudaError_t e1 = cudaEventRecord(g.join, g.gs);
+            const cudaError_t e2 = cudaStreamWaitEvent(base, g.join, 0);
+            if (!rc && (e1 != cudaSuccess || e2 != cudaSuccess)) rc = fail(SFP_ECUDA, "stream join failed");
+        }
+    }
+    b->cur = b->stream;
+    return rc;
+}
+
+void drop_graph(sfp_batch* b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_chunk = 0;
+}
+
+// One chunk through a CUDA graph: captured on the batch's capture stream the
+// first time a chunk of this length is issued, then replayed on its stream.
+int graph_chunk(sfp_batch* b, int64_t chunk)
+{
+    if (!b->graph || b->graph_chunk != chunk) {
+        drop_graph(b);
+        CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        const int64_t l0 = b->launches;
+        const int rc = issue_chunk(b, chunk, b->cap);
+        b->graph_launches = b->launches - l0;
+        b->launches = l0;                 // captured, not run: counted per replay below
+        cudaGraph_t gph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->cap, &gph);
+        if (rc) {
+            if (gph) cudaGraphDestroy(gph);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(SFP_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        const cudaError_t ei = cudaGraphInstantiate(&b->graph, gph, 0);
+        cudaGraphDestroy(gph);
+        if (ei != cudaSuccess) {
+            b->graph = nullptr;
+            return fail(SFP_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+        }
+        b->graph_chunk = chunk;
+    }
+    CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
+    b->launches += b->graph_launches;
+    return SFP_OK;
+}
+
 int step_all(sfp_batch* b, int64_t n_steps)
 {
+    bool staged = false;
+    for (auto& g : b->groups) staged = staged || !(g.fused && b->path == SFP_PATH_FUSED);
+    const bool graphs = b->use_graph && !b->timing && b->integrator == SFP_INTEGRATOR_MODES;
     for (int64_t s = 0; s < n_steps;) {
         // steps up to the next observable sample: one launch per fused group,
         // one launch per stage and step for the others
         int64_t chunk = std::min<int64_t>(n_steps - s, kMaxFusedSteps);
+        if (graphs && staged) chunk = std::min<int64_t>(chunk, 64);   // bounded graph size
         if (b->sample_every > 0) chunk = std::min<int64_t>(chunk, b->sample_every - b->since_sample);
-        for (auto& g : b->groups) {
-            int rc = SFP_OK;
-            if (b->integrator == SFP_INTEGRATOR_EULER) {
-                rc = (b->precision == SFP_FP64) ? step_group_euler<double>(b, g, chunk)
-                                                : step_group_euler<float>(b, g, chunk);
-            } else if (g.fused && b->path == SFP_PATH_FUSED) {
-                rc = step_group_fused(b, g, chunk);
-            } else {
-                for (int64_t k = 0; k < chunk && rc == SFP_OK; ++k)
-                    rc = (b->precision == SFP_FP64) ? step_group<double>(b, g) : step_group<float>(b, g);
-            }
-            if (rc) return rc;
-        }
+        const int rc = graphs ? graph_chunk(b, chunk) : issue_chunk(b, chunk, b->stream);
+        if (rc) return rc;
         s += chunk;
         if (b->sample_every > 0 && (b->since_sample += chunk) == b->sample_every) {
             const int rc = sample_all(b);
@@ -598,9 +674,15 @@ int destroy_impl(sfp_batch* b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     else cudaDeviceSynchronize();
     for (auto& g : b->groups) {
+        if (g.gs) cudaStreamSynchronize(g.gs);
         if (g.tc) sfp::tc_destroy(g.tc);
         if (g.fused) sfp::fused_destroy(g.fused);
+        if (g.gs) cudaStreamDestroy(g.gs);
+        if (g.join) cudaEventDestroy(g.join);
     }
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->fork) cudaEventDestroy(b->fork);
     for (cudaEvent_t e : b->events) cudaEventDestroy(e);
     for (void* p : b->allocs) cudaFree(p);
     delete b;
@@ -859,6 +941,17 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
             destroy_impl(b);
             return fail(SFP_ENOMEM, "HBM budget of %zu bytes exceeded (%zu needed)", hbm_budget_bytes, held);
         }
+    }
+    b->cur = b->stream;
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        for (auto& g : b->groups) {
+            if (e != cudaSuccess || b->groups.size() < 2) break;
+            e = cudaStreamCreateWithFlags(&g.gs, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) { destroy_impl(b); return fail(SFP_ECUDA, "stream creation failed: %s", cudaGetErrorString(e)); }
     }
     *out = b;
     return SFP_OK;
@@ -1205,7 +1298,155 @@ int sfp_set_path(sfp_batch* b, int32_t path)
 {
     if (!b) return fail(SFP_EINVAL, "batch is NULL");
     if (path != SFP_PATH_FUSED && path != SFP_PATH_STAGED) return fail(SFP_EINVAL, "unknown path %d", path);
+    if (b->path != path) drop_graph(b);
     b->path = path;
+    return SFP_OK;
+}
+
+int sfp_set_graph(sfp_batch* b, int32_t enable)
+{
+    if (!b) return fail(SFP_EINVAL, "batch is NULL");
+    if (!enable) drop_graph(b);
+    b->use_graph = enable != 0;
+    return SFP_OK;
+}
+
+int sfp_autotune(sfp_batch* b, int32_t trial_steps, int32_t* chains_per_tile)
+{
+    if (!b) return fail(SFP_EINVAL, "batch is NULL");
+    if (trial_steps < 1) return fail(SFP_EINVAL, "trial_steps must be >= 1");
+    const size_t G = b->groups.size();
+    if (chains_per_tile)
+        for (size_t i = 0; i < G; ++i) chains_per_tile[i] = b->groups[i].fused ? sfp::fused_tile(b->groups[i].fused) : 0;
+    if (b->path != SFP_PATH_FUSED || b->integrator != SFP_INTEGRATOR_MODES || b->timing) return SFP_OK;
+    std::vector<size_t> fg;
+    for (size_t i = 0; i < G; ++i)
+        if (b->groups[i].fused) fg.push_back(i);
+    if (fg.empty()) return SFP_OK;
+    int dev = 0, sms = 148;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // save every group's dynamic state; each trial starts from it again
+    struct Saved { void* R = nullptr; double* com = nullptr; int64_t* step = nullptr; };
+    std::vector<Saved> sv(G);
+    auto release = [&]() {
+        for (auto& x : sv) { cudaFree(x.R); cudaFree(x.com); cudaFree(x.step); }
+    };
+    const size_t es = esize(b);
+    for (size_t i = 0; i < G; ++i) {
+        const Group& g = b->groups[i];
+        const size_t n = (size_t)g.C * 3 * g.M;
+        if (cudaMalloc(&sv[i].R, n * es) != cudaSuccess || cudaMalloc(&sv[i].com, (size_t)g.C * 24) != cudaSuccess ||
+            cudaMalloc(&sv[i].step, (size_t)g.C * 8) != cudaSuccess) {
+            release();
+            return fail(SFP_ENOMEM, "autotune: no memory for the state copy");
+        }
+        CUDA_TRY(cudaMemcpyAsync(sv[i].R, g.R, n * es, cudaMemcpyDeviceToDevice, b->stream));
+        CUDA_TRY(cudaMemcpyAsync(sv[i].com, g.com, (size_t)g.C * 24, cudaMemcpyDeviceToDevice, b->stream));
+        CUDA_TRY(cudaMemcpyAsync(sv[i].step, g.step, (size_t)g.C * 8, cudaMemcpyDeviceToDevice, b->stream));
+    }
+    auto restore = [&]() -> int {
+        for (size_t i = 0; i < G; ++i) {
+            const Group& g = b->groups[i];
+            const size_t n = (size_t)g.C * 3 * g.M;
+            CUDA_TRY(cudaMemcpyAsync(g.R, sv[i].R, n * es, cudaMemcpyDeviceToDevice, b->stream));
+            CUDA_TRY(cudaMemcpyAsync(g.com, sv[i].com, (size_t)g.C * 24, cudaMemcpyDeviceToDevice, b->stream));
+            CUDA_TRY(cudaMemcpyAsync(g.step, sv[i].step, (size_t)g.C * 8, cudaMemcpyDeviceToDevice, b->stream));
+        }
+        return SFP_OK;
+    };
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    // time `fn` (warm-up, then one timed call) on the batch stream, restoring the state after each
+    auto timed = [&](auto&& fn, double* ms) -> int {
+        int rc = fn();
+        if (!rc) rc = restore();
+        if (rc) return rc;
+        CUDA_TRY(cudaEventRecord(e0, b->stream));
+        if ((rc = fn())) return rc;
+        CUDA_TRY(cudaEventRecord(e1, b->stream));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+        *ms = t;
+        return restore();
+    };
+    const bool was_graph = b->use_graph;
+    drop_graph(b);
+    b->use_graph = false;
+    int rc = SFP_OK;
+    // 1. each fused group alone, for a few chains-per-tile candidates
+    std::vector<std::vector<std::pair<int, double>>> cand(fg.size());
+    for (size_t k = 0; k < fg.size() && !rc; ++k) {
+        Group& g = b->groups[fg[k]];
+        std::vector<int> cs;
+        for (double f : {1.0, 0.75, 0.5, 1.0 / 3.0, 0.25}) {
+            const int target = std::max(1, (int)(f * sms));
+            cs.push_back(std::max(1, std::min(42, (g.C + target - 1) / target)));
+        }
+        cs.push_back(42);
+        std::sort(cs.begin(), cs.end());
+        cs.erase(std::unique(cs.begin(), cs.end()), cs.end());
+        for (int c : cs) {
+            if ((rc = sfp::fused_set_tile(g.fused, c))) break;
+            double ms = 0.0;
+            b->cur = b->stream;
+            rc = timed([&]() { return step_group_fused(b, g, trial_steps); }, &ms);
+            if (rc) break;
+            cand[k].push_back({c, ms});
+        }
+    }
+    // 2. combinations: estimated concurrent makespan max(max t, sum t * CTAs / SMs),
+    //    then the best estimate and the best-alone choice are measured together
+    std::vector<int> best_alone(fg.size()), best_est(fg.size());
+    if (!rc) {
+        for (size_t k = 0; k < fg.size(); ++k)
+            best_alone[k] = std::min_element(cand[k].begin(), cand[k].end(),
+                                             [](auto& x, auto& y) { return x.second < y.second; })->first;
+        double best = 1e300;
+        std::vector<size_t> idx(fg.size(), 0);
+        for (;;) {
+            double mx = 0.0, share = 0.0;
+            for (size_t k = 0; k < fg.size(); ++k) {
+                const auto& cnd = cand[k][idx[k]];
+                const Group& g = b->groups[fg[k]];
+                mx = std::max(mx, cnd.second);
+                share += cnd.second * (double)((g.C + cnd.first - 1) / cnd.first) / sms;
+            }
+            const double est = std::max(mx, share);
+            if (est < best) {
+                best = est;
+                for (size_t k = 0; k < fg.size(); ++k) best_est[k] = cand[k][idx[k]].first;
+            }
+            size_t k = 0;
+            while (k < fg.size() && ++idx[k] == cand[k].size()) idx[k++] = 0;
+            if (k == fg.size()) break;
+        }
+        double t_est = 0.0, t_alone = 0.0;
+        auto set_all = [&](const std::vector<int>& v) -> int {
+            for (size_t k = 0; k < fg.size(); ++k) {
+                const int r = sfp::fused_set_tile(b->groups[fg[k]].fused, v[k]);
+                if (r) return r;
+            }
+            return SFP_OK;
+        };
+        auto whole = [&]() { return issue_chunk(b, trial_steps, b->stream); };
+        if (!(rc = set_all(best_est))) rc = timed(whole, &t_est);
+        if (!rc && best_alone != best_est && !(rc = set_all(best_alone))) rc = timed(whole, &t_alone);
+        if (!rc && best_alone != best_est && t_est <= t_alone) rc = set_all(best_est);
+    }
+    b->cur = b->stream;
+    b->use_graph = was_graph;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int rr = restore();
+    cudaStreamSynchronize(b->stream);
+    release();
+    if (rc) return rc;
+    if (rr) return rr;
+    if (chains_per_tile)
+        for (size_t i = 0; i < G; ++i) chains_per_tile[i] = b->groups[i].fused ? sfp::fused_tile(b->groups[i].fused) : 0;
     return SFP_OK;
 }
 
@@ -1216,6 +1457,7 @@ int sfp_set_integrator(sfp_batch* b, int32_t integrator)
         return fail(SFP_EINVAL, "unknown integrator %d", integrator);
     for (const auto& g : b->groups)
         if (g.limited) return fail(SFP_ENOTSUP, "serving pools step in mode space only");
+    if (b->integrator != integrator) drop_graph(b);
     b->integrator = integrator;
     return SFP_OK;
 }

@@ -1,0 +1,77 @@
+"""Uneven-length batches (64/128/256/512 bp, Table 1 steps): groups on their
+own streams, CUDA-graph replay of step chunks, and the chains-per-tile
+autotuner.  None of them may change a trajectory."""
+import numpy as np
+import pytest
+
+import paper_1411_3487_gb300 as sfp
+from oracle import oracle as O
+from paper_1411_3487_gb300 import build
+
+pytestmark = pytest.mark.gpu
+
+DT = {64: 10.0, 128: 50.0, 256: 100.0, 512: 100.0}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    build.build()
+
+
+def mixed(C, seed=3):
+    rng = np.random.default_rng(seed)
+    lengths = rng.choice([64, 128, 256, 512], size=C)
+    return [{"n_beads": int(M), "dtau": DT[int(M)], "job_id": i,
+             "shear_rate_per_s": 0.0 if i % 3 else 5e7} for i, M in enumerate(lengths)]
+
+
+def run(chains, steps, graph=False, autotune=False):
+    b = sfp.Batch(chains, seed=7)
+    b.init_equilibrium(0)
+    tiles = None
+    if autotune:
+        before = [x.copy() for x in b.modes()]
+        tiles = b.autotune(5)
+        after = b.modes()
+        assert all(np.array_equal(x, y) for x, y in zip(before, after))
+        assert np.all(b.observe(sfp.SFP_OBS_STEP) == 0)
+    if graph:
+        b.set_graph(True)
+    for k in (37, 100, 63):
+        b.step(k)
+    out = b.modes(), b.observe(sfp.SFP_OBS_COM), b.observe(sfp.SFP_OBS_STEP), b.info()["launches"]
+    b.close()
+    return out, tiles
+
+
+def test_graph_replay_and_autotune_leave_trajectories_unchanged():
+    chains = mixed(600)
+    (ref, _) = run(chains, 200)
+    (gr, _) = run(chains, 200, graph=True)
+    (at, tiles) = run(chains, 200, autotune=True)
+    for (a, b) in ((ref, gr), (ref, at)):
+        assert all(np.array_equal(x, y) for x, y in zip(a[0], b[0]))
+        assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    assert np.all(ref[2] == 200)
+    # a replay counts the kernels it runs; with graphs the staged 512-bp group caps
+    # chunks at 64 steps, so the 100-step call is two chunks: one more launch for
+    # each of the three fused groups
+    assert gr[3] == ref[3] + 3
+    assert len(tiles) == 4 and sum(1 for t in tiles if 1 <= t <= 42) == 3 and tiles.count(0) == 1
+
+
+def test_concurrent_groups_match_the_oracle():
+    chains = mixed(40, seed=11)
+    b = sfp.Batch(chains, seed=7)
+    starts = [O.Model(c["n_beads"], dtau=c["dtau"]).equilibrium_start(7, c["job_id"]) for c in chains]
+    b.set_modes(starts)
+    b.set_graph(True)
+    b.step(90)
+    G = b.modes()
+    c_ps = sfp.derive()["c_ps"]
+    for i in (0, 7, 13, 22, 39):
+        c = chains[i]
+        m = O.Model(c["n_beads"], dtau=c["dtau"])
+        ref = m.run_modes(starts[i][None], 7, [c["job_id"]], 0, 90, shear=c["shear_rate_per_s"] * c_ps * 1e-12)[0]
+        err = np.linalg.norm(G[i][:, 1:] - ref[:, 1:]) / np.linalg.norm(ref[:, 1:])
+        assert err < 1e-5, (i, err)
