@@ -452,8 +452,8 @@ def run_precision(args, rank):
     build.build()
     torch.cuda.set_device(0)
     out = {}
-    for name, prec in (("tf32x3_tcgen05", sfp.SFP_FP32), ("fp32_cuda_cores", sfp.SFP_FP32_SIMT),
-                       ("fp64", sfp.SFP_FP64)):
+    for name, prec in (("tf32x3_tcgen05", sfp.SFP_FP32), ("bf16x3_tcgen05", sfp.SFP_MIXED_BF16),
+                       ("fp32_cuda_cores", sfp.SFP_FP32_SIMT), ("fp64", sfp.SFP_FP64)):
         e = errors(sfp, O, prec, steps=2000, every=20, sub=32)
         b = sfp.Batch([{"n_beads": 512, "dtau": 100.0}] * 16384, seed=1, precision=prec)
         b.init_equilibrium(0)

@@ -80,11 +80,17 @@ typedef struct sfp_chain_desc {
 } sfp_chain_desc;
 
 /* Arithmetic of the step.
- * SFP_FP32       FP32 state; transforms on the tensor cores (tcgen05) with
- *                a three-pass TF32 hi/lo split, FP32 accumulate.
- * SFP_FP64       FP64 throughout (CUDA cores).
- * SFP_FP32_SIMT  FP32 throughout on the CUDA cores: the plain path. */
-enum { SFP_FP32 = 0, SFP_FP64 = 1, SFP_FP32_SIMT = 4 };
+ * SFP_FP32        FP32 state; transforms on the tensor cores (tcgen05) with
+ *                 a three-pass TF32 hi/lo split, FP32 accumulate (fused step
+ *                 for 64/128/256 beads, staged otherwise).
+ * SFP_FP64        FP64 throughout (CUDA cores).
+ * SFP_MIXED_BF16  FP32 state; staged transforms on the tensor cores with a
+ *                 three-pass BF16 hi/lo split (kind::f16), FP32 accumulate:
+ *                 about 16 bits per product, so trajectories drift from the
+ *                 FP64 oracle by ~1e-4 rather than ~1e-6 (see the error per
+ *                 observable of bench.py --workload precision).
+ * SFP_FP32_SIMT   FP32 throughout on the CUDA cores: the plain path. */
+enum { SFP_FP32 = 0, SFP_FP64 = 1, SFP_MIXED_BF16 = 2, SFP_FP32_SIMT = 4 };
 
 typedef struct sfp_batch sfp_batch;   /* opaque */
 

@@ -815,7 +815,7 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
     *out = nullptr;
     if (!chains || n_chains <= 0) return fail(SFP_EINVAL, "need n_chains > 0 and a chain array");
     if (seed >> 32) return fail(SFP_EINVAL, "seed must be < 2^32");
-    if (precision != SFP_FP32 && precision != SFP_FP64 && precision != SFP_FP32_SIMT)
+    if (precision != SFP_FP32 && precision != SFP_FP64 && precision != SFP_FP32_SIMT && precision != SFP_MIXED_BF16)
         return fail(SFP_EINVAL, "unknown precision %d", precision);
     Derived dv;
     int rc = derive(params, &dv);
@@ -923,9 +923,10 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
         if ((rc = load_modes_dev(b, g, g.stage))) { destroy_impl(b); return rc; }
         e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) { destroy_impl(b); return fail(SFP_ECUDA, "create: %s", cudaGetErrorString(e)); }
-        if (precision == SFP_FP32 && sfp::tc_supported(M)) {
+        if ((precision == SFP_FP32 || precision == SFP_MIXED_BF16) && sfp::tc_supported(M)) {
             rc = sfp::tc_create(&g.tc, M, 3 * g.C, g.tab.chi.data(), g.tab.phiT.data(), (const float*)g.R,
-                                (float*)g.r, (const float*)g.fz, (float*)g.yz, b->bad, b->stream);
+                                (float*)g.r, (const float*)g.fz, (float*)g.yz, b->bad, b->stream,
+                                precision == SFP_MIXED_BF16);
             if (rc) { destroy_impl(b); return rc; }
         }
         if (precision == SFP_FP32 && sfp::fused_supported(M)) {

@@ -87,6 +87,19 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
     return d;
 }
 
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle (64-byte rows),
+// 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)(512 >> 4) << 32;        // stride byte offset
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)4 << 61;                 // 64-byte swizzle
+    return d;
+}
+
 // Instruction descriptor: kind::tf32, FP32 accumulate, both operands K-major.
 __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n)
 {

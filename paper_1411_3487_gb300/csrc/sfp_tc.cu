@@ -19,6 +19,7 @@
 // frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -181,11 +182,221 @@ int make_map(CUtensorMap* m, const float* base, int rows, int cols, int box_rows
     return make_map_2d(m, base, rows, cols, box_rows);
 }
 
+// ---------------------------------------------------------------------------
+// BF16 variant (SFP_MIXED_BF16): the FP32 A tile (TMA, 128-byte swizzle) is
+// split by threads into BF16 hi = rn(x) and lo = rn(x - hi) in 64-byte-swizzled
+// K-major tiles; the tables are BF16 hi/lo from the host; three kind::f16 passes
+// per K step (A_hi B_lo + A_lo B_hi + A_hi B_hi), FP32 accumulate.  About 16 bits
+// per product instead of the TF32 split's 21.
+// ---------------------------------------------------------------------------
+constexpr int kStagesBf = 3;
+
+template <int NT>
+struct SmemBf {
+    static constexpr int kA32 = kRows * kKB * 4;     // FP32 tile from TMA, 16 KB
+    static constexpr int kA = kRows * kKB * 2;       // BF16 tile, 8 KB
+    static constexpr int kB = NT * kKB * 2;          // BF16 table tile, NT x 64 B
+    static constexpr int kStage = kA32 + 2 * kA + 2 * kB;
+    static constexpr int kBytes = kStagesBf * kStage + 1024 + 1024;
+};
+
+__device__ __forceinline__ uint32_t swz128(int r, int k) { return (uint32_t)(r * 128 + ((((k >> 2) ^ (r & 7)) << 4)) + ((k & 3) << 2)); }
+
+__device__ __forceinline__ uint16_t bf16_bits(float x)
+{
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kThreads, 1)
+k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
+               const __grid_constant__ CUtensorMap tmBl, float* __restrict__ Out, int J, int M, int* err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    using S = SmemBf<NT>;
+    constexpr int ST = kStagesBf;
+    uint64_t* bars = (uint64_t*)(smem + ST * S::kStage);
+    uint64_t* full = bars;
+    uint64_t* conv = bars + ST;
+    uint64_t* empty = bars + 2 * ST;
+    uint64_t* done = bars + 3 * ST;
+    uint32_t* tmem_slot = (uint32_t*)(bars + 3 * ST + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row0 = blockIdx.x * kRows;
+    const int col0 = blockIdx.y * NT;
+    const int nk = (M + kKB - 1) / kKB;
+    constexpr uint32_t kCols = NT < 32 ? 32 : NT;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&conv[s], 128);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmBh)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmBl)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(kCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % ST;
+                const uint32_t ph = (kb / ST) & 1;
+                if (!mbar_wait(&empty[s], ph ^ 1, err, abort_flag)) break;
+                uint8_t* st = smem + s * S::kStage;
+                uint8_t* bh = st + S::kA32 + 2 * S::kA;
+                mbar_expect_tx(&full[s], S::kA32 + 2 * S::kB);
+                tma_load_2d(st, &tmA, &full[s], kb * kKB, row0);
+                tma_load_2d(bh, &tmBh, &full[s], kb * kKB, col0);
+                tma_load_2d(bh + S::kB, &tmBl, &full[s], kb * kKB, col0);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // kind::f16, BF16 A and B, FP32 accumulate, both K-major
+            constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                                       ((uint32_t)(kRows >> 4) << 24);
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % ST;
+                const uint32_t ph = (kb / ST) & 1;
+                if (!mbar_wait(&conv[s], ph, err, abort_flag)) break;
+                fence_after();
+                const uint32_t st = smem_u32(smem + s * S::kStage);
+                const uint32_t a_hi = st + S::kA32, a_lo = a_hi + S::kA, b_hi = a_lo + S::kA, b_lo = b_hi + S::kB;
+#pragma unroll
+                for (int kk = 0; kk < kKB / 16; ++kk) {
+                    const uint32_t off = kk * 32;   // 16 BF16 = 32 bytes along K
+                    const uint32_t acc = (kb | kk) != 0;
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                 ::"r"(tmem), "l"(sdesc64(a_hi + off)), "l"(sdesc64(b_lo + off)), "r"(idesc), "r"(acc) : "memory");
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                 ::"r"(tmem), "l"(sdesc64(a_lo + off)), "l"(sdesc64(b_hi + off)), "r"(idesc), "r"(1u) : "memory");
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                 ::"r"(tmem), "l"(sdesc64(a_hi + off)), "l"(sdesc64(b_hi + off)), "r"(idesc), "r"(1u) : "memory");
+                }
+                mma_commit(&empty[s]);
+            }
+            mma_commit(done);
+        }
+    } else {
+        // warps 2..5: thread t converts row t of each FP32 tile into BF16 hi / lo
+        const int t = threadIdx.x - 64;   // 0..127
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % ST;
+            const uint32_t ph = (kb / ST) & 1;
+            if (!mbar_wait(&full[s], ph, err, abort_flag)) break;
+            const uint8_t* a32 = smem + s * S::kStage;
+            uint8_t* ah = smem + s * S::kStage + S::kA32;
+            uint8_t* al = ah + S::kA;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {          // 16-byte chunks of 8 BF16
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float4 x = *reinterpret_cast<const float4*>(a32 + swz128(t, 8 * c + 4 * q));
+                    const float xs[4] = {x.x, x.y, x.z, x.w};
+                    uint16_t h[4], l[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        h[i] = bf16_bits(xs[i]);
+                        l[i] = bf16_bits(xs[i] - __bfloat162float(__ushort_as_bfloat16(h[i])));
+                    }
+                    hw[2 * q] = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+                    hw[2 * q + 1] = (uint32_t)h[2] | ((uint32_t)h[3] << 16);
+                    lw[2 * q] = (uint32_t)l[0] | ((uint32_t)l[1] << 16);
+                    lw[2 * q + 1] = (uint32_t)l[2] | ((uint32_t)l[3] << 16);
+                }
+                const uint32_t o = (uint32_t)(t * 64 + ((c ^ ((t >> 1) & 3)) << 4));
+                *reinterpret_cast<uint4*>(ah + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4*>(al + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&conv[s]);
+        }
+        const bool ok = mbar_wait(done, 0, err, abort_flag);
+        fence_after();
+        const int q = warp & 3;
+        const int row = row0 + 32 * q + lane;
+        if (ok) {
+#pragma unroll 1
+            for (int c = 0; c < NT; c += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+                if (row < J) {
+                    float4* o = (float4*)(Out + (size_t)row * M + col0 + c);
+                    o[0] = make_float4(v[0], v[1], v[2], v[3]);
+                    o[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    o[2] = make_float4(v[8], v[9], v[10], v[11]);
+                    o[3] = make_float4(v[12], v[13], v[14], v[15]);
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+    }
+}
+
+// 2-D BF16 table [rows][cols], box 32 cols x box_rows, 64-byte swizzle.
+int make_map_bf16(CUtensorMap* m, const void* base, int rows, int cols, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return report(SFP_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kKB, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return report(SFP_ECUDA, "cuTensorMapEncodeTiled (bf16) failed");
+    return SFP_OK;
+}
+
+uint16_t bf16_round_host(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);   // round to nearest even
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_to_float_host(uint16_t h)
+{
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
 }  // namespace
 
 struct TcPlan {
     int M = 0, rows = 0, NT = 0;
-    float* B[4] = {nullptr, nullptr, nullptr, nullptr};   // chi_hi, chi_lo, phiT_hi, phiT_lo
+    bool bf16 = false;
+    void* B[4] = {nullptr, nullptr, nullptr, nullptr};    // chi_hi, chi_lo, phiT_hi, phiT_lo (FP32 or BF16)
     CUtensorMap mapA[2], mapBh[2], mapBl[2];
     float* out[2] = {nullptr, nullptr};
     int* err = nullptr;
@@ -194,7 +405,7 @@ struct TcPlan {
 bool tc_supported(int M) { return M == 32 || M == 64 || M == 128 || M == 256 || M == 512; }
 
 int tc_create(TcPlan** out, int M, int rows, const double* phi, const double* phiT, const float* R,
-              float* r_out, const float* fz, float* yz_out, int* err, cudaStream_t stream)
+              float* r_out, const float* fz, float* yz_out, int* err, cudaStream_t stream, bool bf16)
 {
     *out = nullptr;
     if (!tc_supported(M)) return report(SFP_ENOTSUP, "tensor-core transforms need M in {32, 64, 128, 256, 512}");
@@ -203,7 +414,53 @@ int tc_create(TcPlan** out, int M, int rows, const double* phi, const double* ph
     p->rows = rows;
     p->NT = M <= 256 ? M : 256;
     p->err = err;
+    p->bf16 = bf16;
     const size_t n = (size_t)M * M;
+    if (bf16) {
+        std::vector<uint16_t> hb(n), lb(n);
+        for (int t = 0; t < 2; ++t) {
+            const double* src = t == 0 ? phi : phiT;
+            for (size_t i = 0; i < n; ++i) {
+                hb[i] = bf16_round_host((float)src[i]);
+                lb[i] = bf16_round_host((float)(src[i] - (double)bf16_to_float_host(hb[i])));
+            }
+            for (int k = 0; k < 2; ++k) {
+                if (cudaMalloc(&p->B[2 * t + k], n * 2) != cudaSuccess) {
+                    tc_destroy(p);
+                    return report(SFP_ENOMEM, "tensor-core table allocation failed");
+                }
+                if (cudaMemcpyAsync(p->B[2 * t + k], k == 0 ? hb.data() : lb.data(), n * 2, cudaMemcpyHostToDevice,
+                                    stream) != cudaSuccess ||
+                    cudaStreamSynchronize(stream) != cudaSuccess) {
+                    tc_destroy(p);
+                    return report(SFP_ECUDA, "tensor-core table upload failed");
+                }
+            }
+        }
+        int rc;
+        if ((rc = make_map(&p->mapA[0], R, rows, M, kRows)) || (rc = make_map(&p->mapA[1], fz, 2 * rows, M, kRows)) ||
+            (rc = make_map_bf16(&p->mapBh[0], p->B[0], M, M, p->NT)) || (rc = make_map_bf16(&p->mapBl[0], p->B[1], M, M, p->NT)) ||
+            (rc = make_map_bf16(&p->mapBh[1], p->B[2], M, M, p->NT)) || (rc = make_map_bf16(&p->mapBl[1], p->B[3], M, M, p->NT))) {
+            tc_destroy(p);
+            return rc;
+        }
+        p->out[0] = r_out;
+        p->out[1] = yz_out;
+        cudaError_t e = cudaSuccess;
+        switch (p->NT) {
+            case 32: e = cudaFuncSetAttribute(k_tc_gemm_bf16<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemBf<32>::kBytes); break;
+            case 64: e = cudaFuncSetAttribute(k_tc_gemm_bf16<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemBf<64>::kBytes); break;
+            case 128: e = cudaFuncSetAttribute(k_tc_gemm_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemBf<128>::kBytes); break;
+            case 256: e = cudaFuncSetAttribute(k_tc_gemm_bf16<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemBf<256>::kBytes); break;
+            default: e = cudaErrorInvalidValue; break;
+        }
+        if (e != cudaSuccess) {
+            tc_destroy(p);
+            return report(SFP_ECUDA, "cudaFuncSetAttribute failed");
+        }
+        *out = p;
+        return SFP_OK;
+    }
     std::vector<float> hi(n), lo(n);
     for (int t = 0; t < 2; ++t) {
         const double* src = t == 0 ? phi : phiT;
@@ -227,8 +484,8 @@ int tc_create(TcPlan** out, int M, int rows, const double* phi, const double* ph
     int rc;
     // inverse: A = R [rows][M], B = chi ; forward: A = f|z [2 rows][M], B = phi^T
     if ((rc = make_map(&p->mapA[0], R, rows, M, kRows)) || (rc = make_map(&p->mapA[1], fz, 2 * rows, M, kRows)) ||
-        (rc = make_map(&p->mapBh[0], p->B[0], M, M, p->NT)) || (rc = make_map(&p->mapBl[0], p->B[1], M, M, p->NT)) ||
-        (rc = make_map(&p->mapBh[1], p->B[2], M, M, p->NT)) || (rc = make_map(&p->mapBl[1], p->B[3], M, M, p->NT))) {
+        (rc = make_map(&p->mapBh[0], (const float*)p->B[0], M, M, p->NT)) || (rc = make_map(&p->mapBl[0], (const float*)p->B[1], M, M, p->NT)) ||
+        (rc = make_map(&p->mapBh[1], (const float*)p->B[2], M, M, p->NT)) || (rc = make_map(&p->mapBl[1], (const float*)p->B[3], M, M, p->NT))) {
         tc_destroy(p);
         return rc;
     }
@@ -254,6 +511,18 @@ int tc_transform(TcPlan* p, int which, cudaStream_t stream)
 {
     const int J = which == 0 ? p->rows : 2 * p->rows;
     dim3 grid((J + kRows - 1) / kRows, p->M / p->NT);
+    if (p->bf16) {
+        switch (p->NT) {
+            case 32: k_tc_gemm_bf16<32><<<grid, kThreads, SmemBf<32>::kBytes, stream>>>(p->mapA[which], p->mapBh[which], p->mapBl[which], p->out[which], J, p->M, p->err); break;
+            case 64: k_tc_gemm_bf16<64><<<grid, kThreads, SmemBf<64>::kBytes, stream>>>(p->mapA[which], p->mapBh[which], p->mapBl[which], p->out[which], J, p->M, p->err); break;
+            case 128: k_tc_gemm_bf16<128><<<grid, kThreads, SmemBf<128>::kBytes, stream>>>(p->mapA[which], p->mapBh[which], p->mapBl[which], p->out[which], J, p->M, p->err); break;
+            case 256: k_tc_gemm_bf16<256><<<grid, kThreads, SmemBf<256>::kBytes, stream>>>(p->mapA[which], p->mapBh[which], p->mapBl[which], p->out[which], J, p->M, p->err); break;
+            default: return report(SFP_ENOTSUP, "unsupported tile width");
+        }
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return report(SFP_ECUDA, cudaGetErrorString(e));
+        return SFP_OK;
+    }
     switch (p->NT) {
         case 32:
             k_tc_gemm<32><<<grid, kThreads, Smem<32>::kBytes, stream>>>(p->mapA[which], p->mapBh[which], p->mapBl[which], p->out[which], J, p->M, p->err);
@@ -275,12 +544,12 @@ int tc_transform(TcPlan* p, int which, cudaStream_t stream)
     return SFP_OK;
 }
 
-size_t tc_bytes(const TcPlan* p) { return p ? (size_t)4 * p->M * p->M * sizeof(float) : 0; }
+size_t tc_bytes(const TcPlan* p) { return p ? (size_t)4 * p->M * p->M * (p->bf16 ? 2 : sizeof(float)) : 0; }
 
 void tc_destroy(TcPlan* p)
 {
     if (!p) return;
-    for (float* b : p->B)
+    for (void* b : p->B)
         if (b) cudaFree(b);
     delete p;
 }

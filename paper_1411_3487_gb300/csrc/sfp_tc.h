@@ -20,8 +20,9 @@ bool tc_supported(int M);
 // phi / phiT are the FP64 tables chi [n][p] / phi^T [p][n]; they are split once
 // into TF32 hi/lo.
 // A wait that times out inside the kernel sets bit 2 of *err.
+// bf16: BF16 hi/lo operands (kind::f16) instead of the TF32 split.
 int tc_create(TcPlan** out, int M, int rows, const double* phi, const double* phiT, const float* R,
-              float* r_out, const float* fz, float* yz_out, int* err, cudaStream_t stream);
+              float* r_out, const float* fz, float* yz_out, int* err, cudaStream_t stream, bool bf16 = false);
 // which = 0: inverse, 1: forward.
 int tc_transform(TcPlan* plan, int which, cudaStream_t stream);
 // Device bytes the plan's tables hold.

@@ -304,3 +304,29 @@ def test_fused_multi_step_launch_is_bit_exact(M, C):
     assert np.array_equal(out[0], out[1])
     ref = O.Model(M, dtau=dtau).run_modes(R, 1, np.arange(C), 0, 37)
     assert rel_err(out[0], ref).max() < TOL[sfp.SFP_FP32]
+
+
+@pytest.mark.parametrize("M,C", [(256, 40), (512, 6), (64, 45)])
+def test_bf16_transforms_against_the_oracle(M, C):
+    """SFP_MIXED_BF16: the staged transforms with a three-pass BF16 hi/lo split
+    (about 16 bits per product).  One step's stages and a 100-step trajectory
+    against the oracle, with bounds from that precision: bonds are sums of
+    terms up to ~1e2 d, so ~1e-3 absolute; the state relative error ~1e-4."""
+    dtau = {64: 10.0, 256: 100.0, 512: 100.0}[M]
+    m = O.Model(M, dtau=dtau)
+    R0 = starts(M, C, dtau=dtau)
+    b = sfp.Batch([{"n_beads": M, "dtau": dtau}] * C, seed=1, precision=sfp.SFP_MIXED_BF16)
+    b.set_modes(R0)
+    b.step(1)
+    r_ref = np.stack([m.modes_to_beads(x) for x in R0])
+    u_ref = np.zeros_like(r_ref)
+    u_ref[:, :, 1:] = np.diff(r_ref, axis=2)
+    assert np.abs(b.probe(sfp.SFP_PROBE_BONDS) - u_ref).max() < 1e-2
+    z_ref = np.stack([O.bead_normals(1, j, 0, 0, M) for j in range(C)])
+    Z_ref = np.einsum("np,can->cap", m.tables()["phi"], z_ref)
+    assert np.abs(b.probe(sfp.SFP_PROBE_ZMODE) - Z_ref).max() < 1e-3
+    b.step(99)
+    ref = m.run_modes(R0, 1, np.arange(C), 0, 100)
+    e = rel_err(b.modes(), ref)
+    print("bf16", M, "trajectory error after 100 steps", e.max())
+    assert e.max() < 1e-3

@@ -22,7 +22,8 @@ def built():
 # whose slow amplitudes reach ~1e4 at 512 bp, so FP32 rounding of the state
 # shows there at ~1e-5 (measured 1.1e-5 and 1.3e-5 with the TF32 split).
 @pytest.mark.parametrize("precision,tol,tol_local", [(sfp.SFP_FP32, 1e-5, 1e-4), (sfp.SFP_FP32_SIMT, 1e-5, 1e-4),
-                                                     (sfp.SFP_FP64, 1e-9, 1e-9)], ids=["tf32x3", "fp32", "fp64"])
+                                                     (sfp.SFP_MIXED_BF16, 1e-3, 1e-2),
+                                                     (sfp.SFP_FP64, 1e-9, 1e-9)], ids=["tf32x3", "fp32", "bf16x3", "fp64"])
 def test_error_per_observable_16384x512(precision, tol, tol_local):
     e = errors(sfp, O, precision, steps=400, every=20, sub=8)
     print(precision, e)
