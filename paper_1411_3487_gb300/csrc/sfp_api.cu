@@ -929,11 +929,11 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
                                 precision == SFP_MIXED_BF16);
             if (rc) { destroy_impl(b); return rc; }
         }
-        if (precision == SFP_FP32 && sfp::fused_supported(M)) {
+        if ((precision == SFP_FP32 || precision == SFP_MIXED_BF16) && sfp::fused_supported(M)) {
             std::vector<double> w = g.tab.w;
             w[0] = g.tab.w0;
             rc = sfp::fused_create(&g.fused, M, g.C, g.tab.chi.data(), g.tab.phi.data(), g.tab.h.data(), w.data(),
-                                   (float*)g.R, b->stream);
+                                   (float*)g.R, b->stream, precision == SFP_MIXED_BF16);
             if (rc) { destroy_impl(b); return rc; }
         }
         b->held += sfp::tc_bytes(g.tc) + sfp::fused_bytes(g.fused);

@@ -41,8 +41,10 @@
 // frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <vector>
 
 #include "../../include/sfp.h"
@@ -62,15 +64,25 @@ constexpr int kComputeWarps = 16;
 constexpr int kCompute = 32 * kComputeWarps;  // 512 threads
 constexpr int kThreads = 64 + kCompute;
 
-template <int NB>
+// Shared memory of one CTA.  A stage holds [R (FP32, BF16 operands only)]
+// [A hi][A lo][B hi][B lo] for one K block of 32: TF32 operands are FP32-sized
+// with a 128-byte swizzle (the R tile is split in place in A hi); BF16
+// operands are 2 bytes with a 64-byte swizzle, the FP32 R tile converted from
+// its own staging tile.
+template <int NB, bool BF>
 struct FSmem {
-    static constexpr int kStages = NB == 256 ? 2 : NB == 128 ? 3 : 4;
-    static constexpr int kA = kRows * kKB * 4;            // 16 KB
-    static constexpr int kB = NB * kKB * 4;               // NB x 128 B
-    static constexpr int kStage = 2 * kA + 2 * kB;        // A hi, A lo, B hi, B lo
+    static constexpr int kEl = BF ? 2 : 4;
+    static constexpr int kA = kRows * kKB * kEl;          // 16 KB (TF32) / 8 KB (BF16)
+    static constexpr int kB = NB * kKB * kEl;             // NB x 128 B / NB x 64 B
+    static constexpr int kR = BF ? kRows * kKB * 4 : 0;   // FP32 R staging (BF16)
+    static constexpr int kStage = kR + 2 * kA + 2 * kB;
+    static constexpr int kStages = BF ? (192 * 1024) / kStage : (NB == 256 ? 2 : NB == 128 ? 3 : 4);
+    static constexpr int kRT = kRows * kKB * 4;           // an FP32 R block of the epilogue, 16 KB
     static constexpr int kU = kRows * kKB * 4;            // bond-vector staging
     static constexpr int kMisc = 4096;
     static constexpr int kBytes = kStages * kStage + kU + kMisc + 1024;
+    static_assert(kStages <= 4, "stage barriers");
+    static_assert(kStages * kStage >= NB / kKB * kRT, "the epilogue reloads the R tile into the stages");
 };
 
 // Byte offset of element (r, k), k < 32, in a 128-byte-swizzled K-major tile.
@@ -79,21 +91,39 @@ __device__ __forceinline__ uint32_t swz(int r, int k)
     return (uint32_t)(r * 128 + ((((k >> 2) ^ (r & 7)) << 4)) + ((k & 3) << 2));
 }
 
-__device__ __forceinline__ void put_hi_lo(uint8_t* hi, uint8_t* lo, int r, int k, float x)
+// Byte offset of element (r, k), k < 32, in a 64-byte-swizzled K-major BF16 tile.
+__device__ __forceinline__ uint32_t swz_bf(int r, int k)
 {
-    const float h = tf32_rna(x);
-    const uint32_t o = swz(r, k);
-    *reinterpret_cast<float*>(hi + o) = h;
-    *reinterpret_cast<float*>(lo + o) = tf32_rna(x - h);
+    return (uint32_t)(r * 64 + ((((k >> 3) ^ ((r >> 1) & 3)) << 4)) + ((k & 7) << 1));
 }
 
-template <int NB>
+__device__ __forceinline__ uint16_t bf16_rn(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float bf16_f(uint16_t h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
+
+// Operand element (r, k) as hi / lo parts: TF32 (rna) or BF16 (round to nearest even).
+template <bool BF>
+__device__ __forceinline__ void put_hi_lo(uint8_t* hi, uint8_t* lo, int r, int k, float x)
+{
+    if constexpr (BF) {
+        const uint16_t h = bf16_rn(x);
+        const uint32_t o = swz_bf(r, k);
+        *reinterpret_cast<uint16_t*>(hi + o) = h;
+        *reinterpret_cast<uint16_t*>(lo + o) = bf16_rn(x - bf16_f(h));
+    } else {
+        const float h = tf32_rna(x);
+        const uint32_t o = swz(r, k);
+        *reinterpret_cast<float*>(hi + o) = h;
+        *reinterpret_cast<float*>(lo + o) = tf32_rna(x - h);
+    }
+}
+
+template <int NB, bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
 k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmRst,
              const __grid_constant__ CUtensorMap tmChiH, const __grid_constant__ CUtensorMap tmChiL,
              const __grid_constant__ CUtensorMap tmFH, const __grid_constant__ CUtensorMap tmFL, const FusedArgs a)
 {
-    using S = FSmem<NB>;
+    using S = FSmem<NB, BF>;
     constexpr int ST = S::kStages;
     constexpr int KB = NB / kKB;        // inverse K blocks = forward bead blocks
     constexpr int NBLK = 3 * KB;        // inverse / noise blocks interleaved, then force blocks
@@ -181,11 +211,11 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 const uint32_t ph = (gb / ST) & 1;
                 if (!mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag)) { ok = false; break; }
                 uint8_t* st = stage0 + s * S::kStage;
-                uint8_t* bh = st + 2 * S::kA;
+                uint8_t* bh = st + S::kR + 2 * S::kA;
                 uint8_t* bl = bh + S::kB;
                 if (blk < 2 * KB && (blk & 1) == 0) {
-                    const int nb = blk >> 1;          // inverse: R tile and chi
-                    mbar_expect_tx(&full[s], S::kA + 2 * S::kB);
+                    const int nb = blk >> 1;          // inverse: R tile (FP32) and chi
+                    mbar_expect_tx(&full[s], S::kRT + 2 * S::kB);
                     tma_load_2d(st, &tmR, &full[s], nb * kKB, row0);
                     tma_load_2d(bh, &tmChiH, &full[s], nb * kKB, 0);
                     tma_load_2d(bl, &tmChiL, &full[s], nb * kKB, 0);
@@ -201,8 +231,8 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             // every stage is free once the forward MMAs are done: reload the R tile
             // (KB column blocks of 128 rows x 32) there for the epilogue
             if (ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag)) {
-                mbar_expect_tx(r_full, KB * S::kA);
-                for (int k = 0; k < KB; ++k) tma_load_2d(stage0 + k * S::kA, &tmR, r_full, k * kKB, row0);
+                mbar_expect_tx(r_full, KB * S::kRT);
+                for (int k = 0; k < KB; ++k) tma_load_2d(stage0 + k * S::kRT, &tmR, r_full, k * kKB, row0);
             } else {
                 ok = false;
             }
@@ -211,7 +241,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32(kRows, NB);
+            constexpr uint32_t idesc = BF ? idesc_bf16(kRows, NB) : idesc_tf32(kRows, NB);
             bool ok = true;
             for (int sp = 0; sp < a.n_steps; ++sp) {
             for (int blk = 0; blk < NBLK; ++blk) {
@@ -223,16 +253,26 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 if (ok) {
                     fence_after();
                     const uint32_t st = smem_u32(stage0 + s * S::kStage);
-                    const uint32_t a_hi = st, a_lo = st + S::kA, b_hi = st + 2 * S::kA, b_lo = b_hi + S::kB;
+                    const uint32_t a_hi = st + S::kR, a_lo = a_hi + S::kA, b_hi = a_lo + S::kA, b_lo = b_hi + S::kB;
                     const bool inv = blk < 2 * KB && (blk & 1) == 0;
                     const uint32_t d = inv ? t_u : t_inc;
                     const bool first = blk <= 1;       // first inverse block, first noise block
+                    if constexpr (BF) {
 #pragma unroll
-                    for (int kk = 0; kk < kKB / 8; ++kk) {
-                        const uint32_t off = kk * 32;   // 8 TF32 = 32 bytes along K
-                        mma_tf32(d, sdesc(a_hi + off), sdesc(b_lo + off), idesc, (first && kk == 0) ? 0u : 1u);
-                        mma_tf32(d, sdesc(a_lo + off), sdesc(b_hi + off), idesc, 1u);
-                        mma_tf32(d, sdesc(a_hi + off), sdesc(b_hi + off), idesc, 1u);
+                        for (int kk = 0; kk < kKB / 16; ++kk) {
+                            const uint32_t off = kk * 32;   // 16 BF16 = 32 bytes along K
+                            mma_bf16(d, sdesc64(a_hi + off), sdesc64(b_lo + off), idesc, (first && kk == 0) ? 0u : 1u);
+                            mma_bf16(d, sdesc64(a_lo + off), sdesc64(b_hi + off), idesc, 1u);
+                            mma_bf16(d, sdesc64(a_hi + off), sdesc64(b_hi + off), idesc, 1u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < kKB / 8; ++kk) {
+                            const uint32_t off = kk * 32;   // 8 TF32 = 32 bytes along K
+                            mma_tf32(d, sdesc(a_hi + off), sdesc(b_lo + off), idesc, (first && kk == 0) ? 0u : 1u);
+                            mma_tf32(d, sdesc(a_lo + off), sdesc(b_hi + off), idesc, 1u);
+                            mma_tf32(d, sdesc(a_hi + off), sdesc(b_hi + off), idesc, 1u);
+                        }
                     }
                 }
                 mma_commit(&empty[s]);
@@ -278,7 +318,33 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 const int blk = g0 + 2 * nb, s = blk % ST;
                 const uint32_t ph = (blk / ST) & 1;
                 ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
-                if (ok) {
+                if (ok && BF) {
+                    // row ct/4, BF16 chunk ct%4 (8 values) from the FP32 staging tile
+                    const uint8_t* r32 = stage0 + s * S::kStage;
+                    uint8_t* ah = stage0 + s * S::kStage + S::kR;
+                    uint8_t* al = ah + S::kA;
+                    const int r = ct >> 2, c = ct & 3;
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const float4 x = *reinterpret_cast<const float4*>(r32 + swz(r, 8 * c + 4 * h2));
+                        const float xs[4] = {x.x, x.y, x.z, x.w};
+                        uint16_t hh[4], ll[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            hh[i] = bf16_rn(xs[i]);
+                            ll[i] = bf16_rn(xs[i] - bf16_f(hh[i]));
+                        }
+                        hw[2 * h2] = (uint32_t)hh[0] | ((uint32_t)hh[1] << 16);
+                        hw[2 * h2 + 1] = (uint32_t)hh[2] | ((uint32_t)hh[3] << 16);
+                        lw[2 * h2] = (uint32_t)ll[0] | ((uint32_t)ll[1] << 16);
+                        lw[2 * h2 + 1] = (uint32_t)ll[2] | ((uint32_t)ll[3] << 16);
+                    }
+                    const uint32_t o = swz_bf(r, 8 * c);
+                    *reinterpret_cast<uint4*>(ah + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4*>(al + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    fence_proxy_async();
+                } else if (ok) {
                     float4* ah = (float4*)(stage0 + s * S::kStage);
                     float4* al = (float4*)(stage0 + s * S::kStage + S::kA);
 #pragma unroll
@@ -302,14 +368,14 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 const uint32_t ph = (blk / ST) & 1;
                 ok = ok && mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
                 if (ok) {
-                    uint8_t* ah = stage0 + s * S::kStage;
+                    uint8_t* ah = stage0 + s * S::kStage + S::kR;
                     uint8_t* al = ah + S::kA;
 #pragma unroll
                     for (int i = 0; i < kPer; ++i) {
                         const int c = cw + kComputeWarps * i;
                         if (c < a.cpt) {
 #pragma unroll
-                            for (int x = 0; x < 3; ++x) put_hi_lo(ah, al, 3 * c + x, lane, zz[i][x]);
+                            for (int x = 0; x < 3; ++x) put_hi_lo<BF>(ah, al, 3 * c + x, lane, zz[i][x]);
                         }
                     }
                     fence_proxy_async();
@@ -359,14 +425,14 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 const uint32_t ph = (blk / ST) & 1;
                 ok = ok && mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
                 if (ok) {
-                    uint8_t* ah = stage0 + s * S::kStage;
+                    uint8_t* ah = stage0 + s * S::kStage + S::kR;
                     uint8_t* al = ah + S::kA;
 #pragma unroll
                     for (int i = 0; i < kPer; ++i) {
                         const int c = cw + kComputeWarps * i;
                         if (c < a.cpt) {
 #pragma unroll
-                            for (int x = 0; x < 3; ++x) put_hi_lo(ah, al, 3 * c + x, lane, vv[i][x]);
+                            for (int x = 0; x < 3; ++x) put_hi_lo<BF>(ah, al, 3 * c + x, lane, vv[i][x]);
                         }
                     }
                     fence_proxy_async();
@@ -384,7 +450,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 #pragma unroll 1
         for (int k = grp; k < NB / 16; k += kComputeWarps / 4) {
             const int p0 = 16 * k;
-            uint8_t* blk = stage0 + (p0 / kKB) * S::kA;
+            uint8_t* blk = stage0 + (p0 / kKB) * S::kRT;
             const int kin = p0 % kKB;
             float d[16], r[16];
             tmem_ld16(t_inc + ((uint32_t)(32 * q) << 16) + (uint32_t)p0, d);
@@ -432,7 +498,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         named_bar(1, kCompute);   // tile and col0 complete
         if (ct == 0) {
             if (ok) {
-                for (int k = 0; k < KB; ++k) tma_store_2d(&tmRst, stage0 + k * S::kA, k * kKB, row0);
+                for (int k = 0; k < KB; ++k) tma_store_2d(&tmRst, stage0 + k * S::kRT, k * kKB, row0);
                 tma_store_commit();
                 tma_store_wait();   // R is in global memory and the stages are free again
             }
@@ -464,21 +530,55 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 
 struct FusedPlan {
     int M = 0, C = 0, cpt = kChains;
-    float* tab[4] = {nullptr, nullptr, nullptr, nullptr};   // chi_hi, chi_lo, F_hi, F_lo
+    bool bf16 = false;
+    void* tab[4] = {nullptr, nullptr, nullptr, nullptr};    // chi_hi, chi_lo, F_hi, F_lo (TF32 or BF16)
     float* R = nullptr;
     CUtensorMap tmR, tmRst, tmChiH, tmChiL, tmFH, tmFL;
 };
 
 bool fused_supported(int M) { return M == 64 || M == 128 || M == 256; }
 
-template <int NB>
+template <int NB, bool BF>
 static cudaError_t set_smem()
 {
-    return cudaFuncSetAttribute(k_fused_step<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, FSmem<NB>::kBytes);
+    return cudaFuncSetAttribute(k_fused_step<NB, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, FSmem<NB, BF>::kBytes);
+}
+
+// 2-D BF16 table [rows][cols], box 32 cols x box_rows, 64-byte swizzle.
+static int make_map_bf16(CUtensorMap* m, const void* base, int rows, int cols, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return report(SFP_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kKB, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return report(SFP_ECUDA, "cuTensorMapEncodeTiled (bf16) failed");
+    return SFP_OK;
+}
+
+static uint16_t bf16_host(double x)
+{
+    const float f = (float)x;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);   // round to nearest even
+    return (uint16_t)(u >> 16);
+}
+
+static double bf16_value(uint16_t h)
+{
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
 }
 
 int fused_create(FusedPlan** out, int M, int C, const double* chi, const double* phi, const double* h,
-                 const double* w, float* R, cudaStream_t stream)
+                 const double* w, float* R, cudaStream_t stream, bool bf16)
 {
     *out = nullptr;
     if (!fused_supported(M)) return report(SFP_ENOTSUP, "the fused step needs M in {64, 128, 256}");
@@ -486,6 +586,7 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
     p->M = M;
     p->C = C;
     p->R = R;
+    p->bf16 = bf16;
     // one wave: chains per tile = ceil(C / SMs), at most 42 (fused_set_tile changes it)
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -503,20 +604,28 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
         }
     const double* src[2] = {chi, F.data()};
     const size_t cnt[2] = {mm, 2 * mm};
+    const size_t el = bf16 ? 2 : 4;
     for (int t = 0; t < 2; ++t) {
         std::vector<float> hi(cnt[t]), lo(cnt[t]);
+        std::vector<uint16_t> hb(bf16 ? cnt[t] : 0), lb(bf16 ? cnt[t] : 0);
         for (size_t i = 0; i < cnt[t]; ++i) {
-            hi[i] = tf32_round_host(src[t][i]);
-            lo[i] = tf32_round_host(src[t][i] - (double)hi[i]);
+            if (bf16) {
+                hb[i] = bf16_host(src[t][i]);
+                lb[i] = bf16_host(src[t][i] - bf16_value(hb[i]));
+            } else {
+                hi[i] = tf32_round_host(src[t][i]);
+                lo[i] = tf32_round_host(src[t][i] - (double)hi[i]);
+            }
         }
         for (int k = 0; k < 2; ++k) {
-            float*& d = p->tab[2 * t + k];
-            if (cudaMalloc(&d, cnt[t] * sizeof(float)) != cudaSuccess) {
+            void*& d = p->tab[2 * t + k];
+            const void* hsrc = bf16 ? (const void*)(k == 0 ? hb.data() : lb.data())
+                                    : (const void*)(k == 0 ? hi.data() : lo.data());
+            if (cudaMalloc(&d, cnt[t] * el) != cudaSuccess) {
                 fused_destroy(p);
                 return report(SFP_ENOMEM, "fused-step table allocation failed");
             }
-            if (cudaMemcpyAsync(d, k == 0 ? hi.data() : lo.data(), cnt[t] * sizeof(float), cudaMemcpyHostToDevice,
-                                stream) != cudaSuccess ||
+            if (cudaMemcpyAsync(d, hsrc, cnt[t] * el, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
                 cudaStreamSynchronize(stream) != cudaSuccess) {
                 fused_destroy(p);
                 return report(SFP_ECUDA, "fused-step table upload failed");
@@ -525,14 +634,25 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
     }
     int rc;
     // the store box is the tile's 3 cpt rows: a tile must not write the next tile's chains
-    if ((rc = make_map_2d(&p->tmR, R, 3 * C, M, kRows)) || (rc = make_map_2d(&p->tmRst, R, 3 * C, M, 3 * p->cpt)) ||
-        (rc = make_map_2d(&p->tmChiH, p->tab[0], M, M, M)) ||
-        (rc = make_map_2d(&p->tmChiL, p->tab[1], M, M, M)) || (rc = make_map_2d(&p->tmFH, p->tab[2], 2 * M, M, M)) ||
-        (rc = make_map_2d(&p->tmFL, p->tab[3], 2 * M, M, M))) {
+    if ((rc = make_map_2d(&p->tmR, R, 3 * C, M, kRows)) || (rc = make_map_2d(&p->tmRst, R, 3 * C, M, 3 * p->cpt))) {
         fused_destroy(p);
         return rc;
     }
-    const cudaError_t e = M == 256 ? set_smem<256>() : M == 128 ? set_smem<128>() : set_smem<64>();
+    if (bf16)
+        rc = make_map_bf16(&p->tmChiH, p->tab[0], M, M, M) ? -1 : make_map_bf16(&p->tmChiL, p->tab[1], M, M, M) ? -1 :
+             make_map_bf16(&p->tmFH, p->tab[2], 2 * M, M, M) ? -1 : make_map_bf16(&p->tmFL, p->tab[3], 2 * M, M, M);
+    else
+        rc = make_map_2d(&p->tmChiH, (const float*)p->tab[0], M, M, M) ? -1 :
+             make_map_2d(&p->tmChiL, (const float*)p->tab[1], M, M, M) ? -1 :
+             make_map_2d(&p->tmFH, (const float*)p->tab[2], 2 * M, M, M) ? -1 :
+             make_map_2d(&p->tmFL, (const float*)p->tab[3], 2 * M, M, M);
+    if (rc) {
+        fused_destroy(p);
+        return SFP_ECUDA;
+    }
+    cudaError_t e;
+    if (bf16) e = M == 256 ? set_smem<256, true>() : M == 128 ? set_smem<128, true>() : set_smem<64, true>();
+    else e = M == 256 ? set_smem<256, false>() : M == 128 ? set_smem<128, false>() : set_smem<64, false>();
     if (e != cudaSuccess) {
         fused_destroy(p);
         return report(SFP_ECUDA, "cudaFuncSetAttribute (fused step) failed");
@@ -545,19 +665,19 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
 {
     if (args.cpt != p->cpt) return report(SFP_EINVAL, "fused step: chains per tile differ from the plan's");
     const dim3 grid((unsigned)((p->C + p->cpt - 1) / p->cpt));
-    switch (p->M) {
-        case 256:
-            k_fused_step<256><<<grid, kThreads, FSmem<256>::kBytes, stream>>>(p->tmR, p->tmRst, p->tmChiH, p->tmChiL, p->tmFH, p->tmFL, args);
-            break;
-        case 128:
-            k_fused_step<128><<<grid, kThreads, FSmem<128>::kBytes, stream>>>(p->tmR, p->tmRst, p->tmChiH, p->tmChiL, p->tmFH, p->tmFL, args);
-            break;
-        case 64:
-            k_fused_step<64><<<grid, kThreads, FSmem<64>::kBytes, stream>>>(p->tmR, p->tmRst, p->tmChiH, p->tmChiL, p->tmFH, p->tmFL, args);
-            break;
-        default:
-            return report(SFP_ENOTSUP, "unsupported fused-step length");
+#define SFP_FUSED_LAUNCH(NBV, BFV)                                                                   \
+    k_fused_step<NBV, BFV><<<grid, kThreads, FSmem<NBV, BFV>::kBytes, stream>>>(p->tmR, p->tmRst, p->tmChiH, \
+                                                                            p->tmChiL, p->tmFH, p->tmFL, args)
+    switch (p->M * 2 + (p->bf16 ? 1 : 0)) {
+        case 512: SFP_FUSED_LAUNCH(256, false); break;
+        case 513: SFP_FUSED_LAUNCH(256, true); break;
+        case 256: SFP_FUSED_LAUNCH(128, false); break;
+        case 257: SFP_FUSED_LAUNCH(128, true); break;
+        case 128: SFP_FUSED_LAUNCH(64, false); break;
+        case 129: SFP_FUSED_LAUNCH(64, true); break;
+        default: return report(SFP_ENOTSUP, "unsupported fused-step length");
     }
+#undef SFP_FUSED_LAUNCH
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return report(SFP_ECUDA, cudaGetErrorString(e));
     return SFP_OK;
@@ -565,7 +685,7 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
 
 int fused_tile(const FusedPlan* p) { return p->cpt; }
 
-size_t fused_bytes(const FusedPlan* p) { return p ? (size_t)6 * p->M * p->M * sizeof(float) : 0; }
+size_t fused_bytes(const FusedPlan* p) { return p ? (size_t)6 * p->M * p->M * (p->bf16 ? 2 : 4) : 0; }
 
 int fused_set_tile(FusedPlan* p, int cpt)
 {
@@ -581,7 +701,7 @@ int fused_set_tile(FusedPlan* p, int cpt)
 void fused_destroy(FusedPlan* p)
 {
     if (!p) return;
-    for (float* t : p->tab)
+    for (void* t : p->tab)
         if (t) cudaFree(t);
     delete p;
 }

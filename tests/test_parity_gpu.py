@@ -315,7 +315,7 @@ def test_bf16_transforms_against_the_oracle(M, C):
     dtau = {64: 10.0, 256: 100.0, 512: 100.0}[M]
     m = O.Model(M, dtau=dtau)
     R0 = starts(M, C, dtau=dtau)
-    b = sfp.Batch([{"n_beads": M, "dtau": dtau}] * C, seed=1, precision=sfp.SFP_MIXED_BF16)
+    b = make_batch(M, C, dtau, (sfp.SFP_MIXED_BF16, sfp.SFP_PATH_STAGED))
     b.set_modes(R0)
     b.step(1)
     r_ref = np.stack([m.modes_to_beads(x) for x in R0])
@@ -330,3 +330,38 @@ def test_bf16_transforms_against_the_oracle(M, C):
     e = rel_err(b.modes(), ref)
     print("bf16", M, "trajectory error after 100 steps", e.max())
     assert e.max() < 1e-3
+
+
+@pytest.mark.parametrize("M,C", [(256, 50), (128, 90), (64, 100)])
+def test_bf16_fused_step_against_the_oracle(M, C):
+    """SFP_MIXED_BF16 on the one-kernel step (kind::f16 MMAs on BF16 hi/lo
+    operands, the R tile split in the kernel): 1000 steps against the oracle.
+    A three-pass BF16 product carries ~17 bits, so the per-step error is a few
+    1e-7 of the state and the 1000-step bound is the FP32 one, 1e-5.  The staged
+    BF16 path rounds the force in bead space (phi^T f, terms up to ~1e2 larger
+    than their sum) and is held to 2e-5 on the same trajectory."""
+    dtau = {64: 10.0, 128: 50.0, 256: 100.0}[M]
+    m = O.Model(M, dtau=dtau)
+    R = starts(M, C, dtau=dtau)
+    fused = make_batch(M, C, dtau, (sfp.SFP_MIXED_BF16, sfp.SFP_PATH_FUSED))
+    staged = make_batch(M, C, dtau, (sfp.SFP_MIXED_BF16, sfp.SFP_PATH_STAGED))
+    fused.set_modes(R)
+    staged.set_modes(R)
+    done = 0
+    for mark in (1, 100, 1000):
+        R = m.run_modes(R, 1, np.arange(C), done, mark - done)
+        fused.step(mark - done)
+        staged.step(mark - done)
+        done = mark
+        G = fused.modes()
+        e = rel_err(G, R)
+        print("bf16 fused", M, "step", mark, "error", e.max())
+        assert e.max() < 1e-5, (mark, e.max())
+        es = rel_err(staged.modes(), R)
+        print("bf16 staged", M, "step", mark, "error", es.max())
+        assert es.max() < 2e-5, (mark, es.max())
+        dcm = np.abs(G[:, :, 0] - R[:, :, 0]).max() / math.sqrt(M)
+        assert dcm < 1e-5 * math.sqrt(6 * TSTAR * dtau * mark / M) + 1e-9
+    assert np.all(fused.observe(sfp.SFP_OBS_STEP) == 1000)
+    with pytest.raises(sfp.SfpError):
+        fused.probe(sfp.SFP_PROBE_DH)
