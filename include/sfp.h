@@ -181,9 +181,10 @@ int sfp_set_path(sfp_batch *b, int32_t path);
  * several length groups runs each group on its own stream, forked from and
  * joined back into the batch's stream, so the groups share the GPU.
  * sfp_autotune(b, trial_steps, out): chooses the chains per tile of every
- * fused group (1..42) by timing candidates for trial_steps steps, alone and
- * together; the state, noise counters and trajectory are restored after every
- * trial (it allocates a temporary copy of the state outside the HBM budget).
+ * fused group (4..40, a multiple of 4) by timing candidates for trial_steps
+ * steps, alone and together; the state, noise counters and trajectory are
+ * restored after every trial (it allocates a temporary copy of the state
+ * outside the HBM budget).
  * out, if not NULL, receives each group's choice (0 for staged groups), in
  * order of first appearance of each (n_beads, dtau) in the chain list. */
 int sfp_set_graph(sfp_batch *b, int32_t enable);

@@ -1384,9 +1384,9 @@ int sfp_autotune(sfp_batch* b, int32_t trial_steps, int32_t* chains_per_tile)
         std::vector<int> cs;
         for (double f : {1.0, 0.75, 0.5, 1.0 / 3.0, 0.25}) {
             const int target = std::max(1, (int)(f * sms));
-            cs.push_back(std::max(1, std::min(42, (g.C + target - 1) / target)));
+            cs.push_back(std::min(40, ((g.C + target - 1) / target + 3) / 4 * 4));
         }
-        cs.push_back(42);
+        cs.push_back(40);
         std::sort(cs.begin(), cs.end());
         cs.erase(std::unique(cs.begin(), cs.end()), cs.end());
         for (int c : cs) {

@@ -1,10 +1,16 @@
-// sfp_fused.cu -- mode-space steps (Sec. 4) for tiles of 42 chains of the
-// SFP_FP32 path, M = 64, 128 or 256 beads, n_steps per launch.
+// sfp_fused.cu -- mode-space steps (Sec. 4) for tiles of up to 40 chains of
+// the SFP_FP32 and SFP_MIXED_BF16 paths, M = 64, 128 or 256 beads, n_steps
+// per launch.
 //
-// A tile's chain-axis rows j = 3c + alpha (up to 42 chains, 126 rows; the
-// rest padding) are the 128 TMEM lanes; bead / mode indices are TMEM
+// The 128 TMEM lanes hold a tile's chain-axis rows: lane quarter q (rows
+// 32 q .. 32 q + 31) holds chains q cpq .. q cpq + cpq - 1 of the tile
+// (cpq <= 10 chains per quarter), chain k of the quarter in rows 32 q + 3 k +
+// alpha; the rest of a quarter is padding.  A chain's three axes therefore sit
+// in three lanes of one warp, so |u_n| and the shear term take warp shuffles
+// instead of a trip through shared memory.  Bead / mode indices are TMEM
 // columns.  Fewer chains per tile give more CTAs on small batches: the MMA
-// time of a tile is fixed by its 128 rows, the noise and force work is not.  Per step and tile:
+// time of a tile is fixed by its 128 rows, the noise and force work is not.
+// Per step and tile:
 //   inverse  (Eq. e5)   D_u[j][n]   = sum_p R[j][p] chi[n][p]            (bonds)
 //   force    (Eq. e11)  v_n = u_n (1/|u_n| - (1 - 2 nu)),  v_0 = 0
 //   noise    (Eq. b5)   z_n ~ N(0,1), Philox keyed by (seed, job, step, n)
@@ -14,31 +20,31 @@
 //   update   (Eqs. d3, btum)  R_p += -(1 - e^{-zeta_p dtau}) R_p + D_inc_p
 //                             (+ shear g_p R^y_p on the x rows); p = 0 feeds the
 //                             FP64 centre of mass.
-// ΔH is never formed on its own: Eq. e11 makes it chi^T v, so the bead-space
-// stencil of the staged path is not needed, and h_p, w_p are folded into one
-// stacked table so a single accumulator holds the whole increment.
+// DeltaH is never formed on its own: Eq. e11 makes it chi^T v, so the
+// bead-space stencil of the staged path is not needed, and h_p, w_p are folded
+// into one stacked table so a single accumulator holds the whole increment.
 //
-// Both contractions run on the tcgen05 tensor cores as three TF32 passes
-// (A_hi B_lo + A_lo B_hi + A_hi B_hi, FP32 accumulate in TMEM), which keeps
-// FP32 accuracy.  Roles (576 threads):
-//   warp 0      TMA producer: R tiles and chi hi/lo (inverse), F hi/lo (forward)
-//   warp 1      TMEM allocation; one thread issues every MMA and commit
-//   warps 2..17 split R tiles into TF32 hi/lo; read D_u (warps 2..5) into a
-//               swizzled staging buffer; write v and z blocks (hi/lo) as the
-//               A operand of the forward MMAs; epilogue from D_inc.  Sixteen
-//               warps keep enough Philox / Box-Muller chains in flight to
-//               hide their latency behind the MMAs.
-// Block order (K blocks of 32): inverse block nb and noise block nb alternate
-// (inv 0, z 0, inv 1, z 1, ...), then the force blocks v 0 .. v KB-1.  The
-// noise half of the forward contraction does not depend on the state, so its
-// Philox / Box-Muller work overlaps the inverse MMAs; only the force blocks
-// wait for the bond vectors.
+// Both contractions run on the tcgen05 tensor cores as three passes
+// (A_hi B_lo + A_lo B_hi + A_hi B_hi, FP32 accumulate in TMEM): TF32 parts
+// (kind::tf32) for SFP_FP32, BF16 parts (kind::f16) for SFP_MIXED_BF16.
+// Roles (768 threads):
+//   warp 0       TMA producer: R tiles and chi hi/lo (inverse), F hi/lo (forward)
+//   warp 1       TMEM allocation; one thread issues every MMA and commit
+//   warps 2..9   compute: split the R tiles into hi/lo, read D_u (two warps per
+//                lane quarter) and write the force blocks, epilogue from D_inc
+//   warps 10..23 noise: Philox / Box-Muller normals written as the noise
+//                blocks; the most arithmetic of a step, on warps of their own
+//                so that it runs beside the R split and the force
+// Block order (K blocks of 32; sched_decode): the inverse blocks first, with
+// half of the noise blocks between them, then the force blocks with the other
+// half.  The noise half of the forward contraction does not depend on the
+// state; only the force blocks wait for the bond vectors.
 // Chains never interact, so a CTA runs all n_steps of its tile without any
 // grid-wide synchronisation: TMEM stays allocated, the tables stream again
 // from L2, and the state goes through global memory (L2) between steps.
-// Every mbarrier wait is bounded (1 s); after a timeout the CTA raises bit 1
-// of the error word, skips all further work but still passes every barrier,
-// frees its TMEM and returns.
+// Every wait is bounded (1 s); after a timeout the CTA raises bit 1 of the
+// error word, skips all further work but still passes every barrier, frees
+// its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -58,11 +64,16 @@ namespace {
 using namespace ptx;
 
 constexpr int kRows = 128;                   // UMMA M = TMEM lanes
-constexpr int kChains = 42;                  // most chains per tile (126 of 128 rows)
+constexpr int kChains = 40;                  // most chains per tile: 10 per TMEM lane quarter
+constexpr int kQuarter = 32 * 128;           // bytes of 32 rows of a 128-byte-swizzled tile
 constexpr int kKB = 32;                      // K block: 32 FP32 = one 128-byte swizzle row
-constexpr int kComputeWarps = 16;
-constexpr int kCompute = 32 * kComputeWarps;  // 512 threads
-constexpr int kThreads = 64 + kCompute;
+constexpr int kComputeWarps = 8;             // R split, residual force, epilogue
+constexpr int kNoiseWarps = 14;              // Philox normals of the noise blocks
+constexpr int kCompute = 32 * kComputeWarps;  // 256 threads
+constexpr int kThreads = 64 + kCompute + 32 * kNoiseWarps;
+// A stage's A operand is written by one group, whose warps arrive once each
+// (lane 0, after __syncwarp) with weights that add up to the same count.
+constexpr int kReadyCount = kComputeWarps * kNoiseWarps;
 
 // Shared memory of one CTA.  A stage holds [R (FP32, BF16 operands only)]
 // [A hi][A lo][B hi][B lo] for one K block of 32: TF32 operands are FP32-sized
@@ -78,9 +89,9 @@ struct FSmem {
     static constexpr int kStage = kR + 2 * kA + 2 * kB;
     static constexpr int kStages = BF ? (192 * 1024) / kStage : (NB == 256 ? 2 : NB == 128 ? 3 : 4);
     static constexpr int kRT = kRows * kKB * 4;           // an FP32 R block of the epilogue, 16 KB
-    static constexpr int kU = kRows * kKB * 4;            // bond-vector staging
-    static constexpr int kMisc = 4096;
-    static constexpr int kBytes = kStages * kStage + kU + kMisc + 1024;
+    static constexpr int kMisc = 4096;   // per-chain keys, steps, shear, stops; tables; barriers
+    static constexpr int kBytes = kStages * kStage + kMisc + 1024;
+    static_assert(kBytes <= 227 * 1024, "shared memory of one CTA");
     static_assert(kStages <= 4, "stage barriers");
     static_assert(kStages * kStage >= NB / kKB * kRT, "the epilogue reloads the R tile into the stages");
 };
@@ -117,32 +128,68 @@ __device__ __forceinline__ void put_hi_lo(uint8_t* hi, uint8_t* lo, int r, int k
     }
 }
 
+// Order of the 3 KB blocks of one step (KB = NB / 32 bead blocks, H = KB / 2).
+// Inverse blocks I_k (R chi^T into D_u) come first, noise blocks N_j (w phi^T z)
+// and force blocks F_k (h chi^T v) accumulate into D_inc.  The noise blocks are
+// spread over both phases so that the noise warps draw while the compute warps
+// split R (phase 1) or form the force (phase 2):
+//   phase 1: I_0 N_0 I_1 | I_2 N_1 I_3 | ... (3 H blocks, ends with I_{KB-1})
+//   phase 2: F_0 N_H | F_1 N_{H+1} | ... | F_{H-1} N_{KB-1} | F_H ... F_{KB-1}
+template <int KB>
+__device__ __forceinline__ void sched_decode(int blk, int& kind, int& nb)   // kind: 0 I, 1 N, 2 F
+{
+    constexpr int H = KB / 2;
+    if (blk < 3 * H) {
+        const int m = blk / 3, r = blk - 3 * (blk / 3);
+        kind = r == 1 ? 1 : 0;
+        nb = r == 0 ? 2 * m : r == 1 ? m : 2 * m + 1;
+    } else {
+        const int b = blk - 3 * H;
+        if (b < 2 * H) {
+            kind = (b & 1) ? 1 : 2;
+            nb = (b & 1) ? H + (b >> 1) : b >> 1;
+        } else {
+            kind = 2;
+            nb = b - H;
+        }
+    }
+}
+template <int KB> __device__ __forceinline__ int sched_inv(int k) { return 3 * (k >> 1) + ((k & 1) ? 2 : 0); }
+template <int KB> __device__ __forceinline__ int sched_noise(int j)
+{
+    return j < KB / 2 ? 3 * j + 1 : 3 * (KB / 2) + 2 * (j - KB / 2) + 1;
+}
+template <int KB> __device__ __forceinline__ int sched_force(int k)
+{
+    return k < KB / 2 ? 3 * (KB / 2) + 2 * k : 2 * KB + k;
+}
+
 template <int NB, bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
-k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmRst,
-             const __grid_constant__ CUtensorMap tmChiH, const __grid_constant__ CUtensorMap tmChiL,
-             const __grid_constant__ CUtensorMap tmFH, const __grid_constant__ CUtensorMap tmFL, const FusedArgs a)
+k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmChiH,
+             const __grid_constant__ CUtensorMap tmChiL, const __grid_constant__ CUtensorMap tmFH,
+             const __grid_constant__ CUtensorMap tmFL, const FusedArgs a)
 {
     using S = FSmem<NB, BF>;
     constexpr int ST = S::kStages;
     constexpr int KB = NB / kKB;        // inverse K blocks = forward bead blocks
-    constexpr int NBLK = 3 * KB;        // inverse / noise blocks interleaved, then force blocks
+    constexpr int NBLK = 3 * KB;        // blocks of one step, in the order of sched_decode
+    static_assert(KB % 2 == 0, "the block schedule pairs bead blocks");
     constexpr uint32_t kCols = 2 * NB;  // D_u in [0, NB), D_inc in [NB, 2 NB)
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* stage0 = smem;
-    float* U = (float*)(smem + ST * S::kStage);
-    uint8_t* misc = smem + ST * S::kStage + S::kU;
+    uint8_t* misc = smem + ST * S::kStage;
     uint32_t* s_job = (uint32_t*)misc;
     int64_t* s_step = (int64_t*)(misc + 256);
-    double* s_shear = (double*)(misc + 640);
-    float* s_dm = (float*)(misc + 1024);
-    float* s_g = (float*)(misc + 2048);
-    uint64_t* bars = (uint64_t*)(misc + 3072);
-    int64_t* s_stop = (int64_t*)(misc + 3328);
+    double* s_shear = (double*)(misc + 576);
+    int64_t* s_stop = (int64_t*)(misc + 896);
+    float* s_dm = (float*)(misc + 1216);        // NB <= 256
+    float* s_g = (float*)(misc + 2240);
+    uint64_t* bars = (uint64_t*)(misc + 3264);
     uint64_t* full = bars;              // TMA bytes landed                 (1 + tx)
-    uint64_t* ready = bars + 4;         // A operand prepared by threads    (256)
+    uint64_t* ready = bars + 4;         // A operand written by one group   (kReadyCount)
     uint64_t* empty = bars + 8;         // MMAs done with the stage         (commit)
     uint64_t* u_done = bars + 12;       // all inverse MMAs done            (commit)
     uint64_t* inc_done = bars + 13;     // all forward MMAs done            (commit)
@@ -150,16 +197,18 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     uint64_t* epi_done = bars + 15;     // epilogue stored R, stages free   (1)
     uint32_t* tmem_slot = (uint32_t*)(bars + 16);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    int* s_freed = (int*)(tmem_slot + 2);   // last block whose stage the producer saw released
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cpq = a.cpt >> 2;         // chains per TMEM lane quarter (rows 32 q + 3 k + axis)
     const int c0 = blockIdx.x * a.cpt;
     const int Ct = min(a.cpt, a.C - c0);
-    const int row0 = 3 * c0;
+    const uint32_t rblock = 4u * 3u * (uint32_t)cpq * 128u;   // bytes of one R column block
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < ST; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&ready[s], kCompute);
+            mbar_init(&ready[s], kReadyCount);
             mbar_init(&empty[s], 1);
         }
         mbar_init(u_done, 1);
@@ -167,13 +216,17 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         mbar_init(r_full, 1);
         mbar_init(epi_done, 1);
         *abort_flag = 0;
+        *s_freed = -1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmR)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmRst)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmChiH)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmChiL)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmFH)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmFL)) : "memory");
+    }
+    for (int p = threadIdx.x; p < NB; p += kThreads) {
+        s_dm[p] = a.dm[p];
+        s_g[p] = a.g[p];
     }
     for (int i = threadIdx.x; i < kChains; i += kThreads) {
         const bool live = i < Ct;
@@ -181,10 +234,6 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         s_step[i] = live ? a.step[c0 + i] : 0;
         s_stop[i] = (live && a.stop) ? a.stop[c0 + i] : INT64_MAX;
         s_shear[i] = live ? a.shear[c0 + i] : 0.0;
-    }
-    for (int p = threadIdx.x; p < NB; p += kThreads) {
-        s_dm[p] = a.dm[p];
-        s_g[p] = a.g[p];
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -210,29 +259,34 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 const int s = gb % ST;
                 const uint32_t ph = (gb / ST) & 1;
                 if (!mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag)) { ok = false; break; }
+                st_release_smem(s_freed, gb);   // block gb may be written into stage s
                 uint8_t* st = stage0 + s * S::kStage;
                 uint8_t* bh = st + S::kR + 2 * S::kA;
                 uint8_t* bl = bh + S::kB;
-                if (blk < 2 * KB && (blk & 1) == 0) {
-                    const int nb = blk >> 1;          // inverse: R tile (FP32) and chi
-                    mbar_expect_tx(&full[s], S::kRT + 2 * S::kB);
-                    tma_load_2d(st, &tmR, &full[s], nb * kKB, row0);
+                int kind, nb;
+                sched_decode<KB>(blk, kind, nb);
+                if (kind == 0) {
+                    // inverse: the R tile (FP32, one box per lane quarter) and chi
+                    mbar_expect_tx(&full[s], rblock + 2 * S::kB);
                     tma_load_2d(bh, &tmChiH, &full[s], nb * kKB, 0);
                     tma_load_2d(bl, &tmChiL, &full[s], nb * kKB, 0);
+                    for (int q = 0; q < 4; ++q)
+                        tma_load_2d(st + q * kQuarter, &tmR, &full[s], nb * kKB, 3 * (c0 + q * cpq));
                 } else {
                     // noise block nb: rows w_p phi (t = 1); force block nb: rows h_p chi (t = 0)
-                    const bool noise = blk < 2 * KB;
-                    const int nb = noise ? blk >> 1 : blk - 2 * KB;
+                    const bool noise = kind == 1;
                     mbar_expect_tx(&full[s], 2 * S::kB);
                     tma_load_2d(bh, &tmFH, &full[s], nb * kKB, noise ? NB : 0);
                     tma_load_2d(bl, &tmFL, &full[s], nb * kKB, noise ? NB : 0);
                 }
             }
             // every stage is free once the forward MMAs are done: reload the R tile
-            // (KB column blocks of 128 rows x 32) there for the epilogue
+            // (KB column blocks of [128 rows][32]) there for the epilogue
             if (ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag)) {
-                mbar_expect_tx(r_full, KB * S::kRT);
-                for (int k = 0; k < KB; ++k) tma_load_2d(stage0 + k * S::kRT, &tmR, r_full, k * kKB, row0);
+                mbar_expect_tx(r_full, KB * rblock);
+                for (int k = 0; k < KB; ++k)
+                    for (int q = 0; q < 4; ++q)
+                        tma_load_2d(stage0 + k * S::kRT + q * kQuarter, &tmR, r_full, k * kKB, 3 * (c0 + q * cpq));
             } else {
                 ok = false;
             }
@@ -248,14 +302,15 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 const int gb = sp * NBLK + blk;
                 const int s = gb % ST;
                 const uint32_t ph = (gb / ST) & 1;
+                int kind, nb;
+                sched_decode<KB>(blk, kind, nb);
                 ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
                 ok = ok && mbar_wait(&ready[s], ph, a.err, abort_flag);
                 if (ok) {
                     fence_after();
                     const uint32_t st = smem_u32(stage0 + s * S::kStage);
                     const uint32_t a_hi = st + S::kR, a_lo = a_hi + S::kA, b_hi = a_lo + S::kA, b_lo = b_hi + S::kB;
-                    const bool inv = blk < 2 * KB && (blk & 1) == 0;
-                    const uint32_t d = inv ? t_u : t_inc;
+                    const uint32_t d = kind == 0 ? t_u : t_inc;
                     const bool first = blk <= 1;       // first inverse block, first noise block
                     if constexpr (BF) {
 #pragma unroll
@@ -276,54 +331,113 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                     }
                 }
                 mma_commit(&empty[s]);
-                if (blk == 2 * KB - 2) mma_commit(u_done);
+                if (blk == sched_inv<KB>(KB - 1)) mma_commit(u_done);
             }
             mma_commit(inc_done);
             }
         }
-    } else {
-        // ---------------- compute warps 2..17
-        const int cw = warp - 2;            // 0..15
-        const int ct = threadIdx.x - 64;    // 0..511
-        const int q = warp & 3;             // TMEM lane quarter this warp may access
+    } else if (warp >= 2 + kComputeWarps) {
+        // ---------------- noise warps: Philox normals of noise block j (Eq. b5),
+        // drawn into registers, then written as hi / lo operands once the stage is
+        // free.  Chains c = nw + kNoiseWarps i of the tile, bead n = 32 j + lane.
+        const int nw = warp - 2 - kComputeWarps;
+        constexpr int kPerN = (kChains + kNoiseWarps - 1) / kNoiseWarps;
+        int rb[kPerN];                  // first row of each chain: 32 quarter + 3 slot
+#pragma unroll
+        for (int i = 0; i < kPerN; ++i) {
+            const int c = nw + kNoiseWarps * i;
+            rb[i] = c < a.cpt ? 32 * (c / cpq) + 3 * (c % cpq) : -1;
+        }
         bool ok = true;
-
-        constexpr int kPer = (kChains + kComputeWarps - 1) / kComputeWarps;   // 3
-        // Each warp owns chains c = cw + 16 i (i < 3) and bead n = 32 nb + lane of
-        // every force / noise block; values are computed into registers first and
-        // written once the stage is free, so the arithmetic overlaps earlier MMAs.
-
-        const int grp = cw >> 2;                      // 4 groups of 4 warps (one per lane quarter)
+#pragma unroll 1
+        for (int sp = 0; sp < a.n_steps; ++sp) {
+#pragma unroll 1
+            for (int j = 0; j < KB; ++j) {
+                const int n = j * kKB + lane;
+                // The first kPerN - 1 chain slots (30 chains) are drawn without a
+                // branch, so their Philox / Box-Muller chains interleave; a slot past
+                // the tile's chains draws for job 0 and is zeroed.
+                float zz[kPerN][3];
+#pragma unroll
+                for (int i = 0; i < kPerN - 1; ++i) {
+                    const int c = nw + kNoiseWarps * i;
+                    Normals<float>::draw(a.seed, s_job[c], s_step[c] + sp, (uint32_t)n, 0u, zz[i]);
+                }
+                zz[kPerN - 1][0] = zz[kPerN - 1][1] = zz[kPerN - 1][2] = 0.f;
+                if (nw + kNoiseWarps * (kPerN - 1) < Ct)
+                    Normals<float>::draw(a.seed, s_job[nw + kNoiseWarps * (kPerN - 1)],
+                                         s_step[nw + kNoiseWarps * (kPerN - 1)] + sp, (uint32_t)n, 0u, zz[kPerN - 1]);
+#pragma unroll
+                for (int i = 0; i < kPerN - 1; ++i)
+                    if (nw + kNoiseWarps * i >= Ct) zz[i][0] = zz[i][1] = zz[i][2] = 0.f;
+                const int blk = sp * NBLK + sched_noise<KB>(j), s = blk % ST;
+                // Consecutive noise blocks may lie more than ST blocks apart, where a
+                // parity wait on the stage's barrier is ambiguous: wait instead until
+                // the producer has seen the stage released for this block (which it
+                // does in block order, after the previous step's epilogue).
+                ok = ok && count_wait(s_freed, blk, a.err, abort_flag);
+                if (ok) {
+                    uint8_t* ah = stage0 + s * S::kStage + S::kR;
+                    uint8_t* al = ah + S::kA;
+#pragma unroll
+                    for (int i = 0; i < kPerN; ++i) {
+                        if (rb[i] >= 0) {
+#pragma unroll
+                            for (int x = 0; x < 3; ++x) put_hi_lo<BF>(ah, al, rb[i] + x, lane, zz[i][x]);
+                        }
+                    }
+                    fence_proxy_async();
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cnt(&ready[s], kReadyCount / kNoiseWarps);
+            }
+        }
+    } else {
+        // ---------------- compute warps 2..9: two per TMEM lane quarter q; lane
+        // 3 k + axis of quarter q is axis `axis` of the quarter's chain k.
+        const int cw = warp - 2;            // 0..7
+        const int ct = threadIdx.x - 64;    // 0..255
+        const int q = warp & 3;             // TMEM lane quarter this warp may access
+        const int half = cw >> 2;           // which 16 of a block's 32 columns
         const int row = 32 * q + lane;
-        const int crow = row / 3, ax = row - 3 * (row / 3);
-        const bool live = row < 3 * Ct;
-        float* col0 = U;                              // D_inc[j][0] per row (epilogue)
+        const int kq = lane / 3, ax = lane - 3 * (lane / 3);
+        const bool inrow = kq < cpq;        // the row belongs to a chain slot of the tile
+        const int cl = inrow ? cpq * q + kq : 0;   // chain of the tile
+        const bool live = inrow && cl < Ct;
+        const int src0 = lane - ax;         // lane of axis 0 of this chain
+        // the chain's FP64 centre of mass, on its axis-0 lane of a first-half warp
+        const bool own_cm = half == 0 && live && ax == 0;
+        double cm_x = 0.0, cm_y = 0.0, cm_z = 0.0;
+        if (own_cm) {
+            const double* cm = a.com + 3 * (size_t)(c0 + cl);
+            cm_x = cm[0];
+            cm_y = cm[1];
+            cm_z = cm[2];
+        }
+        bool ok = true;
         bool finite = true;
+        auto arrive = [&](int s) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cnt(&ready[s], kReadyCount / kComputeWarps);
+        };
 #pragma unroll 1
         for (int sp = 0; sp < a.n_steps; ++sp) {
         const int g0 = sp * NBLK;                     // global index of this step's first block
-        // (1) per bead block nb: split the R tile of inverse block nb into TF32
-        //     hi / lo (in place), and write noise block nb (Eq. b5)
+        // (1) split the R tile of each inverse block into hi / lo operands
 #pragma unroll 1
         for (int nb = 0; nb < KB; ++nb) {
-            const int n = nb * kKB + lane;
-            float zz[kPer][3];
+            const int blk = g0 + sched_inv<KB>(nb), s = blk % ST;
+            const uint32_t ph = (blk / ST) & 1;
+            ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
+            if (ok && BF) {
+                // row t/4, BF16 chunk t%4 (8 values) from the FP32 staging tile
+                const uint8_t* r32 = stage0 + s * S::kStage;
+                uint8_t* ah = stage0 + s * S::kStage + S::kR;
+                uint8_t* al = ah + S::kA;
 #pragma unroll
-            for (int i = 0; i < kPer; ++i) {
-                const int c = cw + kComputeWarps * i;
-                zz[i][0] = zz[i][1] = zz[i][2] = 0.f;
-                if (c < Ct) Normals<float>::draw(a.seed, s_job[c], s_step[c] + sp, (uint32_t)n, 0u, zz[i]);
-            }
-            {
-                const int blk = g0 + 2 * nb, s = blk % ST;
-                const uint32_t ph = (blk / ST) & 1;
-                ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
-                if (ok && BF) {
-                    // row ct/4, BF16 chunk ct%4 (8 values) from the FP32 staging tile
-                    const uint8_t* r32 = stage0 + s * S::kStage;
-                    uint8_t* ah = stage0 + s * S::kStage + S::kR;
-                    uint8_t* al = ah + S::kA;
-                    const int r = ct >> 2, c = ct & 3;
+                for (int e = 0; e < kRows * 4 / kCompute; ++e) {
+                    const int t = ct + kCompute * e;
+                    const int r = t >> 2, c = t & 3;
                     uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int h2 = 0; h2 < 2; ++h2) {
@@ -343,112 +457,93 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                     const uint32_t o = swz_bf(r, 8 * c);
                     *reinterpret_cast<uint4*>(ah + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                     *reinterpret_cast<uint4*>(al + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                    fence_proxy_async();
-                } else if (ok) {
-                    float4* ah = (float4*)(stage0 + s * S::kStage);
-                    float4* al = (float4*)(stage0 + s * S::kStage + S::kA);
-#pragma unroll
-                    for (int i = 0; i < S::kA / 16 / kCompute; ++i) {
-                        const int e = ct + kCompute * i;
-                        const float4 x = ah[e];
-                        float4 h, l;
-                        h.x = tf32_rna(x.x); l.x = tf32_rna(x.x - h.x);
-                        h.y = tf32_rna(x.y); l.y = tf32_rna(x.y - h.y);
-                        h.z = tf32_rna(x.z); l.z = tf32_rna(x.z - h.z);
-                        h.w = tf32_rna(x.w); l.w = tf32_rna(x.w - h.w);
-                        ah[e] = h;
-                        al[e] = l;
-                    }
-                    fence_proxy_async();
                 }
-                mbar_arrive(&ready[s]);
-            }
-            {
-                const int blk = g0 + 2 * nb + 1, s = blk % ST;
-                const uint32_t ph = (blk / ST) & 1;
-                ok = ok && mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
-                if (ok) {
-                    uint8_t* ah = stage0 + s * S::kStage + S::kR;
-                    uint8_t* al = ah + S::kA;
+                fence_proxy_async();
+            } else if (ok) {
+                float4* ah = (float4*)(stage0 + s * S::kStage);
+                float4* al = (float4*)(stage0 + s * S::kStage + S::kA);
 #pragma unroll
-                    for (int i = 0; i < kPer; ++i) {
-                        const int c = cw + kComputeWarps * i;
-                        if (c < a.cpt) {
-#pragma unroll
-                            for (int x = 0; x < 3; ++x) put_hi_lo<BF>(ah, al, 3 * c + x, lane, zz[i][x]);
-                        }
-                    }
-                    fence_proxy_async();
+                for (int i = 0; i < S::kA / 16 / kCompute; ++i) {
+                    const int e = ct + kCompute * i;
+                    const float4 x = ah[e];
+                    float4 h, l;
+                    h.x = tf32_rna(x.x); l.x = tf32_rna(x.x - h.x);
+                    h.y = tf32_rna(x.y); l.y = tf32_rna(x.y - h.y);
+                    h.z = tf32_rna(x.z); l.z = tf32_rna(x.z - h.z);
+                    h.w = tf32_rna(x.w); l.w = tf32_rna(x.w - h.w);
+                    ah[e] = h;
+                    al[e] = l;
                 }
-                mbar_arrive(&ready[s]);
+                fence_proxy_async();
             }
+            arrive(s);
         }
 
-        // (2) per bead block nb: bond vectors from D_u -> residual force v (Eq. e11)
+        // (2) per bead block nb: bond vectors from D_u -> residual force v (Eq. e11),
+        //     |u_n| from the chain's three rows by warp shuffles
         ok = ok && mbar_wait(u_done, sp & 1, a.err, abort_flag);
         fence_after();
 #pragma unroll 1
         for (int nb = 0; nb < KB; ++nb) {
-            const int n = nb * kKB + lane;
-            if (cw < 4) {
-                // rows 32q..32q+31 of D_u, columns 32nb..32nb+31 -> U (swizzled rows)
-                const int r = 32 * q + lane;
-                float v[16];
+            const int col = nb * kKB + 16 * half;       // first bead of this warp's 16
+            float v[16];
+            tmem_ld16(t_u + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    tmem_ld16(t_u + ((uint32_t)(32 * q) << 16) + (uint32_t)(nb * kKB + 16 * h), v);
-#pragma unroll
-                    for (int k4 = 0; k4 < 4; ++k4)
-                        *reinterpret_cast<float4*>((uint8_t*)U + swz(r, 16 * h + 4 * k4)) =
-                            make_float4(v[4 * k4], v[4 * k4 + 1], v[4 * k4 + 2], v[4 * k4 + 3]);
-                }
+            for (int i = 0; i < 16; ++i) {
+                const float sq = v[i] * v[i];
+                const float t = sq + __shfl_down_sync(0xffffffffu, sq, 1) + __shfl_down_sync(0xffffffffu, sq, 2);
+                const float fac = __shfl_sync(0xffffffffu, rsqrtf(t) - a.c12nu, src0);
+                v[i] = (live && col + i >= 1) ? v[i] * fac : 0.f;
             }
-            named_bar(1, kCompute);
-            float vv[kPer][3];
+            const int blk = g0 + sched_force<KB>(nb), s = blk % ST;
+            const uint32_t ph = (blk / ST) & 1;
+            ok = ok && mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
+            if (ok && inrow) {
+                uint8_t* ah = stage0 + s * S::kStage + S::kR;
+                uint8_t* al = ah + S::kA;
+                if constexpr (BF) {
 #pragma unroll
-            for (int i = 0; i < kPer; ++i) {
-                const int c = cw + kComputeWarps * i;
-                float u[3] = {0.f, 0.f, 0.f};
-                if (c < a.cpt) {
+                    for (int h8 = 0; h8 < 2; ++h8) {
+                        uint32_t hw[4], lw[4];
 #pragma unroll
-                    for (int x = 0; x < 3; ++x)
-                        u[x] = *reinterpret_cast<const float*>((const uint8_t*)U + swz(3 * c + x, lane));
-                }
-                const bool live = c < Ct && n >= 1;
-                const float s2 = live ? rsqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) - a.c12nu : 0.f;
-#pragma unroll
-                for (int x = 0; x < 3; ++x) vv[i][x] = live ? u[x] * s2 : 0.f;
-            }
-            named_bar(1, kCompute);   // U is free for the next bead block
-            {
-                const int blk = g0 + 2 * KB + nb, s = blk % ST;
-                const uint32_t ph = (blk / ST) & 1;
-                ok = ok && mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
-                if (ok) {
-                    uint8_t* ah = stage0 + s * S::kStage + S::kR;
-                    uint8_t* al = ah + S::kA;
-#pragma unroll
-                    for (int i = 0; i < kPer; ++i) {
-                        const int c = cw + kComputeWarps * i;
-                        if (c < a.cpt) {
-#pragma unroll
-                            for (int x = 0; x < 3; ++x) put_hi_lo<BF>(ah, al, 3 * c + x, lane, vv[i][x]);
+                        for (int i = 0; i < 4; ++i) {
+                            const float x0 = v[8 * h8 + 2 * i], x1 = v[8 * h8 + 2 * i + 1];
+                            const uint16_t h0 = bf16_rn(x0), h1 = bf16_rn(x1);
+                            hw[i] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                            lw[i] = (uint32_t)bf16_rn(x0 - bf16_f(h0)) | ((uint32_t)bf16_rn(x1 - bf16_f(h1)) << 16);
                         }
+                        const uint32_t o = swz_bf(row, 16 * half + 8 * h8);
+                        *reinterpret_cast<uint4*>(ah + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4*>(al + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                     }
-                    fence_proxy_async();
+                } else {
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        float4 h, l;
+                        h.x = tf32_rna(v[4 * k4]);     l.x = tf32_rna(v[4 * k4] - h.x);
+                        h.y = tf32_rna(v[4 * k4 + 1]); l.y = tf32_rna(v[4 * k4 + 1] - h.y);
+                        h.z = tf32_rna(v[4 * k4 + 2]); l.z = tf32_rna(v[4 * k4 + 2] - h.z);
+                        h.w = tf32_rna(v[4 * k4 + 3]); l.w = tf32_rna(v[4 * k4 + 3] - h.w);
+                        const uint32_t o = swz(row, 16 * half + 4 * k4);
+                        *reinterpret_cast<float4*>(ah + o) = h;
+                        *reinterpret_cast<float4*>(al + o) = l;
+                    }
                 }
-                mbar_arrive(&ready[s]);
             }
+            if (ok) fence_proxy_async();
+            arrive(s);
         }
 
         // (3) epilogue: R += -dm R + D_inc (+ shear) on the R tile that the producer
         // reloaded into the stage memory (KB blocks of [128 rows][32], swizzled),
-        // in place, 16 columns at a time; then TMA-stored back (126 rows).
+        // in place, 16 columns at a time; then TMA-stored back (3 cpq rows per quarter).
         ok = ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag);
         ok = ok && mbar_wait(r_full, sp & 1, a.err, abort_flag);
         fence_after();
+        // a chain whose step counter has reached its stop step stays as it is
+        const bool adv = live && s_step[cl] + sp < s_stop[cl];
 #pragma unroll 1
-        for (int k = grp; k < NB / 16; k += kComputeWarps / 4) {
+        for (int k = half; k < NB / 16; k += 2) {
             const int p0 = 16 * k;
             uint8_t* blk = stage0 + (p0 / kKB) * S::kRT;
             const int kin = p0 % kKB;
@@ -459,63 +554,64 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 const float4 x = *reinterpret_cast<const float4*>(blk + swz(row, kin + 4 * k4));
                 r[4 * k4] = x.x; r[4 * k4 + 1] = x.y; r[4 * k4 + 2] = x.z; r[4 * k4 + 3] = x.w;
             }
-            float ry[16];
-            if (has_shear) {
-                // start-of-step R^y of this chain (row 3c+1), read before anyone writes
-                const int ry_row = min(3 * crow + 1, kRows - 1);
-#pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4) {
-                    const float4 x = *reinterpret_cast<const float4*>(blk + swz(ry_row, kin + 4 * k4));
-                    ry[4 * k4] = x.x; ry[4 * k4 + 1] = x.y; ry[4 * k4 + 2] = x.z; ry[4 * k4 + 3] = x.w;
-                }
-                named_bar(2 + grp, 128);
-            }
-            // a chain whose step counter has reached its stop step stays as it is
-            const bool adv = live && s_step[crow] + sp < s_stop[crow];
             float o[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) o[i] = adv ? r[i] + fmaf(-s_dm[p0 + i], r[i], d[i]) : r[i];
-            if (has_shear && adv && ax == 0) {
-                const float sh = (float)s_shear[crow];
+            if (has_shear) {
+                // start-of-step R^y of this chain: the next lane's row (axis 1)
+                const float sh = (float)s_shear[cl];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) o[i] += sh * s_g[p0 + i] * ry[i];
+                for (int i = 0; i < 16; ++i) {
+                    const float ry = __shfl_down_sync(0xffffffffu, r[i], 1);
+                    if (adv && ax == 0) o[i] += sh * s_g[p0 + i] * ry;
+                }
             }
             if (p0 == 0) {
-                col0[row] = d[0];
+                // centre of mass in FP64 (p = 0 of Eq. d3 with zeta_0 = 0), kept in
+                // registers for the whole launch
+                const float d1 = __shfl_down_sync(0xffffffffu, d[0], 1);
+                const float d2 = __shfl_down_sync(0xffffffffu, d[0], 2);
+                if (adv && ax == 0) {
+                    const double ycm = cm_y;
+                    cm_x += (double)d[0] * a.inv_sqrtM + s_shear[cl] * a.dtau * ycm;
+                    cm_y += (double)d1 * a.inv_sqrtM;
+                    cm_z += (double)d2 * a.inv_sqrtM;
+                }
                 o[0] = 0.f;
             }
             if (live) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) finite = finite && isfinite(o[i]);
             }
+            if (inrow) {
 #pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4)
-                *reinterpret_cast<float4*>(blk + swz(row, kin + 4 * k4)) =
-                    make_float4(o[4 * k4], o[4 * k4 + 1], o[4 * k4 + 2], o[4 * k4 + 3]);
-            if (has_shear) named_bar(2 + grp, 128);
+                for (int k4 = 0; k4 < 4; ++k4)
+                    *reinterpret_cast<float4*>(blk + swz(row, kin + 4 * k4)) =
+                        make_float4(o[4 * k4], o[4 * k4 + 1], o[4 * k4 + 2], o[4 * k4 + 3]);
+            }
         }
         fence_proxy_async();
-        named_bar(1, kCompute);   // tile and col0 complete
+        fence_before();           // D_inc read before the next step's MMAs write it
+        named_bar(1, kCompute);   // the tile is complete
         if (ct == 0) {
             if (ok) {
-                for (int k = 0; k < KB; ++k) tma_store_2d(&tmRst, stage0 + k * S::kRT, k * kKB, row0);
+                for (int k = 0; k < KB; ++k)
+                    for (int qq = 0; qq < 4; ++qq)
+                        tma_store_2d(&tmR, stage0 + k * S::kRT + qq * kQuarter, k * kKB, 3 * (c0 + qq * cpq));
                 tma_store_commit();
                 tma_store_wait();   // R is in global memory and the stages are free again
             }
             mbar_arrive(epi_done);
         }
-        if (ok && grp == 0 && live && ax == 0 && s_step[crow] + sp < s_stop[crow]) {
-            // centre of mass in FP64 (p = 0 of Eq. d3 with zeta_0 = 0)
-            double* cm = a.com + 3 * (size_t)(c0 + crow);
-            const double ycm = cm[1];
-            cm[0] += (double)col0[row] * a.inv_sqrtM + s_shear[crow] * a.dtau * ycm;
-            cm[1] += (double)col0[row + 1] * a.inv_sqrtM;
-            cm[2] += (double)col0[row + 2] * a.inv_sqrtM;
-        }
-        named_bar(1, kCompute);   // col0 read before the next step reuses U
         }   // steps
-        if (ok && grp == 0 && live && ax == 0)
-            a.step[c0 + crow] = max(s_step[crow], min(s_step[crow] + (int64_t)a.n_steps, s_stop[crow]));
+        if (ok && own_cm) {
+            double* cm = a.com + 3 * (size_t)(c0 + cl);
+            cm[0] = cm_x;
+            cm[1] = cm_y;
+            cm[2] = cm_z;
+        }
+        if (ok && half == 0 && live && ax == 0)
+            a.step[c0 + cl] = max(s_step[cl], min(s_step[cl] + (int64_t)a.n_steps, s_stop[cl]));
         if (!finite) atomicOr(a.err, 1);
     }
     fence_before();
@@ -533,8 +629,11 @@ struct FusedPlan {
     bool bf16 = false;
     void* tab[4] = {nullptr, nullptr, nullptr, nullptr};    // chi_hi, chi_lo, F_hi, F_lo (TF32 or BF16)
     float* R = nullptr;
-    CUtensorMap tmR, tmRst, tmChiH, tmChiL, tmFH, tmFL;
+    CUtensorMap tmR, tmChiH, tmChiL, tmFH, tmFL;
 };
+
+// Chains per tile: a multiple of 4 (one share per TMEM lane quarter), 4..kChains.
+static int round_tile(int cpt) { return std::min(kChains, std::max(4, (cpt + 3) / 4 * 4)); }
 
 bool fused_supported(int M) { return M == 64 || M == 128 || M == 256; }
 
@@ -587,11 +686,12 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
     p->C = C;
     p->R = R;
     p->bf16 = bf16;
-    // one wave: chains per tile = ceil(C / SMs), at most 42 (fused_set_tile changes it)
+    // one wave: chains per tile = ceil(C / SMs) rounded up to a multiple of 4, at
+    // most 40 (fused_set_tile changes it)
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         sms = 148;
-    p->cpt = std::max(1, std::min(kChains, (C + sms - 1) / sms));
+    p->cpt = round_tile((C + sms - 1) / sms);
     const size_t mm = (size_t)M * M;
     // chi [n][p] (row n = 0 and column p = 0 are zero) and F [2M][M]:
     // F[p][n] = h_p chi[n][p] (Eq. f2 weight on DeltaH = chi^T v, Eq. e11),
@@ -633,8 +733,9 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
         }
     }
     int rc;
-    // the store box is the tile's 3 cpt rows: a tile must not write the next tile's chains
-    if ((rc = make_map_2d(&p->tmR, R, 3 * C, M, kRows)) || (rc = make_map_2d(&p->tmRst, R, 3 * C, M, 3 * p->cpt))) {
+    // one box per lane quarter of the tile, 3 cpt / 4 rows: a tile never writes
+    // the next tile's chains
+    if ((rc = make_map_2d(&p->tmR, R, 3 * C, M, 3 * (p->cpt / 4)))) {
         fused_destroy(p);
         return rc;
     }
@@ -666,8 +767,8 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
     if (args.cpt != p->cpt) return report(SFP_EINVAL, "fused step: chains per tile differ from the plan's");
     const dim3 grid((unsigned)((p->C + p->cpt - 1) / p->cpt));
 #define SFP_FUSED_LAUNCH(NBV, BFV)                                                                   \
-    k_fused_step<NBV, BFV><<<grid, kThreads, FSmem<NBV, BFV>::kBytes, stream>>>(p->tmR, p->tmRst, p->tmChiH, \
-                                                                            p->tmChiL, p->tmFH, p->tmFL, args)
+    k_fused_step<NBV, BFV><<<grid, kThreads, FSmem<NBV, BFV>::kBytes, stream>>>(p->tmR, p->tmChiH, p->tmChiL, \
+                                                                            p->tmFH, p->tmFL, args)
     switch (p->M * 2 + (p->bf16 ? 1 : 0)) {
         case 512: SFP_FUSED_LAUNCH(256, false); break;
         case 513: SFP_FUSED_LAUNCH(256, true); break;
@@ -689,11 +790,12 @@ size_t fused_bytes(const FusedPlan* p) { return p ? (size_t)6 * p->M * p->M * (p
 
 int fused_set_tile(FusedPlan* p, int cpt)
 {
-    if (cpt < 1 || cpt > kChains) return report(SFP_EINVAL, "chains per tile must be 1..42");
+    if (cpt < 1 || cpt > kChains) return report(SFP_EINVAL, "chains per tile must be 1..40");
+    cpt = round_tile(cpt);
     CUtensorMap m;
-    const int rc = make_map_2d(&m, p->R, 3 * p->C, p->M, 3 * cpt);
+    const int rc = make_map_2d(&m, p->R, 3 * p->C, p->M, 3 * (cpt / 4));
     if (rc) return rc;
-    p->tmRst = m;
+    p->tmR = m;
     p->cpt = cpt;
     return SFP_OK;
 }

@@ -25,7 +25,7 @@ struct FusedArgs {
     double inv_sqrtM;
     double dtau;
     int n_steps;            // steps per launch (>= 1)
-    int cpt;                // chains per tile (1..42), as in the plan (fused_tile)
+    int cpt;                // chains per tile (4..40, a multiple of 4), as in the plan (fused_tile)
 };
 
 // True when a group of M beads can take the fused step (M = 64, 128 or 256).
@@ -40,7 +40,8 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
                  const double* w, float* R, cudaStream_t stream, bool bf16 = false);
 // args.n_steps steps of every chain of the group, in one launch.
 int fused_step(FusedPlan* plan, const FusedArgs& args, cudaStream_t stream);
-// Chains per tile of the plan, and a new value (1..42; rebuilds the store map).
+// Chains per tile of the plan, and a new value (1..40, rounded up to a multiple
+// of 4: one share per TMEM lane quarter; rebuilds the R map).
 int fused_tile(const FusedPlan* plan);
 // Device bytes the plan's tables hold.
 size_t fused_bytes(const FusedPlan* plan);

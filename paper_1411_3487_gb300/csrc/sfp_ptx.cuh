@@ -37,6 +37,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// Arrive with a weight of `count` (one thread standing for its warp).
+__device__ __forceinline__ void mbar_arrive_cnt(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 {
@@ -51,13 +56,58 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
+// try_wait that may suspend the thread for up to `ns` nanoseconds while the
+// phase is incomplete (it resumes as soon as the phase completes), so waiting
+// warps leave their issue slots to the working ones.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait on an mbarrier phase; false (and error bit 2) after kTimeoutNs.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, volatile int* abort_flag)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_sleep(bar, parity, 1000u)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > kTimeoutNs) {
+            atomicOr(err, 2);
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+// A monotonic progress counter in shared memory: release store by its one
+// writer, acquire loads by the waiters.
+__device__ __forceinline__ void st_release_smem(int* p, int v)
+{
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_smem(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+// Wait until *c >= target; bounded like mbar_wait.
+__device__ __forceinline__ bool count_wait(const int* c, int target, int* err, volatile int* abort_flag)
+{
+    if (ld_acquire_smem(c) >= target) return true;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        __nanosleep(32);
+        if (ld_acquire_smem(c) >= target) return true;
         if (*abort_flag) return false;
         if (globaltimer() - t0 > kTimeoutNs) {
             atomicOr(err, 2);
@@ -161,6 +211,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
 
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Orders this thread's generic-proxy global writes before later async-proxy
+// (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // TMA tile store shared -> global (bulk-group completion), its commit, and a
 // wait until every committed store of this thread has completed.

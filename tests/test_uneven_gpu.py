@@ -57,7 +57,7 @@ def test_graph_replay_and_autotune_leave_trajectories_unchanged():
     # chunks at 64 steps, so the 100-step call is two chunks: one more launch for
     # each of the three fused groups
     assert gr[3] == ref[3] + 3
-    assert len(tiles) == 4 and sum(1 for t in tiles if 1 <= t <= 42) == 3 and tiles.count(0) == 1
+    assert len(tiles) == 4 and sum(1 for t in tiles if 4 <= t <= 40 and t % 4 == 0) == 3 and tiles.count(0) == 1
 
 
 def test_concurrent_groups_match_the_oracle():
