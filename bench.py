@@ -3,12 +3,18 @@
 Workload: 4096 independent 256-bp dsDNA chains, FP32 state, dt = 15.9 ps
 (dtau ~ 100, Table 2), equilibrium-sampled starts, zero shear, per-chain
 Philox streams.  A bench "step" is one Langevin step of the whole batch
-(inverse transform, force + noise, forward transform, mode update).
+(inverse transform, force + noise, forward transform, mode update).  The K
+timed steps run as sfp_step calls of --steps-per-call steps (20; one fused
+launch each) with the L2 flushed before every call; the one-step-per-call
+figure is reported beside it.
 
 Prints one JSON line (rank 0).  Metric: bead-timesteps/s (chains x beads x
 steps / s); simulated ns/s per chain is reported beside it.
   --impl reference   time the FP64 CPU oracle on the host cores instead
-  --precision simt   time the plain FP32 CUDA-core path instead of tcgen05
+  --precision bf16   (default) fused step, transforms as three BF16 tcgen05
+                     passes (hi/lo split, FP32 accumulate; SFP_MIXED_BF16)
+  --precision tf32   the same with three TF32 passes (SFP_FP32)
+  --precision simt   the plain FP32 CUDA-core path (no tensor cores)
   --path staged      time the per-stage tcgen05 kernels instead of the fused step
 """
 from __future__ import annotations
@@ -30,6 +36,7 @@ C_CHAINS, M_BEADS, DT_PS = 4096, 256, 15.9
 WORKLOAD = "dsDNA 4096 chains x 256 bp, FP32 state, dt 15.9 ps, equilibrium starts, no shear"
 METRIC, UNIT = "bead-timesteps/s", "bead-steps/s"
 L2_FLUSH_BYTES = 256 << 20
+PREC_NAME, DTYPE = {}, {}     # filled once the library is imported
 
 
 def parse():
@@ -37,8 +44,10 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps-per-call", type=int, default=20,
+                    help="Langevin steps per sfp_step call (one fused launch); L2 is flushed between calls")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="tc", choices=["tc", "simt"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "tc", "simt"])
     ap.add_argument("--path", default="fused", choices=["fused", "staged"])
     ap.add_argument("--workload", default="batch", choices=["batch", "serving", "precision", "uneven"])
     ap.add_argument("--serve-seconds", type=float, default=20.0)
@@ -180,7 +189,13 @@ def run_native(args, rank, world, local):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
-    precision = sfp.SFP_FP32 if args.precision == "tc" else sfp.SFP_FP32_SIMT
+    PREC_NAME.update({sfp.SFP_MIXED_BF16: "SFP_MIXED_BF16", sfp.SFP_FP32: "SFP_FP32",
+                      sfp.SFP_FP32_SIMT: "SFP_FP32_SIMT"})
+    DTYPE.update({sfp.SFP_MIXED_BF16: "f32 (bf16x3 transforms)", sfp.SFP_FP32: "f32 (tf32x3 transforms)",
+                  sfp.SFP_FP32_SIMT: "f32"})
+    precision = {"bf16": sfp.SFP_MIXED_BF16, "tf32": sfp.SFP_FP32, "tc": sfp.SFP_FP32,
+                 "simt": sfp.SFP_FP32_SIMT}[args.precision]
+    tensor = precision in (sfp.SFP_FP32, sfp.SFP_MIXED_BF16)
     # weak scaling: every rank owns its own 4096 chains (disjoint job ids)
     from paper_1411_3487_gb300 import shard
     chains = [{"n_beads": M_BEADS, "dt_ps": DT_PS, "job_id": j}
@@ -190,26 +205,29 @@ def run_native(args, rank, world, local):
     if precision == sfp.SFP_FP32_SIMT:
         path = sfp.SFP_PATH_STAGED
 
-    def timed_steps(prec, pth, steps, warmup, with_clocks):
+    def timed_steps(prec, pth, steps, warmup, with_clocks, per_call=1):
+        """`steps` timed Langevin steps as sfp_step calls of `per_call` steps,
+        the L2 flushed before every call; returns per-call times (ms)."""
         b = sfp.Batch(chains, seed=1, precision=prec, stream=stream)
         b.set_path(pth)
         b.init_equilibrium(0)
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
         for _ in range(warmup):
-            b.step(1)
+            b.step(per_call)
             flush.zero_()
         torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        calls = [per_call] * (steps // per_call) + ([steps % per_call] if steps % per_call else [])
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in calls]
         launches0 = b.info()["launches"]
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         clk = ClockSampler(local) if with_clocks else None
         b.stage_timing(True)                  # per-stage CUDA events on the batch's stream
-        for e0, e1 in ev:
-            flush.zero_()                     # L2 flushed between timed steps
+        for (e0, e1), n in zip(ev, calls):
+            flush.zero_()                     # L2 flushed between timed calls
             e0.record(stream)
-            b.step(1)
+            b.step(n)
             e1.record(stream)
         torch.cuda.synchronize()
         clocks = clk.stop() if clk else None
@@ -221,7 +239,8 @@ def run_native(args, rank, world, local):
         ms = [a.elapsed_time(c) for a, c in ev]
         return b, ms, launches, clocks, kern
 
-    b, ms, launches, clocks, kern = timed_steps(precision, path, args.steps, args.warmup, True)
+    spc = max(1, args.steps_per_call)
+    b, ms, launches, clocks, kern = timed_steps(precision, path, args.steps, args.warmup, True, spc)
     tot_ms = float(sum(ms))
     if world > 1:
         t = torch.tensor([tot_ms], device="cuda")
@@ -236,11 +255,9 @@ def run_native(args, rank, world, local):
     pk, how = peaks()
     roof = roofline(kern, pk, how, precision, path, sfp)
 
-    # sustained: many steps per sfp_step call (one fused launch per call), the way a
-    # simulation runs; the state stays in L2 between the steps of a call, so this is
-    # reported beside the L2-flushed per-step value, not as it
+    # sustained: 4 back-to-back calls of 100 steps, no flush at all (a long run)
     sustained = None
-    if path == sfp.SFP_PATH_FUSED and precision == sfp.SFP_FP32:
+    if path == sfp.SFP_PATH_FUSED and tensor:
         per_call, calls = 100, 4
         b.step(per_call)
         torch.cuda.synchronize()
@@ -258,17 +275,26 @@ def run_native(args, rank, world, local):
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = end_to_end(sfp, b, torch, min(args.steps, 50))
 
-    plain = staged = None
+    plain = staged = other = single = None
     if not args.no_plain and precision != sfp.SFP_FP32_SIMT:
         b.close()
-        _, ms_p, _, _, _ = timed_steps(sfp.SFP_FP32_SIMT, sfp.SFP_PATH_STAGED, min(args.steps, 100), 3, False)
-        plain = {"value": beads * len(ms_p) / (sum(ms_p) * 1e-3), "unit": UNIT,
-                 "ms_per_step": float(sum(ms_p) / len(ms_p)), "path": "plain FP32 CUDA-core path"}
+        n_o = min(args.steps, 100)
+
+        def leg(prec, pth, per_call, what):
+            _, ms_l, _, _, k_l = timed_steps(prec, pth, n_o, 3, False, per_call)
+            return {"value": beads * n_o / (sum(ms_l) * 1e-3), "unit": UNIT, "ms_per_step": float(sum(ms_l) / n_o),
+                    "steps_per_call": per_call, "kernels_us": k_l, "path": what}
+
+        plain = leg(sfp.SFP_FP32_SIMT, sfp.SFP_PATH_STAGED, spc, "plain FP32 CUDA-core path")
         if path == sfp.SFP_PATH_FUSED:
-            _, ms_s, _, _, k_s = timed_steps(sfp.SFP_FP32, sfp.SFP_PATH_STAGED, min(args.steps, 100), 3, False)
-            staged = {"value": beads * len(ms_s) / (sum(ms_s) * 1e-3), "unit": UNIT,
-                      "ms_per_step": float(sum(ms_s) / len(ms_s)), "kernels_us": k_s,
-                      "path": "tcgen05 transforms, one kernel per stage"}
+            staged = leg(precision, sfp.SFP_PATH_STAGED, spc, "tcgen05 transforms, one kernel per stage (same precision)")
+            # one step per call: every step a launch of its own after an L2 flush
+            single = leg(precision, sfp.SFP_PATH_FUSED, 1, "fused step, one step per call and launch")
+            # the fused step with the other tensor-core split, same workload and timing
+            o_prec = sfp.SFP_FP32 if precision == sfp.SFP_MIXED_BF16 else sfp.SFP_MIXED_BF16
+            other = leg(o_prec, sfp.SFP_PATH_FUSED, spc, "fused step")
+            other.update({"precision": PREC_NAME[o_prec], "dtype": DTYPE[o_prec],
+                          "roofline": roofline(other["kernels_us"], pk, how, o_prec, sfp.SFP_PATH_FUSED, sfp)})
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -282,15 +308,18 @@ def run_native(args, rank, world, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if precision == sfp.SFP_FP32_SIMT else "f32 (tf32x3 transforms)",
+            "dtype": DTYPE[precision],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "chains_per_gpu": C_CHAINS, "beads": M_BEADS, "dt_ps": DT_PS,
-                       "dtau": dtau, "precision": "SFP_FP32" if precision == sfp.SFP_FP32 else "SFP_FP32_SIMT",
-                       "path": "fused" if (path == sfp.SFP_PATH_FUSED and precision == sfp.SFP_FP32) else "staged",
-                       "l2": "flushed between timed steps (256 MB write)"},
+                       "dtau": dtau, "precision": PREC_NAME[precision],
+                       "path": "fused" if (path == sfp.SFP_PATH_FUSED and tensor) else "staged",
+                       "steps_per_call": spc,
+                       "l2": f"flushed (256 MB write) before every timed sfp_step call of {spc} steps; "
+                             "inside a call the state stays in L2, as in a run"},
             "sim_ns_per_s_per_chain": DT_PS * 1e-3 * args.steps / (tot_ms * 1e-3),
             "roofline": roof, "kernels_us": kern, "cpu_baseline": cpu, "e2e": e2e,
-            "sustained": sustained, "plain_path": plain, "staged_path": staged, "clocks": clocks,
+            "sustained": sustained, "plain_path": plain, "staged_path": staged,
+            "other_split_fused": other, "single_step_calls": single, "clocks": clocks,
             "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)
@@ -321,31 +350,44 @@ def roofline(kern, pk, how, precision, path, sfp):
     """Roofline of the dominant kernel from its live CUDA-event time.
 
     Algorithmic work of the transforms: 18 M flops per bead-step (inverse
-    2 M x 3 rows, forward 2 M x 6 rows per chain); the SFP_FP32 kernels execute
-    each product as three TF32 MMAs (hi/lo split), so the tensor pipe does
-    54 M TF32 flops per bead-step, compared with the TF32 dense peak."""
+    2 M x 3 rows, forward 2 M x 6 rows per chain); the tensor-core kernels
+    execute each product as three MMAs (hi/lo split), so the tensor pipe does
+    54 M flops per bead-step, compared with the dense peak of the MMA type
+    (measured BF16; TF32 from it by the nominal 1.1/2.25 ratio)."""
     if not kern:
         return None
     M, beads = M_BEADS, C_CHAINS * M_BEADS
     tf32_peak = pk.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
     src = f"{how} bf16 x 1.1/2.25 (nominal tf32/bf16 dense ratio)"
+    if precision == sfp.SFP_MIXED_BF16 and path == sfp.SFP_PATH_FUSED:
+        us = kern.get("inverse_us")          # the fused kernel is recorded as the first stage
+        flops = 3 * 18.0 * M * beads
+        peak = pk.get("bf16_tflops", 1900.0)
+        traffic = measured_traffic("fused_step_bf16_4096x256.md", "paper_1411_3487_gb300/csrc/sfp_fused.cu")
+        return {"bound": "tensor", "kernel": "k_fused_step<256, bf16> (whole step, bf16x3)",
+                "achieved": flops / (us * 1e-6) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / (us * 1e-6) / 1e12 / peak, "traffic": traffic,
+                "traffic_unit": "DRAM bytes per launch (ncu, profiles/fused_step_bf16_4096x256.md)",
+                "algorithmic_bytes": 24 * beads, "kernel_us": us, "peak_source": f"{how} bf16 dense (burst)"}
     if precision == sfp.SFP_FP32 and path == sfp.SFP_PATH_FUSED:
         us = kern.get("inverse_us")          # the fused kernel is recorded as the first stage
         flops = 3 * 18.0 * M * beads
         traffic = measured_traffic("fused_step_4096x256.md", "paper_1411_3487_gb300/csrc/sfp_fused.cu")
-        return {"bound": "tensor", "kernel": "k_fused_step<256> (whole step, tf32x3)",
+        return {"bound": "tensor", "kernel": "k_fused_step<256, tf32> (whole step, tf32x3)",
                 "achieved": flops / (us * 1e-6) / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
                 "frac": flops / (us * 1e-6) / 1e12 / tf32_peak, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per launch (ncu, profiles/fused_step_4096x256.md)",
                 "algorithmic_bytes": 24 * beads, "kernel_us": us, "peak_source": src}
-    if precision == sfp.SFP_FP32:
-        # forward transform: [DeltaH|Z] = phi^T [f|z], 2*rows x M x M, three TF32 passes
+    if precision in (sfp.SFP_FP32, sfp.SFP_MIXED_BF16):
+        # forward transform: [DeltaH|Z] = phi^T [f|z], 2*rows x M x M, three passes
+        bf = precision == sfp.SFP_MIXED_BF16
+        peak = pk.get("bf16_tflops", 1900.0) if bf else tf32_peak
         us = kern.get("forward_us")
         flops = 3 * 2.0 * (6 * C_CHAINS) * M * M
-        return {"bound": "tensor", "kernel": "k_tc_gemm<256> forward transform (tf32x3)",
-                "achieved": flops / (us * 1e-6) / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
-                "frac": flops / (us * 1e-6) / 1e12 / tf32_peak, "traffic": None, "kernel_us": us,
-                "peak_source": src}
+        return {"bound": "tensor", "kernel": "k_tc_gemm forward transform (%s)" % ("bf16x3" if bf else "tf32x3"),
+                "achieved": flops / (us * 1e-6) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / (us * 1e-6) / 1e12 / peak, "traffic": None, "kernel_us": us,
+                "peak_source": f"{how} bf16 dense (burst)" if bf else src}
     us = kern.get("forward_us")
     flops = 2.0 * (6 * C_CHAINS) * M * M
     peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
