@@ -193,11 +193,11 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     uint64_t* empty = bars + 8;         // MMAs done with the stage         (commit)
     uint64_t* u_done = bars + 12;       // all inverse MMAs done            (commit)
     uint64_t* inc_done = bars + 13;     // all forward MMAs done            (commit)
-    uint64_t* r_full = bars + 14;       // R tile reloaded for the epilogue (1 + tx)
-    uint64_t* epi_done = bars + 15;     // epilogue stored R, stages free   (1)
+    uint64_t* epi_done = bars + 15;     // epilogue stored R, stages free   (kComputeWarps)
     uint32_t* tmem_slot = (uint32_t*)(bars + 16);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     int* s_freed = (int*)(tmem_slot + 2);   // last block whose stage the producer saw released
+    uint64_t* r_blk = bars + 18;        // R column block k reloaded for the epilogue (1 + tx), k < KB
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cpq = a.cpt >> 2;         // chains per TMEM lane quarter (rows 32 q + 3 k + axis)
@@ -213,8 +213,8 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         }
         mbar_init(u_done, 1);
         mbar_init(inc_done, 1);
-        mbar_init(r_full, 1);
-        mbar_init(epi_done, 1);
+        for (int k = 0; k < KB; ++k) mbar_init(&r_blk[k], 1);
+        mbar_init(epi_done, kComputeWarps);
         *abort_flag = 0;
         *s_freed = -1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -283,10 +283,11 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             // every stage is free once the forward MMAs are done: reload the R tile
             // (KB column blocks of [128 rows][32]) there for the epilogue
             if (ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag)) {
-                mbar_expect_tx(r_full, KB * rblock);
-                for (int k = 0; k < KB; ++k)
+                for (int k = 0; k < KB; ++k) {
+                    mbar_expect_tx(&r_blk[k], rblock);
                     for (int q = 0; q < 4; ++q)
-                        tma_load_2d(stage0 + k * S::kRT + q * kQuarter, &tmR, r_full, k * kKB, 3 * (c0 + q * cpq));
+                        tma_load_2d(stage0 + k * S::kRT + q * kQuarter, &tmR, &r_blk[k], k * kKB, 3 * (c0 + q * cpq));
+                }
             } else {
                 ok = false;
             }
@@ -348,48 +349,68 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             const int c = nw + kNoiseWarps * i;
             rb[i] = c < a.cpt ? 32 * (c / cpq) + 3 * (c % cpq) : -1;
         }
+        // The first kPerN - 1 chain slots (30 chains) are drawn without a branch, so
+        // their Philox / Box-Muller chains interleave; a slot past the tile's
+        // chains draws for job 0 and is zeroed.
+        auto draw = [&](int qn, float (&zz)[kPerN][3]) {
+            const int sp = qn / KB, n = (qn - sp * KB) * kKB + lane;
+#pragma unroll
+            for (int i = 0; i < kPerN - 1; ++i) {
+                const int c = nw + kNoiseWarps * i;
+                Normals<float>::draw(a.seed, s_job[c], s_step[c] + sp, (uint32_t)n, 0u, zz[i]);
+            }
+            zz[kPerN - 1][0] = zz[kPerN - 1][1] = zz[kPerN - 1][2] = 0.f;
+            if (nw + kNoiseWarps * (kPerN - 1) < Ct)
+                Normals<float>::draw(a.seed, s_job[nw + kNoiseWarps * (kPerN - 1)],
+                                     s_step[nw + kNoiseWarps * (kPerN - 1)] + sp, (uint32_t)n, 0u, zz[kPerN - 1]);
+#pragma unroll
+            for (int i = 0; i < kPerN - 1; ++i)
+                if (nw + kNoiseWarps * i >= Ct) zz[i][0] = zz[i][1] = zz[i][2] = 0.f;
+        };
+        // Noise blocks in sequence qn = KB step + j.  Block qn is drawn into `cur`;
+        // if its stage is not free yet, block qn + 1 is drawn into `nxt` meanwhile
+        // (the noise does not depend on the state), so the noise warps keep
+        // drawing while the stages are held, e.g. through the epilogue.
         bool ok = true;
+        const int nq = a.n_steps * KB;
+        float cur[kPerN][3], nxt[kPerN][3];
+        bool have_nxt = false;
+        draw(0, cur);
 #pragma unroll 1
-        for (int sp = 0; sp < a.n_steps; ++sp) {
-#pragma unroll 1
-            for (int j = 0; j < KB; ++j) {
-                const int n = j * kKB + lane;
-                // The first kPerN - 1 chain slots (30 chains) are drawn without a
-                // branch, so their Philox / Box-Muller chains interleave; a slot past
-                // the tile's chains draws for job 0 and is zeroed.
-                float zz[kPerN][3];
+        for (int qn = 0; qn < nq; ++qn) {
+            const int sp = qn / KB, j = qn - sp * KB;
+            const int blk = sp * NBLK + sched_noise<KB>(j), s = blk % ST;
+            // Consecutive noise blocks may lie more than ST blocks apart, where a
+            // parity wait on the stage's barrier is ambiguous: wait instead until
+            // the producer has seen the stage released for this block (which it
+            // does in block order, after the previous step's epilogue).
+            if (!have_nxt && qn + 1 < nq && ld_acquire_smem(s_freed) < blk) {
+                draw(qn + 1, nxt);
+                have_nxt = true;
+            }
+            ok = ok && count_wait(s_freed, blk, a.err, abort_flag);
+            if (ok) {
+                uint8_t* ah = stage0 + s * S::kStage + S::kR;
+                uint8_t* al = ah + S::kA;
 #pragma unroll
-                for (int i = 0; i < kPerN - 1; ++i) {
-                    const int c = nw + kNoiseWarps * i;
-                    Normals<float>::draw(a.seed, s_job[c], s_step[c] + sp, (uint32_t)n, 0u, zz[i]);
-                }
-                zz[kPerN - 1][0] = zz[kPerN - 1][1] = zz[kPerN - 1][2] = 0.f;
-                if (nw + kNoiseWarps * (kPerN - 1) < Ct)
-                    Normals<float>::draw(a.seed, s_job[nw + kNoiseWarps * (kPerN - 1)],
-                                         s_step[nw + kNoiseWarps * (kPerN - 1)] + sp, (uint32_t)n, 0u, zz[kPerN - 1]);
+                for (int i = 0; i < kPerN; ++i) {
+                    if (rb[i] >= 0) {
 #pragma unroll
-                for (int i = 0; i < kPerN - 1; ++i)
-                    if (nw + kNoiseWarps * i >= Ct) zz[i][0] = zz[i][1] = zz[i][2] = 0.f;
-                const int blk = sp * NBLK + sched_noise<KB>(j), s = blk % ST;
-                // Consecutive noise blocks may lie more than ST blocks apart, where a
-                // parity wait on the stage's barrier is ambiguous: wait instead until
-                // the producer has seen the stage released for this block (which it
-                // does in block order, after the previous step's epilogue).
-                ok = ok && count_wait(s_freed, blk, a.err, abort_flag);
-                if (ok) {
-                    uint8_t* ah = stage0 + s * S::kStage + S::kR;
-                    uint8_t* al = ah + S::kA;
-#pragma unroll
-                    for (int i = 0; i < kPerN; ++i) {
-                        if (rb[i] >= 0) {
-#pragma unroll
-                            for (int x = 0; x < 3; ++x) put_hi_lo<BF>(ah, al, rb[i] + x, lane, zz[i][x]);
-                        }
+                        for (int x = 0; x < 3; ++x) put_hi_lo<BF>(ah, al, rb[i] + x, lane, cur[i][x]);
                     }
-                    fence_proxy_async();
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive_cnt(&ready[s], kReadyCount / kNoiseWarps);
+                fence_proxy_async();
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cnt(&ready[s], kReadyCount / kNoiseWarps);
+            if (have_nxt) {
+#pragma unroll
+                for (int i = 0; i < kPerN; ++i)
+#pragma unroll
+                    for (int x = 0; x < 3; ++x) cur[i][x] = nxt[i][x];
+                have_nxt = false;
+            } else if (qn + 1 < nq) {
+                draw(qn + 1, cur);
             }
         }
     } else {
@@ -535,74 +556,77 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         }
 
         // (3) epilogue: R += -dm R + D_inc (+ shear) on the R tile that the producer
-        // reloaded into the stage memory (KB blocks of [128 rows][32], swizzled),
-        // in place, 16 columns at a time; then TMA-stored back (3 cpq rows per quarter).
+        // reloads into the stage memory (KB column blocks of [128 rows][32],
+        // swizzled, each with its own barrier), in place.  A warp owns the 32 rows
+        // of its lane quarter in every other column block and TMA-stores each
+        // (block, quarter) box as soon as it is done.
         ok = ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag);
-        ok = ok && mbar_wait(r_full, sp & 1, a.err, abort_flag);
         fence_after();
         // a chain whose step counter has reached its stop step stays as it is
         const bool adv = live && s_step[cl] + sp < s_stop[cl];
 #pragma unroll 1
-        for (int k = half; k < NB / 16; k += 2) {
-            const int p0 = 16 * k;
-            uint8_t* blk = stage0 + (p0 / kKB) * S::kRT;
-            const int kin = p0 % kKB;
-            float d[16], r[16];
-            tmem_ld16(t_inc + ((uint32_t)(32 * q) << 16) + (uint32_t)p0, d);
+        for (int kb = half; kb < KB; kb += 2) {
+            ok = ok && mbar_wait(&r_blk[kb], sp & 1, a.err, abort_flag);
+            uint8_t* blk = stage0 + kb * S::kRT;
+#pragma unroll 1
+            for (int kin = 0; kin < kKB; kin += 16) {
+                const int p0 = kb * kKB + kin;
+                float d[16], r[16];
+                tmem_ld16(t_inc + ((uint32_t)(32 * q) << 16) + (uint32_t)p0, d);
 #pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4) {
-                const float4 x = *reinterpret_cast<const float4*>(blk + swz(row, kin + 4 * k4));
-                r[4 * k4] = x.x; r[4 * k4 + 1] = x.y; r[4 * k4 + 2] = x.z; r[4 * k4 + 3] = x.w;
-            }
-            float o[16];
+                for (int k4 = 0; k4 < 4; ++k4) {
+                    const float4 x = *reinterpret_cast<const float4*>(blk + swz(row, kin + 4 * k4));
+                    r[4 * k4] = x.x; r[4 * k4 + 1] = x.y; r[4 * k4 + 2] = x.z; r[4 * k4 + 3] = x.w;
+                }
+                float o[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) o[i] = adv ? r[i] + fmaf(-s_dm[p0 + i], r[i], d[i]) : r[i];
-            if (has_shear) {
-                // start-of-step R^y of this chain: the next lane's row (axis 1)
-                const float sh = (float)s_shear[cl];
+                for (int i = 0; i < 16; ++i) o[i] = adv ? r[i] + fmaf(-s_dm[p0 + i], r[i], d[i]) : r[i];
+                if (has_shear) {
+                    // start-of-step R^y of this chain: the next lane's row (axis 1)
+                    const float sh = (float)s_shear[cl];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float ry = __shfl_down_sync(0xffffffffu, r[i], 1);
-                    if (adv && ax == 0) o[i] += sh * s_g[p0 + i] * ry;
+                    for (int i = 0; i < 16; ++i) {
+                        const float ry = __shfl_down_sync(0xffffffffu, r[i], 1);
+                        if (adv && ax == 0) o[i] += sh * s_g[p0 + i] * ry;
+                    }
+                }
+                if (p0 == 0) {
+                    // centre of mass in FP64 (p = 0 of Eq. d3 with zeta_0 = 0), kept in
+                    // registers for the whole launch
+                    const float d1 = __shfl_down_sync(0xffffffffu, d[0], 1);
+                    const float d2 = __shfl_down_sync(0xffffffffu, d[0], 2);
+                    if (adv && ax == 0) {
+                        const double ycm = cm_y;
+                        cm_x += (double)d[0] * a.inv_sqrtM + s_shear[cl] * a.dtau * ycm;
+                        cm_y += (double)d1 * a.inv_sqrtM;
+                        cm_z += (double)d2 * a.inv_sqrtM;
+                    }
+                    o[0] = 0.f;
+                }
+                if (live) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) finite = finite && isfinite(o[i]);
+                }
+                if (inrow) {
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4)
+                        *reinterpret_cast<float4*>(blk + swz(row, kin + 4 * k4)) =
+                            make_float4(o[4 * k4], o[4 * k4 + 1], o[4 * k4 + 2], o[4 * k4 + 3]);
                 }
             }
-            if (p0 == 0) {
-                // centre of mass in FP64 (p = 0 of Eq. d3 with zeta_0 = 0), kept in
-                // registers for the whole launch
-                const float d1 = __shfl_down_sync(0xffffffffu, d[0], 1);
-                const float d2 = __shfl_down_sync(0xffffffffu, d[0], 2);
-                if (adv && ax == 0) {
-                    const double ycm = cm_y;
-                    cm_x += (double)d[0] * a.inv_sqrtM + s_shear[cl] * a.dtau * ycm;
-                    cm_y += (double)d1 * a.inv_sqrtM;
-                    cm_z += (double)d2 * a.inv_sqrtM;
-                }
-                o[0] = 0.f;
-            }
-            if (live) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) finite = finite && isfinite(o[i]);
-            }
-            if (inrow) {
-#pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4)
-                    *reinterpret_cast<float4*>(blk + swz(row, kin + 4 * k4)) =
-                        make_float4(o[4 * k4], o[4 * k4 + 1], o[4 * k4 + 2], o[4 * k4 + 3]);
-            }
-        }
-        fence_proxy_async();
-        fence_before();           // D_inc read before the next step's MMAs write it
-        named_bar(1, kCompute);   // the tile is complete
-        if (ct == 0) {
-            if (ok) {
-                for (int k = 0; k < KB; ++k)
-                    for (int qq = 0; qq < 4; ++qq)
-                        tma_store_2d(&tmR, stage0 + k * S::kRT + qq * kQuarter, k * kKB, 3 * (c0 + qq * cpq));
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0 && ok) {
+                tma_store_2d(&tmR, blk + q * kQuarter, kb * kKB, 3 * (c0 + q * cpq));
                 tma_store_commit();
-                tma_store_wait();   // R is in global memory and the stages are free again
             }
-            mbar_arrive(epi_done);
         }
+        // R is in global memory and this warp's stage rows are free again; D_inc
+        // has been read before the next step's MMAs write it
+        if (lane == 0 && ok) tma_store_wait();
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(epi_done);
         }   // steps
         if (ok && own_cm) {
             double* cm = a.com + 3 * (size_t)(c0 + cl);
