@@ -43,9 +43,9 @@ template <> struct Normals<float> {
             make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), n, tag), make_uint2(seed, job));
         const float ra = sqrtf(-2.0f * logf(u01f(w.x)));
         const float rb = sqrtf(-2.0f * logf(u01f(w.z)));
-        float sa, ca, sb, cb;
+        float sa, ca;
         sincospif(2.0f * u01f(w.y), &sa, &ca);
-        sincospif(2.0f * u01f(w.w), &sb, &cb);
+        const float cb = cospif(2.0f * u01f(w.w));   // the pair's second value is not used
         g[0] = ra * ca; g[1] = ra * sa; g[2] = rb * cb;
     }
 };

@@ -22,14 +22,17 @@ from paper_1411_3487_gb300 import _lib, build
 pytestmark = pytest.mark.gpu
 
 TSTAR, NU = 0.034, 0.35
-TOL = {sfp.SFP_FP32_SIMT: 1e-5, sfp.SFP_FP32: 1e-5, sfp.SFP_FP64: 1e-9}
-# A "precision" parameter is (precision, kernel path): the SFP_FP32 path runs
-# fused (one kernel per step, M = 64/128/256) by default, or staged.
+TOL = {sfp.SFP_FP32_SIMT: 1e-5, sfp.SFP_FP32: 1e-5, sfp.SFP_MIXED_BF16: 1e-5, sfp.SFP_FP64: 1e-9}
+# A "precision" parameter is (precision, kernel path): the SFP_FP32 and
+# SFP_MIXED_BF16 paths run fused (one kernel per step, M = 64/128/256) by
+# default, or staged.
 SIMT = pytest.param((sfp.SFP_FP32_SIMT, sfp.SFP_PATH_STAGED), id="simt")
 TC = pytest.param((sfp.SFP_FP32, sfp.SFP_PATH_FUSED), id="tcgen05")
 TCS = pytest.param((sfp.SFP_FP32, sfp.SFP_PATH_STAGED), id="tcgen05_staged")
 F64 = pytest.param((sfp.SFP_FP64, sfp.SFP_PATH_STAGED), id="fp64")
-PRECISIONS = [SIMT, TC, TCS, F64]
+BF = pytest.param((sfp.SFP_MIXED_BF16, sfp.SFP_PATH_FUSED), id="bf16")
+BFS = pytest.param((sfp.SFP_MIXED_BF16, sfp.SFP_PATH_STAGED), id="bf16_staged")
+PRECISIONS = [SIMT, TC, TCS, F64, BF, BFS]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -219,7 +222,7 @@ def test_positions_round_trip_and_shape_observables():
         assert shape[c, :3] == pytest.approx(ref[:3] * d["d_nm"] ** 2, rel=1e-10)
 
 
-@pytest.mark.parametrize("precision", [SIMT, TC, TCS])
+@pytest.mark.parametrize("precision", [SIMT, TC, TCS, BF])
 def test_full_size_256bp_sampled(precision):
     """The 4096 x 256-bp workload at full size, in the benchmark's launch
     configuration; six sampled chains recomputed by the oracle."""
@@ -251,7 +254,7 @@ def test_budget_and_errors():
         b.step(-1)
 
 
-@pytest.mark.parametrize("precision", [SIMT, TC])
+@pytest.mark.parametrize("precision", [SIMT, TC, BF])
 def test_nonfinite_state_is_reported(precision):
     M, C = 64, 4
     b = make_batch(M, C, 10.0, precision)
