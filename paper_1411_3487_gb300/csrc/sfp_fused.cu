@@ -74,6 +74,11 @@ constexpr int kThreads = 64 + kCompute + 32 * kNoiseWarps;
 // A stage's A operand is written by one group, whose warps arrive once each
 // (lane 0, after __syncwarp) with weights that add up to the same count.
 constexpr int kReadyCount = kComputeWarps * kNoiseWarps;
+// Noise warps 10 + 4 t + u share lane quarter (2 + u) & 3: how many there are for
+// each u, and so for each quarter q (u = (q + 2) & 3).
+__device__ constexpr int kNoiseInQ[4] = {(kNoiseWarps + 3) / 4, (kNoiseWarps + 2) / 4, (kNoiseWarps + 1) / 4,
+                                         kNoiseWarps / 4};
+static_assert(2 + kComputeWarps == 10 && kComputeWarps == 8, "warp numbering of the quarters");
 
 // Shared memory of one CTA.  A stage holds [R (FP32, BF16 operands only)]
 // [A hi][A lo][B hi][B lo] for one K block of 32: TF32 operands are FP32-sized
@@ -193,7 +198,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     uint64_t* empty = bars + 8;         // MMAs done with the stage         (commit)
     uint64_t* u_done = bars + 12;       // all inverse MMAs done            (commit)
     uint64_t* inc_done = bars + 13;     // all forward MMAs done            (commit)
-    uint64_t* epi_done = bars + 15;     // epilogue stored R, stages free   (kComputeWarps)
+    uint64_t* epi_done = bars + 15;     // epilogue stored R, stages free   (every worker warp)
     uint32_t* tmem_slot = (uint32_t*)(bars + 16);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     int* s_freed = (int*)(tmem_slot + 2);   // last block whose stage the producer saw released
@@ -214,7 +219,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         mbar_init(u_done, 1);
         mbar_init(inc_done, 1);
         for (int k = 0; k < KB; ++k) mbar_init(&r_blk[k], 1);
-        mbar_init(epi_done, kComputeWarps);
+        mbar_init(epi_done, kComputeWarps + kNoiseWarps);
         *abort_flag = 0;
         *s_freed = -1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -246,6 +251,89 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     const uint32_t tmem = *tmem_slot;
     const uint32_t t_u = tmem, t_inc = tmem + NB;
     const bool has_shear = __syncthreads_or(threadIdx.x < Ct && s_shear[threadIdx.x] != 0.0) != 0;
+
+    // Epilogue of step sp (R += -dm R + D_inc (+ shear), Eqs. d3, btum) on the R
+    // tile that the producer reloads into the stage memory (KB column blocks of
+    // [128 rows][32], swizzled, each with its own barrier), in place.  The
+    // compute and noise warps of lane quarter q share it: worker w of nw takes
+    // the quarter's rows of column blocks w, w + nw, ... and TMA-stores each
+    // (block, quarter) box as soon as it is done.  Worker 0 (a compute warp)
+    // holds the centre of mass, which column block 0 updates.
+    auto epilogue = [&](int sp, int q, int w, int nw, bool& ok, bool& finite, double& cm_x, double& cm_y,
+                        double& cm_z) {
+        const int row = 32 * q + lane;
+        const int kq = lane / 3, ax = lane - 3 * (lane / 3);
+        const bool inrow = kq < cpq;
+        const int cl = inrow ? cpq * q + kq : 0;
+        const bool live = inrow && cl < Ct;
+        ok = ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag);
+        fence_after();
+        // a chain whose step counter has reached its stop step stays as it is
+        const bool adv = live && s_step[cl] + sp < s_stop[cl];
+#pragma unroll 1
+        for (int kb = w; kb < KB; kb += nw) {
+            ok = ok && mbar_wait(&r_blk[kb], sp & 1, a.err, abort_flag);
+            uint8_t* blk = stage0 + kb * S::kRT;
+#pragma unroll 1
+            for (int kin = 0; kin < kKB; kin += 16) {
+                const int p0 = kb * kKB + kin;
+                float d[16], r[16];
+                tmem_ld16(t_inc + ((uint32_t)(32 * q) << 16) + (uint32_t)p0, d);
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) {
+                    const float4 x = *reinterpret_cast<const float4*>(blk + swz(row, kin + 4 * k4));
+                    r[4 * k4] = x.x; r[4 * k4 + 1] = x.y; r[4 * k4 + 2] = x.z; r[4 * k4 + 3] = x.w;
+                }
+                float o[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) o[i] = adv ? r[i] + fmaf(-s_dm[p0 + i], r[i], d[i]) : r[i];
+                if (has_shear) {
+                    // start-of-step R^y of this chain: the next lane's row (axis 1)
+                    const float sh = (float)s_shear[cl];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const float ry = __shfl_down_sync(0xffffffffu, r[i], 1);
+                        if (adv && ax == 0) o[i] += sh * s_g[p0 + i] * ry;
+                    }
+                }
+                if (p0 == 0) {
+                    // centre of mass in FP64 (p = 0 of Eq. d3 with zeta_0 = 0), kept in
+                    // registers for the whole launch
+                    const float d1 = __shfl_down_sync(0xffffffffu, d[0], 1);
+                    const float d2 = __shfl_down_sync(0xffffffffu, d[0], 2);
+                    if (adv && ax == 0) {
+                        const double ycm = cm_y;
+                        cm_x += (double)d[0] * a.inv_sqrtM + s_shear[cl] * a.dtau * ycm;
+                        cm_y += (double)d1 * a.inv_sqrtM;
+                        cm_z += (double)d2 * a.inv_sqrtM;
+                    }
+                    o[0] = 0.f;
+                }
+                if (live) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) finite = finite && isfinite(o[i]);
+                }
+                if (inrow) {
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4)
+                        *reinterpret_cast<float4*>(blk + swz(row, kin + 4 * k4)) =
+                            make_float4(o[4 * k4], o[4 * k4 + 1], o[4 * k4 + 2], o[4 * k4 + 3]);
+                }
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0 && ok) {
+                tma_store_2d(&tmR, blk + q * kQuarter, kb * kKB, 3 * (c0 + q * cpq));
+                tma_store_commit();
+            }
+        }
+        // R is in global memory and this warp's stage rows are free again; D_inc
+        // has been read before the next step's MMAs write it
+        if (lane == 0 && ok) tma_store_wait();
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(epi_done);
+    };
 
     if (warp == 0) {
         // ---------------- TMA producer
@@ -371,7 +459,9 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         // if its stage is not free yet, block qn + 1 is drawn into `nxt` meanwhile
         // (the noise does not depend on the state), so the noise warps keep
         // drawing while the stages are held, e.g. through the epilogue.
-        bool ok = true;
+        bool ok = true, finite = true;
+        double cm_unused[3];
+        const int eq = warp & 3, et = (warp - 2 - kComputeWarps) / 4;   // epilogue quarter, worker 2 + et
         const int nq = a.n_steps * KB;
         float cur[kPerN][3], nxt[kPerN][3];
         bool have_nxt = false;
@@ -403,6 +493,10 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             }
             __syncwarp();
             if (lane == 0) mbar_arrive_cnt(&ready[s], kReadyCount / kNoiseWarps);
+            // after its last noise block, the step's epilogue (this warp's share)
+            if (j == KB - 1)
+                epilogue(sp, eq, 2 + et, 2 + kNoiseInQ[(eq + 2) & 3], ok, finite, cm_unused[0], cm_unused[1],
+                         cm_unused[2]);
             if (have_nxt) {
 #pragma unroll
                 for (int i = 0; i < kPerN; ++i)
@@ -413,6 +507,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 draw(qn + 1, cur);
             }
         }
+        if (!finite) atomicOr(a.err, 1);
     } else {
         // ---------------- compute warps 2..9: two per TMEM lane quarter q; lane
         // 3 k + axis of quarter q is axis `axis` of the quarter's chain k.
@@ -555,78 +650,8 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             arrive(s);
         }
 
-        // (3) epilogue: R += -dm R + D_inc (+ shear) on the R tile that the producer
-        // reloads into the stage memory (KB column blocks of [128 rows][32],
-        // swizzled, each with its own barrier), in place.  A warp owns the 32 rows
-        // of its lane quarter in every other column block and TMA-stores each
-        // (block, quarter) box as soon as it is done.
-        ok = ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag);
-        fence_after();
-        // a chain whose step counter has reached its stop step stays as it is
-        const bool adv = live && s_step[cl] + sp < s_stop[cl];
-#pragma unroll 1
-        for (int kb = half; kb < KB; kb += 2) {
-            ok = ok && mbar_wait(&r_blk[kb], sp & 1, a.err, abort_flag);
-            uint8_t* blk = stage0 + kb * S::kRT;
-#pragma unroll 1
-            for (int kin = 0; kin < kKB; kin += 16) {
-                const int p0 = kb * kKB + kin;
-                float d[16], r[16];
-                tmem_ld16(t_inc + ((uint32_t)(32 * q) << 16) + (uint32_t)p0, d);
-#pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4) {
-                    const float4 x = *reinterpret_cast<const float4*>(blk + swz(row, kin + 4 * k4));
-                    r[4 * k4] = x.x; r[4 * k4 + 1] = x.y; r[4 * k4 + 2] = x.z; r[4 * k4 + 3] = x.w;
-                }
-                float o[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) o[i] = adv ? r[i] + fmaf(-s_dm[p0 + i], r[i], d[i]) : r[i];
-                if (has_shear) {
-                    // start-of-step R^y of this chain: the next lane's row (axis 1)
-                    const float sh = (float)s_shear[cl];
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float ry = __shfl_down_sync(0xffffffffu, r[i], 1);
-                        if (adv && ax == 0) o[i] += sh * s_g[p0 + i] * ry;
-                    }
-                }
-                if (p0 == 0) {
-                    // centre of mass in FP64 (p = 0 of Eq. d3 with zeta_0 = 0), kept in
-                    // registers for the whole launch
-                    const float d1 = __shfl_down_sync(0xffffffffu, d[0], 1);
-                    const float d2 = __shfl_down_sync(0xffffffffu, d[0], 2);
-                    if (adv && ax == 0) {
-                        const double ycm = cm_y;
-                        cm_x += (double)d[0] * a.inv_sqrtM + s_shear[cl] * a.dtau * ycm;
-                        cm_y += (double)d1 * a.inv_sqrtM;
-                        cm_z += (double)d2 * a.inv_sqrtM;
-                    }
-                    o[0] = 0.f;
-                }
-                if (live) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) finite = finite && isfinite(o[i]);
-                }
-                if (inrow) {
-#pragma unroll
-                    for (int k4 = 0; k4 < 4; ++k4)
-                        *reinterpret_cast<float4*>(blk + swz(row, kin + 4 * k4)) =
-                            make_float4(o[4 * k4], o[4 * k4 + 1], o[4 * k4 + 2], o[4 * k4 + 3]);
-                }
-            }
-            fence_proxy_async();
-            __syncwarp();
-            if (lane == 0 && ok) {
-                tma_store_2d(&tmR, blk + q * kQuarter, kb * kKB, 3 * (c0 + q * cpq));
-                tma_store_commit();
-            }
-        }
-        // R is in global memory and this warp's stage rows are free again; D_inc
-        // has been read before the next step's MMAs write it
-        if (lane == 0 && ok) tma_store_wait();
-        fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(epi_done);
+        // (3) epilogue, shared with the noise warps of this lane quarter
+        epilogue(sp, q, half, 2 + kNoiseInQ[(q + 2) & 3], ok, finite, cm_x, cm_y, cm_z);
         }   // steps
         if (ok && own_cm) {
             double* cm = a.com + 3 * (size_t)(c0 + cl);
