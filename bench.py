@@ -423,6 +423,14 @@ def end_to_end(sfp, b, torch, steps):
             "d2h_bytes_per_step": n * 8, "steps": steps, "api": "sfp_set_modes + sfp_step + sfp_observe"}
 
 
+def bench_precision(sfp, args):
+    """The --precision choice as (sfp precision, name)."""
+    prec = {"bf16": sfp.SFP_MIXED_BF16, "tf32": sfp.SFP_FP32, "tc": sfp.SFP_FP32,
+            "simt": sfp.SFP_FP32_SIMT}[args.precision]
+    name = {sfp.SFP_MIXED_BF16: "SFP_MIXED_BF16", sfp.SFP_FP32: "SFP_FP32", sfp.SFP_FP32_SIMT: "SFP_FP32_SIMT"}[prec]
+    return prec, name
+
+
 def run_serving(args, rank):
     """Continuous-batching serving: Poisson arrivals of jobs with lengths
     uniform over 64/128/256/512 bp at their Table 2 steps, 10^U(3,5) steps,
@@ -439,7 +447,9 @@ def run_serving(args, rank):
     dt_ps = {64: 1.59, 128: 7.96, 256: 15.9, 512: 15.9}
     rng = np.random.default_rng(1)
     budget = int(args.serve_budget_mb * (1 << 20))
-    srv = sfp.Server(slots_per_pool=1024, quantum_steps=64, keep_results=False, hbm_budget_bytes=budget)
+    prec, prec_name = bench_precision(sfp, args)
+    srv = sfp.Server(slots_per_pool=1024, quantum_steps=64, keep_results=False, hbm_budget_bytes=budget,
+                     precision=prec)
     clk = ClockSampler(0)
     t0 = time.perf_counter()
     t_next, k, offered = 0.0, 0, 0.0
@@ -472,7 +482,7 @@ def run_serving(args, rank):
                                "10^U(3,5) steps, half sheared U[1e6,1e8]/s",
                    "rate_jobs_per_s": args.serve_rate, "arrival_window_s": args.serve_seconds,
                    "hbm_budget_bytes": budget, "slots_per_pool": 1024, "quantum_steps": 64,
-                   "precision": "SFP_FP32"},
+                   "precision": prec_name},
         "served_bead_steps_per_s": st["bead_steps"] / wall, "offered_bead_steps_per_s": offered / arrivals_s,
         "wall_s": wall, "peak_device_bytes_at_end": st["device_bytes"], "clocks": clocks,
     }
@@ -512,7 +522,7 @@ def run_precision(args, rank):
 
 def run_uneven(args, rank):
     """8192 chains with lengths uniform over 64/128/256/512 bp at their Table 1
-    steps (FP32, equilibrium starts): bead-steps/s of runs of 1000 steps per
+    steps (FP32 state, equilibrium starts): bead-steps/s of runs of 1000 steps per
     call, one launch per fused group per call, groups on their own streams; as
     created, after the chains-per-tile autotuner, and with graph replay."""
     if rank != 0:
@@ -524,6 +534,7 @@ def run_uneven(args, rank):
     build.build()
     torch.cuda.set_device(0)
     dt = {64: 10.0, 128: 50.0, 256: 100.0, 512: 100.0}
+    prec, prec_name = bench_precision(sfp, args)
     rng = np.random.default_rng(1)
     lengths = rng.choice([64, 128, 256, 512], size=8192)
     chains = [{"n_beads": int(M), "dtau": dt[int(M)], "job_id": i} for i, M in enumerate(lengths)]
@@ -531,7 +542,7 @@ def run_uneven(args, rank):
     stream = torch.cuda.current_stream()
     res = {}
     for name in ("as_created", "autotuned", "autotuned_graph"):
-        b = sfp.Batch(chains, seed=1, stream=stream)
+        b = sfp.Batch(chains, seed=1, stream=stream, precision=prec)
         b.init_equilibrium(0)
         tiles = b.autotune(20) if name != "as_created" else None
         if name == "autotuned_graph":
@@ -549,8 +560,8 @@ def run_uneven(args, rank):
         res[name] = {"value": beads * n / (ms * 1e-3), "ms_per_step": ms / n, "chains_per_tile": tiles}
         b.close()
     print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "8192 chains, lengths uniform over "
-                      "64/128/256/512 bp, dtau 10/50/100/100, FP32, 1000 steps per call (state stays in L2)",
-                      "beads": beads, "results": res}), flush=True)
+                      "64/128/256/512 bp, dtau 10/50/100/100, FP32 state, 1000 steps per call (state stays in L2)",
+                      "precision": prec_name, "beads": beads, "results": res}), flush=True)
 
 
 def main():

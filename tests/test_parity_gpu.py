@@ -287,15 +287,16 @@ def test_fused_and_staged_paths_agree():
     assert dcm < 1e-5 * math.sqrt(6 * TSTAR * dtau * 200 / M)
 
 
-@pytest.mark.parametrize("M,C", [(256, 50), (64, 100)])
-def test_fused_multi_step_launch_is_bit_exact(M, C):
+@pytest.mark.parametrize("prec", [sfp.SFP_FP32, sfp.SFP_MIXED_BF16], ids=["tf32", "bf16"])
+@pytest.mark.parametrize("M,C", [(256, 50), (64, 100), (128, 301)])
+def test_fused_multi_step_launch_is_bit_exact(M, C, prec):
     """sfp_step(n) runs n steps in one fused launch; chains are independent, so
     it must reproduce n launches of one step bit for bit (and the oracle)."""
     dtau = 50.0
     R = starts(M, C, dtau=dtau)
     out = []
     for split in (False, True):
-        b = make_batch(M, C, dtau, (sfp.SFP_FP32, sfp.SFP_PATH_FUSED))
+        b = make_batch(M, C, dtau, (prec, sfp.SFP_PATH_FUSED))
         b.set_modes(R)
         if split:
             for _ in range(37):
@@ -306,7 +307,7 @@ def test_fused_multi_step_launch_is_bit_exact(M, C):
         assert np.all(b.observe(sfp.SFP_OBS_STEP) == 37)
     assert np.array_equal(out[0], out[1])
     ref = O.Model(M, dtau=dtau).run_modes(R, 1, np.arange(C), 0, 37)
-    assert rel_err(out[0], ref).max() < TOL[sfp.SFP_FP32]
+    assert rel_err(out[0], ref).max() < TOL[prec]
 
 
 @pytest.mark.parametrize("M,C", [(256, 40), (512, 6), (64, 45)])

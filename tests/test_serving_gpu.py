@@ -40,7 +40,7 @@ def job(M, n_steps, job_id, shear=0.0):
     return {"n_beads": M, "dtau": DT.get(M, 10.0), "n_steps": n_steps, "job_id": job_id, "shear_rate_per_s": shear}
 
 
-@pytest.mark.parametrize("precision", [sfp.SFP_FP32, sfp.SFP_FP64], ids=["fp32", "fp64"])
+@pytest.mark.parametrize("precision", [sfp.SFP_FP32, sfp.SFP_MIXED_BF16, sfp.SFP_FP64], ids=["fp32", "bf16", "fp64"])
 def test_result_is_the_same_alone_and_in_the_mix(precision):
     probe = job(128, 301, 77, 1.0e8)
     with sfp.Server(precision=precision, slots_per_pool=64, quantum_steps=32) as s:
@@ -68,12 +68,12 @@ def test_result_is_the_same_alone_and_in_the_mix(precision):
         t5 = tickets[5]
         st = s.stats()
         assert st["finished"] == 41 and st["running"] == 0
-    if precision == sfp.SFP_FP32:
-        assert rel(mixed, alone) < 1e-6
-    else:
+    if precision == sfp.SFP_FP64:
         assert np.array_equal(mixed, alone)
+    else:
+        assert rel(mixed, alone) < 1e-6
     ref = oracle_run(128, 77, 301, 1.0e8)
-    assert rel(alone, ref) < (1e-5 if precision == sfp.SFP_FP32 else 1e-9)
+    assert rel(alone, ref) < (1e-9 if precision == sfp.SFP_FP64 else 1e-5)
 
 
 def test_jobs_stop_exactly_inside_a_quantum():
