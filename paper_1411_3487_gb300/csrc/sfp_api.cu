@@ -319,12 +319,22 @@ cudaError_t launch_mode_update(cudaStream_t st, T* R, const T* DH, const T* ZM, 
                                const T* dm, const T* h, const T* w, const T* g, const double* shear, int C, int M,
                                double w0, double dtau, int* bad, const int64_t* stop)
 {
+    // blocks of 128 threads (the kernel's launch bound): a row of modes (V per
+    // thread) times as many chains as fill the block
+    auto shape = [&](int lanes, dim3& blk, dim3& grid) {
+        blk = dim3((unsigned)std::min(lanes, 128), (unsigned)std::max(1, 128 / std::min(lanes, 128)));
+        grid = dim3(nblk(lanes, (int)blk.x), chains_y((C + (int)blk.y - 1) / (int)blk.y));
+    };
+    dim3 blk, grid;
+    const double w0_cm = w0 / std::sqrt((double)M);   // noise weight of the centre of mass
     if (sizeof(T) == 4 && M % 4 == 0) {
-        const dim3 grid(nblk(M / 4, 128), chains_y(C));
-        sfp::k_mode_update<T, 4><<<grid, 128, 0, st>>>(R, DH, ZM, com, step, dm, h, w, g, shear, C, M, w0, dtau, bad, stop);
+        shape(M / 4, blk, grid);
+        sfp::k_mode_update<T, 4><<<grid, blk, 0, st>>>(R, DH, ZM, com, step, dm, h, w, g, shear, C, M, w0_cm, dtau, bad,
+                                                        stop);
     } else {
-        const dim3 grid(nblk(M, 128), chains_y(C));
-        sfp::k_mode_update<T, 1><<<grid, 128, 0, st>>>(R, DH, ZM, com, step, dm, h, w, g, shear, C, M, w0, dtau, bad, stop);
+        shape(M, blk, grid);
+        sfp::k_mode_update<T, 1><<<grid, blk, 0, st>>>(R, DH, ZM, com, step, dm, h, w, g, shear, C, M, w0_cm, dtau, bad,
+                                                        stop);
     }
     return cudaGetLastError();
 }

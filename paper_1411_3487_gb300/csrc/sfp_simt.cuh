@@ -163,7 +163,7 @@ k_mode_update(T* __restrict__ R, const T* __restrict__ DH, const T* __restrict__
               double* __restrict__ com, int64_t* __restrict__ step,
               const T* __restrict__ dm, const T* __restrict__ h, const T* __restrict__ w,
               const T* __restrict__ g, const double* __restrict__ shear,
-              int C, int M, double w0, double dtau, int* __restrict__ bad,
+              int C, int M, double w0_cm, double dtau, int* __restrict__ bad,
               const int64_t* __restrict__ stop)
 {
     const int p0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
@@ -173,7 +173,7 @@ k_mode_update(T* __restrict__ R, const T* __restrict__ DH, const T* __restrict__
     load_v<T, V>(h + p0, hh);
     load_v<T, V>(w + p0, ww);
     load_v<T, V>(g + p0, gg);
-    for (int c = blockIdx.y; c < C; c += gridDim.y) {
+    for (int c = blockIdx.y * blockDim.y + threadIdx.y; c < C; c += gridDim.y * blockDim.y) {
         if (stop && step[c] >= stop[c]) continue;
         const size_t b = (size_t)c * 3 * M + p0;
         const double sh = shear[c];
@@ -195,12 +195,12 @@ k_mode_update(T* __restrict__ R, const T* __restrict__ DH, const T* __restrict__
             for (int a = 0; a < 3; ++a) fin = fin && isfinite(o[a][i]);
         }
         if (p0 == 0) {
-            // p = 0: the centre of mass in FP64 (zeta_0 = 0, Eq. d6 limit w_0)
-            const double inv = rsqrt((double)M);
+            // p = 0: the centre of mass in FP64 (zeta_0 = 0, Eq. d6 limit w_0;
+            // w0_cm = w_0 / sqrt(M))
             const double ycm = com[3 * c + 1];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                com[3 * c + a] += w0 * (double)zz[a][0] * inv;
+                com[3 * c + a] += w0_cm * (double)zz[a][0];
                 o[a][0] = r[a][0];
             }
             com[3 * c] += sh * dtau * ycm;
