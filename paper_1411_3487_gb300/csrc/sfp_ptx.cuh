@@ -211,9 +211,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
 
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// Orders this thread's generic-proxy global writes before later async-proxy
-// (TMA) accesses.
-__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // TMA tile store shared -> global (bulk-group completion), its commit, and a
 // wait until every committed store of this thread has completed.
@@ -225,11 +222,6 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void*
 }
 __device__ __forceinline__ void tma_store_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void tma_store_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
-__device__ __forceinline__ void named_bar(int id, int count)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
 
 }  // namespace ptx
 }  // namespace sfp
@@ -273,6 +265,39 @@ inline int make_map_2d(CUtensorMap* m, const float* base, int rows, int cols, in
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return report(-3, "cuTensorMapEncodeTiled failed");
     return 0;
+}
+
+// 2-D BF16 tensor [rows][cols] (cols contiguous), box = 32 cols x box_rows,
+// 64-byte swizzle.  Returns 0 or a negative SFP_E* code (after report()).
+inline int make_map_bf16(CUtensorMap* m, const void* base, int rows, int cols, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return report(-3, "cuTensorMapEncodeTiled unavailable");
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {32u, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return report(-3, "cuTensorMapEncodeTiled (bf16) failed");
+    return 0;
+}
+
+// FP32 -> BF16 bits with round to nearest even (finite values), and back.
+inline uint16_t bf16_round_host(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+inline float bf16_to_float_host(uint16_t h)
+{
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
 }
 
 // Round an FP64 value to the nearest TF32 (ties away from zero on the magnitude),

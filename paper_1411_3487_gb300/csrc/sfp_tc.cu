@@ -359,38 +359,6 @@ k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
 }
 
-// 2-D BF16 table [rows][cols], box 32 cols x box_rows, 64-byte swizzle.
-int make_map_bf16(CUtensorMap* m, const void* base, int rows, int cols, int box_rows)
-{
-    auto fn = encode_fn();
-    if (!fn) return report(SFP_ECUDA, "cuTensorMapEncodeTiled unavailable");
-    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)kKB, (cuuint32_t)box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return report(SFP_ECUDA, "cuTensorMapEncodeTiled (bf16) failed");
-    return SFP_OK;
-}
-
-uint16_t bf16_round_host(float f)
-{
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    u += 0x7FFFu + ((u >> 16) & 1u);   // round to nearest even
-    return (uint16_t)(u >> 16);
-}
-
-float bf16_to_float_host(uint16_t h)
-{
-    const uint32_t u = (uint32_t)h << 16;
-    float f;
-    std::memcpy(&f, &u, 4);
-    return f;
-}
-
 }  // namespace
 
 struct TcPlan {
