@@ -84,11 +84,13 @@ typedef struct sfp_chain_desc {
  *                 a three-pass TF32 hi/lo split, FP32 accumulate (fused step
  *                 for 64/128/256 beads, staged otherwise).
  * SFP_FP64        FP64 throughout (CUDA cores).
- * SFP_MIXED_BF16  FP32 state; staged transforms on the tensor cores with a
- *                 three-pass BF16 hi/lo split (kind::f16), FP32 accumulate:
- *                 about 16 bits per product, so trajectories drift from the
- *                 FP64 oracle by ~1e-4 rather than ~1e-6 (see the error per
- *                 observable of bench.py --workload precision).
+ * SFP_MIXED_BF16  FP32 state; transforms on the tensor cores with a three-pass
+ *                 BF16 hi/lo split (kind::f16), FP32 accumulate (fused step
+ *                 for 64/128/256 beads, staged otherwise).  The hi and lo
+ *                 parts carry about 16 bits of each operand; measured against
+ *                 the FP64 oracle, trajectories differ by 2-3e-6 after 1000
+ *                 steps on the fused step and ~1e-5 on the staged kernels,
+ *                 whose bead-space force has a larger dynamic range.
  * SFP_FP32_SIMT   FP32 throughout on the CUDA cores: the plain path. */
 enum { SFP_FP32 = 0, SFP_FP64 = 1, SFP_MIXED_BF16 = 2, SFP_FP32_SIMT = 4 };
 
@@ -161,7 +163,8 @@ enum { SFP_OBS_MODES = 0, SFP_OBS_POSITIONS = 1, SFP_OBS_COM = 2, SFP_OBS_STEP =
        SFP_OBS_SHAPE = 4, SFP_OBS_ACCUM = 5, SFP_OBS_MODE_POWER = 6, SFP_OBS_COM_MSD = 7 };
 int sfp_observe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
 
-/* Kernel path of the SFP_FP32 step (other precisions ignore it).
+/* Kernel path of the SFP_FP32 and SFP_MIXED_BF16 steps (other precisions
+ * ignore it).
  *   SFP_PATH_FUSED   (default) chains of 64, 128 or 256 beads take one kernel
  *                    per step and group: inverse transform, bond force, noise,
  *                    forward transform and mode update in one launch with the
