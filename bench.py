@@ -120,7 +120,9 @@ def run_reference(args, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"{sample} of {C_CHAINS} chains per step"},
+        "config": {"workload": WORKLOAD, "chains_per_gpu": C_CHAINS, "beads": M_BEADS, "dt_ps": DT_PS,
+                   "dtau": DT_PS / c_ps, "precision": "FP64 oracle (CPU)",
+                   "sample": f"{sample} of {C_CHAINS} chains per step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
                          "sample": f"{sample} chains x 256 beads x {args.steps} steps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
