@@ -41,8 +41,9 @@ template <> struct Normals<float> {
     {
         const uint4 w = philox4x32_10(
             make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), n, tag), make_uint2(seed, job));
-        const float ra = sqrtf(-2.0f * logf(u01f(w.x)));
-        const float rb = sqrtf(-2.0f * logf(u01f(w.z)));
+        // sqrt(t) as t rsqrt(t) (t >= 2^-23 here, never zero or denormal)
+        const float ta = -2.0f * logf(u01f(w.x)), tb = -2.0f * logf(u01f(w.z));
+        const float ra = ta * rsqrtf(ta), rb = tb * rsqrtf(tb);
         float sa, ca;
         sincospif(2.0f * u01f(w.y), &sa, &ca);
         const float cb = cospif(2.0f * u01f(w.w));   // the pair's second value is not used
