@@ -329,13 +329,26 @@ def run_native(args, rank, world, local):
         dist.destroy_process_group()
 
 
-def measured_traffic(profile: str, source: str):
-    """DRAM bytes per launch from a committed ncu summary under profiles/, or None
-    when the kernel source has changed since the counters were taken."""
+KERNEL_SOURCES = ("paper_1411_3487_gb300/csrc/sfp_fused.cu", "paper_1411_3487_gb300/csrc/sfp_device.cuh",
+                  "paper_1411_3487_gb300/csrc/sfp_ptx.cuh")
+
+
+def kernel_sha() -> str:
+    """First 16 hex digits of the SHA-256 of the fused kernel's sources, in order."""
     import hashlib
+    h = hashlib.sha256()
+    for src in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(profile: str, source: str = ""):
+    """DRAM bytes per launch from a committed ncu summary under profiles/, or None
+    when the kernel sources have changed since the counters were taken."""
     try:
         text = open(os.path.join(ROOT, "profiles", profile)).read()
-        sha = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()[:16]
+        sha = kernel_sha()
     except OSError:
         return None
     got = dict(line.split(":", 1) for line in text.splitlines()
