@@ -37,7 +37,11 @@ extern "C" {
 #define SFP_EINVAL     -1   /* bad argument (see sfp_last_error) */
 #define SFP_ENOMEM     -2   /* device allocation failed or exceeds the HBM budget */
 #define SFP_ECUDA      -3   /* a CUDA runtime call failed */
-#define SFP_ETIMEDOUT  -4   /* a bounded device wait gave up */
+#define SFP_ETIMEDOUT  -4   /* a bounded device wait gave up (every wait of the
+                               tensor-core kernels is limited to 1 s; the kernel
+                               then returns and the context stays usable; with
+                               SFP_TEST_STALL=1 in the environment the fused
+                               step stalls on purpose, to test this) */
 #define SFP_ENONFINITE -5   /* a chain's state became non-finite */
 #define SFP_ENOTSUP    -6   /* valid request this build does not support */
 

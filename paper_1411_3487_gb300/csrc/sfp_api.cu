@@ -6,6 +6,7 @@
 // r_cm[c][3]), per-chain keys/shear/step counters, and scratch for the
 // unfused step: r (beads), f|z (force and noise), DeltaH|Z (mode space).
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -305,6 +306,15 @@ int launch_gemm(sfp_batch* b, const T* In, const T* B, T* Out, int J, int Nc, in
 // grid y) and the mode update (4 modes per thread when M % 4 == 0).
 unsigned chains_y(int C) { return (unsigned)std::min(C, 65535); }
 
+// SFP_TEST_STALL=1 in the environment makes fused launches stall on purpose
+// (one bounded wait runs out), to test that a timeout is reported and the
+// context stays usable.
+int stall_test()
+{
+    const char* v = std::getenv("SFP_TEST_STALL");
+    return v && v[0] == '1' ? 1 : 0;
+}
+
 template <typename T>
 cudaError_t launch_force_noise(cudaStream_t st, const T* u, T* f, T* z, int C, int M, T c12nu, uint32_t seed,
                                const uint32_t* job, const int64_t* step)
@@ -410,6 +420,7 @@ int step_group_fused(sfp_batch* b, Group& g, int64_t n_steps)
     a.dtau = g.dtau;
     a.n_steps = (int)n_steps;
     a.cpt = sfp::fused_tile(g.fused);
+    a.stall_test = stall_test();
     if ((rc = sfp::fused_step(g.fused, a, b->cur))) return rc;
     b->launches++;
     g.last_fused = true;

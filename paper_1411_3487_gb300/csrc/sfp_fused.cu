@@ -203,6 +203,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     int* s_freed = (int*)(tmem_slot + 2);   // last block whose stage the producer saw released
     uint64_t* r_blk = bars + 18;        // R column block k reloaded for the epilogue (1 + tx), k < KB
+    uint64_t* never = bars + 26;        // nothing arrives here (the stall test)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cpq = a.cpt >> 2;         // chains per TMEM lane quarter (rows 32 q + 3 k + axis)
@@ -220,6 +221,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         mbar_init(inc_done, 1);
         for (int k = 0; k < KB; ++k) mbar_init(&r_blk[k], 1);
         mbar_init(epi_done, kComputeWarps + kNoiseWarps);
+        mbar_init(never, 1);
         *abort_flag = 0;
         *s_freed = -1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -386,6 +388,9 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         if (lane == 0) {
             constexpr uint32_t idesc = BF ? idesc_bf16(kRows, NB) : idesc_tf32(kRows, NB);
             bool ok = true;
+            // stall test: this wait runs out after its limit, raises the timeout bit
+            // and the abort flag, and every other wait of the CTA then gives up
+            if (a.stall_test) ok = mbar_wait(never, 0, a.err, abort_flag);
             for (int sp = 0; sp < a.n_steps; ++sp) {
             for (int blk = 0; blk < NBLK; ++blk) {
                 const int gb = sp * NBLK + blk;

@@ -26,6 +26,7 @@ struct FusedArgs {
     double dtau;
     int n_steps;            // steps per launch (>= 1)
     int cpt;                // chains per tile (4..40, a multiple of 4), as in the plan (fused_tile)
+    int stall_test;         // 1: the MMA thread first waits on a barrier nothing arrives at (tests the bounded waits)
 };
 
 // True when a group of M beads can take the fused step (M = 64, 128 or 256).

@@ -369,3 +369,28 @@ def test_bf16_fused_step_against_the_oracle(M, C):
     assert np.all(fused.observe(sfp.SFP_OBS_STEP) == 1000)
     with pytest.raises(sfp.SfpError):
         fused.probe(sfp.SFP_PROBE_DH)
+
+
+def test_pipeline_wait_timeout_is_reported(monkeypatch):
+    """Bounded waits: with SFP_TEST_STALL=1 the fused kernel's MMA thread first
+    waits on a barrier that nothing arrives at.  That wait gives up after its
+    1 s limit, raises the timeout bit and the abort flag, every other wait of
+    the CTA gives up too, and the kernel returns: the step reports
+    SFP_ETIMEDOUT, the state is left as it was, and the GPU context stays
+    usable for the next batch."""
+    M, C, dtau = 64, 8, 10.0
+    R = starts(M, C, dtau=dtau)
+    b = make_batch(M, C, dtau, (sfp.SFP_MIXED_BF16, sfp.SFP_PATH_FUSED))
+    b.set_modes(R)
+    monkeypatch.setenv("SFP_TEST_STALL", "1")
+    b.step(1)
+    with pytest.raises(sfp.SfpError) as e:
+        b.modes()
+    assert e.value.code == _lib.SFP_ETIMEDOUT
+    monkeypatch.delenv("SFP_TEST_STALL")
+    b.close()
+    b2 = make_batch(M, C, dtau, (sfp.SFP_MIXED_BF16, sfp.SFP_PATH_FUSED))
+    b2.set_modes(R)
+    b2.step(5)
+    ref = O.Model(M, dtau=dtau).run_modes(R, 1, np.arange(C), 0, 5)
+    assert rel_err(b2.modes(), ref).max() < TOL[sfp.SFP_MIXED_BF16]
