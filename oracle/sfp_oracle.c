@@ -13,7 +13,7 @@
  * modes p = 0..N, M = N+1.  Arrays of vectors are stored axis-major:
  * x[alpha*M + n] for alpha = 0,1,2.
  *
- * Readings of the paper taken here (each one is listed in the design doc):
+ * Readings of the paper taken here, where a passage is ambiguous or garbled:
  *   - Eq. c8 is printed with sqrt(2/(N+1)) for every p and "p = 0..N-1";
  *     the transform is square and orthonormal only with p = 0..N and
  *     phi_{n,0} = 1/sqrt(N+1) (Eq. c2).
