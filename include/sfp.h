@@ -43,7 +43,7 @@ extern "C" {
                                SFP_TEST_STALL=1 in the environment the fused
                                step stalls on purpose, to test this) */
 #define SFP_ENONFINITE -5   /* a chain's state became non-finite */
-#define SFP_ENOTSUP    -6   /* valid request this build does not support */
+#define SFP_ENOTSUP    -6   /* valid request that the library does not support */
 
 /* ---- model parameters (Eqs. a1-a3, Sec. 2A, Sec. 7B) --------------------- */
 typedef struct sfp_params {
