@@ -27,12 +27,12 @@
 // Both contractions run on the tcgen05 tensor cores as three passes
 // (A_hi B_lo + A_lo B_hi + A_hi B_hi, FP32 accumulate in TMEM): TF32 parts
 // (kind::tf32) for SFP_FP32, BF16 parts (kind::f16) for SFP_MIXED_BF16.
-// Roles (768 threads):
+// Roles (640 threads):
 //   warp 0       TMA producer: R tiles and chi hi/lo (inverse), F hi/lo (forward)
 //   warp 1       TMEM allocation; one thread issues every MMA and commit
 //   warps 2..9   compute: split the R tiles into hi/lo, read D_u (two warps per
 //                lane quarter) and write the force blocks, epilogue from D_inc
-//   warps 10..23 noise: Philox / Box-Muller normals written as the noise
+//   warps 10..19 noise: Philox / Box-Muller normals written as the noise
 //                blocks; the most arithmetic of a step, on warps of their own
 //                so that it runs beside the R split and the force
 // Block order (K blocks of 32; sched_decode): the inverse blocks first, with
@@ -68,7 +68,7 @@ constexpr int kChains = 40;                  // most chains per tile: 10 per TME
 constexpr int kQuarter = 32 * 128;           // bytes of 32 rows of a 128-byte-swizzled tile
 constexpr int kKB = 32;                      // K block: 32 FP32 = one 128-byte swizzle row
 constexpr int kComputeWarps = 8;             // R split, residual force, epilogue
-constexpr int kNoiseWarps = 14;              // Philox normals of the noise blocks
+constexpr int kNoiseWarps = 10;              // Philox normals of the noise blocks
 constexpr int kCompute = 32 * kComputeWarps;  // 256 threads
 constexpr int kThreads = 64 + kCompute + 32 * kNoiseWarps;
 // A stage's A operand is written by one group, whose warps arrive once each
