@@ -559,6 +559,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 for (int e = 0; e < kRows * 4 / kCompute; ++e) {
                     const int t = ct + kCompute * e;
                     const int r = t >> 2, c = t & 3;
+                    if ((r & 31) >= 3 * cpq) continue;   // padding rows of a lane quarter
                     uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int h2 = 0; h2 < 2; ++h2) {
@@ -586,6 +587,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 #pragma unroll
                 for (int i = 0; i < S::kA / 16 / kCompute; ++i) {
                     const int e = ct + kCompute * i;
+                    if (((e >> 3) & 31) >= 3 * cpq) continue;   // padding rows of a lane quarter
                     const float4 x = ah[e];
                     float4 h, l;
                     h.x = tf32_rna(x.x); l.x = tf32_rna(x.x - h.x);
