@@ -140,22 +140,23 @@ __device__ __forceinline__ void put_hi_lo(uint8_t* hi, uint8_t* lo, int r, int k
 // split R (phase 1) or form the force (phase 2):
 //   phase 1: I_0 N_0 I_1 | I_2 N_1 I_3 | ... (3 H blocks, ends with I_{KB-1})
 //   phase 2: F_0 N_H | F_1 N_{H+1} | ... | F_{H-1} N_{KB-1} | F_H ... F_{KB-1}
-// With FILL, N_H moves to the end of phase 1, where it keeps the tensor pipe
-// busy while the compute warps read the bond vectors out (the TF32 kernel's
-// MMAs take twice as long, so there the pipe is the scarcer resource):
-//   ... I_{KB-1} N_H | F_0 N_{H+1} | ... | F_{H-2} N_{KB-1} | F_{H-1} ... F_{KB-1}
-template <int KB, bool FILL>
+// With FILL = F > 0, N_H .. N_{H+F-1} move to the end of phase 1, where they
+// keep the tensor pipe busy while the compute warps read the bond vectors out
+// (the TF32 kernel's MMAs take twice as long, so there the pipe is the scarcer
+// resource; it uses F = 1, measured faster than F = 0 or 2; BF16 uses F = 0):
+//   ... I_{KB-1} N_H .. N_{H+F-1} | F_0 N_{H+F} | ... | F_{H-F-1} N_{KB-1} | F_{H-F} ... F_{KB-1}
+template <int KB, int FILL>
 __device__ __forceinline__ void sched_decode(int blk, int& kind, int& nb)   // kind: 0 I, 1 N, 2 F
 {
     constexpr int H = KB / 2;
-    constexpr int P = FILL ? 1 : 0;         // noise blocks moved into phase 1's tail
+    constexpr int P = FILL < H ? FILL : H;   // noise blocks moved into phase 1's tail
     if (blk < 3 * H) {
         const int m = blk / 3, r = blk - 3 * (blk / 3);
         kind = r == 1 ? 1 : 0;
         nb = r == 0 ? 2 * m : r == 1 ? m : 2 * m + 1;
-    } else if (FILL && blk == 3 * H) {
+    } else if (blk < 3 * H + P) {
         kind = 1;
-        nb = H;
+        nb = H + (blk - 3 * H);
     } else {
         const int b = blk - 3 * H - P;
         if (b < 2 * (H - P)) {
@@ -168,14 +169,14 @@ __device__ __forceinline__ void sched_decode(int blk, int& kind, int& nb)   // k
     }
 }
 template <int KB> __device__ __forceinline__ int sched_inv(int k) { return 3 * (k >> 1) + ((k & 1) ? 2 : 0); }
-template <int KB, bool FILL> __device__ __forceinline__ int sched_noise(int j)
+template <int KB, int FILL> __device__ __forceinline__ int sched_noise(int j)
 {
-    constexpr int H = KB / 2, P = FILL ? 1 : 0;
-    return j < H ? 3 * j + 1 : (FILL && j == H) ? 3 * H : 3 * H + P + 2 * (j - H - P) + 1;
+    constexpr int H = KB / 2, P = FILL < H ? FILL : H;
+    return j < H ? 3 * j + 1 : j < H + P ? 3 * H + (j - H) : 3 * H + P + 2 * (j - H - P) + 1;
 }
-template <int KB, bool FILL> __device__ __forceinline__ int sched_force(int k)
+template <int KB, int FILL> __device__ __forceinline__ int sched_force(int k)
 {
-    constexpr int H = KB / 2, P = FILL ? 1 : 0;
+    constexpr int H = KB / 2, P = FILL < H ? FILL : H;
     return k < H - P ? 3 * H + P + 2 * k : 3 * H + P + 2 * (H - P) + (k - (H - P));
 }
 
@@ -364,7 +365,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 uint8_t* bh = st + S::kR + 2 * S::kA;
                 uint8_t* bl = bh + S::kB;
                 int kind, nb;
-                sched_decode<KB, !BF>(blk, kind, nb);
+                sched_decode<KB, BF ? 0 : 1>(blk, kind, nb);
                 if (kind == 0) {
                     // inverse: the R tile (FP32, one box per lane quarter) and chi
                     mbar_expect_tx(&full[s], rblock + 2 * S::kB);
@@ -407,7 +408,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 const int s = gb % ST;
                 const uint32_t ph = (gb / ST) & 1;
                 int kind, nb;
-                sched_decode<KB, !BF>(blk, kind, nb);
+                sched_decode<KB, BF ? 0 : 1>(blk, kind, nb);
                 ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
                 ok = ok && mbar_wait(&ready[s], ph, a.err, abort_flag);
                 if (ok) {
@@ -484,7 +485,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 #pragma unroll 1
         for (int qn = 0; qn < nq; ++qn) {
             const int sp = qn / KB, j = qn - sp * KB;
-            const int blk = sp * NBLK + sched_noise<KB, !BF>(j), s = blk % ST;
+            const int blk = sp * NBLK + sched_noise<KB, BF ? 0 : 1>(j), s = blk % ST;
             // Consecutive noise blocks may lie more than ST blocks apart, where a
             // parity wait on the stage's barrier is ambiguous: wait instead until
             // the producer has seen the stage released for this block (which it
@@ -628,7 +629,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 const float fac = __shfl_sync(0xffffffffu, rsqrtf(t) - a.c12nu, src0);
                 v[i] = (live && col + i >= 1) ? v[i] * fac : 0.f;
             }
-            const int blk = g0 + sched_force<KB, !BF>(nb), s = blk % ST;
+            const int blk = g0 + sched_force<KB, BF ? 0 : 1>(nb), s = blk % ST;
             const uint32_t ph = (blk / ST) & 1;
             ok = ok && mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
             if (ok && inrow) {
