@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--serve-budget-mb", type=float, default=40e3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-512", action="store_true", help="skip the 16384 x 512-bp legs")
     return ap.parse_args()
 
 
@@ -298,6 +299,46 @@ def run_native(args, rank, world, local):
             other.update({"precision": PREC_NAME[o_prec], "dtype": DTYPE[o_prec],
                           "roofline": roofline(other["kernels_us"], pk, how, o_prec, sfp.SFP_PATH_FUSED, sfp)})
 
+    # the mixed-precision workload, 16384 chains x 512 bp at dt 15.9 ps: the fused
+    # step (a tile per cluster of two CTAs) with each split, the staged
+    # tensor-core kernels and the plain path; calls of 20 steps after an L2 flush
+    big = None
+    if rank == 0 and not args.no_512 and precision != sfp.SFP_FP32_SIMT:
+        b.close()
+        big = {"workload": "16384 chains x 512 bp, dt 15.9 ps, equilibrium starts, no shear", "chains": 16384,
+               "beads": 512}
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        for name, prec, pth in (("fused_bf16x3", sfp.SFP_MIXED_BF16, sfp.SFP_PATH_FUSED),
+                                ("fused_tf32x3", sfp.SFP_FP32, sfp.SFP_PATH_FUSED),
+                                ("staged_bf16x3", sfp.SFP_MIXED_BF16, sfp.SFP_PATH_STAGED),
+                                ("plain_fp32", sfp.SFP_FP32_SIMT, sfp.SFP_PATH_STAGED)):
+            bb = sfp.Batch([{"n_beads": 512, "dt_ps": DT_PS, "job_id": j} for j in range(16384)], seed=1,
+                           precision=prec, stream=stream)
+            bb.set_path(pth)
+            bb.init_equilibrium(0)
+            calls = 5 if pth == sfp.SFP_PATH_FUSED else 2
+            for _ in range(2):
+                bb.step(20)
+            torch.cuda.synchronize()
+            t_ms = 0.0
+            for _ in range(calls):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                bb.step(20)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t_ms += e0.elapsed_time(e1)
+            n = 20 * calls
+            big[name] = {"value": 16384 * 512 * n / (t_ms * 1e-3), "unit": UNIT, "us_per_step": 1e3 * t_ms / n}
+            if pth == sfp.SFP_PATH_FUSED:
+                big[name]["kernel"] = "k_fused_step<256, %s, pair>" % ("bf16" if prec == sfp.SFP_MIXED_BF16 else "tf32")
+                big[name]["roofline_tensor_frac"] = (3 * 18 * 512 * 16384 * 512 / (1e-3 * t_ms / n)) / 1e12 / (
+                    pk["bf16_tflops"] * (1.0 if prec == sfp.SFP_MIXED_BF16 else 1.1 / 2.25))
+            bb.modes()      # raises if a kernel reported an error
+            bb.close()
+        del flush
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n_c, n_s = 512, 768
@@ -321,7 +362,8 @@ def run_native(args, rank, world, local):
             "sim_ns_per_s_per_chain": DT_PS * 1e-3 * args.steps / (tot_ms * 1e-3),
             "roofline": roof, "kernels_us": kern, "cpu_baseline": cpu, "e2e": e2e,
             "sustained": sustained, "plain_path": plain, "staged_path": staged,
-            "other_split_fused": other, "single_step_calls": single, "clocks": clocks,
+            "other_split_fused": other, "single_step_calls": single, "mixed_precision_512bp": big,
+            "clocks": clocks,
             "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)

@@ -86,11 +86,11 @@ typedef struct sfp_chain_desc {
 /* Arithmetic of the step.
  * SFP_FP32        FP32 state; transforms on the tensor cores (tcgen05) with
  *                 a three-pass TF32 hi/lo split, FP32 accumulate (fused step
- *                 for 64/128/256 beads, staged otherwise).
+ *                 for 64/128/256/512 beads, staged otherwise).
  * SFP_FP64        FP64 throughout (CUDA cores).
  * SFP_MIXED_BF16  FP32 state; transforms on the tensor cores with a three-pass
  *                 BF16 hi/lo split (kind::f16), FP32 accumulate (fused step
- *                 for 64/128/256 beads, staged otherwise).  The hi and lo
+ *                 for 64/128/256/512 beads, staged otherwise).  The hi and lo
  *                 parts carry about 16 bits of each operand; measured against
  *                 the FP64 oracle, trajectories differ by 2-3e-6 after 1000
  *                 steps on the fused step and ~1e-5 on the staged kernels,
@@ -169,11 +169,13 @@ int sfp_observe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
 
 /* Kernel path of the SFP_FP32 and SFP_MIXED_BF16 steps (other precisions
  * ignore it).
- *   SFP_PATH_FUSED   (default) chains of 64, 128 or 256 beads take one kernel
- *                    per step and group: inverse transform, bond force, noise,
- *                    forward transform and mode update in one launch with the
- *                    intermediates kept on chip (TMEM and shared memory);
- *                    other lengths take the staged path.
+ *   SFP_PATH_FUSED   (default) chains of 64, 128, 256 or 512 beads take one
+ *                    kernel per step and group: inverse transform, bond force,
+ *                    noise, forward transform and mode update in one launch
+ *                    with the intermediates kept on chip (TMEM and shared
+ *                    memory; at 512 beads a tile runs on a cluster of two
+ *                    CTAs, one per half of the bonds and modes); other lengths
+ *                    take the staged path.
  *   SFP_PATH_STAGED  one kernel per stage; keeps the intermediate arrays, so
  *                    sfp_probe works after the step.
  * Both give the same trajectory within FP32 rounding.  SFP_EINVAL otherwise. */

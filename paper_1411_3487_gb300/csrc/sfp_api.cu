@@ -185,7 +185,7 @@ struct Group {
     double* stage = nullptr;      // [C][3][M] FP64 staging
     double* stage2 = nullptr;     // [C][3][M] FP64 staging
     sfp::TcPlan* tc = nullptr;    // tensor-core transform plan (SFP_FP32)
-    sfp::FusedPlan* fused = nullptr;   // one-kernel step (SFP_FP32, M = 64, 128, 256)
+    sfp::FusedPlan* fused = nullptr;   // one-kernel step (SFP_FP32 / SFP_MIXED_BF16, M = 64 .. 512)
     bool last_fused = false;      // the most recent step of this group ran fused
     cudaStream_t gs = nullptr;    // this group's stream (batches of several groups)
     cudaEvent_t join = nullptr;
@@ -1179,6 +1179,7 @@ int sfp_observe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
     int bad = 0;
     CUDA_TRY(cudaMemcpyAsync(&bad, b->bad, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     CUDA_TRY(cudaStreamSynchronize(b->stream));
+    if (bad & 4) return fail(SFP_ECUDA, "a 512-bead fused step ran without its two-CTA cluster");
     if (bad & 2) return fail(SFP_ETIMEDOUT, "a tensor-core pipeline wait timed out");
     if (bad & 1) return fail(SFP_ENONFINITE, "a chain's state became non-finite");
     return SFP_OK;
@@ -1403,8 +1404,9 @@ int sfp_autotune(sfp_batch* b, int32_t trial_steps, int32_t* chains_per_tile)
     for (size_t k = 0; k < fg.size() && !rc; ++k) {
         Group& g = b->groups[fg[k]];
         std::vector<int> cs;
+        const int units = sms / sfp::fused_ctas_per_tile(g.fused);   // tiles that fit one wave
         for (double f : {1.0, 0.75, 0.5, 1.0 / 3.0, 0.25}) {
-            const int target = std::max(1, (int)(f * sms));
+            const int target = std::max(1, (int)(f * units));
             cs.push_back(std::min(40, ((g.C + target - 1) / target + 3) / 4 * 4));
         }
         cs.push_back(40);
@@ -1434,7 +1436,8 @@ int sfp_autotune(sfp_batch* b, int32_t trial_steps, int32_t* chains_per_tile)
                 const auto& cnd = cand[k][idx[k]];
                 const Group& g = b->groups[fg[k]];
                 mx = std::max(mx, cnd.second);
-                share += cnd.second * (double)((g.C + cnd.first - 1) / cnd.first) / sms;
+                share += cnd.second * (double)((g.C + cnd.first - 1) / cnd.first) *
+                         sfp::fused_ctas_per_tile(g.fused) / sms;
             }
             const double est = std::max(mx, share);
             if (est < best) {
@@ -1707,6 +1710,7 @@ int sfp::internal_slots_read(sfp_batch* b, const int32_t* slots, int32_t n, doub
     }
     int bad = 0;
     CUDA_TRY(cudaMemcpy(&bad, b->bad, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bad & 4) return fail(SFP_ECUDA, "a 512-bead fused step ran without its two-CTA cluster");
     if (bad & 2) return fail(SFP_ETIMEDOUT, "a tensor-core pipeline wait timed out");
     if (bad & 1) return fail(SFP_ENONFINITE, "a chain's state became non-finite");
     return SFP_OK;

@@ -1,6 +1,6 @@
 // sfp_fused.cu -- mode-space steps (Sec. 4) for tiles of up to 40 chains of
-// the SFP_FP32 and SFP_MIXED_BF16 paths, M = 64, 128 or 256 beads, n_steps
-// per launch.
+// the SFP_FP32 and SFP_MIXED_BF16 paths, M = 64, 128, 256 or 512 beads,
+// n_steps per launch.
 //
 // The 128 TMEM lanes hold a tile's chain-axis rows: lane quarter q (rows
 // 32 q .. 32 q + 31) holds chains q cpq .. q cpq + cpq - 1 of the tile
@@ -42,9 +42,28 @@
 // Chains never interact, so a CTA runs all n_steps of its tile without any
 // grid-wide synchronisation: TMEM stays allocated, the tables stream again
 // from L2, and the state goes through global memory (L2) between steps.
+//
+// M = 512 (PAIR): D_u and D_inc would take 1024 TMEM columns, twice an SM's
+// 512, so a cluster of two CTAs shares each tile.  CTA h (cluster rank) holds
+// bonds and modes 256 h .. 256 h + 255 (D_u and D_inc halves of 256 columns,
+// B operands = those rows of chi and F) and runs all 3 x 16 K blocks of a
+// step.  The A operand of every block (R split, force or noise, all 128
+// rows) is needed by both: each block has one owner (blocks of schedule index
+// i are owned by CTA i & 1), which writes it into its own stage; the MMA
+// thread then bulk-copies it into the same stage of the other CTA (completing
+// as transaction bytes of that CTA's `full` barrier) as soon as it is written:
+// its loop polls the next block to multiply and the next block to send, so
+// neither waits for the other.  Force blocks are owned
+// by the CTA whose D_u half holds their bonds.  A stage is reused only when
+// the MMAs of both CTAs are done with it (`empty` counts two multicast
+// commits), and a step's first blocks are written only after both CTAs'
+// epilogues of the previous step (`peer_epi`).  Each CTA updates its own mode
+// half; rank 0 holds the centre of mass.
 // Every wait is bounded (1 s); after a timeout the CTA raises bit 1 of the
-// error word, skips all further work but still passes every barrier, frees
-// its TMEM and returns.
+// error word and sets its abort flag; from then on every wait of the CTA gives
+// up at once, and a role that has given up makes no further arrival, commit
+// or copy (arrivals of different blocks could otherwise meet in one phase of a
+// barrier and exceed its count).  The CTA frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -180,7 +199,15 @@ template <int KB, int FILL> __device__ __forceinline__ int sched_force(int k)
     return k < H - P ? 3 * H + P + 2 * k : 3 * H + P + 2 * (H - P) + (k - (H - P));
 }
 
-template <int NB, bool BF>
+// Bead block of force block k (schedule index): a PAIR CTA owns the force
+// blocks of odd or even k, and its D_u half holds bond blocks 8 h .. 8 h + 7.
+template <int KBL, bool PAIR> __device__ __forceinline__ int force_bonds(int k)
+{
+    return PAIR ? KBL * (k & 1) + (k >> 1) : k;
+}
+
+// NB: TMEM columns of each half (D_u, D_inc) of one CTA; M = NB, or 2 NB for PAIR.
+template <int NB, bool BF, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
 k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmChiH,
              const __grid_constant__ CUtensorMap tmChiL, const __grid_constant__ CUtensorMap tmFH,
@@ -188,8 +215,11 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 {
     using S = FSmem<NB, BF>;
     constexpr int ST = S::kStages;
-    constexpr int KB = NB / kKB;        // inverse K blocks = forward bead blocks
+    constexpr int KBL = NB / kKB;       // column blocks of this CTA (epilogue; owned blocks of each kind)
+    constexpr int KB = PAIR ? 2 * KBL : KBL;   // inverse K blocks = forward bead blocks = M / 32
+    constexpr int MB = KB * kKB;        // beads M
     constexpr int NBLK = 3 * KB;        // blocks of one step, in the order of sched_decode
+    constexpr int FILL = BF ? 0 : 1;
     static_assert(KB % 2 == 0, "the block schedule pairs bead blocks");
     constexpr uint32_t kCols = 2 * NB;  // D_u in [0, NB), D_inc in [NB, 2 NB)
 
@@ -213,12 +243,21 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     uint32_t* tmem_slot = (uint32_t*)(bars + 16);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     int* s_freed = (int*)(tmem_slot + 2);   // last block whose stage the producer saw released
-    uint64_t* r_blk = bars + 18;        // R column block k reloaded for the epilogue (1 + tx), k < KB
+    uint64_t* r_blk = bars + 18;        // R column block k reloaded for the epilogue (1 + tx), k < KBL
     uint64_t* never = bars + 26;        // nothing arrives here (the stall test)
+    uint64_t* both_done = bars + 27;    // PAIR: the MMAs of both CTAs done with the step (2 commits)
+    uint64_t* peer_epi = bars + 28;     // PAIR: the other CTA's epilogue done (its producer arrives)
 
+    if (PAIR && cluster_size() != 2u) {
+        // every access to the other CTA below assumes a cluster of two
+        if (threadIdx.x == 0) atomicOr(a.err, 4);
+        return;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cpq = a.cpt >> 2;         // chains per TMEM lane quarter (rows 32 q + 3 k + axis)
-    const int c0 = blockIdx.x * a.cpt;
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;   // PAIR: this CTA's bead / mode half
+    const int col0 = (int)rank * NB;    // first bond and mode of this CTA's TMEM columns
+    const int c0 = (PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x) * a.cpt;
     const int Ct = min(a.cpt, a.C - c0);
     const uint32_t rblock = 4u * 3u * (uint32_t)cpq * 128u;   // bytes of one R column block
 
@@ -226,13 +265,15 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         for (int s = 0; s < ST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&ready[s], kReadyCount);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], PAIR ? 2 : 1);
         }
         mbar_init(u_done, 1);
         mbar_init(inc_done, 1);
-        for (int k = 0; k < KB; ++k) mbar_init(&r_blk[k], 1);
+        for (int k = 0; k < KBL; ++k) mbar_init(&r_blk[k], 1);
         mbar_init(epi_done, kComputeWarps + kNoiseWarps);
         mbar_init(never, 1);
+        mbar_init(both_done, 2);
+        mbar_init(peer_epi, 1);
         *abort_flag = 0;
         *s_freed = -1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -242,11 +283,11 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmFH)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmFL)) : "memory");
     }
-    for (int p = threadIdx.x; p < NB; p += kThreads) {
-        s_dm[p] = a.dm[p];
-        s_g[p] = a.g[p];
+    for (int p = threadIdx.x; p < NB; p += blockDim.x) {
+        s_dm[p] = a.dm[col0 + p];
+        s_g[p] = a.g[col0 + p];
     }
-    for (int i = threadIdx.x; i < kChains; i += kThreads) {
+    for (int i = threadIdx.x; i < kChains; i += blockDim.x) {
         const bool live = i < Ct;
         s_job[i] = live ? a.job[c0 + i] : 0u;
         s_step[i] = live ? a.step[c0 + i] : 0;
@@ -259,15 +300,16 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     fence_before();
-    __syncthreads();
+    if constexpr (PAIR) cluster_sync();   // both CTAs' barriers are initialised
+    else __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
     const uint32_t t_u = tmem, t_inc = tmem + NB;
     const bool has_shear = __syncthreads_or(threadIdx.x < Ct && s_shear[threadIdx.x] != 0.0) != 0;
 
     // Epilogue of step sp (R += -dm R + D_inc (+ shear), Eqs. d3, btum) on the R
-    // tile that the producer reloads into the stage memory (KB column blocks of
-    // [128 rows][32], swizzled, each with its own barrier), in place.  The
+    // tile that the producer reloads into the stage memory (KBL column blocks of
+    // [128 rows][32], swizzled, each with its own barrier; modes col0 + ...), in place.  The
     // compute and noise warps of lane quarter q share it: worker w of nw takes
     // the quarter's rows of column blocks w, w + nw, ... and TMA-stores each
     // (block, quarter) box as soon as it is done.  Worker 0 (a compute warp)
@@ -284,7 +326,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         // a chain whose step counter has reached its stop step stays as it is
         const bool adv = live && s_step[cl] + sp < s_stop[cl];
 #pragma unroll 1
-        for (int kb = w; kb < KB; kb += nw) {
+        for (int kb = w; kb < KBL; kb += nw) {
             ok = ok && mbar_wait(&r_blk[kb], sp & 1, a.err, abort_flag);
             uint8_t* blk = stage0 + kb * S::kRT;
 #pragma unroll 1
@@ -309,7 +351,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                         if (adv && ax == 0) o[i] += sh * s_g[p0 + i] * ry;
                     }
                 }
-                if (p0 == 0) {
+                if (col0 + p0 == 0) {
                     // centre of mass in FP64 (p = 0 of Eq. d3 with zeta_0 = 0), kept in
                     // registers for the whole launch
                     const float d1 = __shfl_down_sync(0xffffffffu, d[0], 1);
@@ -336,7 +378,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             fence_proxy_async();
             __syncwarp();
             if (lane == 0 && ok) {
-                tma_store_2d(&tmR, blk + q * kQuarter, kb * kKB, 3 * (c0 + q * cpq));
+                tma_store_2d(&tmR, blk + q * kQuarter, col0 + kb * kKB, 3 * (c0 + q * cpq));
                 tma_store_commit();
             }
         }
@@ -345,7 +387,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         if (lane == 0 && ok) tma_store_wait();
         fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(epi_done);
+        if (lane == 0 && ok) mbar_arrive(epi_done);
     };
 
     if (warp == 0) {
@@ -353,45 +395,71 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         if (lane == 0) {
           bool ok = true;
           for (int sp = 0; sp < a.n_steps && ok; ++sp) {
-            // the previous step's epilogue used the stage memory and stored R
-            if (sp > 0 && !mbar_wait(epi_done, (sp - 1) & 1, a.err, abort_flag)) break;
+            if (sp > 0) {
+                // the previous step's epilogue used the stage memory and stored R
+                if (!mbar_wait(epi_done, (sp - 1) & 1, a.err, abort_flag)) break;
+                if constexpr (PAIR) {
+                    // ... and so did the other CTA's, into whose stages this CTA copies
+                    mbar_arrive_remote(mapa(smem_u32(peer_epi), rank ^ 1u));
+                    if (!mbar_wait_cl(peer_epi, (sp - 1) & 1, a.err, abort_flag)) break;
+                }
+            }
             for (int blk = 0; blk < NBLK; ++blk) {
                 const int gb = sp * NBLK + blk;
                 const int s = gb % ST;
                 const uint32_t ph = (gb / ST) & 1;
-                if (!mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag)) { ok = false; break; }
+                const bool freed = PAIR ? mbar_wait_cl(&empty[s], ph ^ 1, a.err, abort_flag)
+                                        : mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
+                if (!freed) { ok = false; break; }
                 st_release_smem(s_freed, gb);   // block gb may be written into stage s
                 uint8_t* st = stage0 + s * S::kStage;
                 uint8_t* bh = st + S::kR + 2 * S::kA;
                 uint8_t* bl = bh + S::kB;
                 int kind, nb;
-                sched_decode<KB, BF ? 0 : 1>(blk, kind, nb);
+                sched_decode<KB, FILL>(blk, kind, nb);
+                // PAIR: a block of the other CTA arrives with its A operand copied in
+                const bool own = !PAIR || (uint32_t)(nb & 1) == rank;
+                const uint32_t a_in = own ? 0u : 2u * S::kA;
                 if (kind == 0) {
-                    // inverse: the R tile (FP32, one box per lane quarter) and chi
-                    mbar_expect_tx(&full[s], rblock + 2 * S::kB);
-                    tma_load_2d(bh, &tmChiH, &full[s], nb * kKB, 0);
-                    tma_load_2d(bl, &tmChiL, &full[s], nb * kKB, 0);
-                    for (int q = 0; q < 4; ++q)
-                        tma_load_2d(st + q * kQuarter, &tmR, &full[s], nb * kKB, 3 * (c0 + q * cpq));
+                    // inverse: the R tile (FP32, one box per lane quarter) and chi rows of the bond half
+                    mbar_expect_tx(&full[s], (own ? rblock : 0u) + 2 * S::kB + a_in);
+                    tma_load_2d(bh, &tmChiH, &full[s], nb * kKB, col0);
+                    tma_load_2d(bl, &tmChiL, &full[s], nb * kKB, col0);
+                    if (own)
+                        for (int q = 0; q < 4; ++q)
+                            tma_load_2d(st + q * kQuarter, &tmR, &full[s], nb * kKB, 3 * (c0 + q * cpq));
                 } else {
                     // noise block nb: rows w_p phi (t = 1); force block nb: rows h_p chi (t = 0)
                     const bool noise = kind == 1;
-                    mbar_expect_tx(&full[s], 2 * S::kB);
-                    tma_load_2d(bh, &tmFH, &full[s], nb * kKB, noise ? NB : 0);
-                    tma_load_2d(bl, &tmFL, &full[s], nb * kKB, noise ? NB : 0);
+                    const int x = (noise ? nb : force_bonds<KBL, PAIR>(nb)) * kKB;
+                    mbar_expect_tx(&full[s], 2 * S::kB + a_in);
+                    tma_load_2d(bh, &tmFH, &full[s], x, (noise ? MB : 0) + col0);
+                    tma_load_2d(bl, &tmFL, &full[s], x, (noise ? MB : 0) + col0);
                 }
+                if (!own) mbar_arrive_cnt(&ready[s], kReadyCount);   // no local writer
             }
-            // every stage is free once the forward MMAs are done: reload the R tile
-            // (KB column blocks of [128 rows][32]) there for the epilogue
-            if (ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag)) {
-                for (int k = 0; k < KB; ++k) {
+            // every stage is free once the forward MMAs (of both CTAs) are done:
+            // reload the R tile (KBL column blocks of [128 rows][32]) there for the epilogue
+            bool reload = ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag);
+            if constexpr (PAIR) reload = reload && mbar_wait_cl(both_done, sp & 1, a.err, abort_flag);
+            if (reload) {
+                for (int k = 0; k < KBL; ++k) {
                     mbar_expect_tx(&r_blk[k], rblock);
                     for (int q = 0; q < 4; ++q)
-                        tma_load_2d(stage0 + k * S::kRT + q * kQuarter, &tmR, &r_blk[k], k * kKB, 3 * (c0 + q * cpq));
+                        tma_load_2d(stage0 + k * S::kRT + q * kQuarter, &tmR, &r_blk[k], col0 + k * kKB,
+                                    3 * (c0 + q * cpq));
                 }
             } else {
                 ok = false;
             }
+          }
+          if constexpr (PAIR) {
+              // the other CTA's commits of the last block in each stage have arrived
+              const int G = a.n_steps * NBLK;
+              for (int s = 0; s < ST && s < G && ok; ++s) {
+                  const int gl = s + ST * ((G - 1 - s) / ST);
+                  ok = mbar_wait_cl(&empty[s], (gl / ST) & 1, a.err, abort_flag);
+              }
           }
         }
     } else if (warp == 1) {
@@ -402,49 +470,112 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             // stall test: this wait runs out after its limit, raises the timeout bit
             // and the abort flag, and every other wait of the CTA then gives up
             if (a.stall_test) ok = mbar_wait(never, 0, a.err, abort_flag);
-            for (int sp = 0; sp < a.n_steps; ++sp) {
-            for (int blk = 0; blk < NBLK; ++blk) {
-                const int gb = sp * NBLK + blk;
-                const int s = gb % ST;
-                const uint32_t ph = (gb / ST) & 1;
+            // the MMAs of block gb (its operands are in stage gb % ST) and the commits after them
+            auto issue = [&](int gb) {
+                const int blk = gb % NBLK, s = gb % ST;
                 int kind, nb;
-                sched_decode<KB, BF ? 0 : 1>(blk, kind, nb);
-                ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
-                ok = ok && mbar_wait(&ready[s], ph, a.err, abort_flag);
-                if (ok) {
-                    fence_after();
-                    const uint32_t st = smem_u32(stage0 + s * S::kStage);
-                    const uint32_t a_hi = st + S::kR, a_lo = a_hi + S::kA, b_hi = a_lo + S::kA, b_lo = b_hi + S::kB;
-                    const uint32_t d = kind == 0 ? t_u : t_inc;
-                    const bool first = blk <= 1;       // first inverse block, first noise block
-                    if constexpr (BF) {
+                sched_decode<KB, FILL>(blk, kind, nb);
+                fence_after();
+                const uint32_t st = smem_u32(stage0 + s * S::kStage);
+                const uint32_t a_hi = st + S::kR, a_lo = a_hi + S::kA, b_hi = a_lo + S::kA, b_lo = b_hi + S::kB;
+                const uint32_t d = kind == 0 ? t_u : t_inc;
+                const bool first = blk <= 1;       // first inverse block, first noise block
+                if constexpr (BF) {
 #pragma unroll
-                        for (int kk = 0; kk < kKB / 16; ++kk) {
-                            const uint32_t off = kk * 32;   // 16 BF16 = 32 bytes along K
-                            mma_bf16(d, sdesc64(a_hi + off), sdesc64(b_lo + off), idesc, (first && kk == 0) ? 0u : 1u);
-                            mma_bf16(d, sdesc64(a_lo + off), sdesc64(b_hi + off), idesc, 1u);
-                            mma_bf16(d, sdesc64(a_hi + off), sdesc64(b_hi + off), idesc, 1u);
-                        }
-                    } else {
+                    for (int kk = 0; kk < kKB / 16; ++kk) {
+                        const uint32_t off = kk * 32;   // 16 BF16 = 32 bytes along K
+                        mma_bf16(d, sdesc64(a_hi + off), sdesc64(b_lo + off), idesc, (first && kk == 0) ? 0u : 1u);
+                        mma_bf16(d, sdesc64(a_lo + off), sdesc64(b_hi + off), idesc, 1u);
+                        mma_bf16(d, sdesc64(a_hi + off), sdesc64(b_hi + off), idesc, 1u);
+                    }
+                } else {
 #pragma unroll
-                        for (int kk = 0; kk < kKB / 8; ++kk) {
-                            const uint32_t off = kk * 32;   // 8 TF32 = 32 bytes along K
-                            mma_tf32(d, sdesc(a_hi + off), sdesc(b_lo + off), idesc, (first && kk == 0) ? 0u : 1u);
-                            mma_tf32(d, sdesc(a_lo + off), sdesc(b_hi + off), idesc, 1u);
-                            mma_tf32(d, sdesc(a_hi + off), sdesc(b_hi + off), idesc, 1u);
-                        }
+                    for (int kk = 0; kk < kKB / 8; ++kk) {
+                        const uint32_t off = kk * 32;   // 8 TF32 = 32 bytes along K
+                        mma_tf32(d, sdesc(a_hi + off), sdesc(b_lo + off), idesc, (first && kk == 0) ? 0u : 1u);
+                        mma_tf32(d, sdesc(a_lo + off), sdesc(b_hi + off), idesc, 1u);
+                        mma_tf32(d, sdesc(a_hi + off), sdesc(b_hi + off), idesc, 1u);
                     }
                 }
-                mma_commit(&empty[s]);
+                if constexpr (PAIR) mma_commit_mc(&empty[s], 3);   // both CTAs' stage s
+                else mma_commit(&empty[s]);
                 if (blk == sched_inv<KB>(KB - 1)) mma_commit(u_done);
-            }
-            mma_commit(inc_done);
+                if (blk == NBLK - 1) {
+                    mma_commit(inc_done);
+                    if constexpr (PAIR) mma_commit_mc(both_done, 3);
+                }
+            };
+            const int G = a.n_steps * NBLK;
+            if constexpr (!PAIR) {
+                for (int gb = 0; gb < G && ok; ++gb) {
+                    const int s = gb % ST;
+                    const uint32_t ph = (gb / ST) & 1;
+                    ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
+                    ok = ok && mbar_wait(&ready[s], ph, a.err, abort_flag);
+                    if (ok) issue(gb);
+                }
+            } else {
+                // Two streams of work, polled in turn: the MMAs of every block in
+                // order, and the copy of each block this CTA owns (its A operand,
+                // hi and lo) into the same stage of the other CTA as soon as its
+                // writers are done.  A copy waits for the release counter first
+                // (the stage's previous uses may be the other CTA's blocks), which
+                // makes the `ready` parity exact.
+                const uint32_t peer_stage0 = mapa(smem_u32(stage0), rank ^ 1u);
+                const uint32_t peer_full = mapa(smem_u32(full), rank ^ 1u);
+                auto next_own = [&](int g) {
+                    for (; g < G; ++g) {
+                        int kind, nb;
+                        sched_decode<KB, FILL>(g % NBLK, kind, nb);
+                        if ((uint32_t)(nb & 1) == rank) break;
+                    }
+                    return g;
+                };
+                int mb = 0, cb = next_own(0);
+                uint64_t t0 = globaltimer();
+                while (ok && (mb < G || cb < G)) {
+                    bool moved = false;
+                    if (cb < G) {
+                        const int s = cb % ST;
+                        if (ld_acquire_smem(s_freed) >= cb && mbar_test_wait(&ready[s], (cb / ST) & 1)) {
+                            const uint32_t off = (uint32_t)(s * S::kStage + S::kR);
+                            bulk_copy_to_peer(peer_stage0 + off, stage0 + off, 2u * S::kA, peer_full + 8u * (uint32_t)s);
+                            cb = next_own(cb + 1);
+                            moved = true;
+                        }
+                    }
+                    if (mb < G) {
+                        const int s = mb % ST;
+                        const uint32_t ph = (mb / ST) & 1;
+                        if (mbar_test_wait(&full[s], ph) && mbar_test_wait(&ready[s], ph)) {
+                            issue(mb++);
+                            moved = true;
+                        }
+                    }
+                    if (moved) {
+                        t0 = globaltimer();
+                    } else if (*abort_flag) {
+                        ok = false;
+                    } else if (globaltimer() - t0 > kTimeoutNs) {
+                        atomicOr(a.err, 2);
+                        *abort_flag = 1;
+                        ok = false;
+                    } else {
+                        __nanosleep(20);
+                    }
+                }
+                if (!ok) {
+                    // after a timeout: let copies already issued to the other CTA land
+                    const uint64_t t1 = globaltimer();
+                    while (globaltimer() - t1 < 1000000ull) __nanosleep(1000);
+                }
             }
         }
     } else if (warp >= 2 + kComputeWarps) {
         // ---------------- noise warps: Philox normals of noise block j (Eq. b5),
         // drawn into registers, then written as hi / lo operands once the stage is
-        // free.  Chains c = nw + kNoiseWarps i of the tile, bead n = 32 j + lane.
+        // free.  Chains c = nw + kNoiseWarps i of the tile, bead n = 32 j + lane;
+        // a PAIR CTA draws the blocks j = 2 i + rank.
         const int nw = warp - 2 - kComputeWarps;
         constexpr int kPerN = (kChains + kNoiseWarps - 1) / kNoiseWarps;
         int rb[kPerN];                  // first row of each chain: 32 quarter + 3 slot
@@ -457,7 +588,8 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         // their Philox / Box-Muller chains interleave; a slot past the tile's
         // chains draws for job 0 and is zeroed.
         auto draw = [&](int qn, float (&zz)[kPerN][3]) {
-            const int sp = qn / KB, n = (qn - sp * KB) * kKB + lane;
+            const int sp = qn / KBL, ib = qn - sp * KBL;
+            const int n = (PAIR ? 2 * ib + (int)rank : ib) * kKB + lane;
 #pragma unroll
             for (int i = 0; i < kPerN - 1; ++i) {
                 const int c = nw + kNoiseWarps * i;
@@ -471,21 +603,22 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             for (int i = 0; i < kPerN - 1; ++i)
                 if (nw + kNoiseWarps * i >= Ct) zz[i][0] = zz[i][1] = zz[i][2] = 0.f;
         };
-        // Noise blocks in sequence qn = KB step + j.  Block qn is drawn into `cur`;
+        // Noise blocks in sequence qn = KBL step + i.  Block qn is drawn into `cur`;
         // if its stage is not free yet, block qn + 1 is drawn into `nxt` meanwhile
         // (the noise does not depend on the state), so the noise warps keep
         // drawing while the stages are held, e.g. through the epilogue.
         bool ok = true, finite = true;
         double cm_unused[3];
         const int eq = warp & 3, et = (warp - 2 - kComputeWarps) / 4;   // epilogue quarter, worker 2 + et
-        const int nq = a.n_steps * KB;
+        const int nq = a.n_steps * KBL;
         float cur[kPerN][3], nxt[kPerN][3];
         bool have_nxt = false;
         draw(0, cur);
 #pragma unroll 1
         for (int qn = 0; qn < nq; ++qn) {
-            const int sp = qn / KB, j = qn - sp * KB;
-            const int blk = sp * NBLK + sched_noise<KB, BF ? 0 : 1>(j), s = blk % ST;
+            const int sp = qn / KBL, ib = qn - sp * KBL;
+            const int j = PAIR ? 2 * ib + (int)rank : ib;
+            const int blk = sp * NBLK + sched_noise<KB, FILL>(j), s = blk % ST;
             // Consecutive noise blocks may lie more than ST blocks apart, where a
             // parity wait on the stage's barrier is ambiguous: wait instead until
             // the producer has seen the stage released for this block (which it
@@ -508,9 +641,9 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 fence_proxy_async();
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive_cnt(&ready[s], kReadyCount / kNoiseWarps);
+            if (lane == 0 && ok) mbar_arrive_cnt(&ready[s], kReadyCount / kNoiseWarps);
             // after its last noise block, the step's epilogue (this warp's share)
-            if (j == KB - 1)
+            if (ib == KBL - 1)
                 epilogue(sp, eq, 2 + et, 2 + kNoiseInQ[(eq + 2) & 3], ok, finite, cm_unused[0], cm_unused[1],
                          cm_unused[2]);
             if (have_nxt) {
@@ -538,7 +671,8 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         const bool live = inrow && cl < Ct;
         const int src0 = lane - ax;         // lane of axis 0 of this chain
         // the chain's FP64 centre of mass, on its axis-0 lane of a first-half warp
-        const bool own_cm = half == 0 && live && ax == 0;
+        // (of rank 0, which holds mode 0)
+        const bool own_cm = half == 0 && live && ax == 0 && rank == 0;
         double cm_x = 0.0, cm_y = 0.0, cm_z = 0.0;
         if (own_cm) {
             const double* cm = a.com + 3 * (size_t)(c0 + cl);
@@ -550,16 +684,22 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         bool finite = true;
         auto arrive = [&](int s) {
             __syncwarp();
-            if (lane == 0) mbar_arrive_cnt(&ready[s], kReadyCount / kComputeWarps);
+            if (lane == 0 && ok) mbar_arrive_cnt(&ready[s], kReadyCount / kComputeWarps);
         };
 #pragma unroll 1
         for (int sp = 0; sp < a.n_steps; ++sp) {
         const int g0 = sp * NBLK;                     // global index of this step's first block
-        // (1) split the R tile of each inverse block into hi / lo operands
+        // (1) split the R tile of each inverse block (PAIR: of this CTA's blocks
+        //     nb = 2 i + rank) into hi / lo operands
 #pragma unroll 1
-        for (int nb = 0; nb < KB; ++nb) {
+        for (int ib = 0; ib < KBL; ++ib) {
+            const int nb = PAIR ? 2 * ib + (int)rank : ib;
             const int blk = g0 + sched_inv<KB>(nb), s = blk % ST;
             const uint32_t ph = (blk / ST) & 1;
+            // PAIR: the stage's previous uses may be the other CTA's blocks, which
+            // these warps never waited for, so a parity wait alone could be two
+            // phases ahead; the producer's release counter first makes it exact
+            if constexpr (PAIR) ok = ok && count_wait(s_freed, blk, a.err, abort_flag);
             ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
             if (ok && BF) {
                 // row t/4, BF16 chunk t%4 (8 values) from the FP32 staging tile
@@ -613,13 +753,15 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             arrive(s);
         }
 
-        // (2) per bead block nb: bond vectors from D_u -> residual force v (Eq. e11),
-        //     |u_n| from the chain's three rows by warp shuffles
+        // (2) per bead block of this CTA's D_u: bond vectors -> residual force v
+        //     (Eq. e11), |u_n| from the chain's three rows by warp shuffles; the
+        //     force block's schedule index is k (PAIR: bond block 8 rank + ib)
         ok = ok && mbar_wait(u_done, sp & 1, a.err, abort_flag);
         fence_after();
 #pragma unroll 1
-        for (int nb = 0; nb < KB; ++nb) {
-            const int col = nb * kKB + 16 * half;       // first bead of this warp's 16
+        for (int ib = 0; ib < KBL; ++ib) {
+            const int k = PAIR ? 2 * ib + (int)rank : ib;
+            const int col = ib * kKB + 16 * half;       // first bond (TMEM column) of this warp's 16
             float v[16];
             tmem_ld16(t_u + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
 #pragma unroll
@@ -627,11 +769,14 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 const float sq = v[i] * v[i];
                 const float t = sq + __shfl_down_sync(0xffffffffu, sq, 1) + __shfl_down_sync(0xffffffffu, sq, 2);
                 const float fac = __shfl_sync(0xffffffffu, rsqrtf(t) - a.c12nu, src0);
-                v[i] = (live && col + i >= 1) ? v[i] * fac : 0.f;
+                v[i] = (live && col0 + col + i >= 1) ? v[i] * fac : 0.f;
             }
-            const int blk = g0 + sched_force<KB, BF ? 0 : 1>(nb), s = blk % ST;
+            const int blk = g0 + sched_force<KB, FILL>(k), s = blk % ST;
             const uint32_t ph = (blk / ST) & 1;
-            ok = ok && mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
+            // PAIR: as for the split, the release counter instead of a parity wait
+            // (it also covers the other CTA's MMAs: `empty` counts both)
+            if constexpr (PAIR) ok = ok && count_wait(s_freed, blk, a.err, abort_flag);
+            else ok = ok && mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
             if (ok && inrow) {
                 uint8_t* ah = stage0 + s * S::kStage + S::kR;
                 uint8_t* al = ah + S::kA;
@@ -676,16 +821,24 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             cm[0] = cm_x;
             cm[1] = cm_y;
             cm[2] = cm_z;
-        }
-        if (ok && half == 0 && live && ax == 0)
             a.step[c0 + cl] = max(s_step[cl], min(s_step[cl] + (int64_t)a.n_steps, s_stop[cl]));
+        }
         if (!finite) atomicOr(a.err, 1);
     }
     fence_before();
-    __syncthreads();
+    // PAIR: neither CTA leaves while the other may still copy into or arrive on its shared memory
+    __syncwarp();
+    if constexpr (PAIR) cluster_sync();
+    else __syncthreads();
     if (warp == 1) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+        if (PAIR && lane == 0 && *abort_flag) {
+            // after a timeout the other CTA may have issued a copy into this CTA's
+            // stages just before the cluster barrier: let it land before leaving
+            const uint64_t t0 = globaltimer();
+            while (globaltimer() - t0 < 1000000ull) __nanosleep(1000);
+        }
     }
 }
 
@@ -702,30 +855,35 @@ struct FusedPlan {
 // Chains per tile: a multiple of 4 (one share per TMEM lane quarter), 4..kChains.
 static int round_tile(int cpt) { return std::min(kChains, std::max(4, (cpt + 3) / 4 * 4)); }
 
-bool fused_supported(int M) { return M == 64 || M == 128 || M == 256; }
+bool fused_supported(int M) { return M == 64 || M == 128 || M == 256 || M == 512; }
 
-template <int NB, bool BF>
+template <int NB, bool BF, bool PAIR>
 static cudaError_t set_smem()
 {
-    return cudaFuncSetAttribute(k_fused_step<NB, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, FSmem<NB, BF>::kBytes);
+    return cudaFuncSetAttribute(k_fused_step<NB, BF, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                FSmem<NB, BF>::kBytes);
 }
 
 int fused_create(FusedPlan** out, int M, int C, const double* chi, const double* phi, const double* h,
                  const double* w, float* R, cudaStream_t stream, bool bf16)
 {
     *out = nullptr;
-    if (!fused_supported(M)) return report(SFP_ENOTSUP, "the fused step needs M in {64, 128, 256}");
+    if (!fused_supported(M)) return report(SFP_ENOTSUP, "the fused step needs M in {64, 128, 256, 512}");
     FusedPlan* p = new FusedPlan();
     p->M = M;
     p->C = C;
     p->R = R;
     p->bf16 = bf16;
-    // one wave: chains per tile = ceil(C / SMs) rounded up to a multiple of 4, at
-    // most 40 (fused_set_tile changes it)
+    // the fewest waves of tiles of at most 40 chains (a 512-bead tile takes two
+    // SMs), then the chains spread evenly over the tiles of those waves: chains
+    // per tile = ceil(C / (units x waves)) rounded up to a multiple of 4
+    // (fused_set_tile changes it)
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         sms = 148;
-    p->cpt = round_tile((C + sms - 1) / sms);
+    const int units = M == 512 ? sms / 2 : sms;
+    const int waves = std::max(1, (C + units * kChains - 1) / (units * kChains));
+    p->cpt = round_tile((C + units * waves - 1) / (units * waves));
     const size_t mm = (size_t)M * M;
     // chi [n][p] (row n = 0 and column p = 0 are zero) and F [2M][M]:
     // F[p][n] = h_p chi[n][p] (Eq. f2 weight on DeltaH = chi^T v, Eq. e11),
@@ -773,21 +931,27 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
         fused_destroy(p);
         return rc;
     }
+    // B operand boxes: the rows of one CTA's TMEM half (all M, or 256 of 512)
+    const int bx = std::min(M, 256);
     if (bf16)
-        rc = make_map_bf16(&p->tmChiH, p->tab[0], M, M, M) ? -1 : make_map_bf16(&p->tmChiL, p->tab[1], M, M, M) ? -1 :
-             make_map_bf16(&p->tmFH, p->tab[2], 2 * M, M, M) ? -1 : make_map_bf16(&p->tmFL, p->tab[3], 2 * M, M, M);
+        rc = make_map_bf16(&p->tmChiH, p->tab[0], M, M, bx) ? -1 : make_map_bf16(&p->tmChiL, p->tab[1], M, M, bx) ? -1 :
+             make_map_bf16(&p->tmFH, p->tab[2], 2 * M, M, bx) ? -1 : make_map_bf16(&p->tmFL, p->tab[3], 2 * M, M, bx);
     else
-        rc = make_map_2d(&p->tmChiH, (const float*)p->tab[0], M, M, M) ? -1 :
-             make_map_2d(&p->tmChiL, (const float*)p->tab[1], M, M, M) ? -1 :
-             make_map_2d(&p->tmFH, (const float*)p->tab[2], 2 * M, M, M) ? -1 :
-             make_map_2d(&p->tmFL, (const float*)p->tab[3], 2 * M, M, M);
+        rc = make_map_2d(&p->tmChiH, (const float*)p->tab[0], M, M, bx) ? -1 :
+             make_map_2d(&p->tmChiL, (const float*)p->tab[1], M, M, bx) ? -1 :
+             make_map_2d(&p->tmFH, (const float*)p->tab[2], 2 * M, M, bx) ? -1 :
+             make_map_2d(&p->tmFL, (const float*)p->tab[3], 2 * M, M, bx);
     if (rc) {
         fused_destroy(p);
         return SFP_ECUDA;
     }
     cudaError_t e;
-    if (bf16) e = M == 256 ? set_smem<256, true>() : M == 128 ? set_smem<128, true>() : set_smem<64, true>();
-    else e = M == 256 ? set_smem<256, false>() : M == 128 ? set_smem<128, false>() : set_smem<64, false>();
+    if (bf16)
+        e = M == 512 ? set_smem<256, true, true>() : M == 256 ? set_smem<256, true, false>() :
+            M == 128 ? set_smem<128, true, false>() : set_smem<64, true, false>();
+    else
+        e = M == 512 ? set_smem<256, false, true>() : M == 256 ? set_smem<256, false, false>() :
+            M == 128 ? set_smem<128, false, false>() : set_smem<64, false, false>();
     if (e != cudaSuccess) {
         fused_destroy(p);
         return report(SFP_ECUDA, "cudaFuncSetAttribute (fused step) failed");
@@ -801,9 +965,31 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
     if (args.cpt != p->cpt) return report(SFP_EINVAL, "fused step: chains per tile differ from the plan's");
     const dim3 grid((unsigned)((p->C + p->cpt - 1) / p->cpt));
 #define SFP_FUSED_LAUNCH(NBV, BFV)                                                                   \
-    k_fused_step<NBV, BFV><<<grid, kThreads, FSmem<NBV, BFV>::kBytes, stream>>>(p->tmR, p->tmChiH, p->tmChiL, \
-                                                                            p->tmFH, p->tmFL, args)
+    k_fused_step<NBV, BFV, false><<<grid, kThreads, FSmem<NBV, BFV>::kBytes, stream>>>(p->tmR, p->tmChiH, \
+                                                                  p->tmChiL, p->tmFH, p->tmFL, args)
+    cudaError_t e = cudaSuccess;
     switch (p->M * 2 + (p->bf16 ? 1 : 0)) {
+        case 1024:
+        case 1025: {
+            // two CTAs (a cluster) per tile
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(2u * grid.x);
+            cfg.blockDim = dim3(kThreads);
+            cfg.dynamicSmemBytes = p->bf16 ? FSmem<256, true>::kBytes : FSmem<256, false>::kBytes;
+            cfg.stream = stream;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 2;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            e = p->bf16 ? cudaLaunchKernelEx(&cfg, k_fused_step<256, true, true>, p->tmR, p->tmChiH, p->tmChiL,
+                                             p->tmFH, p->tmFL, args)
+                        : cudaLaunchKernelEx(&cfg, k_fused_step<256, false, true>, p->tmR, p->tmChiH, p->tmChiL,
+                                             p->tmFH, p->tmFL, args);
+            break;
+        }
         case 512: SFP_FUSED_LAUNCH(256, false); break;
         case 513: SFP_FUSED_LAUNCH(256, true); break;
         case 256: SFP_FUSED_LAUNCH(128, false); break;
@@ -813,12 +999,14 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
         default: return report(SFP_ENOTSUP, "unsupported fused-step length");
     }
 #undef SFP_FUSED_LAUNCH
-    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return report(SFP_ECUDA, cudaGetErrorString(e));
     return SFP_OK;
 }
 
 int fused_tile(const FusedPlan* p) { return p->cpt; }
+
+int fused_ctas_per_tile(const FusedPlan* p) { return p->M == 512 ? 2 : 1; }
 
 size_t fused_bytes(const FusedPlan* p) { return p ? (size_t)6 * p->M * p->M * (p->bf16 ? 2 : 4) : 0; }
 

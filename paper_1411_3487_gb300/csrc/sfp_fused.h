@@ -18,7 +18,8 @@ struct FusedArgs {
     const double* shear;    // [C] shear rate in 1/tau
     const float* dm;        // [M] 1 - e^{-zeta_p dtau}
     const float* g;         // [M] shear weights (g_0 = dtau)
-    int* err;               // bit 0: non-finite state, bit 1: a pipeline wait timed out
+    int* err;               // bit 0: non-finite state, bit 1: a pipeline wait timed out,
+                            // bit 2: a 512-bead step launched without its cluster of two
     int C;
     float c12nu;            // 1 - 2 nu
     uint32_t seed;
@@ -44,6 +45,8 @@ int fused_step(FusedPlan* plan, const FusedArgs& args, cudaStream_t stream);
 // Chains per tile of the plan, and a new value (1..40, rounded up to a multiple
 // of 4: one share per TMEM lane quarter; rebuilds the R map).
 int fused_tile(const FusedPlan* plan);
+// CTAs that run one tile: 2 at M = 512 (a cluster pair), else 1.
+int fused_ctas_per_tile(const FusedPlan* plan);
 // Device bytes the plan's tables hold.
 size_t fused_bytes(const FusedPlan* plan);
 int fused_set_tile(FusedPlan* plan, int cpt);

@@ -24,8 +24,8 @@ pytestmark = pytest.mark.gpu
 TSTAR, NU = 0.034, 0.35
 TOL = {sfp.SFP_FP32_SIMT: 1e-5, sfp.SFP_FP32: 1e-5, sfp.SFP_MIXED_BF16: 1e-5, sfp.SFP_FP64: 1e-9}
 # A "precision" parameter is (precision, kernel path): the SFP_FP32 and
-# SFP_MIXED_BF16 paths run fused (one kernel per step, M = 64/128/256) by
-# default, or staged.
+# SFP_MIXED_BF16 paths run fused (one kernel per step, M = 64/128/256/512;
+# a 512-bead tile on a cluster of two CTAs) by default, or staged.
 SIMT = pytest.param((sfp.SFP_FP32_SIMT, sfp.SFP_PATH_STAGED), id="simt")
 TC = pytest.param((sfp.SFP_FP32, sfp.SFP_PATH_FUSED), id="tcgen05")
 TCS = pytest.param((sfp.SFP_FP32, sfp.SFP_PATH_STAGED), id="tcgen05_staged")
@@ -143,7 +143,7 @@ def test_trajectory_64bp_fp64_full_config():
 
 @pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("M,C", [(3, 4), (5, 1), (67, 5), (130, 45), (33, 300), (64, 43), (128, 85),
-                                 (256, 84)])
+                                 (256, 84), (512, 45)])
 def test_ragged_and_tiny_shapes(precision, M, C):
     dtau = 5.0
     m = O.Model(M, dtau=dtau)
@@ -288,7 +288,7 @@ def test_fused_and_staged_paths_agree():
 
 
 @pytest.mark.parametrize("prec", [sfp.SFP_FP32, sfp.SFP_MIXED_BF16], ids=["tf32", "bf16"])
-@pytest.mark.parametrize("M,C", [(256, 50), (64, 100), (128, 301)])
+@pytest.mark.parametrize("M,C", [(256, 50), (64, 100), (128, 301), (512, 85)])
 def test_fused_multi_step_launch_is_bit_exact(M, C, prec):
     """sfp_step(n) runs n steps in one fused launch; chains are independent, so
     it must reproduce n launches of one step bit for bit (and the oracle)."""
@@ -371,14 +371,16 @@ def test_bf16_fused_step_against_the_oracle(M, C):
         fused.probe(sfp.SFP_PROBE_DH)
 
 
-def test_pipeline_wait_timeout_is_reported(monkeypatch):
+@pytest.mark.parametrize("M", [64, 512])
+def test_pipeline_wait_timeout_is_reported(monkeypatch, M):
     """Bounded waits: with SFP_TEST_STALL=1 the fused kernel's MMA thread first
     waits on a barrier that nothing arrives at.  That wait gives up after its
     1 s limit, raises the timeout bit and the abort flag, every other wait of
     the CTA gives up too, and the kernel returns: the step reports
     SFP_ETIMEDOUT, the state is left as it was, and the GPU context stays
-    usable for the next batch."""
-    M, C, dtau = 64, 8, 10.0
+    usable for the next batch.  At 512 beads both CTAs of each cluster stall
+    and meet at the cluster barrier before they leave."""
+    C, dtau = 8, {64: 10.0, 512: 100.0}[M]
     R = starts(M, C, dtau=dtau)
     b = make_batch(M, C, dtau, (sfp.SFP_MIXED_BF16, sfp.SFP_PATH_FUSED))
     b.set_modes(R)
@@ -394,3 +396,50 @@ def test_pipeline_wait_timeout_is_reported(monkeypatch):
     b2.step(5)
     ref = O.Model(M, dtau=dtau).run_modes(R, 1, np.arange(C), 0, 5)
     assert rel_err(b2.modes(), ref).max() < TOL[sfp.SFP_MIXED_BF16]
+
+
+@pytest.mark.parametrize("prec", [sfp.SFP_FP32, sfp.SFP_MIXED_BF16], ids=["tf32", "bf16"])
+def test_fused_512bp_pair_against_the_oracle(prec):
+    """512-bead chains on the fused step: each tile runs on a cluster of two
+    CTAs, one per half of the bonds and modes, which exchange every A operand
+    block.  1000 steps against the oracle at the FP32 bound, on 82 chains
+    (default tile: 4 chains, 21 tiles, the last one with 2) and the centre of
+    mass carried by the first CTA of each pair."""
+    M, C, dtau = 512, 82, 100.0
+    m = O.Model(M, dtau=dtau)
+    R = starts(M, C, dtau=dtau)
+    b = make_batch(M, C, dtau, (prec, sfp.SFP_PATH_FUSED))
+    b.set_modes(R)
+    done = 0
+    for mark in (1, 100, 1000):
+        R = m.run_modes(R, 1, np.arange(C), done, mark - done)
+        b.step(mark - done)
+        done = mark
+        G = b.modes()
+        e = rel_err(G, R)
+        print("fused 512", prec, "step", mark, "error", e.max())
+        assert e.max() < TOL[prec], (mark, e.max())
+        dcm = np.abs(G[:, :, 0] - R[:, :, 0]).max() / math.sqrt(M)
+        assert dcm < 1e-5 * math.sqrt(6 * TSTAR * dtau * mark / M) + 1e-9
+    assert np.all(b.observe(sfp.SFP_OBS_STEP) == 1000)
+
+
+@pytest.mark.parametrize("prec", [sfp.SFP_FP32, sfp.SFP_MIXED_BF16], ids=["tf32", "bf16"])
+def test_full_size_512bp_sampled(prec):
+    """The 16384 x 512-bp mixed-precision workload at full size on the fused
+    step (456 clusters of two CTAs: six waves of tiles of 36 chains); six sampled chains
+    recomputed by the oracle, and free-draining centre-of-mass diffusion over
+    all chains."""
+    M, C, dtau, n = 512, 16384, 100.0, 20
+    b = make_batch(M, C, dtau, (prec, sfp.SFP_PATH_FUSED))
+    b.init_equilibrium(0)
+    R0 = b.modes()
+    b.step(n)
+    G = b.modes()
+    m = O.Model(M, dtau=dtau)
+    pick = np.array([0, 1, 35, 36, 9999, 16383])
+    ref = m.run_modes(R0[pick], 1, pick, 0, n)
+    assert rel_err(G[pick], ref).max() < TOL[prec]
+    dcm = (G[:, :, 0] - R0[:, :, 0]) / math.sqrt(M)
+    msd = np.mean(np.sum(dcm ** 2, axis=1))
+    assert msd == pytest.approx(6 * TSTAR * dtau * n / M, rel=4.5 * math.sqrt(2 / (3 * C)))
