@@ -332,7 +332,7 @@ def run_native(args, rank, world, local):
             n = 20 * calls
             big[name] = {"value": 16384 * 512 * n / (t_ms * 1e-3), "unit": UNIT, "us_per_step": 1e3 * t_ms / n}
             if pth == sfp.SFP_PATH_FUSED:
-                big[name]["kernel"] = "k_fused_step<256, %s, pair>" % ("bf16" if prec == sfp.SFP_MIXED_BF16 else "tf32")
+                big[name]["kernel"] = "k_fused_pair<%s>" % ("bf16" if prec == sfp.SFP_MIXED_BF16 else "tf32")
                 big[name]["roofline_tensor_frac"] = (3 * 18 * 512 * 16384 * 512 / (1e-3 * t_ms / n)) / 1e12 / (
                     pk["bf16_tflops"] * (1.0 if prec == sfp.SFP_MIXED_BF16 else 1.1 / 2.25))
             bb.modes()      # raises if a kernel reported an error

@@ -43,7 +43,7 @@
 // grid-wide synchronisation: TMEM stays allocated, the tables stream again
 // from L2, and the state goes through global memory (L2) between steps.
 //
-// M = 512 (PAIR): D_u and D_inc would take 1024 TMEM columns, twice an SM's
+// M = 512 (k_fused_pair): D_u and D_inc would take 1024 TMEM columns, twice an SM's
 // 512, so a cluster of two CTAs shares each tile.  CTA h (cluster rank) holds
 // bonds and modes 256 h .. 256 h + 255 (D_u and D_inc halves of 256 columns,
 // B operands = those rows of chi and F) and runs all 3 x 16 K blocks of a
@@ -99,19 +99,24 @@ __device__ constexpr int kNoiseInQ[4] = {(kNoiseWarps + 3) / 4, (kNoiseWarps + 2
                                          kNoiseWarps / 4};
 static_assert(2 + kComputeWarps == 10 && kComputeWarps == 8, "warp numbering of the quarters");
 
-// Shared memory of one CTA.  A stage holds [R (FP32, BF16 operands only)]
-// [A hi][A lo][B hi][B lo] for one K block of 32: TF32 operands are FP32-sized
-// with a 128-byte swizzle (the R tile is split in place in A hi); BF16
-// operands are 2 bytes with a 64-byte swizzle, the FP32 R tile converted from
-// its own staging tile.
-template <int NB, bool BF>
+// Shared memory of one CTA.  A stage holds [R][A hi][A lo][B hi][B lo] for one
+// K block of 32: TF32 operands are FP32-sized with a 128-byte swizzle (the R
+// tile of an inverse block lands in A hi and is split in place); BF16
+// operands are 2 bytes with a 64-byte swizzle, and the FP32 R tile (16 KB)
+// either has a staging area R of its own (RS: the single-CTA kernel, three
+// stages at M = 256, measured faster) or lands in A hi + A lo, which the
+// compute warps read out in full before they write the hi and lo parts over
+// it (the 512-bead kernel, four stages instead of three).
+template <int NB, bool BF, bool RS>
 struct FSmem {
     static constexpr int kEl = BF ? 2 : 4;
     static constexpr int kA = kRows * kKB * kEl;          // 16 KB (TF32) / 8 KB (BF16)
     static constexpr int kB = NB * kKB * kEl;             // NB x 128 B / NB x 64 B
-    static constexpr int kR = BF ? kRows * kKB * 4 : 0;   // FP32 R staging (BF16)
+    static constexpr int kR = RS ? kRows * kKB * 4 : 0;   // FP32 R staging (BF16, RS)
     static constexpr int kStage = kR + 2 * kA + 2 * kB;
-    static constexpr int kStages = BF ? (192 * 1024) / kStage : (NB == 256 ? 2 : NB == 128 ? 3 : 4);
+    static_assert(RS || kRows * kKB * 4 <= 2 * kA, "an FP32 R tile fits the A operand region");
+    static constexpr int kStages = BF ? ((192 * 1024) / kStage < 4 ? (192 * 1024) / kStage : 4)
+                                      : (NB == 256 ? 2 : NB == 128 ? 3 : 4);
     static constexpr int kRT = kRows * kKB * 4;           // an FP32 R block of the epilogue, 16 KB
     static constexpr int kMisc = 4096;   // per-chain keys, steps, shear, stops; tables; barriers
     static constexpr int kBytes = kStages * kStage + kMisc + 1024;
@@ -199,24 +204,542 @@ template <int KB, int FILL> __device__ __forceinline__ int sched_force(int k)
     return k < H - P ? 3 * H + P + 2 * k : 3 * H + P + 2 * (H - P) + (k - (H - P));
 }
 
-// Bead block of force block k (schedule index): a PAIR CTA owns the force
-// blocks of odd or even k, and its D_u half holds bond blocks 8 h .. 8 h + 7.
-template <int KBL, bool PAIR> __device__ __forceinline__ int force_bonds(int k)
+// 512 beads: bead block of force block k (schedule index).  CTA h owns the
+// force blocks of k = h mod 2, and its D_u half holds bond blocks 8 h .. 8 h + 7.
+template <int KBL> __device__ __forceinline__ int force_bonds(int k)
 {
-    return PAIR ? KBL * (k & 1) + (k >> 1) : k;
+    return KBL * (k & 1) + (k >> 1);
 }
 
-// NB: TMEM columns of each half (D_u, D_inc) of one CTA; M = NB, or 2 NB for PAIR.
-template <int NB, bool BF, bool PAIR>
+// The step of the 64-, 128- and 256-bead chains: a tile per CTA.
+template <int NB, bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
 k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmChiH,
              const __grid_constant__ CUtensorMap tmChiL, const __grid_constant__ CUtensorMap tmFH,
              const __grid_constant__ CUtensorMap tmFL, const FusedArgs a)
 {
-    using S = FSmem<NB, BF>;
+    using S = FSmem<NB, BF, BF>;        // BF16: a separate FP32 R staging area per stage
+    constexpr int ST = S::kStages;
+    constexpr int KB = NB / kKB;        // inverse K blocks = forward bead blocks
+    constexpr int NBLK = 3 * KB;        // blocks of one step, in the order of sched_decode
+    static_assert(KB % 2 == 0, "the block schedule pairs bead blocks");
+    constexpr uint32_t kCols = 2 * NB;  // D_u in [0, NB), D_inc in [NB, 2 NB)
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* stage0 = smem;
+    uint8_t* misc = smem + ST * S::kStage;
+    uint32_t* s_job = (uint32_t*)misc;
+    int64_t* s_step = (int64_t*)(misc + 256);
+    double* s_shear = (double*)(misc + 576);
+    int64_t* s_stop = (int64_t*)(misc + 896);
+    float* s_dm = (float*)(misc + 1216);        // NB <= 256
+    float* s_g = (float*)(misc + 2240);
+    uint64_t* bars = (uint64_t*)(misc + 3264);
+    uint64_t* full = bars;              // TMA bytes landed                 (1 + tx)
+    uint64_t* ready = bars + 4;         // A operand written by one group   (kReadyCount)
+    uint64_t* empty = bars + 8;         // MMAs done with the stage         (commit)
+    uint64_t* u_done = bars + 12;       // all inverse MMAs done            (commit)
+    uint64_t* inc_done = bars + 13;     // all forward MMAs done            (commit)
+    uint64_t* epi_done = bars + 15;     // epilogue stored R, stages free   (every worker warp)
+    uint32_t* tmem_slot = (uint32_t*)(bars + 16);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    int* s_freed = (int*)(tmem_slot + 2);   // last block whose stage the producer saw released
+    uint64_t* r_blk = bars + 18;        // R column block k reloaded for the epilogue (1 + tx), k < KB
+    uint64_t* never = bars + 26;        // nothing arrives here (the stall test)
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cpq = a.cpt >> 2;         // chains per TMEM lane quarter (rows 32 q + 3 k + axis)
+    const int c0 = blockIdx.x * a.cpt;
+    const int Ct = min(a.cpt, a.C - c0);
+    const uint32_t rblock = 4u * 3u * (uint32_t)cpq * 128u;   // bytes of one R column block
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&ready[s], kReadyCount);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(u_done, 1);
+        mbar_init(inc_done, 1);
+        for (int k = 0; k < KB; ++k) mbar_init(&r_blk[k], 1);
+        mbar_init(epi_done, kComputeWarps + kNoiseWarps);
+        mbar_init(never, 1);
+        *abort_flag = 0;
+        *s_freed = -1;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmR)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmChiH)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmChiL)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmFH)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmFL)) : "memory");
+    }
+    for (int p = threadIdx.x; p < NB; p += kThreads) {
+        s_dm[p] = a.dm[p];
+        s_g[p] = a.g[p];
+    }
+    for (int i = threadIdx.x; i < kChains; i += kThreads) {
+        const bool live = i < Ct;
+        s_job[i] = live ? a.job[c0 + i] : 0u;
+        s_step[i] = live ? a.step[c0 + i] : 0;
+        s_stop[i] = (live && a.stop) ? a.stop[c0 + i] : INT64_MAX;
+        s_shear[i] = live ? a.shear[c0 + i] : 0.0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(kCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t t_u = tmem, t_inc = tmem + NB;
+    const bool has_shear = __syncthreads_or(threadIdx.x < Ct && s_shear[threadIdx.x] != 0.0) != 0;
+
+    // Epilogue of step sp (R += -dm R + D_inc (+ shear), Eqs. d3, btum) on the R
+    // tile that the producer reloads into the stage memory (KB column blocks of
+    // [128 rows][32], swizzled, each with its own barrier), in place.  The
+    // compute and noise warps of lane quarter q share it: worker w of nw takes
+    // the quarter's rows of column blocks w, w + nw, ... and TMA-stores each
+    // (block, quarter) box as soon as it is done.  Worker 0 (a compute warp)
+    // holds the centre of mass, which column block 0 updates.
+    auto epilogue = [&](int sp, int q, int w, int nw, bool& ok, bool& finite, double& cm_x, double& cm_y,
+                        double& cm_z) {
+        const int row = 32 * q + lane;
+        const int kq = lane / 3, ax = lane - 3 * (lane / 3);
+        const bool inrow = kq < cpq;
+        const int cl = inrow ? cpq * q + kq : 0;
+        const bool live = inrow && cl < Ct;
+        ok = ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag);
+        fence_after();
+        // a chain whose step counter has reached its stop step stays as it is
+        const bool adv = live && s_step[cl] + sp < s_stop[cl];
+#pragma unroll 1
+        for (int kb = w; kb < KB; kb += nw) {
+            ok = ok && mbar_wait(&r_blk[kb], sp & 1, a.err, abort_flag);
+            uint8_t* blk = stage0 + kb * S::kRT;
+#pragma unroll 1
+            for (int kin = 0; kin < kKB; kin += 16) {
+                const int p0 = kb * kKB + kin;
+                float d[16], r[16];
+                tmem_ld16(t_inc + ((uint32_t)(32 * q) << 16) + (uint32_t)p0, d);
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) {
+                    const float4 x = *reinterpret_cast<const float4*>(blk + swz(row, kin + 4 * k4));
+                    r[4 * k4] = x.x; r[4 * k4 + 1] = x.y; r[4 * k4 + 2] = x.z; r[4 * k4 + 3] = x.w;
+                }
+                float o[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) o[i] = adv ? r[i] + fmaf(-s_dm[p0 + i], r[i], d[i]) : r[i];
+                if (has_shear) {
+                    // start-of-step R^y of this chain: the next lane's row (axis 1)
+                    const float sh = (float)s_shear[cl];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const float ry = __shfl_down_sync(0xffffffffu, r[i], 1);
+                        if (adv && ax == 0) o[i] += sh * s_g[p0 + i] * ry;
+                    }
+                }
+                if (p0 == 0) {
+                    // centre of mass in FP64 (p = 0 of Eq. d3 with zeta_0 = 0), kept in
+                    // registers for the whole launch
+                    const float d1 = __shfl_down_sync(0xffffffffu, d[0], 1);
+                    const float d2 = __shfl_down_sync(0xffffffffu, d[0], 2);
+                    if (adv && ax == 0) {
+                        const double ycm = cm_y;
+                        cm_x += (double)d[0] * a.inv_sqrtM + s_shear[cl] * a.dtau * ycm;
+                        cm_y += (double)d1 * a.inv_sqrtM;
+                        cm_z += (double)d2 * a.inv_sqrtM;
+                    }
+                    o[0] = 0.f;
+                }
+                if (live) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) finite = finite && isfinite(o[i]);
+                }
+                if (inrow) {
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4)
+                        *reinterpret_cast<float4*>(blk + swz(row, kin + 4 * k4)) =
+                            make_float4(o[4 * k4], o[4 * k4 + 1], o[4 * k4 + 2], o[4 * k4 + 3]);
+                }
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0 && ok) {
+                tma_store_2d(&tmR, blk + q * kQuarter, kb * kKB, 3 * (c0 + q * cpq));
+                tma_store_commit();
+            }
+        }
+        // R is in global memory and this warp's stage rows are free again; D_inc
+        // has been read before the next step's MMAs write it
+        if (lane == 0 && ok) tma_store_wait();
+        fence_before();
+        __syncwarp();
+        if (lane == 0 && ok) mbar_arrive(epi_done);
+    };
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+          bool ok = true;
+          for (int sp = 0; sp < a.n_steps && ok; ++sp) {
+            // the previous step's epilogue used the stage memory and stored R
+            if (sp > 0 && !mbar_wait(epi_done, (sp - 1) & 1, a.err, abort_flag)) break;
+            for (int blk = 0; blk < NBLK; ++blk) {
+                const int gb = sp * NBLK + blk;
+                const int s = gb % ST;
+                const uint32_t ph = (gb / ST) & 1;
+                if (!mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag)) { ok = false; break; }
+                st_release_smem(s_freed, gb);   // block gb may be written into stage s
+                uint8_t* st = stage0 + s * S::kStage;
+                uint8_t* bh = st + S::kR + 2 * S::kA;
+                uint8_t* bl = bh + S::kB;
+                int kind, nb;
+                sched_decode<KB, BF ? 0 : 1>(blk, kind, nb);
+                if (kind == 0) {
+                    // inverse: the R tile (FP32, one box per lane quarter) and chi
+                    mbar_expect_tx(&full[s], rblock + 2 * S::kB);
+                    tma_load_2d(bh, &tmChiH, &full[s], nb * kKB, 0);
+                    tma_load_2d(bl, &tmChiL, &full[s], nb * kKB, 0);
+                    for (int q = 0; q < 4; ++q)
+                        tma_load_2d(st + q * kQuarter, &tmR, &full[s], nb * kKB, 3 * (c0 + q * cpq));
+                } else {
+                    // noise block nb: rows w_p phi (t = 1); force block nb: rows h_p chi (t = 0)
+                    const bool noise = kind == 1;
+                    mbar_expect_tx(&full[s], 2 * S::kB);
+                    tma_load_2d(bh, &tmFH, &full[s], nb * kKB, noise ? NB : 0);
+                    tma_load_2d(bl, &tmFL, &full[s], nb * kKB, noise ? NB : 0);
+                }
+            }
+            // every stage is free once the forward MMAs are done: reload the R tile
+            // (KB column blocks of [128 rows][32]) there for the epilogue
+            if (ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag)) {
+                for (int k = 0; k < KB; ++k) {
+                    mbar_expect_tx(&r_blk[k], rblock);
+                    for (int q = 0; q < 4; ++q)
+                        tma_load_2d(stage0 + k * S::kRT + q * kQuarter, &tmR, &r_blk[k], k * kKB, 3 * (c0 + q * cpq));
+                }
+            } else {
+                ok = false;
+            }
+          }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = BF ? idesc_bf16(kRows, NB) : idesc_tf32(kRows, NB);
+            bool ok = true;
+            // stall test: this wait runs out after its limit, raises the timeout bit
+            // and the abort flag, and every other wait of the CTA then gives up
+            if (a.stall_test) ok = mbar_wait(never, 0, a.err, abort_flag);
+            for (int sp = 0; sp < a.n_steps; ++sp) {
+            for (int blk = 0; blk < NBLK; ++blk) {
+                const int gb = sp * NBLK + blk;
+                const int s = gb % ST;
+                const uint32_t ph = (gb / ST) & 1;
+                int kind, nb;
+                sched_decode<KB, BF ? 0 : 1>(blk, kind, nb);
+                ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
+                ok = ok && mbar_wait(&ready[s], ph, a.err, abort_flag);
+                if (ok) {
+                    fence_after();
+                    const uint32_t st = smem_u32(stage0 + s * S::kStage);
+                    const uint32_t a_hi = st + S::kR, a_lo = a_hi + S::kA, b_hi = a_lo + S::kA, b_lo = b_hi + S::kB;
+                    const uint32_t d = kind == 0 ? t_u : t_inc;
+                    const bool first = blk <= 1;       // first inverse block, first noise block
+                    if constexpr (BF) {
+#pragma unroll
+                        for (int kk = 0; kk < kKB / 16; ++kk) {
+                            const uint32_t off = kk * 32;   // 16 BF16 = 32 bytes along K
+                            mma_bf16(d, sdesc64(a_hi + off), sdesc64(b_lo + off), idesc, (first && kk == 0) ? 0u : 1u);
+                            mma_bf16(d, sdesc64(a_lo + off), sdesc64(b_hi + off), idesc, 1u);
+                            mma_bf16(d, sdesc64(a_hi + off), sdesc64(b_hi + off), idesc, 1u);
+                        }
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < kKB / 8; ++kk) {
+                            const uint32_t off = kk * 32;   // 8 TF32 = 32 bytes along K
+                            mma_tf32(d, sdesc(a_hi + off), sdesc(b_lo + off), idesc, (first && kk == 0) ? 0u : 1u);
+                            mma_tf32(d, sdesc(a_lo + off), sdesc(b_hi + off), idesc, 1u);
+                            mma_tf32(d, sdesc(a_hi + off), sdesc(b_hi + off), idesc, 1u);
+                        }
+                    }
+                }
+                if (ok) {
+                    mma_commit(&empty[s]);
+                    if (blk == sched_inv<KB>(KB - 1)) mma_commit(u_done);
+                }
+            }
+            if (ok) mma_commit(inc_done);
+            }
+        }
+    } else if (warp >= 2 + kComputeWarps) {
+        // ---------------- noise warps: Philox normals of noise block j (Eq. b5),
+        // drawn into registers, then written as hi / lo operands once the stage is
+        // free.  Chains c = nw + kNoiseWarps i of the tile, bead n = 32 j + lane.
+        const int nw = warp - 2 - kComputeWarps;
+        constexpr int kPerN = (kChains + kNoiseWarps - 1) / kNoiseWarps;
+        int rb[kPerN];                  // first row of each chain: 32 quarter + 3 slot
+#pragma unroll
+        for (int i = 0; i < kPerN; ++i) {
+            const int c = nw + kNoiseWarps * i;
+            rb[i] = c < a.cpt ? 32 * (c / cpq) + 3 * (c % cpq) : -1;
+        }
+        // The first kPerN - 1 chain slots (30 chains) are drawn without a branch, so
+        // their Philox / Box-Muller chains interleave; a slot past the tile's
+        // chains draws for job 0 and is zeroed.
+        auto draw = [&](int qn, float (&zz)[kPerN][3]) {
+            const int sp = qn / KB, n = (qn - sp * KB) * kKB + lane;
+#pragma unroll
+            for (int i = 0; i < kPerN - 1; ++i) {
+                const int c = nw + kNoiseWarps * i;
+                Normals<float>::draw(a.seed, s_job[c], s_step[c] + sp, (uint32_t)n, 0u, zz[i]);
+            }
+            zz[kPerN - 1][0] = zz[kPerN - 1][1] = zz[kPerN - 1][2] = 0.f;
+            if (nw + kNoiseWarps * (kPerN - 1) < Ct)
+                Normals<float>::draw(a.seed, s_job[nw + kNoiseWarps * (kPerN - 1)],
+                                     s_step[nw + kNoiseWarps * (kPerN - 1)] + sp, (uint32_t)n, 0u, zz[kPerN - 1]);
+#pragma unroll
+            for (int i = 0; i < kPerN - 1; ++i)
+                if (nw + kNoiseWarps * i >= Ct) zz[i][0] = zz[i][1] = zz[i][2] = 0.f;
+        };
+        // Noise blocks in sequence qn = KB step + j.  Block qn is drawn into `cur`;
+        // if its stage is not free yet, block qn + 1 is drawn into `nxt` meanwhile
+        // (the noise does not depend on the state), so the noise warps keep
+        // drawing while the stages are held, e.g. through the epilogue.
+        bool ok = true, finite = true;
+        double cm_unused[3];
+        const int eq = warp & 3, et = (warp - 2 - kComputeWarps) / 4;   // epilogue quarter, worker 2 + et
+        const int nq = a.n_steps * KB;
+        float cur[kPerN][3], nxt[kPerN][3];
+        bool have_nxt = false;
+        draw(0, cur);
+#pragma unroll 1
+        for (int qn = 0; qn < nq; ++qn) {
+            const int sp = qn / KB, j = qn - sp * KB;
+            const int blk = sp * NBLK + sched_noise<KB, BF ? 0 : 1>(j), s = blk % ST;
+            // Consecutive noise blocks may lie more than ST blocks apart, where a
+            // parity wait on the stage's barrier is ambiguous: wait instead until
+            // the producer has seen the stage released for this block (which it
+            // does in block order, after the previous step's epilogue).
+            if (!have_nxt && qn + 1 < nq && ld_acquire_smem(s_freed) < blk) {
+                draw(qn + 1, nxt);
+                have_nxt = true;
+            }
+            ok = ok && count_wait(s_freed, blk, a.err, abort_flag);
+            if (ok) {
+                uint8_t* ah = stage0 + s * S::kStage + S::kR;
+                uint8_t* al = ah + S::kA;
+#pragma unroll
+                for (int i = 0; i < kPerN; ++i) {
+                    if (rb[i] >= 0) {
+#pragma unroll
+                        for (int x = 0; x < 3; ++x) put_hi_lo<BF>(ah, al, rb[i] + x, lane, cur[i][x]);
+                    }
+                }
+                fence_proxy_async();
+            }
+            __syncwarp();
+            if (lane == 0 && ok) mbar_arrive_cnt(&ready[s], kReadyCount / kNoiseWarps);
+            // after its last noise block, the step's epilogue (this warp's share)
+            if (j == KB - 1)
+                epilogue(sp, eq, 2 + et, 2 + kNoiseInQ[(eq + 2) & 3], ok, finite, cm_unused[0], cm_unused[1],
+                         cm_unused[2]);
+            if (have_nxt) {
+#pragma unroll
+                for (int i = 0; i < kPerN; ++i)
+#pragma unroll
+                    for (int x = 0; x < 3; ++x) cur[i][x] = nxt[i][x];
+                have_nxt = false;
+            } else if (qn + 1 < nq) {
+                draw(qn + 1, cur);
+            }
+        }
+        if (!finite) atomicOr(a.err, 1);
+    } else {
+        // ---------------- compute warps 2..9: two per TMEM lane quarter q; lane
+        // 3 k + axis of quarter q is axis `axis` of the quarter's chain k.
+        const int cw = warp - 2;            // 0..7
+        const int ct = threadIdx.x - 64;    // 0..255
+        const int q = warp & 3;             // TMEM lane quarter this warp may access
+        const int half = cw >> 2;           // which 16 of a block's 32 columns
+        const int row = 32 * q + lane;
+        const int kq = lane / 3, ax = lane - 3 * (lane / 3);
+        const bool inrow = kq < cpq;        // the row belongs to a chain slot of the tile
+        const int cl = inrow ? cpq * q + kq : 0;   // chain of the tile
+        const bool live = inrow && cl < Ct;
+        const int src0 = lane - ax;         // lane of axis 0 of this chain
+        // the chain's FP64 centre of mass, on its axis-0 lane of a first-half warp
+        const bool own_cm = half == 0 && live && ax == 0;
+        double cm_x = 0.0, cm_y = 0.0, cm_z = 0.0;
+        if (own_cm) {
+            const double* cm = a.com + 3 * (size_t)(c0 + cl);
+            cm_x = cm[0];
+            cm_y = cm[1];
+            cm_z = cm[2];
+        }
+        bool ok = true;
+        bool finite = true;
+        auto arrive = [&](int s) {
+            __syncwarp();
+            if (lane == 0 && ok) mbar_arrive_cnt(&ready[s], kReadyCount / kComputeWarps);
+        };
+#pragma unroll 1
+        for (int sp = 0; sp < a.n_steps; ++sp) {
+        const int g0 = sp * NBLK;                     // global index of this step's first block
+        // (1) split the R tile of each inverse block into hi / lo operands
+#pragma unroll 1
+        for (int nb = 0; nb < KB; ++nb) {
+            const int blk = g0 + sched_inv<KB>(nb), s = blk % ST;
+            const uint32_t ph = (blk / ST) & 1;
+            // The stage's previous use may be a noise block these warps never
+            // waited for, so a parity wait alone could be two phases ahead; the
+            // producer's release counter first (that use is consumed) makes it exact.
+            ok = ok && count_wait(s_freed, blk, a.err, abort_flag);
+            ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
+            if (ok && BF) {
+                // row t/4, BF16 chunk t%4 (8 values) from the FP32 staging tile
+                const uint8_t* r32 = stage0 + s * S::kStage;
+                uint8_t* ah = stage0 + s * S::kStage + S::kR;
+                uint8_t* al = ah + S::kA;
+#pragma unroll
+                for (int e = 0; e < kRows * 4 / kCompute; ++e) {
+                    const int t = ct + kCompute * e;
+                    const int r = t >> 2, c = t & 3;
+                    if ((r & 31) >= 3 * cpq) continue;   // padding rows of a lane quarter
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const float4 x = *reinterpret_cast<const float4*>(r32 + swz(r, 8 * c + 4 * h2));
+                        const float xs[4] = {x.x, x.y, x.z, x.w};
+                        uint16_t hh[4], ll[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            hh[i] = bf16_rn(xs[i]);
+                            ll[i] = bf16_rn(xs[i] - bf16_f(hh[i]));
+                        }
+                        hw[2 * h2] = (uint32_t)hh[0] | ((uint32_t)hh[1] << 16);
+                        hw[2 * h2 + 1] = (uint32_t)hh[2] | ((uint32_t)hh[3] << 16);
+                        lw[2 * h2] = (uint32_t)ll[0] | ((uint32_t)ll[1] << 16);
+                        lw[2 * h2 + 1] = (uint32_t)ll[2] | ((uint32_t)ll[3] << 16);
+                    }
+                    const uint32_t o = swz_bf(r, 8 * c);
+                    *reinterpret_cast<uint4*>(ah + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4*>(al + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+                fence_proxy_async();
+            } else if (ok) {
+                float4* ah = (float4*)(stage0 + s * S::kStage);
+                float4* al = (float4*)(stage0 + s * S::kStage + S::kA);
+#pragma unroll
+                for (int i = 0; i < S::kA / 16 / kCompute; ++i) {
+                    const int e = ct + kCompute * i;
+                    if (((e >> 3) & 31) >= 3 * cpq) continue;   // padding rows of a lane quarter
+                    const float4 x = ah[e];
+                    float4 h, l;
+                    h.x = tf32_rna(x.x); l.x = tf32_rna(x.x - h.x);
+                    h.y = tf32_rna(x.y); l.y = tf32_rna(x.y - h.y);
+                    h.z = tf32_rna(x.z); l.z = tf32_rna(x.z - h.z);
+                    h.w = tf32_rna(x.w); l.w = tf32_rna(x.w - h.w);
+                    ah[e] = h;
+                    al[e] = l;
+                }
+                fence_proxy_async();
+            }
+            arrive(s);
+        }
+
+        // (2) per bead block nb: bond vectors from D_u -> residual force v (Eq. e11),
+        //     |u_n| from the chain's three rows by warp shuffles
+        ok = ok && mbar_wait(u_done, sp & 1, a.err, abort_flag);
+        fence_after();
+#pragma unroll 1
+        for (int nb = 0; nb < KB; ++nb) {
+            const int col = nb * kKB + 16 * half;       // first bead of this warp's 16
+            float v[16];
+            tmem_ld16(t_u + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float sq = v[i] * v[i];
+                const float t = sq + __shfl_down_sync(0xffffffffu, sq, 1) + __shfl_down_sync(0xffffffffu, sq, 2);
+                const float fac = __shfl_sync(0xffffffffu, rsqrtf(t) - a.c12nu, src0);
+                v[i] = (live && col + i >= 1) ? v[i] * fac : 0.f;
+            }
+            const int blk = g0 + sched_force<KB, BF ? 0 : 1>(nb), s = blk % ST;
+            const uint32_t ph = (blk / ST) & 1;
+            ok = ok && mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
+            if (ok && inrow) {
+                uint8_t* ah = stage0 + s * S::kStage + S::kR;
+                uint8_t* al = ah + S::kA;
+                if constexpr (BF) {
+#pragma unroll
+                    for (int h8 = 0; h8 < 2; ++h8) {
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float x0 = v[8 * h8 + 2 * i], x1 = v[8 * h8 + 2 * i + 1];
+                            const uint16_t h0 = bf16_rn(x0), h1 = bf16_rn(x1);
+                            hw[i] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                            lw[i] = (uint32_t)bf16_rn(x0 - bf16_f(h0)) | ((uint32_t)bf16_rn(x1 - bf16_f(h1)) << 16);
+                        }
+                        const uint32_t o = swz_bf(row, 16 * half + 8 * h8);
+                        *reinterpret_cast<uint4*>(ah + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4*>(al + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        float4 h, l;
+                        h.x = tf32_rna(v[4 * k4]);     l.x = tf32_rna(v[4 * k4] - h.x);
+                        h.y = tf32_rna(v[4 * k4 + 1]); l.y = tf32_rna(v[4 * k4 + 1] - h.y);
+                        h.z = tf32_rna(v[4 * k4 + 2]); l.z = tf32_rna(v[4 * k4 + 2] - h.z);
+                        h.w = tf32_rna(v[4 * k4 + 3]); l.w = tf32_rna(v[4 * k4 + 3] - h.w);
+                        const uint32_t o = swz(row, 16 * half + 4 * k4);
+                        *reinterpret_cast<float4*>(ah + o) = h;
+                        *reinterpret_cast<float4*>(al + o) = l;
+                    }
+                }
+            }
+            if (ok) fence_proxy_async();
+            arrive(s);
+        }
+
+        // (3) epilogue, shared with the noise warps of this lane quarter
+        epilogue(sp, q, half, 2 + kNoiseInQ[(q + 2) & 3], ok, finite, cm_x, cm_y, cm_z);
+        }   // steps
+        if (ok && own_cm) {
+            double* cm = a.com + 3 * (size_t)(c0 + cl);
+            cm[0] = cm_x;
+            cm[1] = cm_y;
+            cm[2] = cm_z;
+        }
+        if (ok && half == 0 && live && ax == 0)
+            a.step[c0 + cl] = max(s_step[cl], min(s_step[cl] + (int64_t)a.n_steps, s_stop[cl]));
+        if (!finite) atomicOr(a.err, 1);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+    }
+}
+
+// The 512-bead step: a tile on a cluster of two CTAs, CTA h (its rank) holding
+// bonds and modes 256 h .. 256 h + 255 (see the file's header).
+template <bool BF>
+__global__ void __launch_bounds__(kThreads, 1)
+k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmChiH,
+             const __grid_constant__ CUtensorMap tmChiL, const __grid_constant__ CUtensorMap tmFH,
+             const __grid_constant__ CUtensorMap tmFL, const FusedArgs a)
+{
+    constexpr int NB = 256;             // TMEM columns of each half (D_u, D_inc) of this CTA
+    using S = FSmem<NB, BF, false>;
     constexpr int ST = S::kStages;
     constexpr int KBL = NB / kKB;       // column blocks of this CTA (epilogue; owned blocks of each kind)
-    constexpr int KB = PAIR ? 2 * KBL : KBL;   // inverse K blocks = forward bead blocks = M / 32
+    constexpr int KB = 2 * KBL;         // inverse K blocks = forward bead blocks = M / 32
     constexpr int MB = KB * kKB;        // beads M
     constexpr int NBLK = 3 * KB;        // blocks of one step, in the order of sched_decode
     constexpr int FILL = BF ? 0 : 1;
@@ -245,19 +768,19 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     int* s_freed = (int*)(tmem_slot + 2);   // last block whose stage the producer saw released
     uint64_t* r_blk = bars + 18;        // R column block k reloaded for the epilogue (1 + tx), k < KBL
     uint64_t* never = bars + 26;        // nothing arrives here (the stall test)
-    uint64_t* both_done = bars + 27;    // PAIR: the MMAs of both CTAs done with the step (2 commits)
-    uint64_t* peer_epi = bars + 28;     // PAIR: the other CTA's epilogue done (its producer arrives)
+    uint64_t* both_done = bars + 27;    // the MMAs of both CTAs done with the step (2 commits)
+    uint64_t* peer_epi = bars + 28;     // the other CTA's epilogue done (its producer arrives)
 
-    if (PAIR && cluster_size() != 2u) {
+    if (cluster_size() != 2u) {
         // every access to the other CTA below assumes a cluster of two
         if (threadIdx.x == 0) atomicOr(a.err, 4);
         return;
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cpq = a.cpt >> 2;         // chains per TMEM lane quarter (rows 32 q + 3 k + axis)
-    const uint32_t rank = PAIR ? cluster_rank() : 0u;   // PAIR: this CTA's bead / mode half
+    const uint32_t rank = cluster_rank();   // this CTA's bead / mode half
     const int col0 = (int)rank * NB;    // first bond and mode of this CTA's TMEM columns
-    const int c0 = (PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x) * a.cpt;
+    const int c0 = (int)(blockIdx.x >> 1) * a.cpt;
     const int Ct = min(a.cpt, a.C - c0);
     const uint32_t rblock = 4u * 3u * (uint32_t)cpq * 128u;   // bytes of one R column block
 
@@ -265,7 +788,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         for (int s = 0; s < ST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&ready[s], kReadyCount);
-            mbar_init(&empty[s], PAIR ? 2 : 1);
+            mbar_init(&empty[s], 2);      // both CTAs' MMAs
         }
         mbar_init(u_done, 1);
         mbar_init(inc_done, 1);
@@ -300,8 +823,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     fence_before();
-    if constexpr (PAIR) cluster_sync();   // both CTAs' barriers are initialised
-    else __syncthreads();
+    cluster_sync();                     // both CTAs' barriers are initialised
     fence_after();
     const uint32_t tmem = *tmem_slot;
     const uint32_t t_u = tmem, t_inc = tmem + NB;
@@ -398,27 +920,23 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             if (sp > 0) {
                 // the previous step's epilogue used the stage memory and stored R
                 if (!mbar_wait(epi_done, (sp - 1) & 1, a.err, abort_flag)) break;
-                if constexpr (PAIR) {
-                    // ... and so did the other CTA's, into whose stages this CTA copies
-                    mbar_arrive_remote(mapa(smem_u32(peer_epi), rank ^ 1u));
-                    if (!mbar_wait_cl(peer_epi, (sp - 1) & 1, a.err, abort_flag)) break;
-                }
+                // ... and so did the other CTA's, into whose stages this CTA copies
+                mbar_arrive_remote(mapa(smem_u32(peer_epi), rank ^ 1u));
+                if (!mbar_wait_cl(peer_epi, (sp - 1) & 1, a.err, abort_flag)) break;
             }
             for (int blk = 0; blk < NBLK; ++blk) {
                 const int gb = sp * NBLK + blk;
                 const int s = gb % ST;
                 const uint32_t ph = (gb / ST) & 1;
-                const bool freed = PAIR ? mbar_wait_cl(&empty[s], ph ^ 1, a.err, abort_flag)
-                                        : mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
-                if (!freed) { ok = false; break; }
+                if (!mbar_wait_cl(&empty[s], ph ^ 1, a.err, abort_flag)) { ok = false; break; }
                 st_release_smem(s_freed, gb);   // block gb may be written into stage s
                 uint8_t* st = stage0 + s * S::kStage;
                 uint8_t* bh = st + S::kR + 2 * S::kA;
                 uint8_t* bl = bh + S::kB;
                 int kind, nb;
                 sched_decode<KB, FILL>(blk, kind, nb);
-                // PAIR: a block of the other CTA arrives with its A operand copied in
-                const bool own = !PAIR || (uint32_t)(nb & 1) == rank;
+                // a block of the other CTA arrives with its A operand copied in
+                const bool own = (uint32_t)(nb & 1) == rank;
                 const uint32_t a_in = own ? 0u : 2u * S::kA;
                 if (kind == 0) {
                     // inverse: the R tile (FP32, one box per lane quarter) and chi rows of the bond half
@@ -431,7 +949,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 } else {
                     // noise block nb: rows w_p phi (t = 1); force block nb: rows h_p chi (t = 0)
                     const bool noise = kind == 1;
-                    const int x = (noise ? nb : force_bonds<KBL, PAIR>(nb)) * kKB;
+                    const int x = (noise ? nb : force_bonds<KBL>(nb)) * kKB;
                     mbar_expect_tx(&full[s], 2 * S::kB + a_in);
                     tma_load_2d(bh, &tmFH, &full[s], x, (noise ? MB : 0) + col0);
                     tma_load_2d(bl, &tmFL, &full[s], x, (noise ? MB : 0) + col0);
@@ -440,9 +958,8 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             }
             // every stage is free once the forward MMAs (of both CTAs) are done:
             // reload the R tile (KBL column blocks of [128 rows][32]) there for the epilogue
-            bool reload = ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag);
-            if constexpr (PAIR) reload = reload && mbar_wait_cl(both_done, sp & 1, a.err, abort_flag);
-            if (reload) {
+            if (ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag) &&
+                mbar_wait_cl(both_done, sp & 1, a.err, abort_flag)) {
                 for (int k = 0; k < KBL; ++k) {
                     mbar_expect_tx(&r_blk[k], rblock);
                     for (int q = 0; q < 4; ++q)
@@ -453,13 +970,11 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 ok = false;
             }
           }
-          if constexpr (PAIR) {
-              // the other CTA's commits of the last block in each stage have arrived
-              const int G = a.n_steps * NBLK;
-              for (int s = 0; s < ST && s < G && ok; ++s) {
-                  const int gl = s + ST * ((G - 1 - s) / ST);
-                  ok = mbar_wait_cl(&empty[s], (gl / ST) & 1, a.err, abort_flag);
-              }
+          // the other CTA's commits of the last block in each stage have arrived
+          const int G = a.n_steps * NBLK;
+          for (int s = 0; s < ST && s < G && ok; ++s) {
+              const int gl = s + ST * ((G - 1 - s) / ST);
+              ok = mbar_wait_cl(&empty[s], (gl / ST) & 1, a.err, abort_flag);
           }
         }
     } else if (warp == 1) {
@@ -497,24 +1012,15 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                         mma_tf32(d, sdesc(a_hi + off), sdesc(b_hi + off), idesc, 1u);
                     }
                 }
-                if constexpr (PAIR) mma_commit_mc(&empty[s], 3);   // both CTAs' stage s
-                else mma_commit(&empty[s]);
+                mma_commit_mc(&empty[s], 3);   // both CTAs' stage s
                 if (blk == sched_inv<KB>(KB - 1)) mma_commit(u_done);
                 if (blk == NBLK - 1) {
                     mma_commit(inc_done);
-                    if constexpr (PAIR) mma_commit_mc(both_done, 3);
+                    mma_commit_mc(both_done, 3);
                 }
             };
             const int G = a.n_steps * NBLK;
-            if constexpr (!PAIR) {
-                for (int gb = 0; gb < G && ok; ++gb) {
-                    const int s = gb % ST;
-                    const uint32_t ph = (gb / ST) & 1;
-                    ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
-                    ok = ok && mbar_wait(&ready[s], ph, a.err, abort_flag);
-                    if (ok) issue(gb);
-                }
-            } else {
+            {
                 // Two streams of work, polled in turn: the MMAs of every block in
                 // order, and the copy of each block this CTA owns (its A operand,
                 // hi and lo) into the same stage of the other CTA as soon as its
@@ -575,7 +1081,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         // ---------------- noise warps: Philox normals of noise block j (Eq. b5),
         // drawn into registers, then written as hi / lo operands once the stage is
         // free.  Chains c = nw + kNoiseWarps i of the tile, bead n = 32 j + lane;
-        // a PAIR CTA draws the blocks j = 2 i + rank.
+        // this CTA draws the blocks j = 2 i + rank.
         const int nw = warp - 2 - kComputeWarps;
         constexpr int kPerN = (kChains + kNoiseWarps - 1) / kNoiseWarps;
         int rb[kPerN];                  // first row of each chain: 32 quarter + 3 slot
@@ -589,7 +1095,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         // chains draws for job 0 and is zeroed.
         auto draw = [&](int qn, float (&zz)[kPerN][3]) {
             const int sp = qn / KBL, ib = qn - sp * KBL;
-            const int n = (PAIR ? 2 * ib + (int)rank : ib) * kKB + lane;
+            const int n = (2 * ib + (int)rank) * kKB + lane;
 #pragma unroll
             for (int i = 0; i < kPerN - 1; ++i) {
                 const int c = nw + kNoiseWarps * i;
@@ -617,7 +1123,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 #pragma unroll 1
         for (int qn = 0; qn < nq; ++qn) {
             const int sp = qn / KBL, ib = qn - sp * KBL;
-            const int j = PAIR ? 2 * ib + (int)rank : ib;
+            const int j = 2 * ib + (int)rank;
             const int blk = sp * NBLK + sched_noise<KB, FILL>(j), s = blk % ST;
             // Consecutive noise blocks may lie more than ST blocks apart, where a
             // parity wait on the stage's barrier is ambiguous: wait instead until
@@ -689,49 +1195,59 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 #pragma unroll 1
         for (int sp = 0; sp < a.n_steps; ++sp) {
         const int g0 = sp * NBLK;                     // global index of this step's first block
-        // (1) split the R tile of each inverse block (PAIR: of this CTA's blocks
-        //     nb = 2 i + rank) into hi / lo operands
+        // (1) split the R tile of each inverse block of this CTA (nb = 2 i + rank)
+        //     into hi / lo operands
 #pragma unroll 1
         for (int ib = 0; ib < KBL; ++ib) {
-            const int nb = PAIR ? 2 * ib + (int)rank : ib;
+            const int nb = 2 * ib + (int)rank;
             const int blk = g0 + sched_inv<KB>(nb), s = blk % ST;
             const uint32_t ph = (blk / ST) & 1;
-            // PAIR: the stage's previous uses may be the other CTA's blocks, which
-            // these warps never waited for, so a parity wait alone could be two
-            // phases ahead; the producer's release counter first makes it exact
-            if constexpr (PAIR) ok = ok && count_wait(s_freed, blk, a.err, abort_flag);
+            // The stage's previous uses may be blocks these warps never waited for
+            // (noise blocks, or the other CTA's blocks), so a parity wait alone
+            // could be two phases ahead; the producer's release counter first
+            // (the stage's previous use is consumed) makes it exact.
+            ok = ok && count_wait(s_freed, blk, a.err, abort_flag);
             ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
-            if (ok && BF) {
-                // row t/4, BF16 chunk t%4 (8 values) from the FP32 staging tile
-                const uint8_t* r32 = stage0 + s * S::kStage;
-                uint8_t* ah = stage0 + s * S::kStage + S::kR;
-                uint8_t* al = ah + S::kA;
+            if constexpr (BF) {
+                // row t/4, BF16 chunk t%4 (8 values) of the FP32 tile in A hi + A lo:
+                // every compute thread reads its values, the eight compute warps
+                // meet (named barrier 1, always taken by all of them), then the hi
+                // and lo parts overwrite the tile
+                uint8_t* base = stage0 + s * S::kStage;
+                float xv[kRows * 4 / kCompute][8];
 #pragma unroll
                 for (int e = 0; e < kRows * 4 / kCompute; ++e) {
                     const int t = ct + kCompute * e;
                     const int r = t >> 2, c = t & 3;
-                    if ((r & 31) >= 3 * cpq) continue;   // padding rows of a lane quarter
-                    uint32_t hw[4], lw[4];
+                    if (ok && (r & 31) < 3 * cpq) {   // padding rows of a lane quarter stay as they are
 #pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {
-                        const float4 x = *reinterpret_cast<const float4*>(r32 + swz(r, 8 * c + 4 * h2));
-                        const float xs[4] = {x.x, x.y, x.z, x.w};
-                        uint16_t hh[4], ll[4];
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            const float4 x = *reinterpret_cast<const float4*>(base + swz(r, 8 * c + 4 * h2));
+                            xv[e][4 * h2] = x.x; xv[e][4 * h2 + 1] = x.y; xv[e][4 * h2 + 2] = x.z; xv[e][4 * h2 + 3] = x.w;
+                        }
+                    }
+                }
+                __syncwarp();
+                asm volatile("bar.sync 1, %0;" ::"n"(kCompute) : "memory");
+#pragma unroll
+                for (int e = 0; e < kRows * 4 / kCompute; ++e) {
+                    const int t = ct + kCompute * e;
+                    const int r = t >> 2, c = t & 3;
+                    if (ok && (r & 31) < 3 * cpq) {
+                        uint32_t hw[4], lw[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            hh[i] = bf16_rn(xs[i]);
-                            ll[i] = bf16_rn(xs[i] - bf16_f(hh[i]));
+                            const uint16_t h0 = bf16_rn(xv[e][2 * i]), h1 = bf16_rn(xv[e][2 * i + 1]);
+                            hw[i] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                            lw[i] = (uint32_t)bf16_rn(xv[e][2 * i] - bf16_f(h0)) |
+                                    ((uint32_t)bf16_rn(xv[e][2 * i + 1] - bf16_f(h1)) << 16);
                         }
-                        hw[2 * h2] = (uint32_t)hh[0] | ((uint32_t)hh[1] << 16);
-                        hw[2 * h2 + 1] = (uint32_t)hh[2] | ((uint32_t)hh[3] << 16);
-                        lw[2 * h2] = (uint32_t)ll[0] | ((uint32_t)ll[1] << 16);
-                        lw[2 * h2 + 1] = (uint32_t)ll[2] | ((uint32_t)ll[3] << 16);
+                        const uint32_t o = swz_bf(r, 8 * c);
+                        *reinterpret_cast<uint4*>(base + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4*>(base + S::kA + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                     }
-                    const uint32_t o = swz_bf(r, 8 * c);
-                    *reinterpret_cast<uint4*>(ah + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    *reinterpret_cast<uint4*>(al + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                 }
-                fence_proxy_async();
+                if (ok) fence_proxy_async();
             } else if (ok) {
                 float4* ah = (float4*)(stage0 + s * S::kStage);
                 float4* al = (float4*)(stage0 + s * S::kStage + S::kA);
@@ -755,12 +1271,12 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 
         // (2) per bead block of this CTA's D_u: bond vectors -> residual force v
         //     (Eq. e11), |u_n| from the chain's three rows by warp shuffles; the
-        //     force block's schedule index is k (PAIR: bond block 8 rank + ib)
+        //     force block's schedule index is k (bond block 8 rank + ib)
         ok = ok && mbar_wait(u_done, sp & 1, a.err, abort_flag);
         fence_after();
 #pragma unroll 1
         for (int ib = 0; ib < KBL; ++ib) {
-            const int k = PAIR ? 2 * ib + (int)rank : ib;
+            const int k = 2 * ib + (int)rank;
             const int col = ib * kKB + 16 * half;       // first bond (TMEM column) of this warp's 16
             float v[16];
             tmem_ld16(t_u + ((uint32_t)(32 * q) << 16) + (uint32_t)col, v);
@@ -772,11 +1288,9 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                 v[i] = (live && col0 + col + i >= 1) ? v[i] * fac : 0.f;
             }
             const int blk = g0 + sched_force<KB, FILL>(k), s = blk % ST;
-            const uint32_t ph = (blk / ST) & 1;
-            // PAIR: as for the split, the release counter instead of a parity wait
-            // (it also covers the other CTA's MMAs: `empty` counts both)
-            if constexpr (PAIR) ok = ok && count_wait(s_freed, blk, a.err, abort_flag);
-            else ok = ok && mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
+            // as for the split, the release counter instead of a parity wait (it
+            // also covers the other CTA's MMAs, which `empty` counts)
+            ok = ok && count_wait(s_freed, blk, a.err, abort_flag);
             if (ok && inrow) {
                 uint8_t* ah = stage0 + s * S::kStage + S::kR;
                 uint8_t* al = ah + S::kA;
@@ -826,14 +1340,13 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         if (!finite) atomicOr(a.err, 1);
     }
     fence_before();
-    // PAIR: neither CTA leaves while the other may still copy into or arrive on its shared memory
+    // neither CTA leaves while the other may still copy into or arrive on its shared memory
     __syncwarp();
-    if constexpr (PAIR) cluster_sync();
-    else __syncthreads();
+    cluster_sync();
     if (warp == 1) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
-        if (PAIR && lane == 0 && *abort_flag) {
+        if (lane == 0 && *abort_flag) {
             // after a timeout the other CTA may have issued a copy into this CTA's
             // stages just before the cluster barrier: let it land before leaving
             const uint64_t t0 = globaltimer();
@@ -857,11 +1370,17 @@ static int round_tile(int cpt) { return std::min(kChains, std::max(4, (cpt + 3) 
 
 bool fused_supported(int M) { return M == 64 || M == 128 || M == 256 || M == 512; }
 
-template <int NB, bool BF, bool PAIR>
+template <int NB, bool BF>
 static cudaError_t set_smem()
 {
-    return cudaFuncSetAttribute(k_fused_step<NB, BF, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                FSmem<NB, BF>::kBytes);
+    return cudaFuncSetAttribute(k_fused_step<NB, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                FSmem<NB, BF, BF>::kBytes);
+}
+template <bool BF>
+static cudaError_t set_smem_pair()
+{
+    return cudaFuncSetAttribute(k_fused_pair<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                FSmem<256, BF, false>::kBytes);
 }
 
 int fused_create(FusedPlan** out, int M, int C, const double* chi, const double* phi, const double* h,
@@ -947,11 +1466,11 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
     }
     cudaError_t e;
     if (bf16)
-        e = M == 512 ? set_smem<256, true, true>() : M == 256 ? set_smem<256, true, false>() :
-            M == 128 ? set_smem<128, true, false>() : set_smem<64, true, false>();
+        e = M == 512 ? set_smem_pair<true>() : M == 256 ? set_smem<256, true>() :
+            M == 128 ? set_smem<128, true>() : set_smem<64, true>();
     else
-        e = M == 512 ? set_smem<256, false, true>() : M == 256 ? set_smem<256, false, false>() :
-            M == 128 ? set_smem<128, false, false>() : set_smem<64, false, false>();
+        e = M == 512 ? set_smem_pair<false>() : M == 256 ? set_smem<256, false>() :
+            M == 128 ? set_smem<128, false>() : set_smem<64, false>();
     if (e != cudaSuccess) {
         fused_destroy(p);
         return report(SFP_ECUDA, "cudaFuncSetAttribute (fused step) failed");
@@ -965,8 +1484,8 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
     if (args.cpt != p->cpt) return report(SFP_EINVAL, "fused step: chains per tile differ from the plan's");
     const dim3 grid((unsigned)((p->C + p->cpt - 1) / p->cpt));
 #define SFP_FUSED_LAUNCH(NBV, BFV)                                                                   \
-    k_fused_step<NBV, BFV, false><<<grid, kThreads, FSmem<NBV, BFV>::kBytes, stream>>>(p->tmR, p->tmChiH, \
-                                                                  p->tmChiL, p->tmFH, p->tmFL, args)
+    k_fused_step<NBV, BFV><<<grid, kThreads, FSmem<NBV, BFV, BFV>::kBytes, stream>>>(p->tmR, p->tmChiH, \
+                                                                           p->tmChiL, p->tmFH, p->tmFL, args)
     cudaError_t e = cudaSuccess;
     switch (p->M * 2 + (p->bf16 ? 1 : 0)) {
         case 1024:
@@ -975,7 +1494,7 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(2u * grid.x);
             cfg.blockDim = dim3(kThreads);
-            cfg.dynamicSmemBytes = p->bf16 ? FSmem<256, true>::kBytes : FSmem<256, false>::kBytes;
+            cfg.dynamicSmemBytes = p->bf16 ? FSmem<256, true, false>::kBytes : FSmem<256, false, false>::kBytes;
             cfg.stream = stream;
             cudaLaunchAttribute at[1];
             at[0].id = cudaLaunchAttributeClusterDimension;
@@ -984,10 +1503,10 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
             at[0].val.clusterDim.z = 1;
             cfg.attrs = at;
             cfg.numAttrs = 1;
-            e = p->bf16 ? cudaLaunchKernelEx(&cfg, k_fused_step<256, true, true>, p->tmR, p->tmChiH, p->tmChiL,
-                                             p->tmFH, p->tmFL, args)
-                        : cudaLaunchKernelEx(&cfg, k_fused_step<256, false, true>, p->tmR, p->tmChiH, p->tmChiL,
-                                             p->tmFH, p->tmFL, args);
+            e = p->bf16 ? cudaLaunchKernelEx(&cfg, k_fused_pair<true>, p->tmR, p->tmChiH, p->tmChiL, p->tmFH,
+                                             p->tmFL, args)
+                        : cudaLaunchKernelEx(&cfg, k_fused_pair<false>, p->tmR, p->tmChiH, p->tmChiL, p->tmFH,
+                                             p->tmFL, args);
             break;
         }
         case 512: SFP_FUSED_LAUNCH(256, false); break;

@@ -1,6 +1,7 @@
-"""Host model of the synchronisation of the 512-bead fused step (no GPU).
+"""Host model of the synchronisation of the fused step (no GPU).
 
-At M = 512 a tile runs on a cluster of two CTAs.  Each CTA keeps half of the
+The single-CTA kernel (M = 64, 128, 256) and, above all, the 512-bead one:
+at M = 512 a tile runs on a cluster of two CTAs.  Each CTA keeps half of the
 bonds and modes in TMEM, runs all 48 K blocks of a step, writes the A operand
 of the blocks it owns and bulk-copies it into the same stage of the other CTA.
 This test runs both CTAs' roles (TMA producer, MMA issuer and the copies its
@@ -23,12 +24,9 @@ import random
 
 import pytest
 
-KB, KBL = 16, 8          # K blocks per contraction at M = 512; blocks owned per kind
-NBLK = 3 * KB
-
-
-def decode(fill, blk):
-    """(kind, index) of block blk of a step: kind 0 inverse, 1 noise, 2 force."""
+def decode(fill, blk, KB=16):
+    """(kind, index) of block blk of a step of KB K blocks per contraction:
+    kind 0 inverse, 1 noise, 2 force."""
     h = KB // 2
     p = min(fill, h)
     if blk < 3 * h:
@@ -69,17 +67,28 @@ class Barrier:
 
 
 class Pair:
-    def __init__(self, fill, stages, steps, seed, counter_waits=True, tf32=False):
+    """pair: two CTAs at M = 512 (KB = 16), else one CTA with KB K blocks;
+    epi_stages: the stages the epilogue's R tile covers."""
+
+    def __init__(self, fill, stages, steps, seed, counter_waits=True, tf32=False, pair=True, KB=16,
+                 epi_stages=2):
         self.fill, self.st, self.steps = fill, stages, steps
         self.rng = random.Random(seed)
+        # how eagerly asynchronous work (TMA loads, copies, MMA retirement) runs:
+        # uniform among all options, or only now and then, so that it lags
+        self.lag = (None, 0.2, 0.03)[seed % 3]
         self.counter_waits, self.tf32 = counter_waits, tf32
+        self.pair, self.KB, self.epi_stages = pair, KB, epi_stages
+        self.NBLK = 3 * KB
+        self.KBL = KB // 2 if pair else KB
+        self.ncta = 2 if pair else 1
         self.bar = []
-        for r in range(2):
+        for r in range(self.ncta):
             d = {}
             for s in range(stages):
                 d["full", s] = Barrier(f"{r}.full{s}", 1)
                 d["ready", s] = Barrier(f"{r}.ready{s}", 1)
-                d["empty", s] = Barrier(f"{r}.empty{s}", 2)      # both CTAs' MMAs
+                d["empty", s] = Barrier(f"{r}.empty{s}", self.ncta)   # every CTA's MMAs
             for k, c in (("u_done", 1), ("inc_done", 1), ("epi_done", 2), ("r_blk", 1), ("both_done", 2),
                          ("peer_epi", 1)):
                 d[k] = Barrier(f"{r}.{k}", c)
@@ -87,7 +96,7 @@ class Pair:
         self.freed = [-1, -1]             # the producers' release counters
         self.region = {}                  # (cta, stage, region) -> [tag, consumers]
         self.events = []                  # asynchronous work: (target cta, action, label)
-        self.pipe = [[], []]              # MMAs and commits of each CTA, completed in order
+        self.pipe = [[] for _ in range(self.ncta)]   # MMAs and commits of each CTA, in order
         self.left = False
 
     # -- stage regions
@@ -124,23 +133,34 @@ class Pair:
         return lambda: self.freed[r] >= b
 
     def block(self, kind, idx):
-        return next(x for x in range(NBLK) if decode(self.fill, x) == (kind, idx))
+        return next(x for x in range(self.NBLK) if self.dec(x) == (kind, idx))
+
+    def dec(self, blk):
+        return decode(self.fill, blk, self.KB)
+
+    def own(self, idx, r):
+        return (idx & 1) == r if self.pair else True
+
+    def owned(self, r):
+        """indices of the blocks of each kind that CTA r writes, in order"""
+        return [2 * i + r for i in range(self.KBL)] if self.pair else list(range(self.KBL))
 
     # -- roles
     def producer(self, r):
-        bar, st = self.bar[r], self.st
+        bar, st, nblk = self.bar[r], self.st, self.NBLK
         for sp in range(self.steps):
             if sp > 0:
                 yield self.parity(r, "epi_done", sp - 1)
-                self.bar[r ^ 1]["peer_epi"].arrive()
-                yield self.parity(r, "peer_epi", sp - 1)
-            for blk in range(NBLK):
-                b, s = sp * NBLK + blk, (sp * NBLK + blk) % st
+                if self.pair:
+                    self.bar[r ^ 1]["peer_epi"].arrive()
+                    yield self.parity(r, "peer_epi", sp - 1)
+            for blk in range(nblk):
+                b, s = sp * nblk + blk, (sp * nblk + blk) % st
                 if b >= st:
                     yield self.parity(r, ("empty", s), b // st - 1)
                 self.freed[r] = b
-                kind, idx = decode(self.fill, blk)
-                own = (idx & 1) == r
+                kind, idx = self.dec(blk)
+                own = self.own(idx, r)
                 loads_r = kind == 0 and own
                 bar["full", s].arrive(1, tx=1 + loads_r + (not own))
                 self.events.append((r, self.load_b(r, s, b), "B load"))
@@ -150,15 +170,17 @@ class Pair:
                     bar["ready", s].arrive()
                 yield None
             yield self.parity(r, "inc_done", sp)
-            yield self.parity(r, "both_done", sp)
-            for s in range(min(2, st)):         # the epilogue's R tile fills the first stages
+            if self.pair:
+                yield self.parity(r, "both_done", sp)
+            for s in range(self.epi_stages):    # the epilogue's R tile fills the first stages
                 for reg in ("R", "A", "B"):
                     self.put(r, s, reg, ("epilogue", sp), {"compute", "noise"})
             self.events.append((r, lambda r=r: self.bar[r]["r_blk"].arrive(), "R reload"))
-        total = self.steps * NBLK
-        for s in range(min(st, total)):
-            last = s + st * ((total - 1 - s) // st)
-            yield self.parity(r, ("empty", s), last // st)
+        if self.pair:
+            total = self.steps * nblk
+            for s in range(min(st, total)):
+                last = s + st * ((total - 1 - s) // st)
+                yield self.parity(r, ("empty", s), last // st)
 
     def load_b(self, r, s, b):
         def act():
@@ -180,31 +202,33 @@ class Pair:
         return act
 
     def mma(self, r):
-        st = self.st
+        st, nblk = self.st, self.NBLK
         for sp in range(self.steps):
-            for blk in range(NBLK):
-                b, s = sp * NBLK + blk, (sp * NBLK + blk) % st
-                kind, idx = decode(self.fill, blk)
+            for blk in range(nblk):
+                b, s = sp * nblk + blk, (sp * nblk + blk) % st
+                kind, idx = self.dec(blk)
                 yield self.parity(r, ("full", s), b // st)
                 yield self.parity(r, ("ready", s), b // st)
                 self.holds(r, s, "A", b)
                 self.holds(r, s, "B", b)
-                self.pipe[r] += [("mma", s, b), ("commit both", ("empty", s))]
-                if kind == 0 and idx == KB - 1:
+                self.pipe[r] += [("mma", s, b), ("commit all", ("empty", s))]
+                if kind == 0 and idx == self.KB - 1:
                     self.pipe[r].append(("commit", "u_done"))
                 yield None
-            self.pipe[r] += [("commit", "inc_done"), ("commit both", "both_done")]
+            self.pipe[r].append(("commit", "inc_done"))
+            if self.pair:
+                self.pipe[r].append(("commit all", "both_done"))
 
     def sender(self, r):
         """The copies of the MMA thread's polling loop: each block this CTA owns,
         in order, once the release counter has reached it and its writers are done."""
-        st = self.st
+        st, nblk = self.st, self.NBLK
         for sp in range(self.steps):
-            for blk in range(NBLK):
-                kind, idx = decode(self.fill, blk)
-                if (idx & 1) != r:
+            for blk in range(nblk):
+                kind, idx = self.dec(blk)
+                if not self.own(idx, r):
                     continue
-                b, s = sp * NBLK + blk, (sp * NBLK + blk) % st
+                b, s = sp * nblk + blk, (sp * nblk + blk) % st
                 yield self.counter(r, b)
                 yield self.parity(r, ("ready", s), b // st)
                 self.take(r, s, "A", "to copy", b)
@@ -220,11 +244,11 @@ class Pair:
         elif item[0] == "commit":
             self.bar[r][item[1]].arrive()
         else:
-            for t in (0, 1):
+            for t in range(self.ncta):
                 self.bar[t][item[1]].arrive()
 
     def write_block(self, r, kind, idx, sp):
-        b = sp * NBLK + self.block(kind, idx)
+        b = sp * self.NBLK + self.block(kind, idx)
         s = b % self.st
         if self.counter_waits or kind == 1:
             yield self.counter(r, b)
@@ -233,14 +257,14 @@ class Pair:
             self.take(r, s, "A" if self.tf32 else "R", "split", b)
         elif kind == 2 and not self.counter_waits:
             yield self.parity(r, ("empty", s), b // self.st - 1)
-        self.put(r, s, "A", b, {"mma", "to copy"})
+        self.put(r, s, "A", b, {"mma", "to copy"} if self.pair else {"mma"})
         self.bar[r]["ready", s].arrive()
         yield None
 
     def epilogue(self, r, sp, who):
         yield self.parity(r, "inc_done", sp)
         yield self.parity(r, "r_blk", sp)
-        for s in range(min(2, self.st)):
+        for s in range(self.epi_stages):
             for reg in ("R", "A", "B"):
                 self.take(r, s, reg, who, ("epilogue", sp))
         self.bar[r]["epi_done"].arrive()
@@ -248,27 +272,33 @@ class Pair:
 
     def compute(self, r):
         for sp in range(self.steps):
-            for i in range(KBL):
-                yield from self.write_block(r, 0, 2 * i + r, sp)
+            for idx in self.owned(r):
+                yield from self.write_block(r, 0, idx, sp)
             yield self.parity(r, "u_done", sp)
-            for i in range(KBL):
-                yield from self.write_block(r, 2, 2 * i + r, sp)
+            for idx in self.owned(r):
+                yield from self.write_block(r, 2, idx, sp)
             yield from self.epilogue(r, sp, "compute")
 
     def noise(self, r):
         for sp in range(self.steps):
-            for i in range(KBL):
-                yield from self.write_block(r, 1, 2 * i + r, sp)
+            for idx in self.owned(r):
+                yield from self.write_block(r, 1, idx, sp)
             yield from self.epilogue(r, sp, "noise")
 
     def run(self):
-        roles = [[r, g, None, False] for r in range(2)
-                 for g in (self.producer(r), self.mma(r), self.sender(r), self.compute(r), self.noise(r))]
+        roles = []
+        for r in range(self.ncta):
+            gens = [self.producer(r), self.mma(r), self.compute(r), self.noise(r)]
+            if self.pair:
+                gens.append(self.sender(r))
+            roles += [[r, g, None, False] for g in gens]
         while True:
             options = [("role", i) for i, (r, g, ready, done) in enumerate(roles)
                        if not done and (ready is None or ready())]
-            options += [("event", i) for i in range(len(self.events))]
-            options += [("pipe", r) for r in range(2) if self.pipe[r]]
+            later = [("event", i) for i in range(len(self.events))]
+            later += [("pipe", r) for r in range(self.ncta) if self.pipe[r]]
+            if self.lag is None or not options or (later and self.rng.random() < self.lag):
+                options += later
             if not options:
                 if not all(x[3] for x in roles):
                     raise ProtocolError("deadlock")
@@ -281,37 +311,52 @@ class Pair:
                     roles[i][3] = True
             elif kind == "event":
                 if self.left:
-                    raise ProtocolError(f"{self.events[i][2]} after both CTAs left")
+                    raise ProtocolError(f"{self.events[i][2]} after the CTAs left")
                 self.events.pop(i)[1]()
             else:
                 if self.left:
-                    raise ProtocolError("a commit after both CTAs left")
+                    raise ProtocolError("a commit after the CTAs left")
                 self.retire(i)
             if all(x[3] for x in roles) and not self.left:
-                if self.events or self.pipe[0] or self.pipe[1]:
+                if self.events or any(self.pipe):
                     raise ProtocolError("the CTAs leave with copies or commits in flight")
                 self.left = True
 
 
-# BF16: three stages, no noise block in phase 1's tail; TF32: two stages, one.
-CONFIGS = [pytest.param(0, 3, False, id="bf16"), pytest.param(1, 2, True, id="tf32")]
+# The 512-bead kernel: BF16 four stages of 48 KB (the epilogue's R tile, 8 x 16
+# KB, covers three), no noise block in phase 1's tail; TF32 two stages of 96 KB
+# (the tile covers both) and one.
+CONFIGS = [pytest.param(0, 4, False, 3, id="bf16"), pytest.param(1, 2, True, 2, id="tf32")]
 
 
-@pytest.mark.parametrize("fill,stages,tf32", CONFIGS)
+@pytest.mark.parametrize("fill,stages,tf32,epi", CONFIGS)
 @pytest.mark.parametrize("steps", [1, 2, 3])
-def test_pair_protocol_under_random_interleavings(fill, stages, tf32, steps):
+def test_pair_protocol_under_random_interleavings(fill, stages, tf32, epi, steps):
     for seed in range(40):
-        Pair(fill, stages, steps, seed, tf32=tf32).run()
+        Pair(fill, stages, steps, seed, tf32=tf32, epi_stages=epi).run()
 
 
-@pytest.mark.parametrize("fill,stages,tf32", CONFIGS)
-def test_plain_parity_waits_are_caught(fill, stages, tf32):
+@pytest.mark.parametrize("fill,stages,tf32,epi", CONFIGS)
+def test_plain_parity_waits_are_caught(fill, stages, tf32, epi):
     """Negative control: with parity waits where the stage's previous uses
     belong to the other CTA's blocks, a wait can run two phases ahead."""
     caught = 0
     for seed in range(10):
         try:
-            Pair(fill, stages, 1, seed, counter_waits=False, tf32=tf32).run()
+            Pair(fill, stages, 1, seed, counter_waits=False, tf32=tf32, epi_stages=epi).run()
         except ProtocolError:
             caught += 1
     assert caught == 10
+
+
+# The single-CTA kernel: (K blocks, BF16 stages / TF32 stages, R-tile stages).
+SINGLE = [pytest.param(8, 0, 4, False, 3, id="256bp-bf16"), pytest.param(8, 1, 2, True, 2, id="256bp-tf32"),
+          pytest.param(4, 0, 4, False, 2, id="128bp-bf16"), pytest.param(4, 1, 3, True, 2, id="128bp-tf32"),
+          pytest.param(2, 0, 4, False, 2, id="64bp-bf16"), pytest.param(2, 1, 4, True, 1, id="64bp-tf32")]
+
+
+@pytest.mark.parametrize("KB,fill,stages,tf32,epi", SINGLE)
+@pytest.mark.parametrize("steps", [1, 3])
+def test_single_cta_protocol_under_random_interleavings(KB, fill, stages, tf32, epi, steps):
+    for seed in range(30):
+        Pair(fill, stages, steps, seed, tf32=tf32, pair=False, KB=KB, epi_stages=epi).run()
