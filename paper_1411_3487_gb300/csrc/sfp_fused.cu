@@ -167,7 +167,10 @@ __device__ __forceinline__ void put_hi_lo(uint8_t* hi, uint8_t* lo, int r, int k
 // With FILL = F > 0, N_H .. N_{H+F-1} move to the end of phase 1, where they
 // keep the tensor pipe busy while the compute warps read the bond vectors out
 // (the TF32 kernel's MMAs take twice as long, so there the pipe is the scarcer
-// resource; it uses F = 1, measured faster than F = 0 or 2; BF16 uses F = 0):
+// resource; it uses F = 1, measured faster than F = 0 or 2; BF16 uses F = 0;
+// the 512-bead kernel, whose phases are twice as long, F = 4 with BF16 (289
+// against 295 us per step at F = 0; 1, 2, 3, 5, 6, 8 in between) and F = 1
+// with TF32):
 //   ... I_{KB-1} N_H .. N_{H+F-1} | F_0 N_{H+F} | ... | F_{H-F-1} N_{KB-1} | F_{H-F} ... F_{KB-1}
 template <int KB, int FILL>
 __device__ __forceinline__ void sched_decode(int blk, int& kind, int& nb)   // kind: 0 I, 1 N, 2 F
@@ -742,7 +745,7 @@ k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     constexpr int KB = 2 * KBL;         // inverse K blocks = forward bead blocks = M / 32
     constexpr int MB = KB * kKB;        // beads M
     constexpr int NBLK = 3 * KB;        // blocks of one step, in the order of sched_decode
-    constexpr int FILL = BF ? 0 : 1;
+    constexpr int FILL = BF ? 4 : 1;   // noise blocks in phase 1's tail (measured: BF16 4, TF32 1)
     static_assert(KB % 2 == 0, "the block schedule pairs bead blocks");
     constexpr uint32_t kCols = 2 * NB;  // D_u in [0, NB), D_inc in [NB, 2 NB)
 

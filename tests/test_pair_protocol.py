@@ -324,9 +324,10 @@ class Pair:
 
 
 # The 512-bead kernel: BF16 four stages of 48 KB (the epilogue's R tile, 8 x 16
-# KB, covers three), no noise block in phase 1's tail; TF32 two stages of 96 KB
-# (the tile covers both) and one.
-CONFIGS = [pytest.param(0, 4, False, 3, id="bf16"), pytest.param(1, 2, True, 2, id="tf32")]
+# KB, covers three), four noise blocks in phase 1's tail; TF32 two stages of
+# 96 KB (the tile covers both) and one.  Also BF16 with none, the first design.
+CONFIGS = [pytest.param(4, 4, False, 3, id="bf16"), pytest.param(1, 2, True, 2, id="tf32"),
+           pytest.param(0, 4, False, 3, id="bf16-fill0")]
 
 
 @pytest.mark.parametrize("fill,stages,tf32,epi", CONFIGS)
