@@ -124,7 +124,10 @@ int sfp_init_equilibrium(sfp_batch *b, int64_t burn_in_steps);
 /* Set the state from host FP64 arrays, packed per chain as [3][M_c].
  * sfp_set_modes takes mode amplitudes R_p (p = 0..N, Eq. c1) in scaled
  * units, with R_0 = sqrt(N+1) r_cm; sfp_set_positions takes absolute bead
- * positions in nm.  Step counters are left unchanged.  Synchronous. */
+ * positions in nm.  Step counters are left unchanged.  Synchronous.  With one
+ * length group and a page-locked buffer (e.g. cudaHostAlloc), sfp_set_modes
+ * reads the caller's buffer from the GPU directly (no staging copy); the
+ * same holds for SFP_OBS_MODES of sfp_observe. */
 int sfp_set_modes(sfp_batch *b, const double *host_modes, size_t n_doubles);
 int sfp_set_positions(sfp_batch *b, const double *host_pos_nm, size_t n_doubles);
 

@@ -664,6 +664,20 @@ int to_double(sfp_batch* b, const void* src, double* dst, int64_t n)
     return SFP_OK;
 }
 
+// The device address of a page-locked host buffer that the GPU can reach
+// (NVLink-C2C / PCIe loads and stores), or nullptr for pageable memory.  The
+// conversion kernels then read or write the caller's buffer directly instead
+// of staging it with a copy.
+const void* mapped_host(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // Gather host packed [3][M_c] blocks of one group into a contiguous host array.
 void gather_group(const sfp_batch* b, const Group& g, const double* packed, std::vector<double>& out)
 {
@@ -1006,6 +1020,13 @@ int sfp_set_modes(sfp_batch* b, const double* host, size_t n_doubles)
     if (n_doubles < (size_t)(3 * b->total_beads)) return fail(SFP_EINVAL, "need %lld doubles", (long long)(3 * b->total_beads));
     std::vector<double> tmp;
     for (auto& g : b->groups) {
+        const double* dev = b->groups.size() == 1 ? (const double*)mapped_host(host) : nullptr;
+        if (dev) {   // one group, page-locked caller buffer: the kernel reads it directly
+            int rc = load_modes_dev(b, g, dev);
+            if (rc) return rc;
+            CUDA_TRY(cudaStreamSynchronize(b->stream));
+            continue;
+        }
         if (b->groups.size() == 1) {   // packed order is the group order: copy straight from the caller
             CUDA_TRY(cudaMemcpyAsync(g.stage, host, (size_t)g.C * 3 * g.M * 8, cudaMemcpyHostToDevice, b->stream));
         } else {
@@ -1100,11 +1121,15 @@ int sfp_observe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
     for (auto& g : b->groups) {
         const int64_t n = (int64_t)g.C * 3 * g.M;
         if (what == SFP_OBS_MODES) {
+            // one group, page-locked caller buffer: the kernel writes it directly
+            double* direct = b->groups.size() == 1 ? (double*)mapped_host(host_out) : nullptr;
+            double* dst = direct ? direct : g.stage;
             if (b->precision == SFP_FP64)
-                sfp::k_store_modes<double><<<nblk(n, 256), 256, 0, b->stream>>>((const double*)g.R, g.com, g.stage, g.C, g.M, std::sqrt((double)g.M));
+                sfp::k_store_modes<double><<<nblk(n, 256), 256, 0, b->stream>>>((const double*)g.R, g.com, dst, g.C, g.M, std::sqrt((double)g.M));
             else
-                sfp::k_store_modes<float><<<nblk(n, 256), 256, 0, b->stream>>>((const float*)g.R, g.com, g.stage, g.C, g.M, std::sqrt((double)g.M));
+                sfp::k_store_modes<float><<<nblk(n, 256), 256, 0, b->stream>>>((const float*)g.R, g.com, dst, g.C, g.M, std::sqrt((double)g.M));
             CUDA_TRY(cudaGetLastError());
+            if (direct) continue;   // the error-word read below waits for the stream
             if (b->groups.size() == 1) {
                 CUDA_TRY(cudaMemcpyAsync(host_out, g.stage, n * 8, cudaMemcpyDeviceToHost, b->stream));
                 CUDA_TRY(cudaStreamSynchronize(b->stream));

@@ -443,3 +443,32 @@ def test_full_size_512bp_sampled(prec):
     dcm = (G[:, :, 0] - R0[:, :, 0]) / math.sqrt(M)
     msd = np.mean(np.sum(dcm ** 2, axis=1))
     assert msd == pytest.approx(6 * TSTAR * dtau * n / M, rel=4.5 * math.sqrt(2 / (3 * C)))
+
+
+def test_page_locked_and_pageable_buffers_agree():
+    """sfp_set_modes and the SFP_OBS_MODES read of sfp_observe take a
+    page-locked host buffer straight from the GPU (no staging copy) and a
+    pageable one through a copy: both give the same state, bit for bit."""
+    import ctypes as ct
+    import torch
+    M, C, dtau = 256, 40, 100.0
+    R = starts(M, C, dtau=dtau)
+    n = R.size
+    out = []
+    for pinned in (False, True):
+        b = make_batch(M, C, dtau, (sfp.SFP_MIXED_BF16, sfp.SFP_PATH_FUSED))
+        if pinned:
+            hin = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+            hout = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        else:
+            hin, hout = np.empty(n), np.empty(n)
+        hin[:] = R.ravel()
+        L = _lib.load()
+        _lib.check(L.sfp_set_modes(b._h, hin.ctypes.data, n))
+        _lib.check(L.sfp_step(b._h, 7))
+        _lib.check(L.sfp_observe(b._h, sfp.SFP_OBS_MODES, hout.ctypes.data, n * 8))
+        out.append(hout.reshape(R.shape).copy())
+        b.close()
+    assert np.array_equal(out[0], out[1])
+    ref = O.Model(M, dtau=dtau).run_modes(R, 1, np.arange(C), 0, 7)
+    assert rel_err(out[1], ref).max() < TOL[sfp.SFP_MIXED_BF16]
