@@ -77,8 +77,8 @@ def peaks():
 
 # ------------------------------------------------------------------ oracle (CPU)
 
-def cpu_oracle_rate(n_chains: int, n_steps: int, seed: int = 1):
-    """Time the FP64 oracle on a sample of the workload (all host threads)."""
+def cpu_oracle_rate(n_chains: int, n_steps: int, seed: int = 1, nthreads: int = 0):
+    """Time the FP64 oracle on a sample of the workload (all host threads, or nthreads)."""
     sys.path.insert(0, ROOT)
     from oracle import oracle as O
     import paper_1411_3487_gb300 as sfp_mod  # noqa: F401  (only for the time unit)
@@ -90,11 +90,11 @@ def cpu_oracle_rate(n_chains: int, n_steps: int, seed: int = 1):
     m = O.Model(M_BEADS, dtau=DT_PS / c_ps)
     R = np.stack([m.equilibrium_start(seed, j) for j in range(n_chains)])
     jobs = np.arange(n_chains)
-    m.run_modes(R, seed, jobs, 0, 1)                       # warm (page-in, thread pool)
+    m.run_modes(R, seed, jobs, 0, 1, nthreads=nthreads)    # warm (page-in, thread pool)
     t0 = time.perf_counter()
-    m.run_modes(R, seed, jobs, 0, n_steps)
+    m.run_modes(R, seed, jobs, 0, n_steps, nthreads=nthreads)
     dt = time.perf_counter() - t0
-    return n_chains * M_BEADS * n_steps / dt, dt, O.threads()
+    return n_chains * M_BEADS * n_steps / dt, dt, (nthreads or O.threads())
 
 
 def run_reference(args, rank):
@@ -343,8 +343,11 @@ def run_native(args, rank, world, local):
     if rank == 0 and not args.no_cpu_baseline:
         n_c, n_s = 512, 768
         rate, secs, cores = cpu_oracle_rate(n_c, n_s)
+        rate1, secs1, _ = cpu_oracle_rate(16, 96, nthreads=1)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{n_c} chains x 256 beads x {n_s} steps ({secs:.1f} s)"}
+               "sample": f"{n_c} chains x 256 beads x {n_s} steps ({secs:.1f} s)",
+               "one_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                              "sample": f"16 chains x 256 beads x 96 steps ({secs1:.1f} s)"}}
 
     if rank == 0:
         line = {
