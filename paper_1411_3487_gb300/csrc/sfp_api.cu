@@ -551,7 +551,16 @@ int issue_chunk(sfp_batch* b, int64_t chunk, cudaStream_t base)
         for (auto& g : b->groups) CUDA_TRY(cudaStreamWaitEvent(g.gs, b->fork, 0));
     }
     int rc = SFP_OK;
-    for (auto& g : b->groups) {
+    // the groups with the most transform work (C M^2) are issued first, so that
+    // the longest launch starts first when the groups share the GPU
+    std::vector<size_t> order(b->groups.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        const Group &gx = b->groups[x], &gy = b->groups[y];
+        return (double)gx.C * gx.M * gx.M > (double)gy.C * gy.M * gy.M;
+    });
+    for (size_t gi : order) {
+        Group& g = b->groups[gi];
         b->cur = conc ? g.gs : base;
         if (b->integrator == SFP_INTEGRATOR_EULER) {
             rc = (b->precision == SFP_FP64) ? step_group_euler<double>(b, g, chunk)
