@@ -53,6 +53,7 @@ struct Job {
 
 struct Pool {
     sfp_batch* b = nullptr;
+    cudaStream_t stream = nullptr;  // the pool's own stream: pools of different shapes overlap
     int M = 0;
     double dtau = 0.0;
     int cap = 0;
@@ -73,7 +74,6 @@ struct sfp_server {
     sfp_server_config cfg{};
     double c_ps = 0.0;
     int device = 0;
-    cudaStream_t stream = nullptr;
     std::chrono::steady_clock::time_point t0;
 
     // shared with submitting / polling threads, guarded by mu
@@ -129,14 +129,22 @@ int make_pool(sfp_server* s, int M, double dtau, int cap, std::unique_ptr<Pool>*
         if (s->held >= s->cfg.hbm_budget_bytes) return SFP_ENOMEM;
         left = s->cfg.hbm_budget_bytes - s->held;
     }
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+        return srv_fail(SFP_ECUDA, "pool stream creation failed");
     sfp_batch* b = nullptr;
-    int rc = sfp_create(&s->params, d.data(), cap, s->cfg.seed, s->cfg.precision, s->stream, left, &b);
-    if (rc) return rc;
+    int rc = sfp_create(&s->params, d.data(), cap, s->cfg.seed, s->cfg.precision, st, left, &b);
+    if (rc) {
+        cudaStreamDestroy(st);
+        return rc;
+    }
     if ((rc = sfp::internal_idle_all(b))) {
         sfp_destroy(b);
+        cudaStreamDestroy(st);
         return rc;
     }
     std::unique_ptr<Pool> p(new Pool());
+    p->stream = st;
     sfp::internal_shape(b, nullptr, nullptr, nullptr, &p->bytes);
     p->b = b;
     p->M = M;
@@ -154,6 +162,7 @@ int make_pool(sfp_server* s, int M, double dtau, int cap, std::unique_ptr<Pool>*
 void drop_pool(sfp_server* s, size_t i)
 {
     sfp_destroy(s->pools[i]->b);
+    cudaStreamDestroy(s->pools[i]->stream);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->held -= s->pools[i]->bytes;
@@ -320,9 +329,17 @@ void worker_main(sfp_server* s)
         }
         int rc = admit(s);
         if (!rc) {
+            // one quantum of every pool with active slots, each on its own stream
+            // (queued without waiting, so the shapes share the GPU), the pool
+            // with the most work (active slots x M^2) first
+            std::vector<Pool*> order;
+            for (auto& p : s->pools)
+                if (p->active > 0) order.push_back(p.get());
+            std::stable_sort(order.begin(), order.end(), [](const Pool* x, const Pool* y) {
+                return (double)x->active * x->M * x->M > (double)y->active * y->M * y->M;
+            });
             bool any = false;
-            for (auto& p : s->pools) {
-                if (p->active == 0) continue;
+            for (Pool* p : order) {
                 any = true;
                 rc = sfp_step(p->b, s->cfg.quantum_steps);
                 if (rc) {
@@ -345,7 +362,10 @@ void worker_main(sfp_server* s)
             break;
         }
     }
-    for (auto& p : s->pools) sfp_destroy(p->b);
+    for (auto& p : s->pools) {
+        sfp_destroy(p->b);
+        cudaStreamDestroy(p->stream);
+    }
     s->pools.clear();
     std::lock_guard<std::mutex> lk(s->mu);
     s->held = 0;
@@ -394,11 +414,10 @@ int sfp_server_create(const sfp_params* params, const sfp_server_config* cfg, sf
     s->cfg = *cfg;
     s->c_ps = dv[2];
     s->t0 = std::chrono::steady_clock::now();
-    cudaError_t e = cudaGetDevice(&s->device);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    const cudaError_t e = cudaGetDevice(&s->device);
     if (e != cudaSuccess) {
         delete s;
-        return srv_fail(SFP_ECUDA, std::string("server stream: ") + cudaGetErrorString(e));
+        return srv_fail(SFP_ECUDA, std::string("server device: ") + cudaGetErrorString(e));
     }
     s->worker = std::thread(worker_main, s);
     *out = s;
@@ -505,7 +524,6 @@ int sfp_server_destroy(sfp_server* s)
         s->cv.notify_all();
     }
     if (s->worker.joinable()) s->worker.join();
-    if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return SFP_OK;
 }
