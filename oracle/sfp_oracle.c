@@ -33,7 +33,9 @@
  * from its published definition.  key = (seed, job_id); counter =
  * (step_lo, step_hi, index, tag).  Uniforms use the top 23 bits,
  * u = (floor(x / 2^9) + 1/2) / 2^23, so they are exact in FP32 as well.
- * Box-Muller on (x0,x1) gives the x and y normals, (x2,x3) gives z.
+ * Box-Muller on the word pairs (x0,x1) and (x2,x3) gives four normals per
+ * call, all used: the normal of bead n, axis alpha is number k = 3n + alpha
+ * of the step, value k mod 4 of the call with index k / 4.
  */
 #include <math.h>
 #include <stdint.h>
@@ -80,12 +82,13 @@ double orc_u01(uint32_t x)
     return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);   /* 2^-23 */
 }
 
-/* Three standard normals for one (step, index, tag) of one chain. */
-static void normals3(uint32_t seed, uint32_t job, int64_t step, uint32_t index,
-                     uint32_t tag, double n3[3])
+/* Four standard normals from Philox call `call` of one chain: Box-Muller on
+ * the word pairs (0,1) and (2,3), both values of each pair used. */
+static void normals4(uint32_t seed, uint32_t job, int64_t step, uint32_t call,
+                     uint32_t tag, double n4[4])
 {
     const uint32_t ctr[4] = {(uint32_t)((uint64_t)step & 0xffffffffu),
-                             (uint32_t)((uint64_t)step >> 32), index, tag};
+                             (uint32_t)((uint64_t)step >> 32), call, tag};
     const uint32_t key[2] = {seed, job};
     uint32_t x[4];
     orc_philox4x32_10(ctr, key, x);
@@ -93,19 +96,26 @@ static void normals3(uint32_t seed, uint32_t job, int64_t step, uint32_t index,
     const double ta = 2.0 * ORC_PI * orc_u01(x[1]);
     const double rb = sqrt(-2.0 * log(orc_u01(x[2])));
     const double tb = 2.0 * ORC_PI * orc_u01(x[3]);
-    n3[0] = ra * cos(ta);
-    n3[1] = ra * sin(ta);
-    n3[2] = rb * cos(tb);
+    n4[0] = ra * cos(ta);
+    n4[1] = ra * sin(ta);
+    n4[2] = rb * cos(tb);
+    n4[3] = rb * sin(tb);
 }
 
-/* z[alpha*M + n] ~ N(0,1): the per-bead thermal noise of step `step`. */
+/* z[alpha*M + n] ~ N(0,1): the per-bead thermal noise of step `step`.  The
+ * normal of bead n, axis alpha has index k = 3n + alpha and is value k mod 4
+ * of Philox call k / 4, so the 3M normals of a step take ceil(3M/4) calls. */
 void orc_bead_normals(uint32_t seed, uint32_t job, int64_t step, uint32_t tag,
                       int M, double *z)
 {
-    for (int n = 0; n < M; ++n) {
-        double g[3];
-        normals3(seed, job, step, (uint32_t)n, tag, g);
-        z[n] = g[0]; z[M + n] = g[1]; z[2 * M + n] = g[2];
+    const int K = 3 * M;
+    for (int call = 0; 4 * call < K; ++call) {
+        double g[4];
+        normals4(seed, job, step, (uint32_t)call, tag, g);
+        for (int e = 0; e < 4 && 4 * call + e < K; ++e) {
+            const int k = 4 * call + e;
+            z[(k % 3) * M + k / 3] = g[e];
+        }
     }
 }
 

@@ -365,6 +365,30 @@ def test_bead_normals_statistics():
     assert abs(lag) < 4.5 / math.sqrt(zz[1:].size)
 
 
+def test_bead_normals_use_every_box_muller_value_once():
+    """Four normals per Philox call, each used by exactly one (bead, axis).
+
+    Flattened in the order k = 3n + alpha, the normals of a step follow the
+    calls' words: the two values of a Box-Muller pair share their radius, so
+    z_{2i}^2 + z_{2i+1}^2 = -2 ln u(word 4c or 4c + 2) of call c exactly, and
+    no two (bead, axis) slots hold the same value (a slot mapped twice, or a
+    call index shifted by one, would repeat values or break the pairing)."""
+    for M in (7, 64, 65, 256):
+        z = O.bead_normals(3, 11, 5, 0, M)           # [3][M]
+        k = z.T.ravel()                              # k = 3 n + alpha
+        assert np.unique(k).size == k.size
+        for c in range(len(k) // 4):
+            w = O.philox4x32_10([5, 0, c, 0], [3, 11])
+            for pair in range(2):
+                r2 = k[4 * c + 2 * pair] ** 2 + k[4 * c + 2 * pair + 1] ** 2
+                assert r2 == pytest.approx(-2.0 * math.log(O.u01(int(w[2 * pair]))), rel=1e-12)
+        # lag correlation along k over many steps: the pairs are uncorrelated
+        zz = np.stack([O.bead_normals(3, 11, s, 0, M).T.ravel() for s in range(400)])
+        for lag in (1, 2, 3, 4):
+            r = np.corrcoef(zz[:, :-lag].ravel(), zz[:, lag:].ravel())[0, 1]
+            assert abs(r) < 4.5 / math.sqrt(zz[:, lag:].size)
+
+
 # ---------------------------------------------------------------- Monte Carlo (Sec. 5A)
 
 def _two_bond_quadrature(T, nu, n=1500):
