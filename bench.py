@@ -36,6 +36,10 @@ C_CHAINS, M_BEADS, DT_PS = 4096, 256, 15.9
 WORKLOAD = "dsDNA 4096 chains x 256 bp, FP32 state, dt 15.9 ps, equilibrium starts, no shear"
 METRIC, UNIT = "bead-timesteps/s", "bead-steps/s"
 L2_FLUSH_BYTES = 256 << 20
+# the scaled time unit c = T* (1 - 2 nu)^2 a^2 xi / kT (Eq. g2) from the printed
+# dsDNA values (T* = 0.034, nu = 0.35, a^2 xi / kT = 52.0 ps): the oracle legs
+# take their step from it, not from the library
+C_PS = 0.034 * (1.0 - 2.0 * 0.35) ** 2 * 52.0
 PREC_NAME, DTYPE = {}, {}     # filled once the library is imported
 
 
@@ -81,13 +85,7 @@ def cpu_oracle_rate(n_chains: int, n_steps: int, seed: int = 1, nthreads: int = 
     """Time the FP64 oracle on a sample of the workload (all host threads, or nthreads)."""
     sys.path.insert(0, ROOT)
     from oracle import oracle as O
-    import paper_1411_3487_gb300 as sfp_mod  # noqa: F401  (only for the time unit)
-    c_ps = 0.15912
-    try:
-        c_ps = sfp_mod.derive()["c_ps"]
-    except Exception:
-        pass
-    m = O.Model(M_BEADS, dtau=DT_PS / c_ps)
+    m = O.Model(M_BEADS, dtau=DT_PS / C_PS)
     R = np.stack([m.equilibrium_start(seed, j) for j in range(n_chains)])
     jobs = np.arange(n_chains)
     m.run_modes(R, seed, jobs, 0, 1, nthreads=nthreads)    # warm (page-in, thread pool)
@@ -102,8 +100,7 @@ def run_reference(args, rank):
         return
     sys.path.insert(0, ROOT)
     from oracle import oracle as O
-    c_ps = 0.15912
-    m = O.Model(M_BEADS, dtau=DT_PS / c_ps)
+    m = O.Model(M_BEADS, dtau=DT_PS / C_PS)
     sample = 32
     R = np.stack([m.equilibrium_start(1, j) for j in range(sample)])
     jobs = np.arange(sample)
@@ -122,7 +119,7 @@ def run_reference(args, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "chains_per_gpu": C_CHAINS, "beads": M_BEADS, "dt_ps": DT_PS,
-                   "dtau": DT_PS / c_ps, "precision": "FP64 oracle (CPU)",
+                   "dtau": DT_PS / C_PS, "precision": "FP64 oracle (CPU)",
                    "sample": f"{sample} of {C_CHAINS} chains per step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
                          "sample": f"{sample} chains x 256 beads x {args.steps} steps"},

@@ -83,20 +83,24 @@ typedef struct sfp_chain_desc {
     uint64_t job_id;           /* Philox key word of this chain's noise; < 2^32 */
 } sfp_chain_desc;
 
-/* Arithmetic of the step.
- * SFP_FP32        FP32 state; transforms on the tensor cores (tcgen05) with
- *                 a three-pass TF32 hi/lo split, FP32 accumulate (fused step
- *                 for 64/128/256/512 beads, staged otherwise).
+/* Arithmetic of the step.  In every mode the centre of mass, its MSD windows
+ * and the sampled sums are FP64 on the GPU.
+ * SFP_FP32 (= SFP_MIXED_TF32)
+ *                 FP32 state, forces and update; the two transforms run on the
+ *                 tensor cores (tcgen05, kind::tf32) as a three-pass TF32
+ *                 hi/lo split (A_hi B_lo + A_lo B_hi + A_hi B_hi) with FP32
+ *                 accumulation, which keeps FP32 trajectory accuracy (fused
+ *                 step for 64/128/256/512 beads, staged otherwise).  The name
+ *                 says what the state is; the transforms are TF32x3.
  * SFP_FP64        FP64 throughout (CUDA cores).
- * SFP_MIXED_BF16  FP32 state; transforms on the tensor cores with a three-pass
- *                 BF16 hi/lo split (kind::f16), FP32 accumulate (fused step
- *                 for 64/128/256/512 beads, staged otherwise).  The hi and lo
- *                 parts carry about 16 bits of each operand; measured against
- *                 the FP64 oracle, trajectories differ by 2-3e-6 after 1000
- *                 steps on the fused step and ~1e-5 on the staged kernels,
- *                 whose bead-space force has a larger dynamic range.
+ * SFP_MIXED_BF16  as SFP_FP32, but the transforms as a three-pass BF16 hi/lo
+ *                 split (kind::f16, BF16 A and B), FP32 accumulate: hi and lo
+ *                 carry about 16 bits of each operand.  Both the fused step
+ *                 and the staged kernels form DeltaH = chi^T v in bond form
+ *                 (Eq. e11); trajectories stay within 1e-5 of the FP64 oracle
+ *                 after 1000 steps.
  * SFP_FP32_SIMT   FP32 throughout on the CUDA cores: the plain path. */
-enum { SFP_FP32 = 0, SFP_FP64 = 1, SFP_MIXED_BF16 = 2, SFP_FP32_SIMT = 4 };
+enum { SFP_FP32 = 0, SFP_MIXED_TF32 = 0, SFP_FP64 = 1, SFP_MIXED_BF16 = 2, SFP_FP32_SIMT = 4 };
 
 typedef struct sfp_batch sfp_batch;   /* opaque */
 
@@ -135,8 +139,9 @@ int sfp_set_positions(sfp_batch *b, const double *host_pos_nm, size_t n_doubles)
 int sfp_set_step(sfp_batch *b, int64_t step);
 
 /* Advance every chain by n_steps mode-space steps (Sec. 4):
- *   bond vectors u = chi R (Eq. e5); DeltaH from the bond forces (Eq. e11); bead noise
- *   z ~ N(0,1) keyed by (seed, job_id, step, bead) and projected (Eq. c4);
+ *   bond vectors u = chi R (Eq. e5); DeltaH = chi^T v from the bond forces
+ *   (Eq. e11); bead noise z ~ N(0,1) keyed by (seed, job_id, step, bead, axis)
+ *   (see SFP_PROBE_NOISE) and projected (Eq. c4);
  *   R_p <- e^{-zeta_p dtau} R_p + h_p DeltaH_p + w_p Z_p (Eqs. d3, d6, f2);
  *   shear adds gamma g_p R^y_p to R^x_p (Eq. btum); the centre of mass
  *   (p = 0) is carried in FP64.
@@ -230,10 +235,14 @@ int sfp_set_sampling(sfp_batch *b, int32_t every_steps);
  * units, for checking each stage on its own:
  *   SFP_PROBE_BONDS  bond vectors u_n = r_n - r_{n-1} = sum_p chi_{n,p} R_p
  *                    (Eq. e5) at index n = 1..N; index 0 holds 0
- *   SFP_PROBE_FORCE  f_n = v_n - v_{n+1}, v_n = u_n (1/|u_n| - (1-2nu)),
- *                    v_0 = v_{N+1} = 0, so that phi^T f = DeltaH (Eq. e11)
- *   SFP_PROBE_NOISE  bead normals z of that step (Eq. b5, unit variance)
- *   SFP_PROBE_DH     phi^T f = DeltaH_p (Eq. e11)
+ *   SFP_PROBE_FORCE  bond forces v_n = u_n (1/|u_n| - (1-2nu)) at n = 1..N,
+ *                    index 0 holds 0, so that chi^T v = DeltaH (Eq. e11)
+ *   SFP_PROBE_NOISE  bead normals z of that step (Eq. b5, unit variance):
+ *                    the normal of bead n, axis alpha is number k = 3n + alpha
+ *                    of the step, value k mod 4 of Philox call k / 4 (counter
+ *                    (step_lo, step_hi, k / 4, 0), key (seed, job_id);
+ *                    Box-Muller on the word pairs (0,1) and (2,3))
+ *   SFP_PROBE_DH     chi^T v = DeltaH_p (Eq. e11)
  *   SFP_PROBE_ZMODE  phi^T z = Z_p (Eq. c4)
  * SFP_EINVAL if no step has run since the batch was created or its state set,
  * or if the last step ran on SFP_PATH_FUSED (set SFP_PATH_STAGED first). */
@@ -295,7 +304,7 @@ typedef struct sfp_server sfp_server;   /* opaque */
 
 typedef struct sfp_server_config {
     uint64_t seed;               /* Philox key word 0 (< 2^32) */
-    int32_t  precision;          /* SFP_FP32, SFP_FP32_SIMT or SFP_FP64 */
+    int32_t  precision;          /* any precision of sfp_create (SFP_MIXED_BF16 is fastest) */
     int32_t  slots_per_pool;     /* chains per pool (one pool per allocation) */
     int32_t  quantum_steps;      /* steps per round of the request loop */
     int32_t  keep_results;       /* 1: keep each job's final modes for sfp_server_result_modes */
@@ -338,7 +347,10 @@ int sfp_server_poll(sfp_server *s, sfp_job_result *out, int32_t max_results, int
 int sfp_server_result_modes(sfp_server *s, uint64_t ticket, double *host_modes, size_t n_doubles);
 /* Block until no job is waiting or running, or timeout_s passes (SFP_ETIMEDOUT). */
 int sfp_server_wait_idle(sfp_server *s, double timeout_s);
-/* out[0..9]: jobs submitted, finished, waiting, running; device bytes held;
+/* out[0..9]: jobs submitted, finished, waiting, running; device bytes held
+ * by the server's pools (the library's fixed SFP_NOALLOC_SCRATCH_BYTES array,
+ * resident on every device that loads the library, is outside both this count
+ * and the HBM budget);
  * p50, p99 and max latency (finish - submit, s); server clock (s); bead-steps
  * of the finished jobs. */
 int sfp_server_stats(sfp_server *s, double out[10]);
@@ -374,12 +386,15 @@ const char *sfp_server_last_error(void);
  *   com_dev    FP64 device array [n_chains][3], centre of mass in scaled
  *              units (in/out).
  *   cuda_stream  the stream to queue the work on (NULL = legacy default).
- * Scratch needed: 4 * (2 M^2 + 4 M + 15 n_chains M) bytes plus
+ * Scratch needed: 4 * (3 M^2 + 4 M + 15 n_chains M) bytes plus
  * 24 * n_chains bytes (each piece rounded up to 256 bytes); a request that does
  * not fit returns SFP_EINVAL with the limit in sfp_last_error().
- * The first call on each device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current), so make that first call
- * before any stream capture.  Every call shares the one array, which keeps
+ * Every call looks up the array's device address on the current device with
+ * cudaGetSymbolAddress (a host-side query, so a device reset does not leave a
+ * stale address behind); make the first call on a device before any stream
+ * capture, since it loads the library's device code there.  The array is not
+ * part of any batch's or server's HBM budget or held-bytes count.  Every call
+ * shares the one array, which keeps
  * the previous call's contents; calls whose work overlaps on the GPU (two
  * streams, or two host threads) race on it and must be serialised by the
  * caller.  Asynchronous on cuda_stream; non-finite states are not reported. */

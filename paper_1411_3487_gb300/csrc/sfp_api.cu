@@ -12,7 +12,6 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -94,7 +93,7 @@ int derive(const sfp_params* p, Derived* d)
 // FP64 tables of one (M, dtau), the closed forms of Eqs. c8, c9, e9, d3, d6, f2
 // written for accuracy: 1 - cos t = 2 sin^2(t/2), 1 - e^{-x} = -expm1(-x).
 struct Tables {
-    std::vector<double> phi, phiT, chi, dm, h, w, g;   // chi[n][p] = phi[n][p] - phi[n-1][p], chi[0][p] = 0
+    std::vector<double> phi, phiT, chi, chiT, dm, h, w, g;   // chi[n][p] = phi[n][p] - phi[n-1][p], chi[0][p] = 0
     double w0;
 };
 
@@ -111,9 +110,12 @@ void make_tables(int M, double Tstar, double nu, double dtau, Tables* t)
         }
     // Eq. e3 (first form): bond vectors u_n = sum_p chi_{n,p} R_p (Eq. e5); row n = 0 is zero.
     t->chi.assign((size_t)M * M, 0.0);
+    t->chiT.assign((size_t)M * M, 0.0);
     for (int n = 1; n < M; ++n)
-        for (int p = 1; p < M; ++p)
+        for (int p = 1; p < M; ++p) {
             t->chi[(size_t)n * M + p] = t->phi[(size_t)n * M + p] - t->phi[(size_t)(n - 1) * M + p];
+            t->chiT[(size_t)p * M + n] = t->chi[(size_t)n * M + p];   // DeltaH = chi^T v (Eq. e11)
+        }
     t->dm.assign(M, 0.0); t->h.assign(M, 0.0); t->w.assign(M, 0.0); t->g.assign(M, 0.0);
     t->w0 = std::sqrt(2.0 * Tstar * dtau);
     t->g[0] = dtau;
@@ -177,11 +179,11 @@ struct Group {
     double* slot_shear = nullptr;
     double* gather = nullptr;     // [kGather][3][M] + [kGather][3] + [kGather] FP64 / i64
     void* psiT = nullptr;         // [p][k] = sum_{n >= k} phi_{n,p} (bonds -> modes; Euler path)
-    void *chi = nullptr, *phiT = nullptr, *dm = nullptr, *h = nullptr, *w = nullptr, *g = nullptr;
+    void *chi = nullptr, *chiT = nullptr, *phiT = nullptr, *dm = nullptr, *h = nullptr, *w = nullptr, *g = nullptr;
     double *phi_d = nullptr, *phiT_d = nullptr;   // FP64 copies for conversions
-    void* r = nullptr;            // [C][3][M] bond vectors u (slot n = 0 unused)
-    void* fz = nullptr;           // [2][C][3][M]
-    void* yz = nullptr;           // [2][C][3][M]
+    void* r = nullptr;            // [C][3][M] bond vectors u (slot n = 0 holds 0)
+    void* fz = nullptr;           // [2][C][3][M] bond forces v and bead noise z
+    void* yz = nullptr;           // [2][C][3][M] DeltaH and Z
     double* stage = nullptr;      // [C][3][M] FP64 staging
     double* stage2 = nullptr;     // [C][3][M] FP64 staging
     sfp::TcPlan* tc = nullptr;    // tensor-core transform plan (SFP_FP32)
@@ -302,8 +304,7 @@ int launch_gemm(sfp_batch* b, const T* In, const T* B, T* Out, int J, int Nc, in
     return SFP_OK;
 }
 
-// Launch the staged force + noise kernel (one thread per bead, chains on
-// grid y) and the mode update (4 modes per thread when M % 4 == 0).
+// Chains on grid y of the mode update (4 modes per thread when M % 4 == 0).
 unsigned chains_y(int C) { return (unsigned)std::min(C, 65535); }
 
 // SFP_TEST_STALL=1 in the environment makes fused launches stall on purpose
@@ -315,12 +316,17 @@ int stall_test()
     return v && v[0] == '1' ? 1 : 0;
 }
 
+// Launch the staged bond force + noise kernel: one thread per chain and quad
+// of beads (float4 rows when M % 4 == 0).
 template <typename T>
-cudaError_t launch_force_noise(cudaStream_t st, const T* u, T* f, T* z, int C, int M, T c12nu, uint32_t seed,
+cudaError_t launch_force_noise(cudaStream_t st, const T* u, T* v, T* z, int C, int M, T c12nu, uint32_t seed,
                                const uint32_t* job, const int64_t* step)
 {
-    const dim3 grid(nblk(M, 128), chains_y(C));
-    sfp::k_force_noise<T><<<grid, 128, 0, st>>>(u, f, z, C, M, c12nu, seed, job, step);
+    const unsigned grid = nblk((int64_t)C * ((M + 3) / 4), 128);
+    if (sizeof(T) == 4 && M % 4 == 0)
+        sfp::k_force_noise<T, true><<<grid, 128, 0, st>>>(u, v, z, C, M, c12nu, seed, job, step);
+    else
+        sfp::k_force_noise<T, false><<<grid, 128, 0, st>>>(u, v, z, C, M, c12nu, seed, job, step);
     return cudaGetLastError();
 }
 
@@ -445,16 +451,17 @@ int step_group(sfp_batch* b, Group& g)
     if (rc) return rc;
     if (g.tc) b->launches++;
     if ((rc = mark(b, 1))) return rc;
-    // a2 + a3: residual bond force and bead noise
+    // a2 + a3: residual bond force v (Eq. e11) and bead noise
     {
         const T c12 = (T)(1.0 - 2.0 * b->dv.nu);
         CUDA_TRY(launch_force_noise<T>(b->cur, r, fz, fz + n, C, M, c12, b->seed, g.job, g.step));
         b->launches++;
     }
     if ((rc = mark(b, 2))) return rc;
-    // a4: [DeltaH | Z] = phi^T [f | z]  (forward transform, Eqs. c4, e11)
+    // a4: DeltaH = chi^T v (Eq. e11), Z = phi^T z (Eq. c4): the forward transform
     if (g.tc) rc = sfp::tc_transform(g.tc, 1, b->cur);
-    else rc = launch_gemm<T>(b, fz, (const T*)g.phiT, yz, 6 * C, M, M);
+    else if (!(rc = launch_gemm<T>(b, fz, (const T*)g.chiT, yz, 3 * C, M, M)))
+        rc = launch_gemm<T>(b, fz + n, (const T*)g.phiT, yz + n, 3 * C, M, M);
     if (rc) return rc;
     if (g.tc) b->launches++;
     if ((rc = mark(b, 3))) return rc;
@@ -738,26 +745,17 @@ int destroy_impl(sfp_batch* b)
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SFP_NOALLOC_SCRATCH_BYTES];
 
-std::mutex g_noalloc_mu;
-constexpr int kMaxDevices = 64;
-void* g_noalloc_addr[kMaxDevices] = {};
-
-// Device address of g_noalloc_scratch on the current device (looked up once per
-// device; the host-side name is only a stand-in and must never reach a kernel).
+// Device address of g_noalloc_scratch on the current device.  The host-side
+// name is only a stand-in and must never reach a kernel.  The address is looked
+// up on every call (a host-side query, not a stream operation), so it stays
+// right after the device's primary context has been reset and recreated.
 int noalloc_scratch(unsigned char** out)
 {
-    int dev = -1;
-    CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(SFP_ENOTSUP, "device ordinal %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(SFP_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
-        g_noalloc_addr[dev] = p;
-    }
-    *out = (unsigned char*)g_noalloc_addr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(SFP_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+    *out = (unsigned char*)p;
     return SFP_OK;
 }
 
@@ -766,14 +764,16 @@ __device__ __forceinline__ double phi_dev(int M, int n, int p)
 {
     return (p == 0) ? rsqrt((double)M) : sqrt(2.0 / M) * cospi((double)p * (n + 0.5) / M);
 }
-__global__ void k_noalloc_tables(float* chi, float* phiT, float* dm, float* h, float* w, float* g,
+__global__ void k_noalloc_tables(float* chi, float* chiT, float* phiT, float* dm, float* h, float* w, float* g,
                                  int M, double Tstar, double nu, double dtau)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < (int64_t)M * M) {
         const int n = (int)(t / M), p = (int)(t % M);
         phiT[(size_t)p * M + n] = (float)phi_dev(M, n, p);
-        chi[(size_t)n * M + p] = (n == 0 || p == 0) ? 0.f : (float)(phi_dev(M, n, p) - phi_dev(M, n - 1, p));
+        const float c = (n == 0 || p == 0) ? 0.f : (float)(phi_dev(M, n, p) - phi_dev(M, n - 1, p));
+        chi[(size_t)n * M + p] = c;
+        chiT[(size_t)p * M + n] = c;
     }
     if (t < M) {
         const int p = (int)t;
@@ -914,7 +914,7 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
         if ((rc = dalloc(b, &g.R, n * es)) || (rc = dalloc_t(b, &g.com, (size_t)g.C * 3 * 8)) ||
             (rc = dalloc_t(b, &g.job, (size_t)g.C * 4)) || (rc = dalloc_t(b, &g.shear, (size_t)g.C * 8)) ||
             (rc = dalloc_t(b, &g.step, (size_t)g.C * 8)) || (rc = dalloc_t(b, &g.stop, (size_t)g.C * 8)) ||
-            (rc = dalloc(b, &g.chi, (size_t)M * M * es)) ||
+            (rc = dalloc(b, &g.chi, (size_t)M * M * es)) || (rc = dalloc(b, &g.chiT, (size_t)M * M * es)) ||
             (rc = dalloc(b, &g.phiT, (size_t)M * M * es)) || (rc = dalloc(b, &g.dm, M * es)) ||
             (rc = dalloc(b, &g.h, M * es)) || (rc = dalloc(b, &g.w, M * es)) || (rc = dalloc(b, &g.g, M * es)) ||
             (rc = dalloc_t(b, &g.phi_d, (size_t)M * M * 8)) || (rc = dalloc_t(b, &g.phiT_d, (size_t)M * M * 8)) ||
@@ -924,7 +924,8 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
             destroy_impl(b);
             return rc;
         }
-        if ((rc = upload_typed(b, g.chi, g.tab.chi)) || (rc = upload_typed(b, g.phiT, g.tab.phiT)) ||
+        if ((rc = upload_typed(b, g.chi, g.tab.chi)) || (rc = upload_typed(b, g.chiT, g.tab.chiT)) ||
+            (rc = upload_typed(b, g.phiT, g.tab.phiT)) ||
             (rc = upload_typed(b, g.dm, g.tab.dm)) || (rc = upload_typed(b, g.h, g.tab.h)) ||
             (rc = upload_typed(b, g.w, g.tab.w)) || (rc = upload_typed(b, g.g, g.tab.g))) {
             destroy_impl(b);
@@ -968,7 +969,8 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
         e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) { destroy_impl(b); return fail(SFP_ECUDA, "create: %s", cudaGetErrorString(e)); }
         if ((precision == SFP_FP32 || precision == SFP_MIXED_BF16) && sfp::tc_supported(M)) {
-            rc = sfp::tc_create(&g.tc, M, 3 * g.C, g.tab.chi.data(), g.tab.phiT.data(), (const float*)g.R,
+            rc = sfp::tc_create(&g.tc, M, 3 * g.C, g.tab.chi.data(), g.tab.chiT.data(), g.tab.phiT.data(),
+                                (const float*)g.R,
                                 (float*)g.r, (const float*)g.fz, (float*)g.yz, b->bad, b->stream,
                                 precision == SFP_MIXED_BF16);
             if (rc) { destroy_impl(b); return rc; }
@@ -1584,7 +1586,9 @@ int sfp_step_noalloc(const sfp_params* params, const sfp_chain_desc* chain, int3
     if (!chain || !modes_dev || !com_dev) return fail(SFP_EINVAL, "NULL argument");
     if (n_chains <= 0 || n_steps < 0 || step0 < 0) return fail(SFP_EINVAL, "need n_chains > 0, n_steps >= 0, step0 >= 0");
     if (seed >> 32) return fail(SFP_EINVAL, "seed must be < 2^32");
-    if (chain->job_id + (uint64_t)n_chains - 1 >= (1ull << 32)) return fail(SFP_EINVAL, "job_id + n_chains - 1 must be < 2^32");
+    if (chain->reserved != 0) return fail(SFP_EINVAL, "reserved must be 0");
+    if ((chain->job_id >> 32) || chain->job_id + (uint64_t)n_chains - 1 >= (1ull << 32))
+        return fail(SFP_EINVAL, "job_id + n_chains - 1 must be < 2^32");
     if (chain->n_beads < 3 || chain->n_beads > 4096) return fail(SFP_EINVAL, "n_beads %d outside 3..4096", chain->n_beads);
     Derived dv;
     int rc = derive(params, &dv);
@@ -1594,10 +1598,11 @@ int sfp_step_noalloc(const sfp_params* params, const sfp_chain_desc* chain, int3
     if (!std::isfinite(chain->shear_rate_per_s)) return fail(SFP_EINVAL, "shear rate not finite");
     const int M = chain->n_beads, C = n_chains;
     const size_t fM = (size_t)M * sizeof(float), n = (size_t)C * 3 * M;
-    // carve the array: chi | phiT | dm h w g | u | f z | DeltaH Z | step | job | shear | flag
+    // carve the array: chi | chiT | phiT | dm h w g | u | v z | DeltaH Z | step | job | shear | flag
     size_t off = 0;
     auto take = [&off](size_t bytes) { const size_t o = off; off += align256(bytes); return o; };
-    const size_t o_chi = take(fM * M), o_phiT = take(fM * M), o_dm = take(fM), o_h = take(fM), o_w = take(fM),
+    const size_t o_chi = take(fM * M), o_chiT = take(fM * M), o_phiT = take(fM * M), o_dm = take(fM),
+                 o_h = take(fM), o_w = take(fM),
                  o_g = take(fM), o_r = take(n * 4), o_fz = take(2 * n * 4), o_yz = take(2 * n * 4),
                  o_step = take((size_t)C * 8), o_job = take((size_t)C * 4), o_sh = take((size_t)C * 8),
                  o_bad = take(sizeof(int));
@@ -1608,6 +1613,7 @@ int sfp_step_noalloc(const sfp_params* params, const sfp_chain_desc* chain, int3
     if ((rc = noalloc_scratch(&base))) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     float* chi = (float*)(base + o_chi);
+    float* chiT = (float*)(base + o_chiT);
     float* phiT = (float*)(base + o_phiT);
     float *dm = (float*)(base + o_dm), *h = (float*)(base + o_h), *w = (float*)(base + o_w), *g = (float*)(base + o_g);
     float* r = (float*)(base + o_r);
@@ -1616,7 +1622,8 @@ int sfp_step_noalloc(const sfp_params* params, const sfp_chain_desc* chain, int3
     int64_t* step = (int64_t*)(base + o_step);
     uint32_t* job = (uint32_t*)(base + o_job);
     double* shear = (double*)(base + o_sh);
-    k_noalloc_tables<<<nblk((int64_t)M * M, 256), 256, 0, st>>>(chi, phiT, dm, h, w, g, M, dv.Tstar, dv.nu, dtau);
+    k_noalloc_tables<<<nblk((int64_t)M * M, 256), 256, 0, st>>>(chi, chiT, phiT, dm, h, w, g, M, dv.Tstar, dv.nu,
+                                                                 dtau);
     k_noalloc_prep<<<nblk(C, 128), 128, 0, st>>>(modes_dev, step, job, shear, (int*)(base + o_bad), C, M, step0,
                                                   (uint32_t)chain->job_id, chain->shear_rate_per_s * dv.c_ps * 1e-12);
     CUDA_TRY(cudaGetLastError());
@@ -1626,7 +1633,8 @@ int sfp_step_noalloc(const sfp_params* params, const sfp_chain_desc* chain, int3
     for (int64_t s = 0; s < n_steps; ++s) {
         CUDA_TRY(gemm_on<float>(st, modes_dev, chi, r, 3 * C, M, M));
         CUDA_TRY(launch_force_noise<float>(st, r, fz, fz + n, C, M, c12, (uint32_t)seed, job, step));
-        CUDA_TRY(gemm_on<float>(st, fz, phiT, yz, 6 * C, M, M));
+        CUDA_TRY(gemm_on<float>(st, fz, chiT, yz, 3 * C, M, M));
+        CUDA_TRY(gemm_on<float>(st, fz + n, phiT, yz + n, 3 * C, M, M));
         CUDA_TRY(launch_mode_update<float>(st, modes_dev, yz, yz + n, com_dev, step, dm, h, w, g, shear, C, M, w0,
                                            dtau, bad, nullptr));
     }

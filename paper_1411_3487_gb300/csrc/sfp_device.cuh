@@ -32,38 +32,54 @@ __device__ __forceinline__ double u01d(uint32_t x)
     return (double)(x >> 9) * 1.1920928955078125e-07 + 5.9604644775390625e-08;
 }
 
-// Three N(0,1) draws for bead `n` at `step` (Box-Muller: words 0,1 -> x,y;
-// words 2,3 -> z, second value unused).
+// Bead noise (Eq. b5).  The normals of one chain and step are numbered
+// k = 3 n + alpha (bead n, axis alpha); normal k is value k % 4 of Philox call
+// k / 4, counter (step_lo, step_hi, call, tag), key (seed, job).  A call gives
+// four normals by Box-Muller on its word pairs (0,1) and (2,3), both values of
+// each pair used.  Beads 4t .. 4t+3 (12 normals) take exactly calls 3t .. 3t+2.
 template <typename T> struct Normals;
 template <> struct Normals<float> {
-    static __device__ __forceinline__ void draw(uint32_t seed, uint32_t job, int64_t step,
-                                                uint32_t n, uint32_t tag, float g[3])
+    static __device__ __forceinline__ void draw4(uint32_t seed, uint32_t job, int64_t step,
+                                                 uint32_t call, uint32_t tag, float g[4])
     {
         const uint4 w = philox4x32_10(
-            make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), n, tag), make_uint2(seed, job));
+            make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), call, tag), make_uint2(seed, job));
         // sqrt(t) as t rsqrt(t) (t >= 2^-23 here, never zero or denormal)
         const float ta = -2.0f * logf(u01f(w.x)), tb = -2.0f * logf(u01f(w.z));
         const float ra = ta * rsqrtf(ta), rb = tb * rsqrtf(tb);
-        float sa, ca;
+        float sa, ca, sb, cb;
         sincospif(2.0f * u01f(w.y), &sa, &ca);
-        const float cb = cospif(2.0f * u01f(w.w));   // the pair's second value is not used
-        g[0] = ra * ca; g[1] = ra * sa; g[2] = rb * cb;
+        sincospif(2.0f * u01f(w.w), &sb, &cb);
+        g[0] = ra * ca; g[1] = ra * sa; g[2] = rb * cb; g[3] = rb * sb;
     }
 };
 template <> struct Normals<double> {
-    static __device__ __forceinline__ void draw(uint32_t seed, uint32_t job, int64_t step,
-                                                uint32_t n, uint32_t tag, double g[3])
+    static __device__ __forceinline__ void draw4(uint32_t seed, uint32_t job, int64_t step,
+                                                 uint32_t call, uint32_t tag, double g[4])
     {
         const uint4 w = philox4x32_10(
-            make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), n, tag), make_uint2(seed, job));
+            make_uint4((uint32_t)step, (uint32_t)((uint64_t)step >> 32), call, tag), make_uint2(seed, job));
         const double ra = sqrt(-2.0 * log(u01d(w.x)));
         const double rb = sqrt(-2.0 * log(u01d(w.z)));
         double sa, ca, sb, cb;
         sincospi(2.0 * u01d(w.y), &sa, &ca);
         sincospi(2.0 * u01d(w.w), &sb, &cb);
-        g[0] = ra * ca; g[1] = ra * sa; g[2] = rb * cb;
+        g[0] = ra * ca; g[1] = ra * sa; g[2] = rb * cb; g[3] = rb * sb;
     }
 };
+
+// The normals of beads 4t .. 4t+3 of one chain and step: z[alpha][i] is bead
+// 4t + i, axis alpha (calls 3t, 3t+1, 3t+2).
+template <typename T>
+__device__ __forceinline__ void bead_quad_normals(uint32_t seed, uint32_t job, int64_t step, uint32_t t,
+                                                  uint32_t tag, T z[3][4])
+{
+    T g[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Normals<T>::draw4(seed, job, step, 3u * t + (uint32_t)c, tag, g[c]);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) z[k % 3][k / 3] = g[k / 4][k % 4];
+}
 
 template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
 template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }

@@ -214,6 +214,66 @@ template <int KBL> __device__ __forceinline__ int force_bonds(int k)
     return KBL * (k & 1) + (k >> 1);
 }
 
+// Noise of one 32-bead block of a tile (Eq. b5).  The normals of a chain and
+// step are numbered k = 3 n + alpha, four per Philox call, so beads
+// 32 jb .. 32 jb + 31 are calls 24 jb .. 24 jb + 23 of every chain.  The tile's
+// cpt x 24 (chain, call) items are cut into chunks of 32, one item per lane
+// (cpt is a multiple of 4, so the chunks are full); chunk h of the noise
+// warps' block number qn goes to noise warp (h + qn) mod kNoiseWarps, so that
+// the warp holding one chunk more than the others changes from block to block.
+// Items of chains past the tile's last chain (a partial tile) are drawn for
+// that slot's empty key and written as zeros.
+constexpr int kCallsPerBlock = kKB * 3 / 4;                                         // 24
+constexpr int kChunksPerWarp = ((kChains * kCallsPerBlock + 31) / 32 + kNoiseWarps - 1) / kNoiseWarps;
+static_assert(kChains % 4 == 0 && (4 * kCallsPerBlock) % 32 == 0, "full chunks");
+
+__device__ __forceinline__ int noise_h0(int nw, int qn) { return (nw + kNoiseWarps - qn % kNoiseWarps) % kNoiseWarps; }
+
+__device__ __forceinline__ void noise_draw(float (&zz)[kChunksPerWarp][4], int nw, int qn, int jb, int sp,
+                                           int lane, int cpt, int Ct, uint32_t seed, const uint32_t* s_job,
+                                           const int64_t* s_step)
+{
+    const int nch = cpt * kCallsPerBlock / 32;
+    const int h0 = noise_h0(nw, qn);
+#pragma unroll
+    for (int i = 0; i < kChunksPerWarp; ++i) {
+        const int h = h0 + kNoiseWarps * i;
+        if (h < nch) {   // the same for the whole warp
+            const int f = 32 * h + lane;
+            const int cl = f / kCallsPerBlock, call = f - kCallsPerBlock * cl;
+            Normals<float>::draw4(seed, s_job[cl], s_step[cl] + sp, (uint32_t)(kCallsPerBlock * jb + call), 0u,
+                                  zz[i]);
+            if (cl >= Ct) zz[i][0] = zz[i][1] = zz[i][2] = zz[i][3] = 0.f;
+        }
+    }
+}
+
+// The drawn items as hi / lo parts of the block's A operand: value e of item
+// (chain cl, call) is normal k = 4 call + e, i.e. bead k / 3 of the block (the
+// column) and axis k % 3 of the chain (row 32 quarter + 3 slot + axis).
+template <bool BF>
+__device__ __forceinline__ void noise_put(uint8_t* ah, uint8_t* al, const float (&zz)[kChunksPerWarp][4], int nw,
+                                          int qn, int lane, int cpt, int cpq)
+{
+    const int nch = cpt * kCallsPerBlock / 32;
+    const int h0 = noise_h0(nw, qn);
+#pragma unroll
+    for (int i = 0; i < kChunksPerWarp; ++i) {
+        const int h = h0 + kNoiseWarps * i;
+        if (h < nch) {
+            const int f = 32 * h + lane;
+            const int cl = f / kCallsPerBlock, call = f - kCallsPerBlock * cl;
+            const int quarter = cl / cpq;
+            const int rb = 32 * quarter + 3 * (cl - cpq * quarter);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = 4 * call + e, n = k / 3;
+                put_hi_lo<BF>(ah, al, rb + (k - 3 * n), n, zz[i][e]);
+            }
+        }
+    }
+}
+
 // The step of the 64-, 128- and 256-bead chains: a tile per CTA.
 template <int NB, bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -480,33 +540,12 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         }
     } else if (warp >= 2 + kComputeWarps) {
         // ---------------- noise warps: Philox normals of noise block j (Eq. b5),
-        // drawn into registers, then written as hi / lo operands once the stage is
-        // free.  Chains c = nw + kNoiseWarps i of the tile, bead n = 32 j + lane.
+        // drawn into registers (noise_draw), then written as hi / lo operands once
+        // the stage is free (noise_put).
         const int nw = warp - 2 - kComputeWarps;
-        constexpr int kPerN = (kChains + kNoiseWarps - 1) / kNoiseWarps;
-        int rb[kPerN];                  // first row of each chain: 32 quarter + 3 slot
-#pragma unroll
-        for (int i = 0; i < kPerN; ++i) {
-            const int c = nw + kNoiseWarps * i;
-            rb[i] = c < a.cpt ? 32 * (c / cpq) + 3 * (c % cpq) : -1;
-        }
-        // The first kPerN - 1 chain slots (30 chains) are drawn without a branch, so
-        // their Philox / Box-Muller chains interleave; a slot past the tile's
-        // chains draws for job 0 and is zeroed.
-        auto draw = [&](int qn, float (&zz)[kPerN][3]) {
-            const int sp = qn / KB, n = (qn - sp * KB) * kKB + lane;
-#pragma unroll
-            for (int i = 0; i < kPerN - 1; ++i) {
-                const int c = nw + kNoiseWarps * i;
-                Normals<float>::draw(a.seed, s_job[c], s_step[c] + sp, (uint32_t)n, 0u, zz[i]);
-            }
-            zz[kPerN - 1][0] = zz[kPerN - 1][1] = zz[kPerN - 1][2] = 0.f;
-            if (nw + kNoiseWarps * (kPerN - 1) < Ct)
-                Normals<float>::draw(a.seed, s_job[nw + kNoiseWarps * (kPerN - 1)],
-                                     s_step[nw + kNoiseWarps * (kPerN - 1)] + sp, (uint32_t)n, 0u, zz[kPerN - 1]);
-#pragma unroll
-            for (int i = 0; i < kPerN - 1; ++i)
-                if (nw + kNoiseWarps * i >= Ct) zz[i][0] = zz[i][1] = zz[i][2] = 0.f;
+        auto draw = [&](int qn, float (&zz)[kChunksPerWarp][4]) {
+            const int sp = qn / KB;
+            noise_draw(zz, nw, qn, qn - sp * KB, sp, lane, a.cpt, Ct, a.seed, s_job, s_step);
         };
         // Noise blocks in sequence qn = KB step + j.  Block qn is drawn into `cur`;
         // if its stage is not free yet, block qn + 1 is drawn into `nxt` meanwhile
@@ -516,7 +555,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         double cm_unused[3];
         const int eq = warp & 3, et = (warp - 2 - kComputeWarps) / 4;   // epilogue quarter, worker 2 + et
         const int nq = a.n_steps * KB;
-        float cur[kPerN][3], nxt[kPerN][3];
+        float cur[kChunksPerWarp][4], nxt[kChunksPerWarp][4];
         bool have_nxt = false;
         draw(0, cur);
 #pragma unroll 1
@@ -535,13 +574,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             if (ok) {
                 uint8_t* ah = stage0 + s * S::kStage + S::kR;
                 uint8_t* al = ah + S::kA;
-#pragma unroll
-                for (int i = 0; i < kPerN; ++i) {
-                    if (rb[i] >= 0) {
-#pragma unroll
-                        for (int x = 0; x < 3; ++x) put_hi_lo<BF>(ah, al, rb[i] + x, lane, cur[i][x]);
-                    }
-                }
+                noise_put<BF>(ah, al, cur, nw, qn, lane, a.cpt, cpq);
                 fence_proxy_async();
             }
             __syncwarp();
@@ -552,9 +585,9 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                          cm_unused[2]);
             if (have_nxt) {
 #pragma unroll
-                for (int i = 0; i < kPerN; ++i)
+                for (int i = 0; i < kChunksPerWarp; ++i)
 #pragma unroll
-                    for (int x = 0; x < 3; ++x) cur[i][x] = nxt[i][x];
+                    for (int x = 0; x < 4; ++x) cur[i][x] = nxt[i][x];
                 have_nxt = false;
             } else if (qn + 1 < nq) {
                 draw(qn + 1, cur);
@@ -1082,35 +1115,12 @@ k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         }
     } else if (warp >= 2 + kComputeWarps) {
         // ---------------- noise warps: Philox normals of noise block j (Eq. b5),
-        // drawn into registers, then written as hi / lo operands once the stage is
-        // free.  Chains c = nw + kNoiseWarps i of the tile, bead n = 32 j + lane;
-        // this CTA draws the blocks j = 2 i + rank.
+        // drawn into registers (noise_draw), then written as hi / lo operands once
+        // the stage is free (noise_put); this CTA draws the blocks j = 2 i + rank.
         const int nw = warp - 2 - kComputeWarps;
-        constexpr int kPerN = (kChains + kNoiseWarps - 1) / kNoiseWarps;
-        int rb[kPerN];                  // first row of each chain: 32 quarter + 3 slot
-#pragma unroll
-        for (int i = 0; i < kPerN; ++i) {
-            const int c = nw + kNoiseWarps * i;
-            rb[i] = c < a.cpt ? 32 * (c / cpq) + 3 * (c % cpq) : -1;
-        }
-        // The first kPerN - 1 chain slots (30 chains) are drawn without a branch, so
-        // their Philox / Box-Muller chains interleave; a slot past the tile's
-        // chains draws for job 0 and is zeroed.
-        auto draw = [&](int qn, float (&zz)[kPerN][3]) {
-            const int sp = qn / KBL, ib = qn - sp * KBL;
-            const int n = (2 * ib + (int)rank) * kKB + lane;
-#pragma unroll
-            for (int i = 0; i < kPerN - 1; ++i) {
-                const int c = nw + kNoiseWarps * i;
-                Normals<float>::draw(a.seed, s_job[c], s_step[c] + sp, (uint32_t)n, 0u, zz[i]);
-            }
-            zz[kPerN - 1][0] = zz[kPerN - 1][1] = zz[kPerN - 1][2] = 0.f;
-            if (nw + kNoiseWarps * (kPerN - 1) < Ct)
-                Normals<float>::draw(a.seed, s_job[nw + kNoiseWarps * (kPerN - 1)],
-                                     s_step[nw + kNoiseWarps * (kPerN - 1)] + sp, (uint32_t)n, 0u, zz[kPerN - 1]);
-#pragma unroll
-            for (int i = 0; i < kPerN - 1; ++i)
-                if (nw + kNoiseWarps * i >= Ct) zz[i][0] = zz[i][1] = zz[i][2] = 0.f;
+        auto draw = [&](int qn, float (&zz)[kChunksPerWarp][4]) {
+            const int sp = qn / KBL;
+            noise_draw(zz, nw, qn, 2 * (qn - sp * KBL) + (int)rank, sp, lane, a.cpt, Ct, a.seed, s_job, s_step);
         };
         // Noise blocks in sequence qn = KBL step + i.  Block qn is drawn into `cur`;
         // if its stage is not free yet, block qn + 1 is drawn into `nxt` meanwhile
@@ -1120,7 +1130,7 @@ k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         double cm_unused[3];
         const int eq = warp & 3, et = (warp - 2 - kComputeWarps) / 4;   // epilogue quarter, worker 2 + et
         const int nq = a.n_steps * KBL;
-        float cur[kPerN][3], nxt[kPerN][3];
+        float cur[kChunksPerWarp][4], nxt[kChunksPerWarp][4];
         bool have_nxt = false;
         draw(0, cur);
 #pragma unroll 1
@@ -1140,13 +1150,7 @@ k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             if (ok) {
                 uint8_t* ah = stage0 + s * S::kStage + S::kR;
                 uint8_t* al = ah + S::kA;
-#pragma unroll
-                for (int i = 0; i < kPerN; ++i) {
-                    if (rb[i] >= 0) {
-#pragma unroll
-                        for (int x = 0; x < 3; ++x) put_hi_lo<BF>(ah, al, rb[i] + x, lane, cur[i][x]);
-                    }
-                }
+                noise_put<BF>(ah, al, cur, nw, qn, lane, a.cpt, cpq);
                 fence_proxy_async();
             }
             __syncwarp();
@@ -1157,9 +1161,9 @@ k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
                          cm_unused[2]);
             if (have_nxt) {
 #pragma unroll
-                for (int i = 0; i < kPerN; ++i)
+                for (int i = 0; i < kChunksPerWarp; ++i)
 #pragma unroll
-                    for (int x = 0; x < 3; ++x) cur[i][x] = nxt[i][x];
+                    for (int x = 0; x < 4; ++x) cur[i][x] = nxt[i][x];
                 have_nxt = false;
             } else if (qn + 1 < nq) {
                 draw(qn + 1, cur);

@@ -70,13 +70,15 @@ k_gemm_nt(const T* __restrict__ In, const T* __restrict__ B, T* __restrict__ Out
 }
 
 // ---------------------------------------------------------------------------
-// Residual bond force + bead noise (Eqs. e4, e5, e11, b5), from bond vectors.
-// One warp per chain; each lane owns 4 consecutive indices per 128-wide chunk.
-//   u_n = sum_p chi_{n,p} R_p (given, n >= 1; slot 0 unused),
-//   v_n = u_n (1/|u_n| - (1 - 2nu)), v_0 = v_{N+1} = 0,
-//   f_n = v_n - v_{n+1}   so that  sum_n phi_{n,p} f_n = DeltaH_p  (Eq. e11).
-// v_{n+1} comes from the next lane by warp shuffle; the chunk edge from one
-// halo load.  z[n] = three N(0,1) draws keyed by (seed, job, step, n, tag 0).
+// Residual bond force + bead noise (Eqs. e4, e5, e11, b5), from bond vectors:
+//   u_n = sum_p chi_{n,p} R_p (given, n >= 1; slot 0 holds 0),
+//   v_n = u_n (1/|u_n| - (1 - 2nu)) for n >= 1, v_0 = 0,
+// so that DeltaH_p = sum_n chi_{n,p} v_n (Eq. e11) is the forward transform of
+// v with the table chi^T; z = the bead normals of (seed, job, step, tag 0).
+// The bond form needs no neighbour: each bond's force is its own.
+// One thread per chain and quad of beads 4t .. 4t+3 (the three Philox calls
+// of those beads' twelve normals); threads of a warp take consecutive quads,
+// so each axis row moves as one coalesced run of float4 (VEC: M % 4 == 0).
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void residual_v(const T u[3], bool ok, T c12nu, T v[3])
@@ -87,38 +89,57 @@ __device__ __forceinline__ void residual_v(const T u[3], bool ok, T c12nu, T v[3
     for (int a = 0; a < 3; ++a) v[a] = u[a] * s;
 }
 
-// One thread per bead n of chain blockIdx.y (grid-stride over chains): the
-// thread evaluates v_n and v_{n+1} from its own two bond loads (the second is
-// the neighbour's, served by L1), so there is no halo exchange; then draws its
-// bead's three normals.  Threads of a warp touch consecutive beads, so every
-// load and store is coalesced; many warps per chain keep enough Philox chains
-// in flight to hide their latency.
-template <typename T>
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(128)
-k_force_noise(const T* __restrict__ ub, T* __restrict__ f, T* __restrict__ z,
+k_force_noise(const T* __restrict__ ub, T* __restrict__ vb, T* __restrict__ z,
               int C, int M, T c12nu, uint32_t seed, const uint32_t* __restrict__ job,
               const int64_t* __restrict__ step)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= M) return;
-    for (int c = blockIdx.y; c < C; c += gridDim.y) {
-        const size_t base = (size_t)c * 3 * M;
-        T u[3], w[3], v0[3], v1[3];
-        const bool has1 = n + 1 < M;
+    const int Q = (M + 3) >> 2;                    // bead quads per chain
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)C * Q) return;
+    const int c = (int)(t / Q), qd = (int)(t - (int64_t)c * Q);
+    const int n0 = 4 * qd;
+    const size_t base = (size_t)c * 3 * M + n0;
+    T u[3][4];
+    if constexpr (VEC) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            u[a] = n >= 1 ? ub[base + (size_t)a * M + n] : T(0);
-            w[a] = has1 ? ub[base + (size_t)a * M + n + 1] : T(0);
+            const float4 x = *reinterpret_cast<const float4*>(ub + base + (size_t)a * M);
+            u[a][0] = x.x; u[a][1] = x.y; u[a][2] = x.z; u[a][3] = x.w;
         }
-        residual_v<T>(u, n >= 1, c12nu, v0);
-        residual_v<T>(w, has1, c12nu, v1);
-        T g[3];
-        Normals<T>::draw(seed, job[c], step[c], (uint32_t)n, 0u, g);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) u[a][i] = n0 + i < M ? ub[base + (size_t)a * M + i] : T(0);
+    }
+    T g[3][4];
+    bead_quad_normals<T>(seed, job[c], step[c], (uint32_t)qd, 0u, g);
+    T v[3][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const T ui[3] = {u[0][i], u[1][i], u[2][i]};
+        T vi[3];
+        residual_v<T>(ui, n0 + i >= 1 && n0 + i < M, c12nu, vi);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[a][i] = vi[a];
+    }
+    if constexpr (VEC) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            f[base + (size_t)a * M + n] = v0[a] - v1[a];
-            z[base + (size_t)a * M + n] = g[a];
+            *reinterpret_cast<float4*>(vb + base + (size_t)a * M) = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
+            *reinterpret_cast<float4*>(z + base + (size_t)a * M) = make_float4(g[a][0], g[a][1], g[a][2], g[a][3]);
         }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (n0 + i < M) {
+                    vb[base + (size_t)a * M + i] = v[a][i];
+                    z[base + (size_t)a * M + i] = g[a][i];
+                }
     }
 }
 
@@ -572,13 +593,18 @@ __global__ void k_euler_bonds(T* __restrict__ U, double* __restrict__ com, int64
         __syncthreads();
         // bead noise of this step into su (the bonds are in registers now)
         double zs[3] = {0.0, 0.0, 0.0};
-        for (int n = threadIdx.x; n < M; n += blockDim.x) {
-            T g[3];
-            Normals<T>::draw(seed, jb, st, (uint32_t)n, 0u, g);
+        for (int qd = threadIdx.x; 4 * qd < M; qd += blockDim.x) {
+            T g[3][4];
+            bead_quad_normals<T>(seed, jb, st, (uint32_t)qd, 0u, g);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                su[a * M + n] = g[a];
-                zs[a] += (double)g[a];
+            for (int i = 0; i < 4; ++i) {
+                const int n = 4 * qd + i;
+                if (n >= M) break;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    su[a * M + n] = g[a][i];
+                    zs[a] += (double)g[a][i];
+                }
             }
         }
         // block sum of the noise (centre of mass)

@@ -2,8 +2,11 @@
 // tensor cores (tcgen05), FP32-accurate through a three-pass TF32 split.
 //
 //   Out[j][i] = sum_k In[j][k] * B[i][k]        (NT: both operands K-contiguous)
-//   inverse (Eq. e5):  In = R   [3C][M], B = chi   [n][p]  -> Out = u (bonds)
-//   forward (Eq. c4):  In = f|z [6C][M], B = phi^T [p][n]  -> Out = DeltaH|Z
+//   inverse (Eq. e5):       In = R [3C][M], B = chi   [n][p]  -> Out = u (bonds)
+//   forward (Eqs. e11, c4): In = v [3C][M], B = chi^T [p][n]  -> Out = DeltaH
+//                           In = z [3C][M], B = phi^T [p][n]  -> Out = Z
+// The two halves of the forward transform are one launch: blockIdx.z picks
+// the half (its rows of In and Out, and its table).
 //
 // Each CTA owns 128 rows j (one UMMA M = 128 tile) and NT output columns
 // (NT = M up to 256; M = 512 uses two column tiles).  The K loop runs over
@@ -48,8 +51,9 @@ struct Smem {
 
 template <int NT>
 __global__ void __launch_bounds__(kThreads, 1)
-k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
-          const __grid_constant__ CUtensorMap tmBl, float* __restrict__ Out, int J, int M, int* err)
+k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh0,
+          const __grid_constant__ CUtensorMap tmBl0, const __grid_constant__ CUtensorMap tmBh1,
+          const __grid_constant__ CUtensorMap tmBl1, float* __restrict__ Out, int J, int M, int* err)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -65,6 +69,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row0 = blockIdx.x * kRows;
     const int col0 = blockIdx.y * NT;
+    const int roff = blockIdx.z * J;    // first row of this half in In and Out
+    const CUtensorMap* tmBh = blockIdx.z ? &tmBh1 : &tmBh0;
+    const CUtensorMap* tmBl = blockIdx.z ? &tmBl1 : &tmBl0;
     const int nk = (M + kKB - 1) / kKB;
     constexpr uint32_t kCols = NT < 32 ? 32 : NT;
 
@@ -78,8 +85,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmBh)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmBl)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmBh)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmBl)) : "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -99,9 +106,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 if (!mbar_wait(&empty[s], ph ^ 1, err, abort_flag)) break;
                 uint8_t* st = smem + s * S::kStage;
                 mbar_expect_tx(&full[s], S::kA + 2 * S::kB);
-                tma_load_2d(st, &tmA, &full[s], kb * kKB, row0);
-                tma_load_2d(st + 2 * S::kA, &tmBh, &full[s], kb * kKB, col0);
-                tma_load_2d(st + 2 * S::kA + S::kB, &tmBl, &full[s], kb * kKB, col0);
+                tma_load_2d(st, &tmA, &full[s], kb * kKB, roff + row0);
+                tma_load_2d(st + 2 * S::kA, tmBh, &full[s], kb * kKB, col0);
+                tma_load_2d(st + 2 * S::kA + S::kB, tmBl, &full[s], kb * kKB, col0);
             }
         }
     } else if (warp == 1) {
@@ -160,7 +167,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
                 if (row < J) {
-                    float4* o = (float4*)(Out + (size_t)row * M + col0 + c);
+                    float4* o = (float4*)(Out + (size_t)(roff + row) * M + col0 + c);
                     o[0] = make_float4(v[0], v[1], v[2], v[3]);
                     o[1] = make_float4(v[4], v[5], v[6], v[7]);
                     o[2] = make_float4(v[8], v[9], v[10], v[11]);
@@ -209,8 +216,9 @@ __device__ __forceinline__ uint16_t bf16_bits(float x)
 
 template <int NT>
 __global__ void __launch_bounds__(kThreads, 1)
-k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
-               const __grid_constant__ CUtensorMap tmBl, float* __restrict__ Out, int J, int M, int* err)
+k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh0,
+          const __grid_constant__ CUtensorMap tmBl0, const __grid_constant__ CUtensorMap tmBh1,
+          const __grid_constant__ CUtensorMap tmBl1, float* __restrict__ Out, int J, int M, int* err)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -227,6 +235,9 @@ k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row0 = blockIdx.x * kRows;
     const int col0 = blockIdx.y * NT;
+    const int roff = blockIdx.z * J;    // first row of this half in In and Out
+    const CUtensorMap* tmBh = blockIdx.z ? &tmBh1 : &tmBh0;
+    const CUtensorMap* tmBl = blockIdx.z ? &tmBl1 : &tmBl0;
     const int nk = (M + kKB - 1) / kKB;
     constexpr uint32_t kCols = NT < 32 ? 32 : NT;
 
@@ -240,8 +251,8 @@ k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmBh)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmBl)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmBh)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmBl)) : "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -262,9 +273,9 @@ k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 uint8_t* st = smem + s * S::kStage;
                 uint8_t* bh = st + S::kA32 + 2 * S::kA;
                 mbar_expect_tx(&full[s], S::kA32 + 2 * S::kB);
-                tma_load_2d(st, &tmA, &full[s], kb * kKB, row0);
-                tma_load_2d(bh, &tmBh, &full[s], kb * kKB, col0);
-                tma_load_2d(bh + S::kB, &tmBl, &full[s], kb * kKB, col0);
+                tma_load_2d(st, &tmA, &full[s], kb * kKB, roff + row0);
+                tma_load_2d(bh, tmBh, &full[s], kb * kKB, col0);
+                tma_load_2d(bh + S::kB, tmBl, &full[s], kb * kKB, col0);
             }
         }
     } else if (warp == 1) {
@@ -342,7 +353,7 @@ k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
                 if (row < J) {
-                    float4* o = (float4*)(Out + (size_t)row * M + col0 + c);
+                    float4* o = (float4*)(Out + (size_t)(roff + row) * M + col0 + c);
                     o[0] = make_float4(v[0], v[1], v[2], v[3]);
                     o[1] = make_float4(v[4], v[5], v[6], v[7]);
                     o[2] = make_float4(v[8], v[9], v[10], v[11]);
@@ -364,16 +375,18 @@ k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 struct TcPlan {
     int M = 0, rows = 0, NT = 0;
     bool bf16 = false;
-    void* B[4] = {nullptr, nullptr, nullptr, nullptr};    // chi_hi, chi_lo, phiT_hi, phiT_lo (FP32 or BF16)
-    CUtensorMap mapA[2], mapBh[2], mapBl[2];
+    // tables t = 0: chi (inverse), 1: chi^T (forward, force half), 2: phi^T
+    // (forward, noise half); B[2 t] hi, B[2 t + 1] lo (FP32 or BF16)
+    void* B[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    CUtensorMap mapA[2], mapBh[3], mapBl[3];
     float* out[2] = {nullptr, nullptr};
     int* err = nullptr;
 };
 
 bool tc_supported(int M) { return M == 32 || M == 64 || M == 128 || M == 256 || M == 512; }
 
-int tc_create(TcPlan** out, int M, int rows, const double* phi, const double* phiT, const float* R,
-              float* r_out, const float* fz, float* yz_out, int* err, cudaStream_t stream, bool bf16)
+int tc_create(TcPlan** out, int M, int rows, const double* chi, const double* chiT, const double* phiT,
+              const float* R, float* r_out, const float* fz, float* yz_out, int* err, cudaStream_t stream, bool bf16)
 {
     *out = nullptr;
     if (!tc_supported(M)) return report(SFP_ENOTSUP, "tensor-core transforms need M in {32, 64, 128, 256, 512}");
@@ -384,89 +397,66 @@ int tc_create(TcPlan** out, int M, int rows, const double* phi, const double* ph
     p->err = err;
     p->bf16 = bf16;
     const size_t n = (size_t)M * M;
-    if (bf16) {
-        std::vector<uint16_t> hb(n), lb(n);
-        for (int t = 0; t < 2; ++t) {
-            const double* src = t == 0 ? phi : phiT;
-            for (size_t i = 0; i < n; ++i) {
-                hb[i] = bf16_round_host((float)src[i]);
-                lb[i] = bf16_round_host((float)(src[i] - (double)bf16_to_float_host(hb[i])));
-            }
-            for (int k = 0; k < 2; ++k) {
-                if (cudaMalloc(&p->B[2 * t + k], n * 2) != cudaSuccess) {
-                    tc_destroy(p);
-                    return report(SFP_ENOMEM, "tensor-core table allocation failed");
-                }
-                if (cudaMemcpyAsync(p->B[2 * t + k], k == 0 ? hb.data() : lb.data(), n * 2, cudaMemcpyHostToDevice,
-                                    stream) != cudaSuccess ||
-                    cudaStreamSynchronize(stream) != cudaSuccess) {
-                    tc_destroy(p);
-                    return report(SFP_ECUDA, "tensor-core table upload failed");
-                }
-            }
-        }
-        int rc;
-        if ((rc = make_map(&p->mapA[0], R, rows, M, kRows)) || (rc = make_map(&p->mapA[1], fz, 2 * rows, M, kRows)) ||
-            (rc = make_map_bf16(&p->mapBh[0], p->B[0], M, M, p->NT)) || (rc = make_map_bf16(&p->mapBl[0], p->B[1], M, M, p->NT)) ||
-            (rc = make_map_bf16(&p->mapBh[1], p->B[2], M, M, p->NT)) || (rc = make_map_bf16(&p->mapBl[1], p->B[3], M, M, p->NT))) {
-            tc_destroy(p);
-            return rc;
-        }
-        p->out[0] = r_out;
-        p->out[1] = yz_out;
-        cudaError_t e = cudaSuccess;
-        switch (p->NT) {
-            case 32: e = cudaFuncSetAttribute(k_tc_gemm_bf16<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemBf<32>::kBytes); break;
-            case 64: e = cudaFuncSetAttribute(k_tc_gemm_bf16<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemBf<64>::kBytes); break;
-            case 128: e = cudaFuncSetAttribute(k_tc_gemm_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemBf<128>::kBytes); break;
-            case 256: e = cudaFuncSetAttribute(k_tc_gemm_bf16<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, SmemBf<256>::kBytes); break;
-            default: e = cudaErrorInvalidValue; break;
-        }
-        if (e != cudaSuccess) {
-            tc_destroy(p);
-            return report(SFP_ECUDA, "cudaFuncSetAttribute failed");
-        }
-        *out = p;
-        return SFP_OK;
-    }
-    std::vector<float> hi(n), lo(n);
-    for (int t = 0; t < 2; ++t) {
-        const double* src = t == 0 ? phi : phiT;
+    const double* src[3] = {chi, chiT, phiT};
+    const size_t el = bf16 ? 2 : sizeof(float);
+    for (int t = 0; t < 3; ++t) {
+        std::vector<float> hi(bf16 ? 0 : n), lo(bf16 ? 0 : n);
+        std::vector<uint16_t> hb(bf16 ? n : 0), lb(bf16 ? n : 0);
         for (size_t i = 0; i < n; ++i) {
-            hi[i] = ptx::tf32_round_host(src[i]);
-            lo[i] = ptx::tf32_round_host(src[i] - (double)hi[i]);
+            if (bf16) {
+                hb[i] = bf16_round_host((float)src[t][i]);
+                lb[i] = bf16_round_host((float)(src[t][i] - (double)bf16_to_float_host(hb[i])));
+            } else {
+                hi[i] = ptx::tf32_round_host(src[t][i]);
+                lo[i] = ptx::tf32_round_host(src[t][i] - (double)hi[i]);
+            }
         }
         for (int k = 0; k < 2; ++k) {
-            if (cudaMalloc(&p->B[2 * t + k], n * sizeof(float)) != cudaSuccess) {
+            const void* h = bf16 ? (const void*)(k == 0 ? hb.data() : lb.data())
+                                 : (const void*)(k == 0 ? hi.data() : lo.data());
+            if (cudaMalloc(&p->B[2 * t + k], n * el) != cudaSuccess) {
                 tc_destroy(p);
                 return report(SFP_ENOMEM, "tensor-core table allocation failed");
             }
-            if (cudaMemcpyAsync(p->B[2 * t + k], k == 0 ? hi.data() : lo.data(), n * sizeof(float),
-                                cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            if (cudaMemcpyAsync(p->B[2 * t + k], h, n * el, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
                 cudaStreamSynchronize(stream) != cudaSuccess) {
                 tc_destroy(p);
                 return report(SFP_ECUDA, "tensor-core table upload failed");
             }
         }
     }
-    int rc;
-    // inverse: A = R [rows][M], B = chi ; forward: A = f|z [2 rows][M], B = phi^T
-    if ((rc = make_map(&p->mapA[0], R, rows, M, kRows)) || (rc = make_map(&p->mapA[1], fz, 2 * rows, M, kRows)) ||
-        (rc = make_map(&p->mapBh[0], (const float*)p->B[0], M, M, p->NT)) || (rc = make_map(&p->mapBl[0], (const float*)p->B[1], M, M, p->NT)) ||
-        (rc = make_map(&p->mapBh[1], (const float*)p->B[2], M, M, p->NT)) || (rc = make_map(&p->mapBl[1], (const float*)p->B[3], M, M, p->NT))) {
+    // inverse: A = R [rows][M]; forward: A = v | z [2 rows][M] (a half per blockIdx.z)
+    int rc = make_map(&p->mapA[0], R, rows, M, kRows);
+    if (!rc) rc = make_map(&p->mapA[1], fz, 2 * rows, M, kRows);
+    for (int t = 0; t < 3 && !rc; ++t) {
+        if (bf16) {
+            rc = make_map_bf16(&p->mapBh[t], p->B[2 * t], M, M, p->NT);
+            if (!rc) rc = make_map_bf16(&p->mapBl[t], p->B[2 * t + 1], M, M, p->NT);
+        } else {
+            rc = make_map(&p->mapBh[t], (const float*)p->B[2 * t], M, M, p->NT);
+            if (!rc) rc = make_map(&p->mapBl[t], (const float*)p->B[2 * t + 1], M, M, p->NT);
+        }
+    }
+    if (rc) {
         tc_destroy(p);
         return rc;
     }
     p->out[0] = r_out;
     p->out[1] = yz_out;
     cudaError_t e = cudaSuccess;
-    switch (p->NT) {
-        case 32: e = cudaFuncSetAttribute(k_tc_gemm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<32>::kBytes); break;
-        case 64: e = cudaFuncSetAttribute(k_tc_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<64>::kBytes); break;
-        case 128: e = cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<128>::kBytes); break;
-        case 256: e = cudaFuncSetAttribute(k_tc_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<256>::kBytes); break;
+#define SFP_TC_ATTR(K, S) cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes)
+    switch (p->NT + (bf16 ? 1 : 0)) {
+        case 32: e = SFP_TC_ATTR(k_tc_gemm<32>, Smem<32>); break;
+        case 64: e = SFP_TC_ATTR(k_tc_gemm<64>, Smem<64>); break;
+        case 128: e = SFP_TC_ATTR(k_tc_gemm<128>, Smem<128>); break;
+        case 256: e = SFP_TC_ATTR(k_tc_gemm<256>, Smem<256>); break;
+        case 33: e = SFP_TC_ATTR(k_tc_gemm_bf16<32>, SmemBf<32>); break;
+        case 65: e = SFP_TC_ATTR(k_tc_gemm_bf16<64>, SmemBf<64>); break;
+        case 129: e = SFP_TC_ATTR(k_tc_gemm_bf16<128>, SmemBf<128>); break;
+        case 257: e = SFP_TC_ATTR(k_tc_gemm_bf16<256>, SmemBf<256>); break;
         default: e = cudaErrorInvalidValue; break;
     }
+#undef SFP_TC_ATTR
     if (e != cudaSuccess) {
         tc_destroy(p);
         return report(SFP_ECUDA, "cudaFuncSetAttribute failed");
@@ -477,42 +467,32 @@ int tc_create(TcPlan** out, int M, int rows, const double* phi, const double* ph
 
 int tc_transform(TcPlan* p, int which, cudaStream_t stream)
 {
-    const int J = which == 0 ? p->rows : 2 * p->rows;
-    dim3 grid((J + kRows - 1) / kRows, p->M / p->NT);
-    if (p->bf16) {
-        switch (p->NT) {
-            case 32: k_tc_gemm_bf16<32><<<grid, kThreads, SmemBf<32>::kBytes, stream>>>(p->mapA[which], p->mapBh[which], p->mapBl[which], p->out[which], J, p->M, p->err); break;
-            case 64: k_tc_gemm_bf16<64><<<grid, kThreads, SmemBf<64>::kBytes, stream>>>(p->mapA[which], p->mapBh[which], p->mapBl[which], p->out[which], J, p->M, p->err); break;
-            case 128: k_tc_gemm_bf16<128><<<grid, kThreads, SmemBf<128>::kBytes, stream>>>(p->mapA[which], p->mapBh[which], p->mapBl[which], p->out[which], J, p->M, p->err); break;
-            case 256: k_tc_gemm_bf16<256><<<grid, kThreads, SmemBf<256>::kBytes, stream>>>(p->mapA[which], p->mapBh[which], p->mapBl[which], p->out[which], J, p->M, p->err); break;
-            default: return report(SFP_ENOTSUP, "unsupported tile width");
-        }
-        const cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return report(SFP_ECUDA, cudaGetErrorString(e));
-        return SFP_OK;
+    // inverse: one table over the rows of R; forward: the force half (chi^T) and
+    // the noise half (phi^T) of [v | z] as grid z = 0, 1
+    const int J = p->rows;
+    const dim3 grid((J + kRows - 1) / kRows, p->M / p->NT, which == 0 ? 1 : 2);
+    const int b0 = which == 0 ? 0 : 1, b1 = which == 0 ? 0 : 2;
+#define SFP_TC_LAUNCH(K, S)                                                                             \
+    K<<<grid, kThreads, S::kBytes, stream>>>(p->mapA[which], p->mapBh[b0], p->mapBl[b0], p->mapBh[b1], \
+                                            p->mapBl[b1], p->out[which], J, p->M, p->err)
+    switch (p->NT + (p->bf16 ? 1 : 0)) {
+        case 32: SFP_TC_LAUNCH(k_tc_gemm<32>, Smem<32>); break;
+        case 64: SFP_TC_LAUNCH(k_tc_gemm<64>, Smem<64>); break;
+        case 128: SFP_TC_LAUNCH(k_tc_gemm<128>, Smem<128>); break;
+        case 256: SFP_TC_LAUNCH(k_tc_gemm<256>, Smem<256>); break;
+        case 33: SFP_TC_LAUNCH(k_tc_gemm_bf16<32>, SmemBf<32>); break;
+        case 65: SFP_TC_LAUNCH(k_tc_gemm_bf16<64>, SmemBf<64>); break;
+        case 129: SFP_TC_LAUNCH(k_tc_gemm_bf16<128>, SmemBf<128>); break;
+        case 257: SFP_TC_LAUNCH(k_tc_gemm_bf16<256>, SmemBf<256>); break;
+        default: return report(SFP_ENOTSUP, "unsupported tile width");
     }
-    switch (p->NT) {
-        case 32:
-            k_tc_gemm<32><<<grid, kThreads, Smem<32>::kBytes, stream>>>(p->mapA[which], p->mapBh[which], p->mapBl[which], p->out[which], J, p->M, p->err);
-            break;
-        case 64:
-            k_tc_gemm<64><<<grid, kThreads, Smem<64>::kBytes, stream>>>(p->mapA[which], p->mapBh[which], p->mapBl[which], p->out[which], J, p->M, p->err);
-            break;
-        case 128:
-            k_tc_gemm<128><<<grid, kThreads, Smem<128>::kBytes, stream>>>(p->mapA[which], p->mapBh[which], p->mapBl[which], p->out[which], J, p->M, p->err);
-            break;
-        case 256:
-            k_tc_gemm<256><<<grid, kThreads, Smem<256>::kBytes, stream>>>(p->mapA[which], p->mapBh[which], p->mapBl[which], p->out[which], J, p->M, p->err);
-            break;
-        default:
-            return report(SFP_ENOTSUP, "unsupported tile width");
-    }
+#undef SFP_TC_LAUNCH
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return report(SFP_ECUDA, cudaGetErrorString(e));
     return SFP_OK;
 }
 
-size_t tc_bytes(const TcPlan* p) { return p ? (size_t)4 * p->M * p->M * (p->bf16 ? 2 : sizeof(float)) : 0; }
+size_t tc_bytes(const TcPlan* p) { return p ? (size_t)6 * p->M * p->M * (p->bf16 ? 2 : sizeof(float)) : 0; }
 
 void tc_destroy(TcPlan* p)
 {

@@ -16,13 +16,14 @@ bool tc_supported(int M);
 
 // Plan the two transforms of one group with M beads and `rows` = 3 * chains:
 // inverse u = chi R (bond vectors, Eq. e5) reads R [rows][M] and writes r_out;
-// forward [DeltaH|Z] = phi^T [f|z] reads fz [2 rows][M] and writes yz_out.
-// phi / phiT are the FP64 tables chi [n][p] / phi^T [p][n]; they are split once
-// into TF32 hi/lo.
+// forward DeltaH = chi^T v (Eq. e11) and Z = phi^T z (Eq. c4) read
+// fz = [v | z] [2 rows][M] and write yz_out = [DeltaH | Z].
+// chi [n][p], chiT [p][n] and phiT [p][n] are FP64 tables; they are split
+// once into TF32 (or, with bf16, BF16) hi / lo parts.
 // A wait that times out inside the kernel sets bit 2 of *err.
-// bf16: BF16 hi/lo operands (kind::f16) instead of the TF32 split.
-int tc_create(TcPlan** out, int M, int rows, const double* phi, const double* phiT, const float* R,
-              float* r_out, const float* fz, float* yz_out, int* err, cudaStream_t stream, bool bf16 = false);
+int tc_create(TcPlan** out, int M, int rows, const double* chi, const double* chiT, const double* phiT,
+              const float* R, float* r_out, const float* fz, float* yz_out, int* err, cudaStream_t stream,
+              bool bf16 = false);
 // which = 0: inverse, 1: forward.
 int tc_transform(TcPlan* plan, int which, cudaStream_t stream);
 // Device bytes the plan's tables hold.

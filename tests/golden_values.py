@@ -18,3 +18,13 @@ def load() -> dict:
 
 
 PAPER = load()
+
+# c = T* (1 - 2 nu)^2 a^2 xi / kT (Eq. g2) from the printed values alone: the
+# scaled time unit in ps, and a shear rate in 1/s as a rate per unit of scaled
+# time (Eq. btum).  Tests convert shear rates with these, never with the
+# library's own constant.
+C_PS = PAPER["Tstar"] * (1.0 - 2.0 * PAPER["nu"]) ** 2 * PAPER["a2xi_over_kT_ps"]
+
+
+def shear_tau(rate_per_s: float) -> float:
+    return rate_per_s * C_PS * 1e-12

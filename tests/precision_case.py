@@ -8,6 +8,10 @@ centre-of-mass windows at lags of 1 and 10 samples).  Each error is
 |GPU - oracle| / |oracle| of the subset's sums (max over chains, modes or lags)."""
 import numpy as np
 
+# d = a (1 - 2 nu) in nm from the printed dsDNA values (a = 0.33 nm, nu = 0.35,
+# Sec. 2A): the oracle's sums are scaled to nm^2 with it, not with the library's
+D_NM = 0.33 * (1.0 - 2.0 * 0.35)
+
 
 def errors(sfp, O, precision, M=512, C=16384, dtau=100.0, steps=2000, every=20, sub=32, seed=1):
     b = sfp.Batch([{"n_beads": M, "dtau": dtau}] * C, seed=seed, precision=precision)
@@ -28,7 +32,7 @@ def errors(sfp, O, precision, M=512, C=16384, dtau=100.0, steps=2000, every=20, 
     g_msd = b.observe(sfp.SFP_OBS_COM_MSD)[:sub]
     g_fin = b.modes()[:sub]
     b.close()
-    d2 = sfp.derive()["d_nm"] ** 2
+    d2 = D_NM ** 2
     shape = np.zeros((sub, 4))
     power = np.zeros((sub, 3, M))
     msd = np.zeros((sub, 4, 2))

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import paper_1411_3487_gb300 as sfp
+from golden_values import PAPER
 from oracle import oracle as O
 from paper_1411_3487_gb300 import build
 
@@ -20,20 +21,23 @@ def built():
     build.build()
 
 
-# (beads, scanned steps, Table 1 column 2 dtau_max, relaxation and sampling time in tau)
+# (beads, scanned steps, Table 1 column 2 dtau_max, relaxation and sampling time
+# in tau, precision of the transforms)
 EQ_SCANS = [
-    (64, (10.0, 20.0, 50.0, 100.0, 200.0), 50.0, 2e5),
-    (128, (25.0, 50.0, 100.0, 200.0, 400.0), 100.0, 3e6),
+    pytest.param(64, (10.0, 20.0, 50.0, 100.0, 200.0), 50.0, 2e5, sfp.SFP_MIXED_TF32, id="N63_tf32x3"),
+    pytest.param(64, (10.0, 20.0, 50.0, 100.0, 200.0), 50.0, 2e5, sfp.SFP_MIXED_BF16, id="N63_bf16x3"),
+    pytest.param(128, (25.0, 50.0, 100.0, 200.0, 400.0), 100.0, 3e6, sfp.SFP_MIXED_TF32, id="N127_tf32x3"),
 ]
 
 
-@pytest.mark.parametrize("M,dtaus,dtau_max,relax", EQ_SCANS, ids=["N63", "N127"])
-def test_dtau_max_from_equilibrium_quantities(M, dtaus, dtau_max, relax):
+@pytest.mark.parametrize("M,dtaus,dtau_max,relax,precision", EQ_SCANS)
+def test_dtau_max_from_equilibrium_quantities(M, dtaus, dtau_max, relax, precision):
     """Scan dtau at N = M - 1: 4096 chains relaxed for `relax` tau, then 200
-    samples over `relax` tau, tensor-core path.  Monte Carlo: the oracle's
-    sampler, 64 chains x 2e4 sweeps after tuning.  Prints the scan; requires
-    every observable within 5% of MC, within two standard errors (the paper
-    takes its error bars into account), for every dtau up to Table 1's value."""
+    samples over `relax` tau, fused tensor-core step (TF32x3, or BF16x3 as in
+    the benchmark's headline).  Monte Carlo: the oracle's sampler, 64 chains x
+    2e4 sweeps after tuning.  Prints the scan; requires every observable within
+    5% of MC, within two standard errors (the paper takes its error bars into
+    account), for every dtau up to Table 1's value."""
     m = O.Model(M, dtau=10.0)
     Cm = 64
     R = np.stack([m.equilibrium_start(9, j) for j in range(Cm)])
@@ -43,11 +47,11 @@ def test_dtau_max_from_equilibrium_quantities(M, dtaus, dtau_max, relax):
     mc_per = obs[:, :3] / obs[:, 3:4]
     mc = mc_per.mean(axis=0)
     mc_se = mc_per.std(axis=0, ddof=1) / math.sqrt(Cm)
-    d2 = sfp.derive()["d_nm"] ** 2
+    d2 = (PAPER["a_nm"] * (1.0 - 2.0 * PAPER["nu"])) ** 2   # d from the printed values (Sec. 2A)
     rows = []
     for dtau in dtaus:
         n = int(round(relax / dtau))
-        b = sfp.Batch([{"n_beads": M, "dtau": dtau}] * 4096, seed=11, precision=sfp.SFP_FP32)
+        b = sfp.Batch([{"n_beads": M, "dtau": dtau}] * 4096, seed=11, precision=precision)
         b.init_equilibrium(0)
         b.step(n)
         b.set_sampling(max(1, n // 200))

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import paper_1411_3487_gb300 as sfp
+from golden_values import shear_tau
 from oracle import oracle as O
 from paper_1411_3487_gb300 import build
 
@@ -36,9 +37,8 @@ def test_euler_matches_oracle(precision, tol, M, C, shear):
     b.step(120)
     b.step(n - 120)                                                # two calls: conversions in between
     G = b.modes()
-    c_ps = sfp.derive()["c_ps"]
     r0 = np.stack([m.modes_to_beads(x) for x in R0])
-    r = m.run_euler(r0, 2, np.arange(C), 0, n, shear=shear * c_ps * 1e-12)
+    r = m.run_euler(r0, 2, np.arange(C), 0, n, shear=shear_tau(shear))
     ref = np.stack([m.beads_to_modes(x) for x in r])
     assert rel_err(G, ref).max() < tol
     # centre of mass: FP64 on both sides, noise projected in FP32 or FP64

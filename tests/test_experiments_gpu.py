@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import paper_1411_3487_gb300 as sfp
+from golden_values import C_PS, PAPER, shear_tau
 from oracle import oracle as O
 from paper_1411_3487_gb300 import build
 from paper_1411_3487_gb300.tumbling import run_tumbling
@@ -64,12 +65,12 @@ def test_headless_tumbling_snapshots():
     n = 6
     pos = run_tumbling(n_snapshots=n)
     assert pos.shape == (n + 1, 3, 255) and np.isfinite(pos).all()
-    d = sfp.derive()
-    dtau = 16.0 / d["c_ps"]
+    dtau = 16.0 / C_PS                       # 16 ps steps, c from the printed values (Eq. g2)
+    d_nm = PAPER["a_nm"] * (1.0 - 2.0 * PAPER["nu"])
     m = O.Model(255, dtau=dtau)
     R = m.equilibrium_start(1, 0)
     steps = int(round(8.0e3 / 16.0))
-    R1 = m.run_modes(R[None], 1, [0], 0, steps, shear=1.54e8 * d["c_ps"] * 1e-12)[0]
-    ref = m.modes_to_beads(R1) * d["d_nm"]
+    R1 = m.run_modes(R[None], 1, [0], 0, steps, shear=shear_tau(1.54e8))[0]
+    ref = m.modes_to_beads(R1) * d_nm
     err = np.linalg.norm(pos[1] - ref) / np.linalg.norm(ref - ref.mean(axis=1, keepdims=True))
     assert err < 1e-5

@@ -1,12 +1,14 @@
 """Observable accumulators of the CUDA path (Sec. 5B) against the oracle, and
 the paper's own acceptance test: equilibrium observables at the largest step
 of Table 1 within 5% of the Monte Carlo benchmark (Sec. 5A)."""
+import functools
 import math
 
 import numpy as np
 import pytest
 
 import paper_1411_3487_gb300 as sfp
+from golden_values import PAPER
 from oracle import oracle as O
 from paper_1411_3487_gb300 import build
 
@@ -21,7 +23,23 @@ def built():
 
 
 def d_nm():
-    return sfp.derive()["d_nm"]
+    """d = a (1 - 2 nu) from the printed values (Sec. 2A): the GPU's sums in nm^2
+    are turned back into scaled units with it, not with the library's d."""
+    return PAPER["a_nm"] * (1.0 - 2.0 * PAPER["nu"])
+
+
+@functools.lru_cache(maxsize=None)
+def monte_carlo_64bp():
+    """The oracle's Monte Carlo benchmark at 64 bp (Sec. 5A): 64 chains x 2e4
+    sweeps after tuning; per-chain means of <|L|^2>, <|u_m|^2>, <|r_m - r_cm|^2>."""
+    M, Cm = 64, 64
+    m = O.Model(M, dtau=10.0)
+    R = np.stack([m.equilibrium_start(9, j) for j in range(Cm)])
+    step, R = m.mc_tuned_steps(R, 9, np.arange(Cm))
+    R, _, _ = m.run_mc(R, 9, np.arange(Cm), 0, 4000, step)
+    R, _, obs = m.run_mc(R, 9, np.arange(Cm), 4000, 20000, step, sample=True)
+    mc_per = obs[:, :3] / obs[:, 3:4]
+    return mc_per.mean(axis=0), mc_per.std(axis=0, ddof=1) / math.sqrt(Cm)
 
 
 @pytest.mark.parametrize("precision,tol", [(sfp.SFP_FP32, 2e-5), (sfp.SFP_FP32_SIMT, 2e-5),
@@ -82,26 +100,21 @@ def test_com_diffusion_is_free_draining():
         assert abs(est / exact - 1) < 5 * math.sqrt(2.0 / 3.0 / n), (lag, est, exact)
 
 
-def test_equilibrium_observables_within_5pct_of_monte_carlo():
+@pytest.mark.parametrize("precision", [sfp.SFP_MIXED_TF32, sfp.SFP_MIXED_BF16], ids=["tf32x3", "bf16x3"])
+def test_equilibrium_observables_within_5pct_of_monte_carlo(precision):
     """The paper's criterion for its step sizes (Sec. 5B, Table 1): at the
     largest step for 64 bp (dtau = 10, i.e. 1.59 ps) the equilibrium values of
     <|L|^2>, <|u_m|^2> and <|r_m - r_cm|^2> from the dynamics lie within 5% of
-    the Monte Carlo benchmark in mode space (Sec. 5A).  GPU: 4096 chains,
-    tensor-core path, 2e4 steps of relaxation, then 2e4 steps sampled every 100.
-    Monte Carlo: the oracle's sampler, 64 chains x 2e4 sweeps after tuning."""
+    the Monte Carlo benchmark in mode space (Sec. 5A).  GPU: 4096 chains on the
+    fused tensor-core step with TF32x3 or with BF16x3 transforms (the precision
+    of the benchmark's headline), 2e4 steps of relaxation, then 2e4 steps
+    sampled every 100.  Monte Carlo: the oracle's sampler, 64 chains x 2e4
+    sweeps after tuning."""
     M, dtau = 64, 10.0
-    m = O.Model(M, dtau=dtau)
-    Cm = 64
-    R = np.stack([m.equilibrium_start(9, j) for j in range(Cm)])
-    step, R = m.mc_tuned_steps(R, 9, np.arange(Cm))
-    R, _, _ = m.run_mc(R, 9, np.arange(Cm), 0, 4000, step)
-    R, _, obs = m.run_mc(R, 9, np.arange(Cm), 4000, 20000, step, sample=True)
-    mc_per = obs[:, :3] / obs[:, 3:4]
-    mc = mc_per.mean(axis=0)
-    mc_se = mc_per.std(axis=0, ddof=1) / math.sqrt(Cm)
+    mc, mc_se = monte_carlo_64bp()
 
     C = 4096
-    b = sfp.Batch([{"n_beads": M, "dtau": dtau}] * C, seed=9, precision=sfp.SFP_FP32)
+    b = sfp.Batch([{"n_beads": M, "dtau": dtau}] * C, seed=9, precision=precision)
     b.init_equilibrium(0)
     b.step(20000)
     b.set_sampling(100)

@@ -1,6 +1,7 @@
 """Error per observable against the FP64 oracle at the 16384 x 512-bp size
-(NEXT-3 precision row): TF32 hi/lo tensor-core transforms (SFP_FP32), plain
-FP32 (SFP_FP32_SIMT) and FP64."""
+(NEXT-3 precision row): TF32 and BF16 hi/lo tensor-core transforms
+(SFP_FP32 = SFP_MIXED_TF32, SFP_MIXED_BF16), plain FP32 (SFP_FP32_SIMT) and FP64.
+The three-pass BF16 split is held to the FP32 bounds."""
 import pytest
 
 import paper_1411_3487_gb300 as sfp
@@ -22,7 +23,7 @@ def built():
 # whose slow amplitudes reach ~1e4 at 512 bp, so FP32 rounding of the state
 # shows there at ~1e-5 (measured 1.1e-5 and 1.3e-5 with the TF32 split).
 @pytest.mark.parametrize("precision,tol,tol_local", [(sfp.SFP_FP32, 1e-5, 1e-4), (sfp.SFP_FP32_SIMT, 1e-5, 1e-4),
-                                                     (sfp.SFP_MIXED_BF16, 1e-3, 1e-2),
+                                                     (sfp.SFP_MIXED_BF16, 1e-5, 1e-4),
                                                      (sfp.SFP_FP64, 1e-9, 1e-9)], ids=["tf32x3", "fp32", "bf16x3", "fp64"])
 def test_error_per_observable_16384x512(precision, tol, tol_local):
     e = errors(sfp, O, precision, steps=400, every=20, sub=8)

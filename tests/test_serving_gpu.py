@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import paper_1411_3487_gb300 as sfp
+from golden_values import shear_tau
 from oracle import oracle as O
 from paper_1411_3487_gb300 import build
 
@@ -32,8 +33,7 @@ def rel(a, b):
 def oracle_run(M, job_id, n_steps, shear_per_s, seed=1):
     m = O.Model(M, dtau=DT[M])
     R0 = m.equilibrium_start(seed, job_id)
-    c_ps = sfp.derive()["c_ps"]
-    return m.run_modes(R0[None], seed, [job_id], 0, n_steps, shear=shear_per_s * c_ps * 1e-12)[0]
+    return m.run_modes(R0[None], seed, [job_id], 0, n_steps, shear=shear_tau(shear_per_s))[0]
 
 
 def job(M, n_steps, job_id, shear=0.0):

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import paper_1411_3487_gb300 as sfp
+from golden_values import shear_tau
 from oracle import oracle as O
 from paper_1411_3487_gb300 import build
 
@@ -67,10 +68,9 @@ def test_concurrent_groups_match_the_oracle():
     b.set_graph(True)
     b.step(90)
     G = b.modes()
-    c_ps = sfp.derive()["c_ps"]
     for i in (0, 7, 13, 22, 39):
         c = chains[i]
         m = O.Model(c["n_beads"], dtau=c["dtau"])
-        ref = m.run_modes(starts[i][None], 7, [c["job_id"]], 0, 90, shear=c["shear_rate_per_s"] * c_ps * 1e-12)[0]
+        ref = m.run_modes(starts[i][None], 7, [c["job_id"]], 0, 90, shear=shear_tau(c["shear_rate_per_s"]))[0]
         err = np.linalg.norm(G[i][:, 1:] - ref[:, 1:]) / np.linalg.norm(ref[:, 1:])
         assert err < 1e-5, (i, err)
