@@ -165,14 +165,26 @@ int sfp_step(sfp_batch *b, int64_t n_steps);
  *                      paper's observables i-iii (Sec. 5B)
  *   SFP_OBS_MODE_POWER FP64 packed [3][M_c]: sums over samples of (R_p^alpha)^2
  *                      in scaled units (R_0 = sqrt(M) r_cm)
- *   SFP_OBS_COM_MSD    FP64 [C][4][2] per chain and lag of 1, 10, 100, 1000
- *                      sampling intervals: sum of |r_cm(t) - r_cm(t - lag)|^2
- *                      (nm^2, FP64 centre of mass, non-overlapping windows) and
- *                      the number of windows; ratio / (6 t_lag) estimates the
- *                      diffusion coefficient kT/((N+1) xi) of Sec. 7B
+ *   SFP_OBS_COM_MSD    FP64 [C][L][2] per chain and lag (L lags of sfp_set_msd_lags,
+ *                      by default 4: 1, 10, 100, 1000 sampling intervals): sum
+ *                      of |r_cm(t) - r_cm(t - lag)|^2 (nm^2, FP64 centre of
+ *                      mass, non-overlapping windows) and the number of
+ *                      windows; ratio / (6 t_lag) estimates the diffusion
+ *                      coefficient kT/((N+1) xi) of Sec. 7B
+ *   SFP_OBS_MID_MSD    FP64 [C][L][2]: the same windows for the middle bead
+ *                      m = floor(N/2) relative to the centre of mass: sum of
+ *                      |(r_m - r_cm)(t) - (r_m - r_cm)(t - lag)|^2 (nm^2) and the
+ *                      number of windows; their ratio is the mean-square
+ *                      displacement Q(t_lag) of observable iii of Sec. 5B
+ *   SFP_OBS_E2E2_MEAN  FP64 [C]: mean |L|^2 over the samples (nm^2), the
+ *                      equilibrium <|L|^2> of observable i (Sec. 5B)
+ *   SFP_OBS_MODE_VAR   FP64 packed [3][M_c]: mean of (R_p^alpha)^2 over the
+ *                      samples (scaled units; equipartition gives about
+ *                      T* / zeta_p for the transverse part, Sec. 4)
  * bytes must be at least the size of the requested array. */
 enum { SFP_OBS_MODES = 0, SFP_OBS_POSITIONS = 1, SFP_OBS_COM = 2, SFP_OBS_STEP = 3,
-       SFP_OBS_SHAPE = 4, SFP_OBS_ACCUM = 5, SFP_OBS_MODE_POWER = 6, SFP_OBS_COM_MSD = 7 };
+       SFP_OBS_SHAPE = 4, SFP_OBS_ACCUM = 5, SFP_OBS_MODE_POWER = 6, SFP_OBS_COM_MSD = 7,
+       SFP_OBS_MID_MSD = 8, SFP_OBS_E2E2_MEAN = 9, SFP_OBS_MODE_VAR = 10 };
 int sfp_observe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
 
 /* Kernel path of the SFP_FP32 and SFP_MIXED_BF16 steps (other precisions
@@ -230,6 +242,13 @@ int sfp_set_integrator(sfp_batch *b, int32_t integrator);
  * sampling and keeps the sums readable.  Accumulators are not part of a
  * checkpoint (sfp_save).  SFP_EINVAL for every_steps < 0. */
 int sfp_set_sampling(sfp_batch *b, int32_t every_steps);
+
+/* Lags of the SFP_OBS_COM_MSD and SFP_OBS_MID_MSD windows, in sampling
+ * intervals: n_lags = 1..8 values, each >= 1 (default 1, 10, 100, 1000).  The
+ * list takes effect at the next sfp_set_sampling(b, every_steps > 0), which
+ * clears the windows; from then on those observables have n_lags rows per
+ * chain.  Host only.  SFP_EINVAL otherwise. */
+int sfp_set_msd_lags(sfp_batch *b, int32_t n_lags, const int32_t *lags);
 
 /* Intermediate arrays of the most recent step, FP64 packed [3][M_c] in scaled
  * units, for checking each stage on its own:

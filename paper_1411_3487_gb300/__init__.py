@@ -13,7 +13,8 @@ import numpy as np
 
 from . import _lib
 from ._lib import (SFP_FP32, SFP_FP32_SIMT, SFP_FP64, SFP_MIXED_BF16, SFP_MIXED_TF32, SFP_OBS_ACCUM, SFP_OBS_COM,
-                   SFP_OBS_COM_MSD, SFP_OBS_MODE_POWER, SFP_OBS_MODES, SFP_OBS_POSITIONS,
+                   SFP_OBS_COM_MSD, SFP_OBS_E2E2_MEAN, SFP_OBS_MID_MSD, SFP_OBS_MODE_POWER, SFP_OBS_MODE_VAR,
+                   SFP_OBS_MODES, SFP_OBS_POSITIONS,
                    SFP_INTEGRATOR_EULER, SFP_INTEGRATOR_MODES, SFP_OBS_SHAPE, SFP_OBS_STEP,
                    SFP_PATH_FUSED, SFP_PATH_STAGED, SFP_PROBE_BONDS, SFP_PROBE_DH,
                    SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_ZMODE, SfpChainDesc, SfpError,
@@ -79,6 +80,7 @@ class Batch:
         self.offsets = np.concatenate([[0], np.cumsum(3 * self.n_beads)])
         self.n_chains = n
         self.precision = precision
+        self._n_lags = self._lags_next = 4
         h = ct.c_void_p()
         _lib.check(L.sfp_create(ct.byref(self.params), arr, n, seed, precision, _stream_handle(stream),
                                 hbm_budget_bytes, ct.byref(h)))
@@ -155,10 +157,19 @@ class Batch:
     def set_sampling(self, every_steps: int) -> None:
         """Sample observables i-iii, mode power and CoM windows every ``every_steps`` steps."""
         _lib.check(_lib.load().sfp_set_sampling(self._h, int(every_steps)))
+        if every_steps > 0:
+            self._n_lags = self._lags_next
+
+    def set_msd_lags(self, lags) -> None:
+        """Lags (in sampling intervals, 1..8 of them) of the CoM and middle-bead MSD
+        windows, used from the next ``set_sampling``."""
+        a = (ct.c_int32 * len(lags))(*[int(x) for x in lags])
+        _lib.check(_lib.load().sfp_set_msd_lags(self._h, len(lags), a))
+        self._lags_next = len(lags)
 
     def observe(self, what: int):
         L = _lib.load()
-        if what in (SFP_OBS_MODES, SFP_OBS_POSITIONS, SFP_OBS_MODE_POWER):
+        if what in (SFP_OBS_MODES, SFP_OBS_POSITIONS, SFP_OBS_MODE_POWER, SFP_OBS_MODE_VAR):
             out = np.zeros(int(self.offsets[-1]))
             _lib.check(L.sfp_observe(self._h, what, out.ctypes.data, out.nbytes))
             return self._unpack(out)
@@ -168,8 +179,10 @@ class Batch:
             out = np.zeros(self.n_chains, dtype=np.int64)
         elif what in (SFP_OBS_SHAPE, SFP_OBS_ACCUM):
             out = np.zeros((self.n_chains, 4))
-        elif what == SFP_OBS_COM_MSD:
-            out = np.zeros((self.n_chains, 4, 2))
+        elif what in (SFP_OBS_COM_MSD, SFP_OBS_MID_MSD):
+            out = np.zeros((self.n_chains, self._n_lags, 2))
+        elif what == SFP_OBS_E2E2_MEAN:
+            out = np.zeros(self.n_chains)
         else:
             raise ValueError(what)
         _lib.check(L.sfp_observe(self._h, what, out.ctypes.data, out.nbytes))

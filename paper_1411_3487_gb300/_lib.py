@@ -18,6 +18,7 @@ SFP_FP32, SFP_FP64, SFP_MIXED_BF16, SFP_FP32_SIMT = 0, 1, 2, 4
 SFP_MIXED_TF32 = SFP_FP32   # FP32 state, TF32x3 transforms
 SFP_OBS_MODES, SFP_OBS_POSITIONS, SFP_OBS_COM, SFP_OBS_STEP, SFP_OBS_SHAPE = 0, 1, 2, 3, 4
 SFP_OBS_ACCUM, SFP_OBS_MODE_POWER, SFP_OBS_COM_MSD = 5, 6, 7
+SFP_OBS_MID_MSD, SFP_OBS_E2E2_MEAN, SFP_OBS_MODE_VAR = 8, 9, 10
 SFP_PATH_FUSED, SFP_PATH_STAGED = 0, 1
 SFP_INTEGRATOR_MODES, SFP_INTEGRATOR_EULER = 0, 1
 SFP_PROBE_BONDS, SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_DH, SFP_PROBE_ZMODE = 0, 1, 2, 3, 4
@@ -27,7 +28,7 @@ EXPORTS = (
     "sfp_params_dsdna", "sfp_derive", "sfp_create", "sfp_init_equilibrium", "sfp_set_modes",
     "sfp_set_positions", "sfp_set_step", "sfp_step", "sfp_observe", "sfp_probe", "sfp_save",
     "sfp_load", "sfp_info", "sfp_destroy", "sfp_last_error", "sfp_philox_words",
-    "sfp_stage_timing", "sfp_stage_times", "sfp_step_noalloc", "sfp_set_sampling",
+    "sfp_stage_timing", "sfp_stage_times", "sfp_step_noalloc", "sfp_set_sampling", "sfp_set_msd_lags",
     "sfp_set_path", "sfp_set_integrator", "sfp_set_graph", "sfp_autotune", "sfp_server_config_default", "sfp_server_create", "sfp_server_submit",
     "sfp_server_poll", "sfp_server_result_modes", "sfp_server_wait_idle", "sfp_server_stats",
     "sfp_server_destroy", "sfp_server_last_error",

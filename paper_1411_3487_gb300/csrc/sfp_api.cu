@@ -195,8 +195,10 @@ struct Group {
     double* obs_tab = nullptr;    // [3][M] rows: phi_N - phi_0, chi_m, phi_m' (p >= 1)
     double* acc_shape = nullptr;  // [C][4]
     double* acc_pow = nullptr;    // [C][3][M]
-    double* msd_snap = nullptr;   // [C][4][3]
-    double* msd_acc = nullptr;    // [C][4][2]
+    double* msd_snap = nullptr;   // [C][kMaxLags][3] centre of mass at the last window edge
+    double* msd_acc = nullptr;    // [C][kMaxLags][2]
+    double* mid_snap = nullptr;   // [C][kMaxLags][3] r_m' - r_cm at the last window edge
+    double* mid_acc = nullptr;    // [C][kMaxLags][2]
 };
 
 struct sfp_batch {
@@ -238,6 +240,8 @@ struct sfp_batch {
     int64_t since_sample = 0;      // steps since the last sample
     int64_t n_samples = 0;         // samples taken since sampling was (re)enabled
     bool sampled = false;          // accumulators exist
+    sfp::SampleLags lags{4, {1, 10, 100, 1000}};        // windows of the running sampling
+    sfp::SampleLags lags_next{4, {1, 10, 100, 1000}};   // taken by the next sfp_set_sampling
 };
 
 namespace {
@@ -482,17 +486,16 @@ int step_group(sfp_batch* b, Group& g)
 // windows for every chain (sample index b->n_samples).
 int sample_all(sfp_batch* b)
 {
-    const int4 lags = make_int4(1, 10, 100, 1000);
     for (auto& g : b->groups) {
         const unsigned grid = nblk(g.C, 4);
         if (b->precision == SFP_FP64)
             sfp::k_sample<double><<<grid, 128, 0, b->stream>>>((const double*)g.R, g.com, g.obs_tab, g.C, g.M,
                                                                g.acc_shape, g.acc_pow, g.msd_snap, g.msd_acc,
-                                                               b->n_samples, lags);
+                                                               g.mid_snap, g.mid_acc, b->n_samples, b->lags);
         else
             sfp::k_sample<float><<<grid, 128, 0, b->stream>>>((const float*)g.R, g.com, g.obs_tab, g.C, g.M,
                                                               g.acc_shape, g.acc_pow, g.msd_snap, g.msd_acc,
-                                                              b->n_samples, lags);
+                                                              g.mid_snap, g.mid_acc, b->n_samples, b->lags);
         b->launches++;
         CUDA_TRY(cudaGetLastError());
     }
@@ -1121,11 +1124,13 @@ int sfp_observe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
         case SFP_OBS_STEP: need = (size_t)b->C * 8; break;
         case SFP_OBS_SHAPE: need = (size_t)b->C * 4 * 8; break;
         case SFP_OBS_ACCUM: need = (size_t)b->C * 4 * 8; break;
-        case SFP_OBS_MODE_POWER: need = packed; break;
-        case SFP_OBS_COM_MSD: need = (size_t)b->C * 8 * 8; break;
+        case SFP_OBS_MODE_POWER: case SFP_OBS_MODE_VAR: need = packed; break;
+        case SFP_OBS_COM_MSD: case SFP_OBS_MID_MSD: need = (size_t)b->C * b->lags.n * 2 * 8; break;
+        case SFP_OBS_E2E2_MEAN: need = (size_t)b->C * 8; break;
         default: return fail(SFP_EINVAL, "unknown observable %d", what);
     }
-    if ((what == SFP_OBS_ACCUM || what == SFP_OBS_MODE_POWER || what == SFP_OBS_COM_MSD) && !b->sampled)
+    if ((what == SFP_OBS_ACCUM || what == SFP_OBS_MODE_POWER || what == SFP_OBS_COM_MSD || what == SFP_OBS_MID_MSD ||
+         what == SFP_OBS_E2E2_MEAN || what == SFP_OBS_MODE_VAR) && !b->sampled)
         return fail(SFP_EINVAL, "observable %d needs sfp_set_sampling first", what);
     if (bytes < need) return fail(SFP_EINVAL, "buffer too small: need %zu bytes", need);
     std::vector<double> tmp;
@@ -1187,22 +1192,47 @@ int sfp_observe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
             CUDA_TRY(cudaStreamSynchronize(b->stream));
             for (int i = 0; i < g.C; ++i)
                 for (int a = 0; a < 3; ++a) ((double*)host_out)[3 * (size_t)g.chains[i] + a] = cm[3 * i + a] * b->dv.d_nm;
-        } else if (what == SFP_OBS_ACCUM || what == SFP_OBS_COM_MSD) {
-            const int w = what == SFP_OBS_ACCUM ? 4 : 8;
-            std::vector<double> a((size_t)g.C * w);
-            CUDA_TRY(cudaMemcpyAsync(a.data(), what == SFP_OBS_ACCUM ? g.acc_shape : g.msd_acc, a.size() * 8,
+        } else if (what == SFP_OBS_ACCUM || what == SFP_OBS_E2E2_MEAN) {
+            std::vector<double> a((size_t)g.C * 4);
+            CUDA_TRY(cudaMemcpyAsync(a.data(), g.acc_shape, a.size() * 8, cudaMemcpyDeviceToHost, b->stream));
+            CUDA_TRY(cudaStreamSynchronize(b->stream));
+            const double d2 = b->dv.d_nm * b->dv.d_nm;
+            double* o = (double*)host_out;
+            for (int i = 0; i < g.C; ++i) {
+                const double* ai = a.data() + 4 * (size_t)i;
+                if (what == SFP_OBS_E2E2_MEAN) {
+                    o[g.chains[i]] = ai[3] > 0.0 ? ai[0] / ai[3] * d2 : 0.0;
+                } else {
+                    // sums in nm^2; the count as it is
+                    for (int k = 0; k < 4; ++k) o[(size_t)4 * g.chains[i] + k] = ai[k] * (k == 3 ? 1.0 : d2);
+                }
+            }
+        } else if (what == SFP_OBS_COM_MSD || what == SFP_OBS_MID_MSD) {
+            const int L = b->lags.n;
+            std::vector<double> a((size_t)g.C * sfp::kMaxLags * 2);
+            CUDA_TRY(cudaMemcpyAsync(a.data(), what == SFP_OBS_COM_MSD ? g.msd_acc : g.mid_acc, a.size() * 8,
                                      cudaMemcpyDeviceToHost, b->stream));
             CUDA_TRY(cudaStreamSynchronize(b->stream));
             const double d2 = b->dv.d_nm * b->dv.d_nm;
             for (int i = 0; i < g.C; ++i)
-                for (int k = 0; k < w; ++k) {
-                    // sums in nm^2; counts as they are
-                    const bool is_count = (what == SFP_OBS_ACCUM) ? k == 3 : (k & 1) == 1;
-                    ((double*)host_out)[(size_t)w * g.chains[i] + k] = a[(size_t)w * i + k] * (is_count ? 1.0 : d2);
+                for (int l = 0; l < L; ++l) {
+                    const double* w = a.data() + ((size_t)i * sfp::kMaxLags + l) * 2;
+                    double* o = (double*)host_out + ((size_t)g.chains[i] * L + l) * 2;
+                    o[0] = w[0] * d2;   // sum in nm^2
+                    o[1] = w[1];        // windows
                 }
-        } else if (what == SFP_OBS_MODE_POWER) {
+        } else if (what == SFP_OBS_MODE_POWER || what == SFP_OBS_MODE_VAR) {
             tmp.resize(n);
             CUDA_TRY(cudaMemcpyAsync(tmp.data(), g.acc_pow, n * 8, cudaMemcpyDeviceToHost, b->stream));
+            if (what == SFP_OBS_MODE_VAR) {
+                std::vector<double> a((size_t)g.C * 4);
+                CUDA_TRY(cudaMemcpyAsync(a.data(), g.acc_shape, a.size() * 8, cudaMemcpyDeviceToHost, b->stream));
+                CUDA_TRY(cudaStreamSynchronize(b->stream));
+                for (int i = 0; i < g.C; ++i) {
+                    const double cnt = a[4 * (size_t)i + 3];
+                    for (int k = 0; k < 3 * g.M; ++k) tmp[(size_t)i * 3 * g.M + k] = cnt > 0.0 ? tmp[(size_t)i * 3 * g.M + k] / cnt : 0.0;
+                }
+            }
             CUDA_TRY(cudaStreamSynchronize(b->stream));
             scatter_group(b, g, tmp, (double*)host_out);
         } else if (what == SFP_OBS_STEP) {
@@ -1538,8 +1568,10 @@ int sfp_set_sampling(sfp_batch* b, int32_t every_steps)
             if ((rc = dalloc_t(b, &g.obs_tab, (size_t)3 * M * 8)) ||
                 (rc = dalloc_t(b, &g.acc_shape, (size_t)g.C * 4 * 8)) ||
                 (rc = dalloc_t(b, &g.acc_pow, (size_t)g.C * 3 * M * 8)) ||
-                (rc = dalloc_t(b, &g.msd_snap, (size_t)g.C * 12 * 8)) ||
-                (rc = dalloc_t(b, &g.msd_acc, (size_t)g.C * 8 * 8)))
+                (rc = dalloc_t(b, &g.msd_snap, (size_t)g.C * sfp::kMaxLags * 3 * 8)) ||
+                (rc = dalloc_t(b, &g.msd_acc, (size_t)g.C * sfp::kMaxLags * 2 * 8)) ||
+                (rc = dalloc_t(b, &g.mid_snap, (size_t)g.C * sfp::kMaxLags * 3 * 8)) ||
+                (rc = dalloc_t(b, &g.mid_acc, (size_t)g.C * sfp::kMaxLags * 2 * 8)))
                 return rc;
             // coefficient rows of L = r_N - r_0, u_m = r_m - r_{m-1} (m = ceil(N/2)) and
             // r_m' - r_cm (m' = floor(N/2)) in terms of R_p (Eq. c1); p = 0 drops out of all three
@@ -1556,13 +1588,30 @@ int sfp_set_sampling(sfp_batch* b, int32_t every_steps)
         }
         CUDA_TRY(cudaMemsetAsync(g.acc_shape, 0, (size_t)g.C * 4 * 8, b->stream));
         CUDA_TRY(cudaMemsetAsync(g.acc_pow, 0, (size_t)g.C * 3 * M * 8, b->stream));
-        CUDA_TRY(cudaMemsetAsync(g.msd_snap, 0, (size_t)g.C * 12 * 8, b->stream));
-        CUDA_TRY(cudaMemsetAsync(g.msd_acc, 0, (size_t)g.C * 8 * 8, b->stream));
+        CUDA_TRY(cudaMemsetAsync(g.msd_snap, 0, (size_t)g.C * sfp::kMaxLags * 3 * 8, b->stream));
+        CUDA_TRY(cudaMemsetAsync(g.msd_acc, 0, (size_t)g.C * sfp::kMaxLags * 2 * 8, b->stream));
+        CUDA_TRY(cudaMemsetAsync(g.mid_snap, 0, (size_t)g.C * sfp::kMaxLags * 3 * 8, b->stream));
+        CUDA_TRY(cudaMemsetAsync(g.mid_acc, 0, (size_t)g.C * sfp::kMaxLags * 2 * 8, b->stream));
     }
+    b->lags = b->lags_next;
     b->sampled = true;
     b->sample_every = every_steps;
     b->n_samples = 0;
     return sample_all(b);
+}
+
+int sfp_set_msd_lags(sfp_batch* b, int32_t n_lags, const int32_t* lags)
+{
+    if (!b || !lags) return fail(SFP_EINVAL, "NULL argument");
+    if (n_lags < 1 || n_lags > sfp::kMaxLags) return fail(SFP_EINVAL, "n_lags must be 1..%d", sfp::kMaxLags);
+    sfp::SampleLags L{};
+    L.n = n_lags;
+    for (int i = 0; i < n_lags; ++i) {
+        if (lags[i] < 1) return fail(SFP_EINVAL, "lag %d is %d; lags are >= 1 sampling intervals", i, lags[i]);
+        L.v[i] = lags[i];
+    }
+    b->lags_next = L;
+    return SFP_OK;
 }
 
 int sfp_philox_words(uint32_t seed, uint32_t job, int64_t step, uint32_t tag, int32_t count,

@@ -229,22 +229,31 @@ static_assert(kChains % 4 == 0 && (4 * kCallsPerBlock) % 32 == 0, "full chunks")
 
 __device__ __forceinline__ int noise_h0(int nw, int qn) { return (nw + kNoiseWarps - qn % kNoiseWarps) % kNoiseWarps; }
 
+// One item: four normals of Philox call `call` of chain slot cl (zeros past the tile's chains).
+__device__ __forceinline__ void noise_item(float (&z)[4], int h, int jb, int sp, int lane, int Ct, uint32_t seed,
+                                           const uint32_t* s_job, const int64_t* s_step)
+{
+    const int f = 32 * h + lane;
+    const int cl = f / kCallsPerBlock, call = f - kCallsPerBlock * cl;
+    Normals<float>::draw4(seed, s_job[cl], s_step[cl] + sp, (uint32_t)(kCallsPerBlock * jb + call), 0u, z);
+    if (cl >= Ct) z[0] = z[1] = z[2] = z[3] = 0.f;
+}
+
 __device__ __forceinline__ void noise_draw(float (&zz)[kChunksPerWarp][4], int nw, int qn, int jb, int sp,
                                            int lane, int cpt, int Ct, uint32_t seed, const uint32_t* s_job,
                                            const int64_t* s_step)
 {
+    static_assert(kChunksPerWarp == 3, "the draw below handles up to three chunks per warp");
     const int nch = cpt * kCallsPerBlock / 32;
     const int h0 = noise_h0(nw, qn);
-#pragma unroll
-    for (int i = 0; i < kChunksPerWarp; ++i) {
-        const int h = h0 + kNoiseWarps * i;
-        if (h < nch) {   // the same for the whole warp
-            const int f = 32 * h + lane;
-            const int cl = f / kCallsPerBlock, call = f - kCallsPerBlock * cl;
-            Normals<float>::draw4(seed, s_job[cl], s_step[cl] + sp, (uint32_t)(kCallsPerBlock * jb + call), 0u,
-                                  zz[i]);
-            if (cl >= Ct) zz[i][0] = zz[i][1] = zz[i][2] = zz[i][3] = 0.f;
-        }
+    // The warp's first two chunks are drawn in one straight-line block, so that
+    // their Philox rounds interleave; the branches are the same for the whole warp.
+    if (h0 + kNoiseWarps < nch) {
+        noise_item(zz[0], h0, jb, sp, lane, Ct, seed, s_job, s_step);
+        noise_item(zz[1], h0 + kNoiseWarps, jb, sp, lane, Ct, seed, s_job, s_step);
+        if (h0 + 2 * kNoiseWarps < nch) noise_item(zz[2], h0 + 2 * kNoiseWarps, jb, sp, lane, Ct, seed, s_job, s_step);
+    } else if (h0 < nch) {
+        noise_item(zz[0], h0, jb, sp, lane, Ct, seed, s_job, s_step);
     }
 }
 
@@ -253,7 +262,7 @@ __device__ __forceinline__ void noise_draw(float (&zz)[kChunksPerWarp][4], int n
 // column) and axis k % 3 of the chain (row 32 quarter + 3 slot + axis).
 template <bool BF>
 __device__ __forceinline__ void noise_put(uint8_t* ah, uint8_t* al, const float (&zz)[kChunksPerWarp][4], int nw,
-                                          int qn, int lane, int cpt, int cpq)
+                                          int qn, int lane, int cpt, const int* s_rowb)
 {
     const int nch = cpt * kCallsPerBlock / 32;
     const int h0 = noise_h0(nw, qn);
@@ -263,8 +272,7 @@ __device__ __forceinline__ void noise_put(uint8_t* ah, uint8_t* al, const float 
         if (h < nch) {
             const int f = 32 * h + lane;
             const int cl = f / kCallsPerBlock, call = f - kCallsPerBlock * cl;
-            const int quarter = cl / cpq;
-            const int rb = 32 * quarter + 3 * (cl - cpq * quarter);
+            const int rb = s_rowb[cl];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int k = 4 * call + e, n = k / 3;
@@ -299,6 +307,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     float* s_dm = (float*)(misc + 1216);        // NB <= 256
     float* s_g = (float*)(misc + 2240);
     uint64_t* bars = (uint64_t*)(misc + 3264);
+    int* s_rowb = (int*)(misc + 3584);          // first A-operand row of each chain slot
     uint64_t* full = bars;              // TMA bytes landed                 (1 + tx)
     uint64_t* ready = bars + 4;         // A operand written by one group   (kReadyCount)
     uint64_t* empty = bars + 8;         // MMAs done with the stage         (commit)
@@ -347,6 +356,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         s_step[i] = live ? a.step[c0 + i] : 0;
         s_stop[i] = (live && a.stop) ? a.stop[c0 + i] : INT64_MAX;
         s_shear[i] = live ? a.shear[c0 + i] : 0.0;
+        s_rowb[i] = i < a.cpt ? 32 * (i / cpq) + 3 * (i % cpq) : 0;
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -574,7 +584,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             if (ok) {
                 uint8_t* ah = stage0 + s * S::kStage + S::kR;
                 uint8_t* al = ah + S::kA;
-                noise_put<BF>(ah, al, cur, nw, qn, lane, a.cpt, cpq);
+                noise_put<BF>(ah, al, cur, nw, qn, lane, a.cpt, s_rowb);
                 fence_proxy_async();
             }
             __syncwarp();
@@ -793,6 +803,7 @@ k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     float* s_dm = (float*)(misc + 1216);        // NB <= 256
     float* s_g = (float*)(misc + 2240);
     uint64_t* bars = (uint64_t*)(misc + 3264);
+    int* s_rowb = (int*)(misc + 3584);          // first A-operand row of each chain slot
     uint64_t* full = bars;              // TMA bytes landed                 (1 + tx)
     uint64_t* ready = bars + 4;         // A operand written by one group   (kReadyCount)
     uint64_t* empty = bars + 8;         // MMAs done with the stage         (commit)
@@ -852,6 +863,7 @@ k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         s_step[i] = live ? a.step[c0 + i] : 0;
         s_stop[i] = (live && a.stop) ? a.stop[c0 + i] : INT64_MAX;
         s_shear[i] = live ? a.shear[c0 + i] : 0.0;
+        s_rowb[i] = i < a.cpt ? 32 * (i / cpq) + 3 * (i % cpq) : 0;
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -1150,7 +1162,7 @@ k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             if (ok) {
                 uint8_t* ah = stage0 + s * S::kStage + S::kR;
                 uint8_t* al = ah + S::kA;
-                noise_put<BF>(ah, al, cur, nw, qn, lane, a.cpt, cpq);
+                noise_put<BF>(ah, al, cur, nw, qn, lane, a.cpt, s_rowb);
                 fence_proxy_async();
             }
             __syncwarp();

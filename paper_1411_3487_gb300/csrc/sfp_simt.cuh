@@ -463,16 +463,25 @@ namespace sfp {
 //   r_m - r_cm (middle bead)= sum_{p>=1} phi_{m',p} R_p,   m' = floor(N/2)
 // tab = [3][M] FP64 coefficient rows for these three sums.  Per chain, adds
 // |L|^2, |u_m|^2, |r_m - r_cm|^2 and 1 to shape[c][0..3] and (R_p^a)^2 to
-// power[c][a][p] (R_0 = sqrt(M) r_cm).  Centre-of-mass displacement over
-// non-overlapping windows of lag[i] samples (sample index k): when k is a
-// multiple of lag[i], adds |r_cm - snap_i|^2 and 1 to msd[c][i][0..1] (from
-// the second window edge on) and sets snap_i = r_cm.
+// power[c][a][p] (R_0 = sqrt(M) r_cm).  Displacements over non-overlapping
+// windows of lag.v[i] samples (sample index k), for the centre of mass (FP64)
+// and for the middle bead relative to it, r_m' - r_cm (observable iii): when
+// k is a multiple of lag.v[i], adds |x - snap_i|^2 and 1 to msd[c][i][0..1]
+// (mid[c][i][0..1]) from the second window edge on and sets snap_i = x.
+// Windows are [c][kMaxLags][...] whatever lag.n is.
 // ---------------------------------------------------------------------------
+constexpr int kMaxLags = 8;
+struct SampleLags {
+    int n;
+    int v[kMaxLags];
+};
+
 template <typename T>
 __global__ void __launch_bounds__(128)
 k_sample(const T* __restrict__ R, const double* __restrict__ com, const double* __restrict__ tab,
          int C, int M, double* __restrict__ shape, double* __restrict__ power,
-         double* __restrict__ snap, double* __restrict__ msd, int64_t k, int4 lag)
+         double* __restrict__ snap, double* __restrict__ msd, double* __restrict__ mid_snap,
+         double* __restrict__ mid, int64_t k, SampleLags lag)
 {
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -503,23 +512,30 @@ k_sample(const T* __restrict__ R, const double* __restrict__ com, const double* 
     sh[1] += s[3] * s[3] + s[4] * s[4] + s[5] * s[5];
     sh[2] += s[6] * s[6] + s[7] * s[7] + s[8] * s[8];
     sh[3] += 1.0;
-    const int lags[4] = {lag.x, lag.y, lag.z, lag.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if (lags[i] <= 0 || k % lags[i] != 0) continue;
-        double* sn = snap + ((size_t)c * 4 + i) * 3;
+    for (int i = 0; i < lag.n && i < kMaxLags; ++i) {
+        if (lag.v[i] <= 0 || k % lag.v[i] != 0) continue;
+        const size_t w = (size_t)c * kMaxLags + i;
+        double* sn = snap + w * 3;
+        double* sm = mid_snap + w * 3;
         if (k > 0) {
-            double d2 = 0.0;
+            double d2 = 0.0, e2 = 0.0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const double d = com[3 * c + a] - sn[a];
+                const double e = s[6 + a] - sm[a];
                 d2 += d * d;
+                e2 += e * e;
             }
-            msd[((size_t)c * 4 + i) * 2] += d2;
-            msd[((size_t)c * 4 + i) * 2 + 1] += 1.0;
+            msd[w * 2] += d2;
+            msd[w * 2 + 1] += 1.0;
+            mid[w * 2] += e2;
+            mid[w * 2 + 1] += 1.0;
         }
 #pragma unroll
-        for (int a = 0; a < 3; ++a) sn[a] = com[3 * c + a];
+        for (int a = 0; a < 3; ++a) {
+            sn[a] = com[3 * c + a];
+            sm[a] = s[6 + a];
+        }
     }
 }
 

@@ -81,6 +81,57 @@ def test_sampled_sums_match_oracle(precision, tol):
     assert np.abs(g_msd[:, :2, 0] - msd[:, :2, 0] * d2).max() < 1e-5 * (msd[:, :2, 0] * d2).max()
 
 
+@pytest.mark.parametrize("precision,tol", [(sfp.SFP_MIXED_BF16, 2e-5), (sfp.SFP_FP64, 1e-9)], ids=["bf16x3", "fp64"])
+def test_middle_bead_msd_windows_match_oracle(precision, tol):
+    """SFP_OBS_MID_MSD: non-overlapping windows of |(r_m - r_cm)(t) - (r_m - r_cm)(t - lag)|^2
+    for the middle bead m = floor(N/2) (observable iii of Sec. 5B) at lags set by
+    sfp_set_msd_lags, with the centre-of-mass windows at the same lags, and the
+    means SFP_OBS_E2E2_MEAN and SFP_OBS_MODE_VAR; against the oracle's trajectory
+    (bead positions from its own inverse transform, Eq. c1)."""
+    M, C, dtau, every, nsamp = 128, 21, 50.0, 3, 61
+    lags = (1, 2, 5, 20, 60)
+    m = O.Model(M, dtau=dtau)
+    R = np.stack([m.equilibrium_start(4, j) for j in range(C)])
+    b = sfp.Batch([{"n_beads": M, "dtau": dtau}] * C, seed=4, precision=precision)
+    b.set_modes(R)
+    b.set_msd_lags(lags)
+    b.set_sampling(every)
+    b.step(every * (nsamp - 1))
+    mm = (M - 1) // 2
+    mid = np.zeros((C, len(lags), 2))
+    com = np.zeros((C, len(lags), 2))
+    snap_m = np.zeros((C, len(lags), 3))
+    snap_c = np.zeros((C, len(lags), 3))
+    L2 = np.zeros(C)
+    power = np.zeros((C, 3, M))
+    for k in range(nsamp):
+        if k:
+            R = m.run_modes(R, 4, np.arange(C), every * (k - 1), every)
+        for c in range(C):
+            r = m.modes_to_beads(R[c])
+            x = r[:, mm] - r.mean(axis=1)
+            cm = r.mean(axis=1)
+            L2[c] += np.sum((r[:, -1] - r[:, 0]) ** 2)
+            power[c] += R[c] ** 2
+            for i, lag in enumerate(lags):
+                if k % lag == 0:
+                    if k:
+                        mid[c, i] += [np.sum((x - snap_m[c, i]) ** 2), 1.0]
+                        com[c, i] += [np.sum((cm - snap_c[c, i]) ** 2), 1.0]
+                    snap_m[c, i] = x
+                    snap_c[c, i] = cm
+    d2 = d_nm() ** 2
+    g_mid = b.observe(sfp.SFP_OBS_MID_MSD)
+    g_com = b.observe(sfp.SFP_OBS_COM_MSD)
+    assert g_mid.shape == (C, len(lags), 2)
+    assert np.array_equal(g_mid[:, :, 1], mid[:, :, 1]) and np.array_equal(g_com[:, :, 1], com[:, :, 1])
+    assert np.abs(g_mid[:, :, 0] / (mid[:, :, 0] * d2) - 1).max() < 10 * tol
+    assert np.abs(g_com[:, :, 0] - com[:, :, 0] * d2).max() < 1e-5 * (com[:, :, 0] * d2).max()
+    assert np.abs(b.observe(sfp.SFP_OBS_E2E2_MEAN) / (L2 / nsamp * d2) - 1).max() < tol
+    var = b.observe(sfp.SFP_OBS_MODE_VAR)
+    assert np.abs(var[:, :, 1:] - power[:, :, 1:] / nsamp).max() < 10 * tol * (power[:, :, 1:] / nsamp).max()
+
+
 def test_com_diffusion_is_free_draining():
     """Centre-of-mass MSD at lags of 1, 10 and 100 steps equals 6 D t with
     D = kT/((N+1) xi) (Sec. 7B): in scaled units 6 T* t/(N+1), exactly, for any
