@@ -54,12 +54,15 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "tc", "simt"])
     ap.add_argument("--path", default="fused", choices=["fused", "staged"])
     ap.add_argument("--workload", default="batch", choices=["batch", "serving", "precision", "uneven"])
-    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="arrival window of the serving workload (config 5 runs 600 s; 60 s keeps the bench short)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-budget-mb", type=float, default=40e3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-512", action="store_true", help="skip the 16384 x 512-bp legs")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the serving, uneven-batch and single-chain FP64 sub-keys of the default line")
     return ap.parse_args()
 
 
@@ -77,6 +80,21 @@ def peaks():
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                 "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_model() -> str:
+    """Host CPU model as lscpu reports it (vendor and model name), else the platform string."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        f = dict(line.split(":", 1) for line in out.splitlines() if ":" in line)
+        parts = [f.get(k, "").strip() for k in ("Vendor ID", "Model name")]
+        name = " ".join(p for p in parts if p)
+        if name:
+            return name
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 # ------------------------------------------------------------------ oracle (CPU)
@@ -122,6 +140,7 @@ def run_reference(args, rank):
                    "dtau": DT_PS / C_PS, "precision": "FP64 oracle (CPU)",
                    "sample": f"{sample} of {C_CHAINS} chains per step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+                         "cpu_model": cpu_model(),
                          "sample": f"{sample} chains x 256 beads x {args.steps} steps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -189,8 +208,7 @@ def run_native(args, rank, world, local):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
-    PREC_NAME.update({sfp.SFP_MIXED_BF16: "SFP_MIXED_BF16", sfp.SFP_FP32: "SFP_FP32",
-                      sfp.SFP_FP32_SIMT: "SFP_FP32_SIMT"})
+    _names(sfp)
     DTYPE.update({sfp.SFP_MIXED_BF16: "f32 (bf16x3 transforms)", sfp.SFP_FP32: "f32 (tf32x3 transforms)",
                   sfp.SFP_FP32_SIMT: "f32"})
     precision = {"bf16": sfp.SFP_MIXED_BF16, "tf32": sfp.SFP_FP32, "tc": sfp.SFP_FP32,
@@ -253,6 +271,9 @@ def run_native(args, rank, world, local):
     ms_step = tot_ms / args.steps
 
     pk, how = peaks()
+    if rank == 0:
+        pk = dict(pk)
+        pk["tf32_tflops"] = tf32_peak(torch)
     roof = roofline(kern, pk, how, precision, path, sfp)
 
     # sustained: 4 back-to-back calls of 100 steps, no flush at all (a long run)
@@ -306,6 +327,7 @@ def run_native(args, rank, world, local):
                "beads": 512}
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
         for name, prec, pth in (("fused_bf16x3", sfp.SFP_MIXED_BF16, sfp.SFP_PATH_FUSED),
+                                ("fused_bf16x2", sfp.SFP_MIXED_BF16_2, sfp.SFP_PATH_FUSED),
                                 ("fused_tf32x3", sfp.SFP_FP32, sfp.SFP_PATH_FUSED),
                                 ("staged_bf16x3", sfp.SFP_MIXED_BF16, sfp.SFP_PATH_STAGED),
                                 ("plain_fp32", sfp.SFP_FP32_SIMT, sfp.SFP_PATH_STAGED)):
@@ -329,19 +351,30 @@ def run_native(args, rank, world, local):
             n = 20 * calls
             big[name] = {"value": 16384 * 512 * n / (t_ms * 1e-3), "unit": UNIT, "us_per_step": 1e3 * t_ms / n}
             if pth == sfp.SFP_PATH_FUSED:
-                big[name]["kernel"] = "k_fused_pair<%s>" % ("bf16" if prec == sfp.SFP_MIXED_BF16 else "tf32")
-                big[name]["roofline_tensor_frac"] = (3 * 18 * 512 * 16384 * 512 / (1e-3 * t_ms / n)) / 1e12 / (
-                    pk["bf16_tflops"] * (1.0 if prec == sfp.SFP_MIXED_BF16 else 1.1 / 2.25))
+                bf = prec in (sfp.SFP_MIXED_BF16, sfp.SFP_MIXED_BF16_2)
+                passes = 2 if prec == sfp.SFP_MIXED_BF16_2 else 3
+                big[name]["kernel"] = "k_fused_pair<%s>" % ({sfp.SFP_MIXED_BF16: "bf16", sfp.SFP_MIXED_BF16_2: "bf16, two passes"}.get(prec, "tf32"))
+                big[name]["roofline_tensor_frac"] = (passes * 18 * 512 * 16384 * 512 / (1e-3 * t_ms / n)) / 1e12 / (
+                    pk["bf16_tflops"] if bf else pk.get("tf32_tflops") or pk["bf16_tflops"] * 1.1 / 2.25)
             bb.modes()      # raises if a kernel reported an error
             bb.close()
         del flush
+
+    # the other workloads of the benchmark: served jobs (p50/p99 latency), the
+    # uneven batch, and the single 64-bp chain in FP64 (one GPU, rank 0 only)
+    serving = uneven = config1 = None
+    if rank == 0 and world == 1 and not args.no_extra and precision != sfp.SFP_FP32_SIMT:
+        b.close()
+        config1 = config1_leg(sfp, torch)
+        uneven = uneven_leg(sfp, torch, precision, 5000)
+        serving = serving_leg(sfp, precision, args.serve_seconds, args.serve_rate, args.serve_budget_mb)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n_c, n_s = 512, 768
         rate, secs, cores = cpu_oracle_rate(n_c, n_s)
         rate1, secs1, _ = cpu_oracle_rate(16, 96, nthreads=1)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
                "sample": f"{n_c} chains x 256 beads x {n_s} steps ({secs:.1f} s)",
                "one_thread": {"value": rate1, "unit": UNIT, "cores": 1,
                               "sample": f"16 chains x 256 beads x 96 steps ({secs1:.1f} s)"}}
@@ -363,6 +396,9 @@ def run_native(args, rank, world, local):
             "roofline": roof, "kernels_us": kern, "cpu_baseline": cpu, "e2e": e2e,
             "sustained": sustained, "plain_path": plain, "staged_path": staged,
             "other_split_fused": other, "single_step_calls": single, "mixed_precision_512bp": big,
+            "serving": serving, "uneven": uneven, "config1_fp64": config1,
+            "tf32_peak": {"value": pk.get("tf32_tflops"), "unit": "TFLOP/s",
+                          "how": "torch.matmul FP32 with TF32 tensor cores, 8192^3, best of 10 (measured live)"},
             "clocks": clocks,
             "gpu_launches": launches,
         }
@@ -414,8 +450,12 @@ def roofline(kern, pk, how, precision, path, sfp):
     if not kern:
         return None
     M, beads = M_BEADS, C_CHAINS * M_BEADS
-    tf32_peak = pk.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
-    src = f"{how} bf16 x 1.1/2.25 (nominal tf32/bf16 dense ratio)"
+    if pk.get("tf32_tflops"):
+        tf32_peak = pk["tf32_tflops"]
+        src = "measured live: torch.matmul TF32 8192^3, best of 10"
+    else:
+        tf32_peak = pk.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
+        src = f"{how} bf16 x 1.1/2.25 (nominal tf32/bf16 dense ratio)"
     if precision == sfp.SFP_MIXED_BF16 and path == sfp.SFP_PATH_FUSED:
         us = kern.get("inverse_us")          # the fused kernel is recorded as the first stage
         flops = 3 * 18.0 * M * beads
@@ -488,29 +528,119 @@ def bench_precision(sfp, args):
     return prec, name
 
 
-def run_serving(args, rank):
-    """Continuous-batching serving: Poisson arrivals of jobs with lengths
-    uniform over 64/128/256/512 bp at their Table 2 steps, 10^U(3,5) steps,
-    shear 0 with probability 1/2 else U[1e6, 1e8] 1/s; p50/p99 latency from
-    submission to the result being on the host."""
-    if rank != 0:
-        return
-    import torch
-    sys.path.insert(0, ROOT)
-    import paper_1411_3487_gb300 as sfp
-    from paper_1411_3487_gb300 import build
-    build.build()
-    torch.cuda.set_device(0)
+def tf32_peak(torch) -> float:
+    """Dense TF32 tensor-core throughput of this GPU (TFLOP/s): torch.matmul on
+    FP32 8192^3 with TF32 allowed, best of 10 (CUDA events), the way the BF16 peak
+    is measured."""
+    n = 8192
+    a = torch.randn(n, n, device="cuda")
+    b = torch.randn(n, n, device="cuda")
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        for _ in range(3):
+            torch.matmul(a, b)
+        best = 1e30
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    del a, b
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+
+
+def config1_leg(sfp, torch):
+    """One 64-bp chain, FP64 on the GPU, dt = 1.59 ps (dtau 10), 2e4 steps from an
+    equilibrium start (CUDA-graph replay of the staged FP64 kernels); beside it the
+    default bead-position Euler scheme of the same chain at dtau = 0.1 (Sec. 3A)."""
+    out = {"workload": "1 chain x 64 bp, FP64, dt 1.59 ps (dtau 10), 2e4 steps, equilibrium start"}
+    for name, dtau, integ, n in (("mode_space", 10.0, sfp.SFP_INTEGRATOR_MODES, 20000),
+                                 ("euler_dtau_0.1", 0.1, sfp.SFP_INTEGRATOR_EULER, 20000)):
+        b = sfp.Batch([{"n_beads": 64, "dtau": dtau}], seed=1, precision=sfp.SFP_FP64)
+        b.init_equilibrium(0)
+        b.set_integrator(integ)
+        b.set_graph(True)
+        b.step(128)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.step(n)
+        b.modes()                          # synchronises; raises on a kernel error
+        dt = time.perf_counter() - t0
+        ps = dtau * C_PS
+        out[name] = {"value": 64 * n / dt, "unit": UNIT, "steps": n, "dtau": dtau, "dt_ps": ps,
+                     "sim_ns_per_s": n * ps * 1e-3 / dt, "wall_s": dt}
+        b.close()
+    out["value"], out["unit"] = out["mode_space"]["value"], UNIT
+    out["sim_ns_per_s_per_chain"] = out["mode_space"]["sim_ns_per_s"]
+    return out
+
+
+def uneven_chains(n=8192, seed=1):
+    dt = {64: 10.0, 128: 50.0, 256: 100.0, 512: 100.0}
+    rng = np.random.default_rng(seed)
+    lengths = rng.choice([64, 128, 256, 512], size=n)
+    return [{"n_beads": int(M), "dtau": dt[int(M)], "job_id": i} for i, M in enumerate(lengths)]
+
+
+def uneven_leg(sfp, torch, prec, steps=5000):
+    """8192 chains, lengths uniform over 64/128/256/512 bp at their Table 1 steps,
+    FP32 state, equilibrium starts: `steps` steps as calls of 1000 (state in L2
+    between the steps of a call), on the tensor-core path as created, after the
+    chains-per-tile autotuner, and autotuned with CUDA-graph replay; and the plain
+    FP32 CUDA-core path on the same chains."""
+    chains = uneven_chains()
+    beads = sum(c["n_beads"] for c in chains)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, p, tune, graph in (("as_created", prec, False, False), ("autotuned", prec, True, False),
+                                 ("autotuned_graph", prec, True, True),
+                                 ("plain_fp32", sfp.SFP_FP32_SIMT, False, True)):
+        b = sfp.Batch(chains, seed=1, stream=stream, precision=p)
+        b.init_equilibrium(0)
+        tiles = b.autotune(20) if tune else None
+        b.set_graph(graph)
+        b.step(100)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        done = 0
+        while done < steps:
+            k = min(1000, steps - done)
+            b.step(k)
+            done += k
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[name] = {"value": beads * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                     "chains_per_tile": tiles, "graph": graph}
+        b.modes()
+        b.close()
+    best = res["autotuned_graph"]
+    return {"workload": "8192 chains, lengths uniform over 64/128/256/512 bp, dtau 10/50/100/100, FP32 state, "
+                        f"{steps} steps in calls of 1000", "precision": PREC_NAME.get(prec, str(prec)),
+            "beads": beads, "steps": steps, "value": best["value"], "unit": UNIT,
+            "vs_plain_fp32": best["value"] / res["plain_fp32"]["value"], "results": res}
+
+
+def serving_leg(sfp, prec, seconds, rate, budget_mb, seed=1):
+    """Continuous-batching serving: Poisson arrivals (`rate` jobs/s for `seconds`)
+    of jobs with lengths uniform over 64/128/256/512 bp at their Table 2 steps,
+    10^U(3,5) steps, shear 0 with probability 1/2 else U[1e6, 1e8] 1/s; latency
+    from submission to the result being on the host; all jobs drained."""
     dt_ps = {64: 1.59, 128: 7.96, 256: 15.9, 512: 15.9}
-    rng = np.random.default_rng(1)
-    budget = int(args.serve_budget_mb * (1 << 20))
-    prec, prec_name = bench_precision(sfp, args)
+    rng = np.random.default_rng(seed)
+    budget = int(budget_mb * (1 << 20))
     srv = sfp.Server(slots_per_pool=1024, quantum_steps=64, keep_results=False, hbm_budget_bytes=budget,
                      precision=prec)
     clk = ClockSampler(0)
     t0 = time.perf_counter()
     t_next, k, offered = 0.0, 0, 0.0
-    while t_next < args.serve_seconds:
+    while t_next < seconds:
         wait = t0 + t_next - time.perf_counter()
         if wait > 0:
             time.sleep(wait)
@@ -520,7 +650,7 @@ def run_serving(args, rank):
         srv.submit({"n_beads": M, "dt_ps": dt_ps[M], "n_steps": n, "shear_rate_per_s": shear, "job_id": k})
         offered += M * n
         k += 1
-        t_next += rng.exponential(1.0 / args.serve_rate)
+        t_next += rng.exponential(1.0 / rate)
     arrivals_s = time.perf_counter() - t0
     srv.wait_idle(3600)
     wall = time.perf_counter() - t0
@@ -530,19 +660,45 @@ def run_serving(args, rank):
     srv.close()
     lat = np.array([r["latency_s"] for r in res])
     bad = sum(1 for r in res if r["status"] != 0)
-    line = {
+    by_len = {}
+    for r in res:
+        by_len.setdefault(int(r["n_beads"]), []).append(r["latency_s"])
+    return {
         "metric": "p50/p99 request latency", "unit": "s", "higher_is_better": False,
         "value": float(np.percentile(lat, 50)), "p50_s": float(np.percentile(lat, 50)),
-        "p99_s": float(np.percentile(lat, 99)), "max_s": float(lat.max()), "jobs": k, "failed": bad,
-        "n_gpus": 1, "data": "synthetic",
-        "config": {"workload": "serving: Poisson arrivals, 64/128/256/512 bp at Table 2 steps, "
-                               "10^U(3,5) steps, half sheared U[1e6,1e8]/s",
-                   "rate_jobs_per_s": args.serve_rate, "arrival_window_s": args.serve_seconds,
-                   "hbm_budget_bytes": budget, "slots_per_pool": 1024, "quantum_steps": 64,
-                   "precision": prec_name},
+        "p99_s": float(np.percentile(lat, 99)), "max_s": float(lat.max()), "jobs": k, "finished": len(res),
+        "failed": bad,
+        "p50_s_by_beads": {str(m): float(np.percentile(v, 50)) for m, v in sorted(by_len.items())},
+        "workload": "Poisson arrivals, 64/128/256/512 bp at Table 2 steps, 10^U(3,5) steps, half sheared "
+                    "U[1e6,1e8]/s, continuous batching",
+        "rate_jobs_per_s": rate, "arrival_window_s": seconds, "arrivals_wall_s": arrivals_s,
+        "hbm_budget_bytes": budget, "slots_per_pool": 1024, "quantum_steps": 64,
+        "precision": PREC_NAME.get(prec, str(prec)),
         "served_bead_steps_per_s": st["bead_steps"] / wall, "offered_bead_steps_per_s": offered / arrivals_s,
-        "wall_s": wall, "peak_device_bytes_at_end": st["device_bytes"], "clocks": clocks,
+        "wall_s": wall, "device_bytes_at_end": st["device_bytes"], "clocks": clocks,
     }
+
+
+def _names(sfp):
+    PREC_NAME.update({sfp.SFP_MIXED_BF16: "SFP_MIXED_BF16", sfp.SFP_FP32: "SFP_FP32",
+                      sfp.SFP_FP32_SIMT: "SFP_FP32_SIMT", sfp.SFP_FP64: "SFP_FP64",
+                      sfp.SFP_MIXED_BF16_2: "SFP_MIXED_BF16_2"})
+
+
+def run_serving(args, rank):
+    """--workload serving: the serving sub-key on its own."""
+    if rank != 0:
+        return
+    import torch
+    sys.path.insert(0, ROOT)
+    import paper_1411_3487_gb300 as sfp
+    from paper_1411_3487_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    _names(sfp)
+    prec, _ = bench_precision(sfp, args)
+    line = serving_leg(sfp, prec, args.serve_seconds, args.serve_rate, args.serve_budget_mb)
+    line.update({"n_gpus": 1, "data": "synthetic"})
     print(json.dumps(line), flush=True)
 
 
@@ -562,6 +718,7 @@ def run_precision(args, rank):
     torch.cuda.set_device(0)
     out = {}
     for name, prec in (("tf32x3_tcgen05", sfp.SFP_FP32), ("bf16x3_tcgen05", sfp.SFP_MIXED_BF16),
+                       ("bf16x2_tcgen05", sfp.SFP_MIXED_BF16_2),
                        ("fp32_cuda_cores", sfp.SFP_FP32_SIMT), ("fp64", sfp.SFP_FP64)):
         e = errors(sfp, O, prec, steps=2000, every=20, sub=32)
         b = sfp.Batch([{"n_beads": 512, "dtau": 100.0}] * 16384, seed=1, precision=prec)
@@ -578,10 +735,7 @@ def run_precision(args, rank):
 
 
 def run_uneven(args, rank):
-    """8192 chains with lengths uniform over 64/128/256/512 bp at their Table 1
-    steps (FP32 state, equilibrium starts): bead-steps/s of runs of 1000 steps per
-    call, one launch per fused group per call, groups on their own streams; as
-    created, after the chains-per-tile autotuner, and with graph replay."""
+    """--workload uneven: the uneven-batch sub-key on its own (--steps steps)."""
     if rank != 0:
         return
     import torch
@@ -590,35 +744,11 @@ def run_uneven(args, rank):
     from paper_1411_3487_gb300 import build
     build.build()
     torch.cuda.set_device(0)
-    dt = {64: 10.0, 128: 50.0, 256: 100.0, 512: 100.0}
-    prec, prec_name = bench_precision(sfp, args)
-    rng = np.random.default_rng(1)
-    lengths = rng.choice([64, 128, 256, 512], size=8192)
-    chains = [{"n_beads": int(M), "dtau": dt[int(M)], "job_id": i} for i, M in enumerate(lengths)]
-    beads = int(lengths.sum())
-    stream = torch.cuda.current_stream()
-    res = {}
-    for name in ("as_created", "autotuned", "autotuned_graph"):
-        b = sfp.Batch(chains, seed=1, stream=stream, precision=prec)
-        b.init_equilibrium(0)
-        tiles = b.autotune(20) if name != "as_created" else None
-        if name == "autotuned_graph":
-            b.set_graph(True)
-        b.step(200)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps // 100 or 1):
-            b.step(1000)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        n = 1000 * (args.steps // 100 or 1)
-        ms = e0.elapsed_time(e1)
-        res[name] = {"value": beads * n / (ms * 1e-3), "ms_per_step": ms / n, "chains_per_tile": tiles}
-        b.close()
-    print(json.dumps({"metric": METRIC, "unit": UNIT, "workload": "8192 chains, lengths uniform over "
-                      "64/128/256/512 bp, dtau 10/50/100/100, FP32 state, 1000 steps per call (state stays in L2)",
-                      "precision": prec_name, "beads": beads, "results": res}), flush=True)
+    _names(sfp)
+    prec, _ = bench_precision(sfp, args)
+    line = uneven_leg(sfp, torch, prec, max(1000, args.steps))
+    line.update({"metric": METRIC, "n_gpus": 1, "data": "synthetic"})
+    print(json.dumps(line), flush=True)
 
 
 def main():

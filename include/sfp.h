@@ -99,8 +99,15 @@ typedef struct sfp_chain_desc {
  *                 and the staged kernels form DeltaH = chi^T v in bond form
  *                 (Eq. e11); trajectories stay within 1e-5 of the FP64 oracle
  *                 after 1000 steps.
+ * SFP_MIXED_BF16_2  as SFP_MIXED_BF16 with two passes, A_lo B_hi + A_hi B_hi:
+ *                 the state operand (R, v, z) keeps its hi/lo split, the
+ *                 tables (chi, h chi, w phi) are rounded to BF16 (about 8
+ *                 bits), so a third fewer MMAs; the error against the FP64
+ *                 oracle is about 1e-3 per step's transform, well above the
+ *                 FP32 tolerance (stated per observable by the precision test).
  * SFP_FP32_SIMT   FP32 throughout on the CUDA cores: the plain path. */
-enum { SFP_FP32 = 0, SFP_MIXED_TF32 = 0, SFP_FP64 = 1, SFP_MIXED_BF16 = 2, SFP_FP32_SIMT = 4 };
+enum { SFP_FP32 = 0, SFP_MIXED_TF32 = 0, SFP_FP64 = 1, SFP_MIXED_BF16 = 2, SFP_MIXED_BF16_2 = 3,
+       SFP_FP32_SIMT = 4 };
 
 typedef struct sfp_batch sfp_batch;   /* opaque */
 

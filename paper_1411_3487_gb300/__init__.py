@@ -12,7 +12,8 @@ import ctypes as ct
 import numpy as np
 
 from . import _lib
-from ._lib import (SFP_FP32, SFP_FP32_SIMT, SFP_FP64, SFP_MIXED_BF16, SFP_MIXED_TF32, SFP_OBS_ACCUM, SFP_OBS_COM,
+from ._lib import (SFP_FP32, SFP_FP32_SIMT, SFP_FP64, SFP_MIXED_BF16, SFP_MIXED_BF16_2, SFP_MIXED_TF32,
+                   SFP_OBS_ACCUM, SFP_OBS_COM,
                    SFP_OBS_COM_MSD, SFP_OBS_E2E2_MEAN, SFP_OBS_MID_MSD, SFP_OBS_MODE_POWER, SFP_OBS_MODE_VAR,
                    SFP_OBS_MODES, SFP_OBS_POSITIONS,
                    SFP_INTEGRATOR_EULER, SFP_INTEGRATOR_MODES, SFP_OBS_SHAPE, SFP_OBS_STEP,
@@ -21,7 +22,7 @@ from ._lib import (SFP_FP32, SFP_FP32_SIMT, SFP_FP64, SFP_MIXED_BF16, SFP_MIXED_
                    SfpParams)
 
 __all__ = ["Batch", "Server", "params_dsdna", "derive", "philox_words", "SfpError", "SFP_FP32",
-           "SFP_MIXED_TF32", "SFP_MIXED_BF16", "SFP_FP64", "SFP_FP32_SIMT"]
+           "SFP_MIXED_TF32", "SFP_MIXED_BF16", "SFP_MIXED_BF16_2", "SFP_FP64", "SFP_FP32_SIMT"]
 
 
 def params_dsdna() -> SfpParams:

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libsfp.so")
 SFP_OK, SFP_EINVAL, SFP_ENOMEM, SFP_ECUDA, SFP_ETIMEDOUT, SFP_ENONFINITE, SFP_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 SFP_FP32, SFP_FP64, SFP_MIXED_BF16, SFP_FP32_SIMT = 0, 1, 2, 4
 SFP_MIXED_TF32 = SFP_FP32   # FP32 state, TF32x3 transforms
+SFP_MIXED_BF16_2 = 3        # FP32 state, two-pass BF16 transforms (tables rounded to BF16)
 SFP_OBS_MODES, SFP_OBS_POSITIONS, SFP_OBS_COM, SFP_OBS_STEP, SFP_OBS_SHAPE = 0, 1, 2, 3, 4
 SFP_OBS_ACCUM, SFP_OBS_MODE_POWER, SFP_OBS_COM_MSD = 5, 6, 7
 SFP_OBS_MID_MSD, SFP_OBS_E2E2_MEAN, SFP_OBS_MODE_VAR = 8, 9, 10

@@ -326,11 +326,12 @@ template <typename T>
 cudaError_t launch_force_noise(cudaStream_t st, const T* u, T* v, T* z, int C, int M, T c12nu, uint32_t seed,
                                const uint32_t* job, const int64_t* step)
 {
-    const unsigned grid = nblk((int64_t)C * ((M + 3) / 4), 128);
+    constexpr int QPT = 1;   // quads per thread (two were measured slower: 14.5 against 12.6 us at 4096 x 256)
+    const unsigned grid = nblk((int64_t)C * (((M + 3) / 4 + QPT - 1) / QPT), 128);
     if (sizeof(T) == 4 && M % 4 == 0)
-        sfp::k_force_noise<T, true><<<grid, 128, 0, st>>>(u, v, z, C, M, c12nu, seed, job, step);
+        sfp::k_force_noise<T, true, QPT><<<grid, 128, 0, st>>>(u, v, z, C, M, c12nu, seed, job, step);
     else
-        sfp::k_force_noise<T, false><<<grid, 128, 0, st>>>(u, v, z, C, M, c12nu, seed, job, step);
+        sfp::k_force_noise<T, false, QPT><<<grid, 128, 0, st>>>(u, v, z, C, M, c12nu, seed, job, step);
     return cudaGetLastError();
 }
 
@@ -862,7 +863,8 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
     *out = nullptr;
     if (!chains || n_chains <= 0) return fail(SFP_EINVAL, "need n_chains > 0 and a chain array");
     if (seed >> 32) return fail(SFP_EINVAL, "seed must be < 2^32");
-    if (precision != SFP_FP32 && precision != SFP_FP64 && precision != SFP_FP32_SIMT && precision != SFP_MIXED_BF16)
+    if (precision != SFP_FP32 && precision != SFP_FP64 && precision != SFP_FP32_SIMT && precision != SFP_MIXED_BF16 &&
+        precision != SFP_MIXED_BF16_2)
         return fail(SFP_EINVAL, "unknown precision %d", precision);
     Derived dv;
     int rc = derive(params, &dv);
@@ -971,18 +973,20 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
         if ((rc = load_modes_dev(b, g, g.stage))) { destroy_impl(b); return rc; }
         e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) { destroy_impl(b); return fail(SFP_ECUDA, "create: %s", cudaGetErrorString(e)); }
-        if ((precision == SFP_FP32 || precision == SFP_MIXED_BF16) && sfp::tc_supported(M)) {
+        const bool bf16 = precision == SFP_MIXED_BF16 || precision == SFP_MIXED_BF16_2;
+        const bool two = precision == SFP_MIXED_BF16_2;
+        if ((precision == SFP_FP32 || bf16) && sfp::tc_supported(M)) {
             rc = sfp::tc_create(&g.tc, M, 3 * g.C, g.tab.chi.data(), g.tab.chiT.data(), g.tab.phiT.data(),
                                 (const float*)g.R,
                                 (float*)g.r, (const float*)g.fz, (float*)g.yz, b->bad, b->stream,
-                                precision == SFP_MIXED_BF16);
+                                bf16, two);
             if (rc) { destroy_impl(b); return rc; }
         }
-        if ((precision == SFP_FP32 || precision == SFP_MIXED_BF16) && sfp::fused_supported(M)) {
+        if ((precision == SFP_FP32 || bf16) && sfp::fused_supported(M)) {
             std::vector<double> w = g.tab.w;
             w[0] = g.tab.w0;
             rc = sfp::fused_create(&g.fused, M, g.C, g.tab.chi.data(), g.tab.phi.data(), g.tab.h.data(), w.data(),
-                                   (float*)g.R, b->stream, precision == SFP_MIXED_BF16);
+                                   (float*)g.R, b->stream, bf16, two);
             if (rc) { destroy_impl(b); return rc; }
         }
         b->held += sfp::tc_bytes(g.tc) + sfp::fused_bytes(g.fused);

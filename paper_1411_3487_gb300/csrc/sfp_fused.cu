@@ -282,8 +282,10 @@ __device__ __forceinline__ void noise_put(uint8_t* ah, uint8_t* al, const float 
     }
 }
 
-// The step of the 64-, 128- and 256-bead chains: a tile per CTA.
-template <int NB, bool BF>
+// The step of the 64-, 128- and 256-bead chains: a tile per CTA.  TWO (BF16
+// only): two passes, A_lo B_hi + A_hi B_hi, the tables taken as their BF16
+// hi part alone (SFP_MIXED_BF16_2).
+template <int NB, bool BF, bool TWO = false>
 __global__ void __launch_bounds__(kThreads, 1)
 k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmChiH,
              const __grid_constant__ CUtensorMap tmChiL, const __grid_constant__ CUtensorMap tmFH,
@@ -526,8 +528,12 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 #pragma unroll
                         for (int kk = 0; kk < kKB / 16; ++kk) {
                             const uint32_t off = kk * 32;   // 16 BF16 = 32 bytes along K
-                            mma_bf16(d, sdesc64(a_hi + off), sdesc64(b_lo + off), idesc, (first && kk == 0) ? 0u : 1u);
-                            mma_bf16(d, sdesc64(a_lo + off), sdesc64(b_hi + off), idesc, 1u);
+                            if constexpr (TWO) {
+                                mma_bf16(d, sdesc64(a_lo + off), sdesc64(b_hi + off), idesc, (first && kk == 0) ? 0u : 1u);
+                            } else {
+                                mma_bf16(d, sdesc64(a_hi + off), sdesc64(b_lo + off), idesc, (first && kk == 0) ? 0u : 1u);
+                                mma_bf16(d, sdesc64(a_lo + off), sdesc64(b_hi + off), idesc, 1u);
+                            }
                             mma_bf16(d, sdesc64(a_hi + off), sdesc64(b_hi + off), idesc, 1u);
                         }
                     } else {
@@ -775,7 +781,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 
 // The 512-bead step: a tile on a cluster of two CTAs, CTA h (its rank) holding
 // bonds and modes 256 h .. 256 h + 255 (see the file's header).
-template <bool BF>
+template <bool BF, bool TWO = false>
 __global__ void __launch_bounds__(kThreads, 1)
 k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmChiH,
              const __grid_constant__ CUtensorMap tmChiL, const __grid_constant__ CUtensorMap tmFH,
@@ -1047,8 +1053,12 @@ k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 #pragma unroll
                     for (int kk = 0; kk < kKB / 16; ++kk) {
                         const uint32_t off = kk * 32;   // 16 BF16 = 32 bytes along K
-                        mma_bf16(d, sdesc64(a_hi + off), sdesc64(b_lo + off), idesc, (first && kk == 0) ? 0u : 1u);
-                        mma_bf16(d, sdesc64(a_lo + off), sdesc64(b_hi + off), idesc, 1u);
+                        if constexpr (TWO) {
+                            mma_bf16(d, sdesc64(a_lo + off), sdesc64(b_hi + off), idesc, (first && kk == 0) ? 0u : 1u);
+                        } else {
+                            mma_bf16(d, sdesc64(a_hi + off), sdesc64(b_lo + off), idesc, (first && kk == 0) ? 0u : 1u);
+                            mma_bf16(d, sdesc64(a_lo + off), sdesc64(b_hi + off), idesc, 1u);
+                        }
                         mma_bf16(d, sdesc64(a_hi + off), sdesc64(b_hi + off), idesc, 1u);
                     }
                 } else {
@@ -1378,7 +1388,7 @@ k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
 
 struct FusedPlan {
     int M = 0, C = 0, cpt = kChains;
-    bool bf16 = false;
+    bool bf16 = false, two = false;
     void* tab[4] = {nullptr, nullptr, nullptr, nullptr};    // chi_hi, chi_lo, F_hi, F_lo (TF32 or BF16)
     float* R = nullptr;
     CUtensorMap tmR, tmChiH, tmChiL, tmFH, tmFL;
@@ -1389,21 +1399,21 @@ static int round_tile(int cpt) { return std::min(kChains, std::max(4, (cpt + 3) 
 
 bool fused_supported(int M) { return M == 64 || M == 128 || M == 256 || M == 512; }
 
-template <int NB, bool BF>
+template <int NB, bool BF, bool TWO = false>
 static cudaError_t set_smem()
 {
-    return cudaFuncSetAttribute(k_fused_step<NB, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_fused_step<NB, BF, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 FSmem<NB, BF, BF>::kBytes);
 }
-template <bool BF>
+template <bool BF, bool TWO = false>
 static cudaError_t set_smem_pair()
 {
-    return cudaFuncSetAttribute(k_fused_pair<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_fused_pair<BF, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 FSmem<256, BF, false>::kBytes);
 }
 
 int fused_create(FusedPlan** out, int M, int C, const double* chi, const double* phi, const double* h,
-                 const double* w, float* R, cudaStream_t stream, bool bf16)
+                 const double* w, float* R, cudaStream_t stream, bool bf16, bool two)
 {
     *out = nullptr;
     if (!fused_supported(M)) return report(SFP_ENOTSUP, "the fused step needs M in {64, 128, 256, 512}");
@@ -1412,6 +1422,7 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
     p->C = C;
     p->R = R;
     p->bf16 = bf16;
+    p->two = bf16 && two;
     // the fewest waves of tiles of at most 40 chains (a 512-bead tile takes two
     // SMs), then the chains spread evenly over the tiles of those waves: chains
     // per tile = ceil(C / (units x waves)) rounded up to a multiple of 4
@@ -1484,7 +1495,10 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
         return SFP_ECUDA;
     }
     cudaError_t e;
-    if (bf16)
+    if (p->two)
+        e = M == 512 ? set_smem_pair<true, true>() : M == 256 ? set_smem<256, true, true>() :
+            M == 128 ? set_smem<128, true, true>() : set_smem<64, true, true>();
+    else if (bf16)
         e = M == 512 ? set_smem_pair<true>() : M == 256 ? set_smem<256, true>() :
             M == 128 ? set_smem<128, true>() : set_smem<64, true>();
     else
@@ -1503,8 +1517,12 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
     if (args.cpt != p->cpt) return report(SFP_EINVAL, "fused step: chains per tile differ from the plan's");
     const dim3 grid((unsigned)((p->C + p->cpt - 1) / p->cpt));
 #define SFP_FUSED_LAUNCH(NBV, BFV)                                                                   \
-    k_fused_step<NBV, BFV><<<grid, kThreads, FSmem<NBV, BFV, BFV>::kBytes, stream>>>(p->tmR, p->tmChiH, \
-                                                                           p->tmChiL, p->tmFH, p->tmFL, args)
+    if (p->two)                                                                                      \
+        k_fused_step<NBV, BFV, BFV><<<grid, kThreads, FSmem<NBV, BFV, BFV>::kBytes, stream>>>(         \
+            p->tmR, p->tmChiH, p->tmChiL, p->tmFH, p->tmFL, args);                                   \
+    else                                                                                             \
+        k_fused_step<NBV, BFV><<<grid, kThreads, FSmem<NBV, BFV, BFV>::kBytes, stream>>>(              \
+            p->tmR, p->tmChiH, p->tmChiL, p->tmFH, p->tmFL, args)
     cudaError_t e = cudaSuccess;
     switch (p->M * 2 + (p->bf16 ? 1 : 0)) {
         case 1024:
@@ -1522,7 +1540,9 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
             at[0].val.clusterDim.z = 1;
             cfg.attrs = at;
             cfg.numAttrs = 1;
-            e = p->bf16 ? cudaLaunchKernelEx(&cfg, k_fused_pair<true>, p->tmR, p->tmChiH, p->tmChiL, p->tmFH,
+            e = p->two ? cudaLaunchKernelEx(&cfg, k_fused_pair<true, true>, p->tmR, p->tmChiH, p->tmChiL, p->tmFH,
+                                            p->tmFL, args)
+              : p->bf16 ? cudaLaunchKernelEx(&cfg, k_fused_pair<true>, p->tmR, p->tmChiH, p->tmChiL, p->tmFH,
                                              p->tmFL, args)
                         : cudaLaunchKernelEx(&cfg, k_fused_pair<false>, p->tmR, p->tmChiH, p->tmChiL, p->tmFH,
                                              p->tmFL, args);

@@ -37,9 +37,10 @@ bool fused_supported(int M);
 // and the per-mode weights h_p (Eq. f2), w_p (Eq. d6; w[0] = sqrt(2 T* dtau)).
 // The forward table F = [h_p chi_{n,p} ; w_p phi_{n,p}] (2M rows p, M columns n)
 // and chi are split once into TF32 hi / lo.  R is the group's state array.
-// bf16: BF16 hi/lo operands (kind::f16) instead of the TF32 split.
+// bf16: BF16 hi/lo operands (kind::f16) instead of the TF32 split; two (with
+// bf16): two passes A_lo B_hi + A_hi B_hi, the tables as their BF16 hi part.
 int fused_create(FusedPlan** out, int M, int C, const double* chi, const double* phi, const double* h,
-                 const double* w, float* R, cudaStream_t stream, bool bf16 = false);
+                 const double* w, float* R, cudaStream_t stream, bool bf16 = false, bool two = false);
 // args.n_steps steps of every chain of the group, in one launch.
 int fused_step(FusedPlan* plan, const FusedArgs& args, cudaStream_t stream);
 // Chains per tile of the plan, and a new value (1..40, rounded up to a multiple

@@ -89,33 +89,27 @@ __device__ __forceinline__ void residual_v(const T u[3], bool ok, T c12nu, T v[3
     for (int a = 0; a < 3; ++a) v[a] = u[a] * s;
 }
 
+// One quad: beads n0 .. n0 + 3 of the chain whose arrays start at base.
 template <typename T, bool VEC>
-__global__ void __launch_bounds__(128)
-k_force_noise(const T* __restrict__ ub, T* __restrict__ vb, T* __restrict__ z,
-              int C, int M, T c12nu, uint32_t seed, const uint32_t* __restrict__ job,
-              const int64_t* __restrict__ step)
+__device__ __forceinline__ void force_noise_quad(const T* __restrict__ ub, T* __restrict__ vb, T* __restrict__ z,
+                                                 size_t base, int n0, int M, T c12nu, uint32_t seed, uint32_t job,
+                                                 int64_t step)
 {
-    const int Q = (M + 3) >> 2;                    // bead quads per chain
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)C * Q) return;
-    const int c = (int)(t / Q), qd = (int)(t - (int64_t)c * Q);
-    const int n0 = 4 * qd;
-    const size_t base = (size_t)c * 3 * M + n0;
     T u[3][4];
     if constexpr (VEC) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float4 x = *reinterpret_cast<const float4*>(ub + base + (size_t)a * M);
+            const float4 x = *reinterpret_cast<const float4*>(ub + base + (size_t)a * M + n0);
             u[a][0] = x.x; u[a][1] = x.y; u[a][2] = x.z; u[a][3] = x.w;
         }
     } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) u[a][i] = n0 + i < M ? ub[base + (size_t)a * M + i] : T(0);
+            for (int i = 0; i < 4; ++i) u[a][i] = n0 + i < M ? ub[base + (size_t)a * M + n0 + i] : T(0);
     }
     T g[3][4];
-    bead_quad_normals<T>(seed, job[c], step[c], (uint32_t)qd, 0u, g);
+    bead_quad_normals<T>(seed, job, step, (uint32_t)(n0 >> 2), 0u, g);
     T v[3][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -128,8 +122,8 @@ k_force_noise(const T* __restrict__ ub, T* __restrict__ vb, T* __restrict__ z,
     if constexpr (VEC) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            *reinterpret_cast<float4*>(vb + base + (size_t)a * M) = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
-            *reinterpret_cast<float4*>(z + base + (size_t)a * M) = make_float4(g[a][0], g[a][1], g[a][2], g[a][3]);
+            *reinterpret_cast<float4*>(vb + base + (size_t)a * M + n0) = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
+            *reinterpret_cast<float4*>(z + base + (size_t)a * M + n0) = make_float4(g[a][0], g[a][1], g[a][2], g[a][3]);
         }
     } else {
 #pragma unroll
@@ -137,9 +131,33 @@ k_force_noise(const T* __restrict__ ub, T* __restrict__ vb, T* __restrict__ z,
 #pragma unroll
             for (int i = 0; i < 4; ++i)
                 if (n0 + i < M) {
-                    vb[base + (size_t)a * M + i] = v[a][i];
-                    z[base + (size_t)a * M + i] = g[a][i];
+                    vb[base + (size_t)a * M + n0 + i] = v[a][i];
+                    z[base + (size_t)a * M + n0 + i] = g[a][i];
                 }
+    }
+}
+
+// QPT consecutive quads per thread (their Philox calls are independent, so
+// they interleave); the last group of a chain may hold fewer.
+template <typename T, bool VEC, int QPT>
+__global__ void __launch_bounds__(128)
+k_force_noise(const T* __restrict__ ub, T* __restrict__ vb, T* __restrict__ z,
+              int C, int M, T c12nu, uint32_t seed, const uint32_t* __restrict__ job,
+              const int64_t* __restrict__ step)
+{
+    const int Q = (M + 3) >> 2;                    // bead quads per chain
+    const int G = (Q + QPT - 1) / QPT;             // groups of QPT quads per chain
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)C * G) return;
+    const int c = (int)(t / G), q0 = (int)(t - (int64_t)c * G) * QPT;
+    const size_t base = (size_t)c * 3 * M;
+    const uint32_t jb = job[c];
+    const int64_t st = step[c];
+    if (q0 + QPT <= Q) {
+#pragma unroll
+        for (int j = 0; j < QPT; ++j) force_noise_quad<T, VEC>(ub, vb, z, base, 4 * (q0 + j), M, c12nu, seed, jb, st);
+    } else {
+        for (int q = q0; q < Q; ++q) force_noise_quad<T, VEC>(ub, vb, z, base, 4 * q, M, c12nu, seed, jb, st);
     }
 }
 
@@ -198,6 +216,7 @@ k_mode_update(T* __restrict__ R, const T* __restrict__ DH, const T* __restrict__
         if (stop && step[c] >= stop[c]) continue;
         const size_t b = (size_t)c * 3 * M + p0;
         const double sh = shear[c];
+        const T shT = (T)sh;                 // one conversion per chain
         T r[3][V], y[3][V], zz[3][V];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -211,7 +230,7 @@ k_mode_update(T* __restrict__ R, const T* __restrict__ DH, const T* __restrict__
         for (int i = 0; i < V; ++i) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) o[a][i] = r[a][i] + fma(-d[i], r[a][i], fma(hh[i], y[a][i], ww[i] * zz[a][i]));
-            o[0][i] += (T)sh * gg[i] * r[1][i];
+            if (shT != T(0)) o[0][i] += shT * gg[i] * r[1][i];
 #pragma unroll
             for (int a = 0; a < 3; ++a) fin = fin && isfinite(o[a][i]);
         }

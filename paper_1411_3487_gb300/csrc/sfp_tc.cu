@@ -214,7 +214,7 @@ __device__ __forceinline__ uint16_t bf16_bits(float x)
     return __bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
-template <int NT>
+template <int NT, bool TWO = false>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh0,
           const __grid_constant__ CUtensorMap tmBl0, const __grid_constant__ CUtensorMap tmBh1,
@@ -294,12 +294,13 @@ k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 for (int kk = 0; kk < kKB / 16; ++kk) {
                     const uint32_t off = kk * 32;   // 16 BF16 = 32 bytes along K
                     const uint32_t acc = (kb | kk) != 0;
+                    if constexpr (!TWO)   // TWO: the tables as their BF16 hi part alone
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                     ::"r"(tmem), "l"(sdesc64(a_hi + off)), "l"(sdesc64(b_lo + off)), "r"(idesc), "r"(acc) : "memory");
                     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                                 ::"r"(tmem), "l"(sdesc64(a_hi + off)), "l"(sdesc64(b_lo + off)), "r"(idesc), "r"(acc) : "memory");
-                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                                 ::"r"(tmem), "l"(sdesc64(a_lo + off)), "l"(sdesc64(b_hi + off)), "r"(idesc), "r"(1u) : "memory");
+                                 ::"r"(tmem), "l"(sdesc64(a_lo + off)), "l"(sdesc64(b_hi + off)), "r"(idesc), "r"(TWO ? acc : 1u) : "memory");
                     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
                                  ::"r"(tmem), "l"(sdesc64(a_hi + off)), "l"(sdesc64(b_hi + off)), "r"(idesc), "r"(1u) : "memory");
@@ -374,7 +375,7 @@ k_tc_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
 struct TcPlan {
     int M = 0, rows = 0, NT = 0;
-    bool bf16 = false;
+    bool bf16 = false, two = false;
     // tables t = 0: chi (inverse), 1: chi^T (forward, force half), 2: phi^T
     // (forward, noise half); B[2 t] hi, B[2 t + 1] lo (FP32 or BF16)
     void* B[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -386,7 +387,8 @@ struct TcPlan {
 bool tc_supported(int M) { return M == 32 || M == 64 || M == 128 || M == 256 || M == 512; }
 
 int tc_create(TcPlan** out, int M, int rows, const double* chi, const double* chiT, const double* phiT,
-              const float* R, float* r_out, const float* fz, float* yz_out, int* err, cudaStream_t stream, bool bf16)
+              const float* R, float* r_out, const float* fz, float* yz_out, int* err, cudaStream_t stream, bool bf16,
+              bool two)
 {
     *out = nullptr;
     if (!tc_supported(M)) return report(SFP_ENOTSUP, "tensor-core transforms need M in {32, 64, 128, 256, 512}");
@@ -396,6 +398,7 @@ int tc_create(TcPlan** out, int M, int rows, const double* chi, const double* ch
     p->NT = M <= 256 ? M : 256;
     p->err = err;
     p->bf16 = bf16;
+    p->two = bf16 && two;
     const size_t n = (size_t)M * M;
     const double* src[3] = {chi, chiT, phiT};
     const size_t el = bf16 ? 2 : sizeof(float);
@@ -450,10 +453,10 @@ int tc_create(TcPlan** out, int M, int rows, const double* chi, const double* ch
         case 64: e = SFP_TC_ATTR(k_tc_gemm<64>, Smem<64>); break;
         case 128: e = SFP_TC_ATTR(k_tc_gemm<128>, Smem<128>); break;
         case 256: e = SFP_TC_ATTR(k_tc_gemm<256>, Smem<256>); break;
-        case 33: e = SFP_TC_ATTR(k_tc_gemm_bf16<32>, SmemBf<32>); break;
-        case 65: e = SFP_TC_ATTR(k_tc_gemm_bf16<64>, SmemBf<64>); break;
-        case 129: e = SFP_TC_ATTR(k_tc_gemm_bf16<128>, SmemBf<128>); break;
-        case 257: e = SFP_TC_ATTR(k_tc_gemm_bf16<256>, SmemBf<256>); break;
+        case 33: e = p->two ? SFP_TC_ATTR((k_tc_gemm_bf16<32, true>), SmemBf<32>) : SFP_TC_ATTR(k_tc_gemm_bf16<32>, SmemBf<32>); break;
+        case 65: e = p->two ? SFP_TC_ATTR((k_tc_gemm_bf16<64, true>), SmemBf<64>) : SFP_TC_ATTR(k_tc_gemm_bf16<64>, SmemBf<64>); break;
+        case 129: e = p->two ? SFP_TC_ATTR((k_tc_gemm_bf16<128, true>), SmemBf<128>) : SFP_TC_ATTR(k_tc_gemm_bf16<128>, SmemBf<128>); break;
+        case 257: e = p->two ? SFP_TC_ATTR((k_tc_gemm_bf16<256, true>), SmemBf<256>) : SFP_TC_ATTR(k_tc_gemm_bf16<256>, SmemBf<256>); break;
         default: e = cudaErrorInvalidValue; break;
     }
 #undef SFP_TC_ATTR
@@ -475,18 +478,26 @@ int tc_transform(TcPlan* p, int which, cudaStream_t stream)
 #define SFP_TC_LAUNCH(K, S)                                                                             \
     K<<<grid, kThreads, S::kBytes, stream>>>(p->mapA[which], p->mapBh[b0], p->mapBl[b0], p->mapBh[b1], \
                                             p->mapBl[b1], p->out[which], J, p->M, p->err)
+#define SFP_TC_LAUNCH_BF(NTV)                                                                           \
+    if (p->two)                                                                                          \
+        k_tc_gemm_bf16<NTV, true><<<grid, kThreads, SmemBf<NTV>::kBytes, stream>>>(                     \
+            p->mapA[which], p->mapBh[b0], p->mapBl[b0], p->mapBh[b1], p->mapBl[b1], p->out[which], J, p->M, p->err); \
+    else                                                                                                 \
+        k_tc_gemm_bf16<NTV><<<grid, kThreads, SmemBf<NTV>::kBytes, stream>>>(                           \
+            p->mapA[which], p->mapBh[b0], p->mapBl[b0], p->mapBh[b1], p->mapBl[b1], p->out[which], J, p->M, p->err)
     switch (p->NT + (p->bf16 ? 1 : 0)) {
         case 32: SFP_TC_LAUNCH(k_tc_gemm<32>, Smem<32>); break;
         case 64: SFP_TC_LAUNCH(k_tc_gemm<64>, Smem<64>); break;
         case 128: SFP_TC_LAUNCH(k_tc_gemm<128>, Smem<128>); break;
         case 256: SFP_TC_LAUNCH(k_tc_gemm<256>, Smem<256>); break;
-        case 33: SFP_TC_LAUNCH(k_tc_gemm_bf16<32>, SmemBf<32>); break;
-        case 65: SFP_TC_LAUNCH(k_tc_gemm_bf16<64>, SmemBf<64>); break;
-        case 129: SFP_TC_LAUNCH(k_tc_gemm_bf16<128>, SmemBf<128>); break;
-        case 257: SFP_TC_LAUNCH(k_tc_gemm_bf16<256>, SmemBf<256>); break;
+        case 33: SFP_TC_LAUNCH_BF(32); break;
+        case 65: SFP_TC_LAUNCH_BF(64); break;
+        case 129: SFP_TC_LAUNCH_BF(128); break;
+        case 257: SFP_TC_LAUNCH_BF(256); break;
         default: return report(SFP_ENOTSUP, "unsupported tile width");
     }
 #undef SFP_TC_LAUNCH
+#undef SFP_TC_LAUNCH_BF
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return report(SFP_ECUDA, cudaGetErrorString(e));
     return SFP_OK;

@@ -19,11 +19,12 @@ bool tc_supported(int M);
 // forward DeltaH = chi^T v (Eq. e11) and Z = phi^T z (Eq. c4) read
 // fz = [v | z] [2 rows][M] and write yz_out = [DeltaH | Z].
 // chi [n][p], chiT [p][n] and phiT [p][n] are FP64 tables; they are split
-// once into TF32 (or, with bf16, BF16) hi / lo parts.
+// once into TF32 (or, with bf16, BF16) hi / lo parts; two (with bf16): two
+// passes A_lo B_hi + A_hi B_hi, the tables as their BF16 hi part alone.
 // A wait that times out inside the kernel sets bit 2 of *err.
 int tc_create(TcPlan** out, int M, int rows, const double* chi, const double* chiT, const double* phiT,
               const float* R, float* r_out, const float* fz, float* yz_out, int* err, cudaStream_t stream,
-              bool bf16 = false);
+              bool bf16 = false, bool two = false);
 // which = 0: inverse, 1: forward.
 int tc_transform(TcPlan* plan, int which, cudaStream_t stream);
 // Device bytes the plan's tables hold.

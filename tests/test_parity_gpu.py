@@ -372,6 +372,33 @@ def test_bf16_fused_step_against_the_oracle(M, C):
         fused.probe(sfp.SFP_PROBE_DH)
 
 
+@pytest.mark.parametrize("M,C", [(256, 50), (512, 12), (100, 7)])
+def test_bf16_two_pass_against_the_oracle(M, C):
+    """SFP_MIXED_BF16_2: two passes (A_lo B_hi + A_hi B_hi), the tables rounded
+    to BF16 (8 bits), so every transform carries ~2^-9 relative error.  The
+    fused kernel rounds its stacked table [h chi; w phi] and the staged kernels
+    chi^T and phi^T, so the two differ by that rounding (measured 1-2e-4 after
+    200 steps) and each stays within 1e-3 of the FP64 oracle over 200 steps
+    (measured 1-2e-4); lengths without tensor-core transforms (100 beads) run
+    FP32 CUDA-core transforms.  The errors are printed."""
+    dtau = 100.0 if M >= 256 else 10.0
+    m = O.Model(M, dtau=dtau)
+    R = starts(M, C, dtau=dtau)
+    out = []
+    for path in (sfp.SFP_PATH_FUSED, sfp.SFP_PATH_STAGED):
+        b = make_batch(M, C, dtau, (sfp.SFP_MIXED_BF16_2, path))
+        b.set_modes(R)
+        b.step(200)
+        out.append(b.modes())
+        b.close()
+    ref = m.run_modes(R, 1, np.arange(C), 0, 200)
+    e_f, e_s = rel_err(out[0], ref).max(), rel_err(out[1], ref).max()
+    print("bf16x2", M, "error after 200 steps: fused", e_f, "staged", e_s, "fused vs staged",
+          rel_err(out[0], out[1]).max())
+    assert e_f < 1e-3 and e_s < 1e-3
+    assert rel_err(out[0], out[1]).max() < 1e-3
+
+
 @pytest.mark.parametrize("M", [64, 512])
 def test_pipeline_wait_timeout_is_reported(monkeypatch, M):
     """Bounded waits: with SFP_TEST_STALL=1 the fused kernel's MMA thread first

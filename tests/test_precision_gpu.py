@@ -1,7 +1,11 @@
 """Error per observable against the FP64 oracle at the 16384 x 512-bp size
 (NEXT-3 precision row): TF32 and BF16 hi/lo tensor-core transforms
 (SFP_FP32 = SFP_MIXED_TF32, SFP_MIXED_BF16), plain FP32 (SFP_FP32_SIMT) and FP64.
-The three-pass BF16 split is held to the FP32 bounds."""
+The three-pass BF16 split is held to the FP32 bounds.  The two-pass split
+(SFP_MIXED_BF16_2: tables rounded to BF16) is not an FP32-accurate mode; its
+errors are printed and held to bounds of their own (measured over 2000 steps
+at 16384 x 512 bp: 3e-4 on the trajectory and |L|^2, 1.5e-3 on the middle
+bond)."""
 import pytest
 
 import paper_1411_3487_gb300 as sfp
@@ -24,7 +28,8 @@ def built():
 # shows there at ~1e-5 (measured 1.1e-5 and 1.3e-5 with the TF32 split).
 @pytest.mark.parametrize("precision,tol,tol_local", [(sfp.SFP_FP32, 1e-5, 1e-4), (sfp.SFP_FP32_SIMT, 1e-5, 1e-4),
                                                      (sfp.SFP_MIXED_BF16, 1e-5, 1e-4),
-                                                     (sfp.SFP_FP64, 1e-9, 1e-9)], ids=["tf32x3", "fp32", "bf16x3", "fp64"])
+                                                     (sfp.SFP_MIXED_BF16_2, 2e-3, 1e-2),
+                                                     (sfp.SFP_FP64, 1e-9, 1e-9)], ids=["tf32x3", "fp32", "bf16x3", "bf16x2", "fp64"])
 def test_error_per_observable_16384x512(precision, tol, tol_local):
     e = errors(sfp, O, precision, steps=400, every=20, sub=8)
     print(precision, e)
