@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--steps-per-call", type=int, default=20,
                     help="Langevin steps per sfp_step call (one fused launch); L2 is flushed between calls")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "tc", "simt"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "bf16x2", "tf32", "tc", "simt"])
     ap.add_argument("--path", default="fused", choices=["fused", "staged"])
     ap.add_argument("--workload", default="batch", choices=["batch", "serving", "precision", "uneven"])
     ap.add_argument("--serve-seconds", type=float, default=60.0,
@@ -210,10 +210,10 @@ def run_native(args, rank, world, local):
     stream = torch.cuda.current_stream()
     _names(sfp)
     DTYPE.update({sfp.SFP_MIXED_BF16: "f32 (bf16x3 transforms)", sfp.SFP_FP32: "f32 (tf32x3 transforms)",
-                  sfp.SFP_FP32_SIMT: "f32"})
-    precision = {"bf16": sfp.SFP_MIXED_BF16, "tf32": sfp.SFP_FP32, "tc": sfp.SFP_FP32,
+                  sfp.SFP_MIXED_BF16_2: "f32 (bf16x2 transforms, tables rounded to bf16)", sfp.SFP_FP32_SIMT: "f32"})
+    precision = {"bf16": sfp.SFP_MIXED_BF16, "bf16x2": sfp.SFP_MIXED_BF16_2, "tf32": sfp.SFP_FP32, "tc": sfp.SFP_FP32,
                  "simt": sfp.SFP_FP32_SIMT}[args.precision]
-    tensor = precision in (sfp.SFP_FP32, sfp.SFP_MIXED_BF16)
+    tensor = precision in (sfp.SFP_FP32, sfp.SFP_MIXED_BF16, sfp.SFP_MIXED_BF16_2)
     # weak scaling: every rank owns its own 4096 chains (disjoint job ids)
     from paper_1411_3487_gb300 import shard
     chains = [{"n_beads": M_BEADS, "dt_ps": DT_PS, "job_id": j}
@@ -456,6 +456,14 @@ def roofline(kern, pk, how, precision, path, sfp):
     else:
         tf32_peak = pk.get("bf16_tflops", 1900.0) * (1.1 / 2.25)
         src = f"{how} bf16 x 1.1/2.25 (nominal tf32/bf16 dense ratio)"
+    if precision == sfp.SFP_MIXED_BF16_2 and path == sfp.SFP_PATH_FUSED:
+        us = kern.get("inverse_us")          # the fused kernel is recorded as the first stage
+        flops = 2 * 18.0 * M * beads
+        peak = pk.get("bf16_tflops", 1900.0)
+        return {"bound": "tensor", "kernel": "k_fused_step<256, bf16, two passes> (whole step, bf16x2)",
+                "achieved": flops / (us * 1e-6) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / (us * 1e-6) / 1e12 / peak, "traffic": None,
+                "algorithmic_bytes": 24 * beads, "kernel_us": us, "peak_source": f"{how} bf16 dense (burst)"}
     if precision == sfp.SFP_MIXED_BF16 and path == sfp.SFP_PATH_FUSED:
         us = kern.get("inverse_us")          # the fused kernel is recorded as the first stage
         flops = 3 * 18.0 * M * beads
@@ -475,9 +483,9 @@ def roofline(kern, pk, how, precision, path, sfp):
                 "frac": flops / (us * 1e-6) / 1e12 / tf32_peak, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per launch (ncu, profiles/fused_step_4096x256.md)",
                 "algorithmic_bytes": 24 * beads, "kernel_us": us, "peak_source": src}
-    if precision in (sfp.SFP_FP32, sfp.SFP_MIXED_BF16):
-        # forward transform: [DeltaH|Z] = phi^T [f|z], 2*rows x M x M, three passes
-        bf = precision == sfp.SFP_MIXED_BF16
+    if precision in (sfp.SFP_FP32, sfp.SFP_MIXED_BF16, sfp.SFP_MIXED_BF16_2):
+        # forward transform: DeltaH = chi^T v and Z = phi^T z, 2*rows x M x M, three passes
+        bf = precision in (sfp.SFP_MIXED_BF16, sfp.SFP_MIXED_BF16_2)
         peak = pk.get("bf16_tflops", 1900.0) if bf else tf32_peak
         us = kern.get("forward_us")
         flops = 3 * 2.0 * (6 * C_CHAINS) * M * M
@@ -522,10 +530,9 @@ def end_to_end(sfp, b, torch, steps):
 
 def bench_precision(sfp, args):
     """The --precision choice as (sfp precision, name)."""
-    prec = {"bf16": sfp.SFP_MIXED_BF16, "tf32": sfp.SFP_FP32, "tc": sfp.SFP_FP32,
+    prec = {"bf16": sfp.SFP_MIXED_BF16, "bf16x2": sfp.SFP_MIXED_BF16_2, "tf32": sfp.SFP_FP32, "tc": sfp.SFP_FP32,
             "simt": sfp.SFP_FP32_SIMT}[args.precision]
-    name = {sfp.SFP_MIXED_BF16: "SFP_MIXED_BF16", sfp.SFP_FP32: "SFP_FP32", sfp.SFP_FP32_SIMT: "SFP_FP32_SIMT"}[prec]
-    return prec, name
+    return prec, PREC_NAME.get(prec, str(prec))
 
 
 def tf32_peak(torch) -> float:

@@ -183,6 +183,12 @@ int sfp_step(sfp_batch *b, int64_t n_steps);
  *                      |(r_m - r_cm)(t) - (r_m - r_cm)(t - lag)|^2 (nm^2) and the
  *                      number of windows; their ratio is the mean-square
  *                      displacement Q(t_lag) of observable iii of Sec. 5B
+ *   SFP_OBS_E2E_MSD    FP64 [C][L][2]: the same windows for the end-to-end vector
+ *                      L: sum of |L(t) - L(t - lag)|^2 (nm^2) and the windows;
+ *                      for a stationary chain <L(t).L(0)> = <|L|^2> - ratio / 2,
+ *                      the time autocorrelation of observable i (Sec. 5B)
+ *   SFP_OBS_BOND_MSD   FP64 [C][L][2]: the same for the middle bond u_m
+ *                      (observable ii)
  *   SFP_OBS_E2E2_MEAN  FP64 [C]: mean |L|^2 over the samples (nm^2), the
  *                      equilibrium <|L|^2> of observable i (Sec. 5B)
  *   SFP_OBS_MODE_VAR   FP64 packed [3][M_c]: mean of (R_p^alpha)^2 over the
@@ -191,7 +197,8 @@ int sfp_step(sfp_batch *b, int64_t n_steps);
  * bytes must be at least the size of the requested array. */
 enum { SFP_OBS_MODES = 0, SFP_OBS_POSITIONS = 1, SFP_OBS_COM = 2, SFP_OBS_STEP = 3,
        SFP_OBS_SHAPE = 4, SFP_OBS_ACCUM = 5, SFP_OBS_MODE_POWER = 6, SFP_OBS_COM_MSD = 7,
-       SFP_OBS_MID_MSD = 8, SFP_OBS_E2E2_MEAN = 9, SFP_OBS_MODE_VAR = 10 };
+       SFP_OBS_MID_MSD = 8, SFP_OBS_E2E2_MEAN = 9, SFP_OBS_MODE_VAR = 10, SFP_OBS_E2E_MSD = 11,
+       SFP_OBS_BOND_MSD = 12 };
 int sfp_observe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
 
 /* Kernel path of the SFP_FP32 and SFP_MIXED_BF16 steps (other precisions
@@ -250,7 +257,7 @@ int sfp_set_integrator(sfp_batch *b, int32_t integrator);
  * checkpoint (sfp_save).  SFP_EINVAL for every_steps < 0. */
 int sfp_set_sampling(sfp_batch *b, int32_t every_steps);
 
-/* Lags of the SFP_OBS_COM_MSD and SFP_OBS_MID_MSD windows, in sampling
+/* Lags of the SFP_OBS_COM_MSD, _MID_MSD, _E2E_MSD and _BOND_MSD windows, in sampling
  * intervals: n_lags = 1..8 values, each >= 1 (default 1, 10, 100, 1000).  The
  * list takes effect at the next sfp_set_sampling(b, every_steps > 0), which
  * clears the windows; from then on those observables have n_lags rows per

@@ -14,7 +14,8 @@ import numpy as np
 from . import _lib
 from ._lib import (SFP_FP32, SFP_FP32_SIMT, SFP_FP64, SFP_MIXED_BF16, SFP_MIXED_BF16_2, SFP_MIXED_TF32,
                    SFP_OBS_ACCUM, SFP_OBS_COM,
-                   SFP_OBS_COM_MSD, SFP_OBS_E2E2_MEAN, SFP_OBS_MID_MSD, SFP_OBS_MODE_POWER, SFP_OBS_MODE_VAR,
+                   SFP_OBS_BOND_MSD, SFP_OBS_COM_MSD, SFP_OBS_E2E2_MEAN, SFP_OBS_E2E_MSD, SFP_OBS_MID_MSD,
+                   SFP_OBS_MODE_POWER, SFP_OBS_MODE_VAR,
                    SFP_OBS_MODES, SFP_OBS_POSITIONS,
                    SFP_INTEGRATOR_EULER, SFP_INTEGRATOR_MODES, SFP_OBS_SHAPE, SFP_OBS_STEP,
                    SFP_PATH_FUSED, SFP_PATH_STAGED, SFP_PROBE_BONDS, SFP_PROBE_DH,
@@ -180,7 +181,7 @@ class Batch:
             out = np.zeros(self.n_chains, dtype=np.int64)
         elif what in (SFP_OBS_SHAPE, SFP_OBS_ACCUM):
             out = np.zeros((self.n_chains, 4))
-        elif what in (SFP_OBS_COM_MSD, SFP_OBS_MID_MSD):
+        elif what in (SFP_OBS_COM_MSD, SFP_OBS_MID_MSD, SFP_OBS_E2E_MSD, SFP_OBS_BOND_MSD):
             out = np.zeros((self.n_chains, self._n_lags, 2))
         elif what == SFP_OBS_E2E2_MEAN:
             out = np.zeros(self.n_chains)

@@ -19,7 +19,7 @@ SFP_MIXED_TF32 = SFP_FP32   # FP32 state, TF32x3 transforms
 SFP_MIXED_BF16_2 = 3        # FP32 state, two-pass BF16 transforms (tables rounded to BF16)
 SFP_OBS_MODES, SFP_OBS_POSITIONS, SFP_OBS_COM, SFP_OBS_STEP, SFP_OBS_SHAPE = 0, 1, 2, 3, 4
 SFP_OBS_ACCUM, SFP_OBS_MODE_POWER, SFP_OBS_COM_MSD = 5, 6, 7
-SFP_OBS_MID_MSD, SFP_OBS_E2E2_MEAN, SFP_OBS_MODE_VAR = 8, 9, 10
+SFP_OBS_MID_MSD, SFP_OBS_E2E2_MEAN, SFP_OBS_MODE_VAR, SFP_OBS_E2E_MSD, SFP_OBS_BOND_MSD = 8, 9, 10, 11, 12
 SFP_PATH_FUSED, SFP_PATH_STAGED = 0, 1
 SFP_INTEGRATOR_MODES, SFP_INTEGRATOR_EULER = 0, 1
 SFP_PROBE_BONDS, SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_DH, SFP_PROBE_ZMODE = 0, 1, 2, 3, 4

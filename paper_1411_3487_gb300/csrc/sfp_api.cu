@@ -199,6 +199,10 @@ struct Group {
     double* msd_acc = nullptr;    // [C][kMaxLags][2]
     double* mid_snap = nullptr;   // [C][kMaxLags][3] r_m' - r_cm at the last window edge
     double* mid_acc = nullptr;    // [C][kMaxLags][2]
+    double* e2e_snap = nullptr;   // [C][kMaxLags][3] L at the last window edge
+    double* e2e_acc = nullptr;    // [C][kMaxLags][2]
+    double* bond_snap = nullptr;  // [C][kMaxLags][3] u_m at the last window edge
+    double* bond_acc = nullptr;   // [C][kMaxLags][2]
 };
 
 struct sfp_batch {
@@ -489,14 +493,14 @@ int sample_all(sfp_batch* b)
 {
     for (auto& g : b->groups) {
         const unsigned grid = nblk(g.C, 4);
+        const sfp::SampleWindows wv{{g.msd_acc, g.mid_acc, g.e2e_acc, g.bond_acc},
+                                    {g.msd_snap, g.mid_snap, g.e2e_snap, g.bond_snap}};
         if (b->precision == SFP_FP64)
             sfp::k_sample<double><<<grid, 128, 0, b->stream>>>((const double*)g.R, g.com, g.obs_tab, g.C, g.M,
-                                                               g.acc_shape, g.acc_pow, g.msd_snap, g.msd_acc,
-                                                               g.mid_snap, g.mid_acc, b->n_samples, b->lags);
+                                                               g.acc_shape, g.acc_pow, wv, b->n_samples, b->lags);
         else
             sfp::k_sample<float><<<grid, 128, 0, b->stream>>>((const float*)g.R, g.com, g.obs_tab, g.C, g.M,
-                                                              g.acc_shape, g.acc_pow, g.msd_snap, g.msd_acc,
-                                                              g.mid_snap, g.mid_acc, b->n_samples, b->lags);
+                                                              g.acc_shape, g.acc_pow, wv, b->n_samples, b->lags);
         b->launches++;
         CUDA_TRY(cudaGetLastError());
     }
@@ -1129,12 +1133,15 @@ int sfp_observe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
         case SFP_OBS_SHAPE: need = (size_t)b->C * 4 * 8; break;
         case SFP_OBS_ACCUM: need = (size_t)b->C * 4 * 8; break;
         case SFP_OBS_MODE_POWER: case SFP_OBS_MODE_VAR: need = packed; break;
-        case SFP_OBS_COM_MSD: case SFP_OBS_MID_MSD: need = (size_t)b->C * b->lags.n * 2 * 8; break;
+        case SFP_OBS_COM_MSD: case SFP_OBS_MID_MSD: case SFP_OBS_E2E_MSD: case SFP_OBS_BOND_MSD:
+            need = (size_t)b->C * b->lags.n * 2 * 8;
+            break;
         case SFP_OBS_E2E2_MEAN: need = (size_t)b->C * 8; break;
         default: return fail(SFP_EINVAL, "unknown observable %d", what);
     }
     if ((what == SFP_OBS_ACCUM || what == SFP_OBS_MODE_POWER || what == SFP_OBS_COM_MSD || what == SFP_OBS_MID_MSD ||
-         what == SFP_OBS_E2E2_MEAN || what == SFP_OBS_MODE_VAR) && !b->sampled)
+         what == SFP_OBS_E2E_MSD || what == SFP_OBS_BOND_MSD || what == SFP_OBS_E2E2_MEAN ||
+         what == SFP_OBS_MODE_VAR) && !b->sampled)
         return fail(SFP_EINVAL, "observable %d needs sfp_set_sampling first", what);
     if (bytes < need) return fail(SFP_EINVAL, "buffer too small: need %zu bytes", need);
     std::vector<double> tmp;
@@ -1211,11 +1218,13 @@ int sfp_observe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
                     for (int k = 0; k < 4; ++k) o[(size_t)4 * g.chains[i] + k] = ai[k] * (k == 3 ? 1.0 : d2);
                 }
             }
-        } else if (what == SFP_OBS_COM_MSD || what == SFP_OBS_MID_MSD) {
+        } else if (what == SFP_OBS_COM_MSD || what == SFP_OBS_MID_MSD || what == SFP_OBS_E2E_MSD ||
+                   what == SFP_OBS_BOND_MSD) {
             const int L = b->lags.n;
             std::vector<double> a((size_t)g.C * sfp::kMaxLags * 2);
-            CUDA_TRY(cudaMemcpyAsync(a.data(), what == SFP_OBS_COM_MSD ? g.msd_acc : g.mid_acc, a.size() * 8,
-                                     cudaMemcpyDeviceToHost, b->stream));
+            const double* src = what == SFP_OBS_COM_MSD ? g.msd_acc : what == SFP_OBS_MID_MSD ? g.mid_acc
+                              : what == SFP_OBS_E2E_MSD ? g.e2e_acc : g.bond_acc;
+            CUDA_TRY(cudaMemcpyAsync(a.data(), src, a.size() * 8, cudaMemcpyDeviceToHost, b->stream));
             CUDA_TRY(cudaStreamSynchronize(b->stream));
             const double d2 = b->dv.d_nm * b->dv.d_nm;
             for (int i = 0; i < g.C; ++i)
@@ -1575,7 +1584,11 @@ int sfp_set_sampling(sfp_batch* b, int32_t every_steps)
                 (rc = dalloc_t(b, &g.msd_snap, (size_t)g.C * sfp::kMaxLags * 3 * 8)) ||
                 (rc = dalloc_t(b, &g.msd_acc, (size_t)g.C * sfp::kMaxLags * 2 * 8)) ||
                 (rc = dalloc_t(b, &g.mid_snap, (size_t)g.C * sfp::kMaxLags * 3 * 8)) ||
-                (rc = dalloc_t(b, &g.mid_acc, (size_t)g.C * sfp::kMaxLags * 2 * 8)))
+                (rc = dalloc_t(b, &g.mid_acc, (size_t)g.C * sfp::kMaxLags * 2 * 8)) ||
+                (rc = dalloc_t(b, &g.e2e_snap, (size_t)g.C * sfp::kMaxLags * 3 * 8)) ||
+                (rc = dalloc_t(b, &g.e2e_acc, (size_t)g.C * sfp::kMaxLags * 2 * 8)) ||
+                (rc = dalloc_t(b, &g.bond_snap, (size_t)g.C * sfp::kMaxLags * 3 * 8)) ||
+                (rc = dalloc_t(b, &g.bond_acc, (size_t)g.C * sfp::kMaxLags * 2 * 8)))
                 return rc;
             // coefficient rows of L = r_N - r_0, u_m = r_m - r_{m-1} (m = ceil(N/2)) and
             // r_m' - r_cm (m' = floor(N/2)) in terms of R_p (Eq. c1); p = 0 drops out of all three
@@ -1594,8 +1607,10 @@ int sfp_set_sampling(sfp_batch* b, int32_t every_steps)
         CUDA_TRY(cudaMemsetAsync(g.acc_pow, 0, (size_t)g.C * 3 * M * 8, b->stream));
         CUDA_TRY(cudaMemsetAsync(g.msd_snap, 0, (size_t)g.C * sfp::kMaxLags * 3 * 8, b->stream));
         CUDA_TRY(cudaMemsetAsync(g.msd_acc, 0, (size_t)g.C * sfp::kMaxLags * 2 * 8, b->stream));
-        CUDA_TRY(cudaMemsetAsync(g.mid_snap, 0, (size_t)g.C * sfp::kMaxLags * 3 * 8, b->stream));
-        CUDA_TRY(cudaMemsetAsync(g.mid_acc, 0, (size_t)g.C * sfp::kMaxLags * 2 * 8, b->stream));
+        for (double* x : {g.mid_snap, g.e2e_snap, g.bond_snap})
+            CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)g.C * sfp::kMaxLags * 3 * 8, b->stream));
+        for (double* x : {g.mid_acc, g.e2e_acc, g.bond_acc})
+            CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)g.C * sfp::kMaxLags * 2 * 8, b->stream));
     }
     b->lags = b->lags_next;
     b->sampled = true;

@@ -483,11 +483,15 @@ namespace sfp {
 // tab = [3][M] FP64 coefficient rows for these three sums.  Per chain, adds
 // |L|^2, |u_m|^2, |r_m - r_cm|^2 and 1 to shape[c][0..3] and (R_p^a)^2 to
 // power[c][a][p] (R_0 = sqrt(M) r_cm).  Displacements over non-overlapping
-// windows of lag.v[i] samples (sample index k), for the centre of mass (FP64)
-// and for the middle bead relative to it, r_m' - r_cm (observable iii): when
-// k is a multiple of lag.v[i], adds |x - snap_i|^2 and 1 to msd[c][i][0..1]
-// (mid[c][i][0..1]) from the second window edge on and sets snap_i = x.
-// Windows are [c][kMaxLags][...] whatever lag.n is.
+// windows of lag.v[i] samples (sample index k) of four vectors x: the centre
+// of mass (FP64), the middle bead relative to it r_m' - r_cm (observable iii),
+// the end-to-end vector L (observable i) and the middle bond u_m (observable
+// ii): when k is a multiple of lag.v[i], adds |x - snap_i|^2 and 1 to the
+// vector's window sums [c][i][0..1] from the second window edge on and sets
+// snap_i = x.  For a stationary X, <X(t).X(0)> = <X^2> - <|X(t) - X(0)|^2> / 2,
+// so the windows of L and u_m give their time autocorrelations.  Windows and
+// snapshots are [c][kMaxLags][...] whatever lag.n is; win[v] and snp[v] hold
+// vector v = 0 (centre of mass), 1 (middle bead), 2 (L), 3 (u_m).
 // ---------------------------------------------------------------------------
 constexpr int kMaxLags = 8;
 struct SampleLags {
@@ -495,12 +499,16 @@ struct SampleLags {
     int v[kMaxLags];
 };
 
+struct SampleWindows {
+    double* win[4];    // [C][kMaxLags][2] per vector
+    double* snp[4];    // [C][kMaxLags][3] per vector
+};
+
 template <typename T>
 __global__ void __launch_bounds__(128)
 k_sample(const T* __restrict__ R, const double* __restrict__ com, const double* __restrict__ tab,
-         int C, int M, double* __restrict__ shape, double* __restrict__ power,
-         double* __restrict__ snap, double* __restrict__ msd, double* __restrict__ mid_snap,
-         double* __restrict__ mid, int64_t k, SampleLags lag)
+         int C, int M, double* __restrict__ shape, double* __restrict__ power, SampleWindows wv,
+         int64_t k, SampleLags lag)
 {
     const int lane = threadIdx.x & 31;
     const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -531,29 +539,26 @@ k_sample(const T* __restrict__ R, const double* __restrict__ com, const double* 
     sh[1] += s[3] * s[3] + s[4] * s[4] + s[5] * s[5];
     sh[2] += s[6] * s[6] + s[7] * s[7] + s[8] * s[8];
     sh[3] += 1.0;
+    const double x[4][3] = {{com[3 * c], com[3 * c + 1], com[3 * c + 2]}, {s[6], s[7], s[8]},
+                            {s[0], s[1], s[2]}, {s[3], s[4], s[5]}};
     for (int i = 0; i < lag.n && i < kMaxLags; ++i) {
         if (lag.v[i] <= 0 || k % lag.v[i] != 0) continue;
         const size_t w = (size_t)c * kMaxLags + i;
-        double* sn = snap + w * 3;
-        double* sm = mid_snap + w * 3;
-        if (k > 0) {
-            double d2 = 0.0, e2 = 0.0;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const double d = com[3 * c + a] - sn[a];
-                const double e = s[6 + a] - sm[a];
-                d2 += d * d;
-                e2 += e * e;
+        for (int v = 0; v < 4; ++v) {
+            double* sn = wv.snp[v] + w * 3;
+            if (k > 0) {
+                double d2 = 0.0;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const double d = x[v][a] - sn[a];
+                    d2 += d * d;
+                }
+                wv.win[v][w * 2] += d2;
+                wv.win[v][w * 2 + 1] += 1.0;
             }
-            msd[w * 2] += d2;
-            msd[w * 2 + 1] += 1.0;
-            mid[w * 2] += e2;
-            mid[w * 2 + 1] += 1.0;
-        }
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            sn[a] = com[3 * c + a];
-            sm[a] = s[6 + a];
+            for (int a = 0; a < 3; ++a) sn[a] = x[v][a];
         }
     }
 }

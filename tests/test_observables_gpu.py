@@ -85,7 +85,8 @@ def test_sampled_sums_match_oracle(precision, tol):
 def test_middle_bead_msd_windows_match_oracle(precision, tol):
     """SFP_OBS_MID_MSD: non-overlapping windows of |(r_m - r_cm)(t) - (r_m - r_cm)(t - lag)|^2
     for the middle bead m = floor(N/2) (observable iii of Sec. 5B) at lags set by
-    sfp_set_msd_lags, with the centre-of-mass windows at the same lags, and the
+    sfp_set_msd_lags, with the centre-of-mass, end-to-end (SFP_OBS_E2E_MSD) and
+    middle-bond (SFP_OBS_BOND_MSD) windows at the same lags, and the
     means SFP_OBS_E2E2_MEAN and SFP_OBS_MODE_VAR; against the oracle's trajectory
     (bead positions from its own inverse transform, Eq. c1)."""
     M, C, dtau, every, nsamp = 128, 21, 50.0, 3, 61
@@ -97,11 +98,15 @@ def test_middle_bead_msd_windows_match_oracle(precision, tol):
     b.set_msd_lags(lags)
     b.set_sampling(every)
     b.step(every * (nsamp - 1))
-    mm = (M - 1) // 2
+    mm, mb = (M - 1) // 2, M // 2
     mid = np.zeros((C, len(lags), 2))
     com = np.zeros((C, len(lags), 2))
+    e2e = np.zeros((C, len(lags), 2))
+    bond = np.zeros((C, len(lags), 2))
     snap_m = np.zeros((C, len(lags), 3))
     snap_c = np.zeros((C, len(lags), 3))
+    snap_e = np.zeros((C, len(lags), 3))
+    snap_b = np.zeros((C, len(lags), 3))
     L2 = np.zeros(C)
     power = np.zeros((C, 3, M))
     for k in range(nsamp):
@@ -111,6 +116,7 @@ def test_middle_bead_msd_windows_match_oracle(precision, tol):
             r = m.modes_to_beads(R[c])
             x = r[:, mm] - r.mean(axis=1)
             cm = r.mean(axis=1)
+            L, um = r[:, -1] - r[:, 0], r[:, mb] - r[:, mb - 1]
             L2[c] += np.sum((r[:, -1] - r[:, 0]) ** 2)
             power[c] += R[c] ** 2
             for i, lag in enumerate(lags):
@@ -118,8 +124,12 @@ def test_middle_bead_msd_windows_match_oracle(precision, tol):
                     if k:
                         mid[c, i] += [np.sum((x - snap_m[c, i]) ** 2), 1.0]
                         com[c, i] += [np.sum((cm - snap_c[c, i]) ** 2), 1.0]
+                        e2e[c, i] += [np.sum((L - snap_e[c, i]) ** 2), 1.0]
+                        bond[c, i] += [np.sum((um - snap_b[c, i]) ** 2), 1.0]
                     snap_m[c, i] = x
                     snap_c[c, i] = cm
+                    snap_e[c, i] = L
+                    snap_b[c, i] = um
     d2 = d_nm() ** 2
     g_mid = b.observe(sfp.SFP_OBS_MID_MSD)
     g_com = b.observe(sfp.SFP_OBS_COM_MSD)
@@ -127,6 +137,10 @@ def test_middle_bead_msd_windows_match_oracle(precision, tol):
     assert np.array_equal(g_mid[:, :, 1], mid[:, :, 1]) and np.array_equal(g_com[:, :, 1], com[:, :, 1])
     assert np.abs(g_mid[:, :, 0] / (mid[:, :, 0] * d2) - 1).max() < 10 * tol
     assert np.abs(g_com[:, :, 0] - com[:, :, 0] * d2).max() < 1e-5 * (com[:, :, 0] * d2).max()
+    for what, ref in ((sfp.SFP_OBS_E2E_MSD, e2e), (sfp.SFP_OBS_BOND_MSD, bond)):
+        g = b.observe(what)
+        assert np.array_equal(g[:, :, 1], ref[:, :, 1])
+        assert np.abs(g[:, :, 0] / (ref[:, :, 0] * d2) - 1).max() < 10 * tol
     assert np.abs(b.observe(sfp.SFP_OBS_E2E2_MEAN) / (L2 / nsamp * d2) - 1).max() < tol
     var = b.observe(sfp.SFP_OBS_MODE_VAR)
     assert np.abs(var[:, :, 1:] - power[:, :, 1:] / nsamp).max() < 10 * tol * (power[:, :, 1:] / nsamp).max()
