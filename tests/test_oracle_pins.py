@@ -470,3 +470,23 @@ def test_bond_path_equals_bead_path(M):
     f = v[:, :M] - v[:, 1:]
     bead_path = f @ phi
     assert np.abs(m.delta_H(r) - bead_path).max() < 1e-12 * max(1.0, np.abs(bead_path).max())
+
+
+def test_stored_monte_carlo_reference_is_the_oracles():
+    """tests/golden/mc_reference.txt (the Monte Carlo benchmark the step-size
+    scans compare with) holds what the oracle's sampler gives: the 64-bead row
+    is recomputed here with the writer's settings and must agree to the stored
+    digits (the sampler is deterministic: Philox-keyed proposals)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mc_reference.txt")
+    row = next(line.split() for line in open(path) if line.split() and line.split()[0] == "64")
+    stored = np.array([float(x) for x in row[1:7]])
+    M, Cm = 64, 64
+    m = O.Model(M, dtau=10.0)
+    R = np.stack([m.equilibrium_start(9, j) for j in range(Cm)])
+    step, R = m.mc_tuned_steps(R, 9, np.arange(Cm))
+    R, _, _ = m.run_mc(R, 9, np.arange(Cm), 0, 4000, step)
+    R, _, obs = m.run_mc(R, 9, np.arange(Cm), 4000, 20000, step, sample=True)
+    per = obs[:, :3] / obs[:, 3:4]
+    mine = np.concatenate([per.mean(axis=0), per.std(axis=0, ddof=1) / math.sqrt(Cm)])
+    assert np.allclose(mine, stored, rtol=1e-9, atol=0)
