@@ -597,17 +597,21 @@ def uneven_chains(n=8192, seed=1):
 def uneven_leg(sfp, torch, prec, steps=5000):
     """8192 chains, lengths uniform over 64/128/256/512 bp at their Table 1 steps,
     FP32 state, equilibrium starts: `steps` steps as calls of 1000 (state in L2
-    between the steps of a call), on the tensor-core path as created, after the
-    chains-per-tile autotuner, and autotuned with CUDA-graph replay; and the plain
-    FP32 CUDA-core path on the same chains."""
+    between the steps of a call), on the tensor-core path (all four lengths in
+    one grouped launch of clusters of two CTAs) as created, after the chains-per-tile
+    autotuner, and autotuned with CUDA-graph replay; the same with one launch
+    per group on its own stream; and the plain FP32 CUDA-core path."""
     chains = uneven_chains()
     beads = sum(c["n_beads"] for c in chains)
     stream = torch.cuda.current_stream()
     res = {}
-    for name, p, tune, graph in (("as_created", prec, False, False), ("autotuned", prec, True, False),
-                                 ("autotuned_graph", prec, True, True),
-                                 ("plain_fp32", sfp.SFP_FP32_SIMT, False, True)):
+    for name, p, tune, graph, grouped in (("as_created", prec, False, False, True),
+                                          ("autotuned", prec, True, False, True),
+                                          ("autotuned_graph", prec, True, True, True),
+                                          ("per_group_launches_autotuned_graph", prec, True, True, False),
+                                          ("plain_fp32", sfp.SFP_FP32_SIMT, False, True, True)):
         b = sfp.Batch(chains, seed=1, stream=stream, precision=p)
+        b.set_grouped(grouped)
         b.init_equilibrium(0)
         tiles = b.autotune(20) if tune else None
         b.set_graph(graph)
@@ -624,7 +628,9 @@ def uneven_leg(sfp, torch, prec, steps=5000):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         res[name] = {"value": beads * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
-                     "chains_per_tile": tiles, "graph": graph}
+                     "chains_per_tile": tiles, "graph": graph,
+                     "launch": "one grouped launch (clusters of two CTAs) for all four lengths"
+                     if grouped and p != sfp.SFP_FP32_SIMT else "per group"}
         b.modes()
         b.close()
     best = res["autotuned_graph"]

@@ -201,15 +201,16 @@ enum { SFP_OBS_MODES = 0, SFP_OBS_POSITIONS = 1, SFP_OBS_COM = 2, SFP_OBS_STEP =
        SFP_OBS_BOND_MSD = 12 };
 int sfp_observe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
 
-/* Kernel path of the SFP_FP32 and SFP_MIXED_BF16 steps (other precisions
- * ignore it).
+/* Kernel path of the step (SFP_FP32_SIMT ignores it).
  *   SFP_PATH_FUSED   (default) chains of 64, 128, 256 or 512 beads take one
  *                    kernel per step and group: inverse transform, bond force,
  *                    noise, forward transform and mode update in one launch
  *                    with the intermediates kept on chip (TMEM and shared
  *                    memory; at 512 beads a tile runs on a cluster of two
  *                    CTAs, one per half of the bonds and modes); other lengths
- *                    take the staged path.
+ *                    take the staged path.  SFP_FP64 chains of up to 2048 beads
+ *                    take one CUDA-core kernel per chunk of steps, a CTA per
+ *                    chain with its state in shared memory between steps.
  *   SFP_PATH_STAGED  one kernel per stage; keeps the intermediate arrays, so
  *                    sfp_probe works after the step.
  * Both give the same trajectory within FP32 rounding.  SFP_EINVAL otherwise. */
@@ -231,6 +232,14 @@ int sfp_set_path(sfp_batch *b, int32_t path);
  * out, if not NULL, receives each group's choice (0 for staged groups), in
  * order of first appearance of each (n_beads, dtau) in the chain list. */
 int sfp_set_graph(sfp_batch *b, int32_t enable);
+/* Grouped launch (default on): the length groups on the fused step (at most
+ * one group each of 64, 128, 256 and 512 beads; any others keep launches of
+ * their own) advance together in one launch of clusters of two CTAs: a
+ * cluster runs either one 512-bead tile on both CTAs or two tiles of the other
+ * lengths, one per CTA, and clusters start in order of tile length (longest
+ * first) as SMs free up.  The trajectories are those of one launch per group.
+ * Off: one launch per group, each on its own stream.  Host only. */
+int sfp_set_grouped(sfp_batch *b, int32_t enable);
 int sfp_autotune(sfp_batch *b, int32_t trial_steps, int32_t *chains_per_tile);
 
 /* Integrator of sfp_step.

@@ -146,6 +146,10 @@ class Batch:
         """Replay each chunk of steps from a captured CUDA graph."""
         _lib.check(_lib.load().sfp_set_graph(self._h, int(bool(enable))))
 
+    def set_grouped(self, enable: bool = True) -> None:
+        """One persistent launch for the 64/128/256-bead groups (default), or one launch per group."""
+        _lib.check(_lib.load().sfp_set_grouped(self._h, int(bool(enable))))
+
     def autotune(self, trial_steps: int = 20) -> list:
         """Choose chains per tile of the fused groups by timing; returns them per group."""
         out = (ct.c_int32 * self.n_chains)()          # at most one group per chain

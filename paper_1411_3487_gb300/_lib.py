@@ -30,7 +30,7 @@ EXPORTS = (
     "sfp_set_positions", "sfp_set_step", "sfp_step", "sfp_observe", "sfp_probe", "sfp_save",
     "sfp_load", "sfp_info", "sfp_destroy", "sfp_last_error", "sfp_philox_words",
     "sfp_stage_timing", "sfp_stage_times", "sfp_step_noalloc", "sfp_set_sampling", "sfp_set_msd_lags",
-    "sfp_set_path", "sfp_set_integrator", "sfp_set_graph", "sfp_autotune", "sfp_server_config_default", "sfp_server_create", "sfp_server_submit",
+    "sfp_set_path", "sfp_set_integrator", "sfp_set_graph", "sfp_set_grouped", "sfp_autotune", "sfp_server_config_default", "sfp_server_create", "sfp_server_submit",
     "sfp_server_poll", "sfp_server_result_modes", "sfp_server_wait_idle", "sfp_server_stats",
     "sfp_server_destroy", "sfp_server_last_error",
 )

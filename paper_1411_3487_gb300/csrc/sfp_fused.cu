@@ -282,24 +282,27 @@ __device__ __forceinline__ void noise_put(uint8_t* ah, uint8_t* al, const float 
     }
 }
 
-// The step of the 64-, 128- and 256-bead chains: a tile per CTA.  TWO (BF16
-// only): two passes, A_lo B_hi + A_hi B_hi, the tables taken as their BF16
-// hi part alone (SFP_MIXED_BF16_2).
-template <int NB, bool BF, bool TWO = false>
-__global__ void __launch_bounds__(kThreads, 1)
-k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmChiH,
-             const __grid_constant__ CUtensorMap tmChiL, const __grid_constant__ CUtensorMap tmFH,
-             const __grid_constant__ CUtensorMap tmFL, const FusedArgs a)
+// The step of the 64-, 128- and 256-bead chains: tile `tile` (chains
+// tile * cpt ...) through a.n_steps steps on one CTA.  TWO (BF16 only): two
+// passes, A_lo B_hi + A_hi B_hi, the tables taken as their BF16 hi part alone
+// (SFP_MIXED_BF16_2).  The caller allocates the 2 NB TMEM columns at `tmem`
+// and passes the CTA's 1024-byte-aligned dynamic shared memory.  The barriers
+// are initialised here, and every arrival on them has landed before the
+// function returns (the producer waits for the MMAs' last commits), so a
+// persistent kernel may run another tile in the same shared memory.  Returns
+// false if a wait gave up.
+template <int NB, bool BF, bool TWO>
+__device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtensorMap& tmChiH,
+                                           const CUtensorMap& tmChiL, const CUtensorMap& tmFH,
+                                           const CUtensorMap& tmFL, const FusedArgs& a, int tile, uint8_t* smem,
+                                           uint32_t tmem)
 {
     using S = FSmem<NB, BF, BF>;        // BF16: a separate FP32 R staging area per stage
     constexpr int ST = S::kStages;
     constexpr int KB = NB / kKB;        // inverse K blocks = forward bead blocks
     constexpr int NBLK = 3 * KB;        // blocks of one step, in the order of sched_decode
     static_assert(KB % 2 == 0, "the block schedule pairs bead blocks");
-    constexpr uint32_t kCols = 2 * NB;  // D_u in [0, NB), D_inc in [NB, 2 NB)
 
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* stage0 = smem;
     uint8_t* misc = smem + ST * S::kStage;
     uint32_t* s_job = (uint32_t*)misc;
@@ -316,15 +319,15 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     uint64_t* u_done = bars + 12;       // all inverse MMAs done            (commit)
     uint64_t* inc_done = bars + 13;     // all forward MMAs done            (commit)
     uint64_t* epi_done = bars + 15;     // epilogue stored R, stages free   (every worker warp)
-    uint32_t* tmem_slot = (uint32_t*)(bars + 16);
-    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-    int* s_freed = (int*)(tmem_slot + 2);   // last block whose stage the producer saw released
+    uint32_t* flags = (uint32_t*)(bars + 16);
+    volatile int* abort_flag = (volatile int*)(flags + 1);
+    int* s_freed = (int*)(flags + 2);   // last block whose stage the producer saw released
     uint64_t* r_blk = bars + 18;        // R column block k reloaded for the epilogue (1 + tx), k < KB
     uint64_t* never = bars + 26;        // nothing arrives here (the stall test)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cpq = a.cpt >> 2;         // chains per TMEM lane quarter (rows 32 q + 3 k + axis)
-    const int c0 = blockIdx.x * a.cpt;
+    const int c0 = tile * a.cpt;
     const int Ct = min(a.cpt, a.C - c0);
     const uint32_t rblock = 4u * 3u * (uint32_t)cpq * 128u;   // bytes of one R column block
 
@@ -360,15 +363,9 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         s_shear[i] = live ? a.shear[c0 + i] : 0.0;
         s_rowb[i] = i < a.cpt ? 32 * (i / cpq) + 3 * (i % cpq) : 0;
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(tmem_slot)), "r"(kCols) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
     fence_before();
     __syncthreads();
     fence_after();
-    const uint32_t tmem = *tmem_slot;
     const uint32_t t_u = tmem, t_inc = tmem + NB;
     const bool has_shear = __syncthreads_or(threadIdx.x < Ct && s_shear[threadIdx.x] != 0.0) != 0;
 
@@ -499,6 +496,13 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
             } else {
                 ok = false;
             }
+          }
+          // the MMAs' commits of the last block of each stage have arrived, so
+          // nothing lands on these barriers after the tile (see above)
+          const int G = a.n_steps * NBLK;
+          for (int s = 0; s < ST && s < G && ok; ++s) {
+              const int gl = s + ST * ((G - 1 - s) / ST);
+              ok = mbar_wait(&empty[s], (gl / ST) & 1, a.err, abort_flag);
           }
         }
     } else if (warp == 1) {
@@ -773,19 +777,58 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     }
     fence_before();
     __syncthreads();
-    if (warp == 1) {
+    return *abort_flag == 0;
+}
+
+// TMEM columns for the 2 NB of a tile (warp 1 allocates into *slot).
+template <uint32_t kCols>
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot)
+{
+    if ((threadIdx.x >> 5) == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(slot)), "r"(kCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+}
+template <uint32_t kCols>
+__device__ __forceinline__ void tmem_free(uint32_t tmem)
+{
+    if ((threadIdx.x >> 5) == 1) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
     }
 }
 
-// The 512-bead step: a tile on a cluster of two CTAs, CTA h (its rank) holding
-// bonds and modes 256 h .. 256 h + 255 (see the file's header).
-template <bool BF, bool TWO = false>
+// One tile per CTA (a launch of one length group).
+template <int NB, bool BF, bool TWO = false>
 __global__ void __launch_bounds__(kThreads, 1)
-k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmChiH,
+k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmChiH,
              const __grid_constant__ CUtensorMap tmChiL, const __grid_constant__ CUtensorMap tmFH,
              const __grid_constant__ CUtensorMap tmFL, const FusedArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint32_t s_tmem;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    tmem_alloc<2 * NB>(&s_tmem);
+    const uint32_t tmem = s_tmem;
+    fused_tile<NB, BF, TWO>(tmR, tmChiH, tmChiL, tmFH, tmFL, a, blockIdx.x, smem, tmem);
+    tmem_free<2 * NB>(tmem);
+}
+
+
+// The 512-bead step: tile `tile` on a cluster of two CTAs, CTA h (its rank)
+// holding bonds and modes 256 h .. 256 h + 255 (see the file's header).  The
+// caller launches clusters of two and allocates the 512 TMEM columns at `tmem`;
+// the tile starts and ends with a cluster barrier.  Returns false if a wait
+// gave up.
+template <bool BF, bool TWO>
+__device__ __forceinline__ bool pair_tile(const CUtensorMap& tmR, const CUtensorMap& tmChiH,
+                                          const CUtensorMap& tmChiL, const CUtensorMap& tmFH,
+                                          const CUtensorMap& tmFL, const FusedArgs& a, int tile, uint8_t* smem,
+                                          uint32_t tmem)
 {
     constexpr int NB = 256;             // TMEM columns of each half (D_u, D_inc) of this CTA
     using S = FSmem<NB, BF, false>;
@@ -796,10 +839,7 @@ k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     constexpr int NBLK = 3 * KB;        // blocks of one step, in the order of sched_decode
     constexpr int FILL = BF ? 4 : 1;   // noise blocks in phase 1's tail (measured: BF16 4, TF32 1)
     static_assert(KB % 2 == 0, "the block schedule pairs bead blocks");
-    constexpr uint32_t kCols = 2 * NB;  // D_u in [0, NB), D_inc in [NB, 2 NB)
 
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* stage0 = smem;
     uint8_t* misc = smem + ST * S::kStage;
     uint32_t* s_job = (uint32_t*)misc;
@@ -816,24 +856,19 @@ k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     uint64_t* u_done = bars + 12;       // all inverse MMAs done            (commit)
     uint64_t* inc_done = bars + 13;     // all forward MMAs done            (commit)
     uint64_t* epi_done = bars + 15;     // epilogue stored R, stages free   (every worker warp)
-    uint32_t* tmem_slot = (uint32_t*)(bars + 16);
-    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-    int* s_freed = (int*)(tmem_slot + 2);   // last block whose stage the producer saw released
+    uint32_t* flags = (uint32_t*)(bars + 16);
+    volatile int* abort_flag = (volatile int*)(flags + 1);
+    int* s_freed = (int*)(flags + 2);   // last block whose stage the producer saw released
     uint64_t* r_blk = bars + 18;        // R column block k reloaded for the epilogue (1 + tx), k < KBL
     uint64_t* never = bars + 26;        // nothing arrives here (the stall test)
     uint64_t* both_done = bars + 27;    // the MMAs of both CTAs done with the step (2 commits)
     uint64_t* peer_epi = bars + 28;     // the other CTA's epilogue done (its producer arrives)
 
-    if (cluster_size() != 2u) {
-        // every access to the other CTA below assumes a cluster of two
-        if (threadIdx.x == 0) atomicOr(a.err, 4);
-        return;
-    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cpq = a.cpt >> 2;         // chains per TMEM lane quarter (rows 32 q + 3 k + axis)
     const uint32_t rank = cluster_rank();   // this CTA's bead / mode half
     const int col0 = (int)rank * NB;    // first bond and mode of this CTA's TMEM columns
-    const int c0 = (int)(blockIdx.x >> 1) * a.cpt;
+    const int c0 = tile * a.cpt;
     const int Ct = min(a.cpt, a.C - c0);
     const uint32_t rblock = 4u * 3u * (uint32_t)cpq * 128u;   // bytes of one R column block
 
@@ -871,15 +906,9 @@ k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
         s_shear[i] = live ? a.shear[c0 + i] : 0.0;
         s_rowb[i] = i < a.cpt ? 32 * (i / cpq) + 3 * (i % cpq) : 0;
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(tmem_slot)), "r"(kCols) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
     fence_before();
     cluster_sync();                     // both CTAs' barriers are initialised
     fence_after();
-    const uint32_t tmem = *tmem_slot;
     const uint32_t t_u = tmem, t_inc = tmem + NB;
     const bool has_shear = __syncthreads_or(threadIdx.x < Ct && s_shear[threadIdx.x] != 0.0) != 0;
 
@@ -1372,16 +1401,101 @@ k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     // neither CTA leaves while the other may still copy into or arrive on its shared memory
     __syncwarp();
     cluster_sync();
-    if (warp == 1) {
-        fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
-        if (lane == 0 && *abort_flag) {
-            // after a timeout the other CTA may have issued a copy into this CTA's
-            // stages just before the cluster barrier: let it land before leaving
-            const uint64_t t0 = globaltimer();
-            while (globaltimer() - t0 < 1000000ull) __nanosleep(1000);
-        }
+    return *abort_flag == 0;
+}
+
+// After a pair tile gave up, the other CTA may have issued a copy into this
+// CTA's stages just before the cluster barrier: let it land before leaving.
+__device__ __forceinline__ void pair_abort_grace()
+{
+    if (threadIdx.x == 32) {
+        const uint64_t t0 = globaltimer();
+        while (globaltimer() - t0 < 1000000ull) __nanosleep(1000);
     }
+}
+
+// One 512-bead tile per cluster of two CTAs (a launch of one length group).
+template <bool BF, bool TWO = false>
+__global__ void __launch_bounds__(kThreads, 1)
+k_fused_pair(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmChiH,
+             const __grid_constant__ CUtensorMap tmChiL, const __grid_constant__ CUtensorMap tmFH,
+             const __grid_constant__ CUtensorMap tmFL, const FusedArgs a)
+{
+    if (cluster_size() != 2u) {
+        // every access to the other CTA assumes a cluster of two
+        if (threadIdx.x == 0) atomicOr(a.err, 4);
+        return;
+    }
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint32_t s_tmem;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    tmem_alloc<512>(&s_tmem);
+    const uint32_t tmem = s_tmem;
+    const bool ok = pair_tile<BF, TWO>(tmR, tmChiH, tmChiL, tmFH, tmFL, a, (int)(blockIdx.x >> 1), smem, tmem);
+    tmem_free<512>(tmem);
+    if (!ok) pair_abort_grace();
+}
+
+
+
+// All length groups of a batch on the fused step (at most one group each of
+// 64, 128, 256 and 512 beads) in one launch of clusters of two CTAs: the first
+// clusters each run a 512-bead tile together (pair_tile), every later cluster
+// two tiles of the other lengths, one per CTA (fused_tile), the 256-bead tiles
+// first, then 128, then 64.  Clusters start in index order as SMs free up, so
+// the longest tiles start first and the short ones fill the tail.
+struct GroupSlot {
+    CUtensorMap tmR, tmChiH, tmChiL, tmFH, tmFL;
+    FusedArgs a;
+    int tiles;      // 0: the slot is unused
+};
+struct GroupedArgs {
+    GroupSlot g[4];     // 512, 256, 128, 64 beads
+    int* err;
+};
+
+// A tile of one slot as a call of its own (not inlined), so that each length's
+// body gets its own register allocation.
+template <int NB, bool BF, bool TWO>
+__device__ __noinline__ bool grouped_tile(const GroupSlot& g, int tile, uint8_t* smem, uint32_t tmem)
+{
+    return fused_tile<NB, BF, TWO>(g.tmR, g.tmChiH, g.tmChiL, g.tmFH, g.tmFL, g.a, tile, smem, tmem);
+}
+template <bool BF, bool TWO>
+__device__ __noinline__ bool grouped_pair(const GroupSlot& g, int tile, uint8_t* smem, uint32_t tmem)
+{
+    return pair_tile<BF, TWO>(g.tmR, g.tmChiH, g.tmChiL, g.tmFH, g.tmFL, g.a, tile, smem, tmem);
+}
+
+template <bool BF, bool TWO>
+__global__ void __launch_bounds__(kThreads, 1)
+k_fused_grouped(const __grid_constant__ GroupedArgs P)
+{
+    if (cluster_size() != 2u) {
+        if (threadIdx.x == 0) atomicOr(P.err, 4);
+        return;
+    }
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint32_t s_tmem;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    tmem_alloc<512>(&s_tmem);
+    const uint32_t tmem = s_tmem;
+    const int k = (int)(blockIdx.x >> 1);
+    const int np = P.g[0].tiles;
+    bool ok = true;
+    if (k < np) {
+        ok = grouped_pair<BF, TWO>(P.g[0], k, smem, tmem);
+    } else {
+        const int item = 2 * (k - np) + (int)cluster_rank();
+        const int n1 = P.g[1].tiles, n2 = n1 + P.g[2].tiles, n3 = n2 + P.g[3].tiles;
+        if (item < n1) ok = grouped_tile<256, BF, TWO>(P.g[1], item, smem, tmem);
+        else if (item < n2) ok = grouped_tile<128, BF, TWO>(P.g[2], item - n1, smem, tmem);
+        else if (item < n3) ok = grouped_tile<64, BF, TWO>(P.g[3], item - n2, smem, tmem);
+    }
+    fence_before();
+    __syncthreads();
+    tmem_free<512>(tmem);
+    if (!ok && k < np) pair_abort_grace();
 }
 
 }  // namespace
@@ -1398,6 +1512,15 @@ struct FusedPlan {
 static int round_tile(int cpt) { return std::min(kChains, std::max(4, (cpt + 3) / 4 * 4)); }
 
 bool fused_supported(int M) { return M == 64 || M == 128 || M == 256 || M == 512; }
+
+// Dynamic shared memory of the grouped kernel: that of its largest tile.
+static int grouped_smem(bool bf16)
+{
+    return bf16 ? std::max({FSmem<256, true, true>::kBytes, FSmem<128, true, true>::kBytes, FSmem<64, true, true>::kBytes,
+                            FSmem<256, true, false>::kBytes})
+                : std::max({FSmem<256, false, false>::kBytes, FSmem<128, false, false>::kBytes,
+                            FSmem<64, false, false>::kBytes});
+}
 
 template <int NB, bool BF, bool TWO = false>
 static cudaError_t set_smem()
@@ -1504,6 +1627,10 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
     else
         e = M == 512 ? set_smem_pair<false>() : M == 256 ? set_smem<256, false>() :
             M == 128 ? set_smem<128, false>() : set_smem<64, false>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(p->two ? k_fused_grouped<true, true> : bf16 ? k_fused_grouped<true, false>
+                                                                             : k_fused_grouped<false, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, grouped_smem(bf16));
     if (e != cudaSuccess) {
         fused_destroy(p);
         return report(SFP_ECUDA, "cudaFuncSetAttribute (fused step) failed");
@@ -1558,6 +1685,46 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
     }
 #undef SFP_FUSED_LAUNCH
     if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return report(SFP_ECUDA, cudaGetErrorString(e));
+    return SFP_OK;
+}
+
+bool fused_groupable(const FusedPlan* p) { return p != nullptr; }
+
+int fused_step_grouped(FusedPlan* const* plans, const FusedArgs* args, int n, cudaStream_t stream)
+{
+    if (n < 1 || n > 4) return report(SFP_EINVAL, "grouped step: 1 to 4 plans");
+    GroupedArgs P;
+    std::memset(&P, 0, sizeof P);
+    const bool bf = plans[0]->bf16, two = plans[0]->two;
+    for (int i = 0; i < n; ++i) {
+        const FusedPlan* p = plans[i];
+        const int slot = p->M == 512 ? 0 : p->M == 256 ? 1 : p->M == 128 ? 2 : p->M == 64 ? 3 : -1;
+        if (slot < 0 || P.g[slot].tiles || p->bf16 != bf || p->two != two || args[i].cpt != p->cpt ||
+            args[i].n_steps != args[0].n_steps)
+            return report(SFP_EINVAL, "grouped step: one plan each of 64, 128, 256, 512 beads, one arithmetic");
+        GroupSlot& g = P.g[slot];
+        g.tmR = p->tmR; g.tmChiH = p->tmChiH; g.tmChiL = p->tmChiL; g.tmFH = p->tmFH; g.tmFL = p->tmFL;
+        g.a = args[i];
+        g.tiles = (p->C + p->cpt - 1) / p->cpt;
+    }
+    P.err = args[0].err;
+    const int small = P.g[1].tiles + P.g[2].tiles + P.g[3].tiles;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2u * (unsigned)(P.g[0].tiles + (small + 1) / 2));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = grouped_smem(bf);
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = two ? cudaLaunchKernelEx(&cfg, k_fused_grouped<true, true>, P)
+                        : bf ? cudaLaunchKernelEx(&cfg, k_fused_grouped<true, false>, P)
+                             : cudaLaunchKernelEx(&cfg, k_fused_grouped<false, false>, P);
     if (e != cudaSuccess) return report(SFP_ECUDA, cudaGetErrorString(e));
     return SFP_OK;
 }

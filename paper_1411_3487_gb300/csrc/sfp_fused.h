@@ -51,6 +51,14 @@ int fused_ctas_per_tile(const FusedPlan* plan);
 // Device bytes the plan's tables hold.
 size_t fused_bytes(const FusedPlan* plan);
 int fused_set_tile(FusedPlan* plan, int cpt);
+// True for plans that the grouped launch takes (every fused plan).
+bool fused_groupable(const FusedPlan* plan);
+// One launch of clusters of two CTAs for up to four plans of different lengths
+// (64, 128, 256, 512) and the same arithmetic, with the args each would get
+// from fused_step (the same n_steps): the 512-bead tiles first (a cluster
+// each), then the others two per cluster, longest first.  Same trajectories as
+// one fused_step per plan.
+int fused_step_grouped(FusedPlan* const* plans, const FusedArgs* args, int n, cudaStream_t stream);
 void fused_destroy(FusedPlan* plan);
 
 }  // namespace sfp

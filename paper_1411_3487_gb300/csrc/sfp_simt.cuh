@@ -252,6 +252,111 @@ k_mode_update(T* __restrict__ R, const T* __restrict__ DH, const T* __restrict__
     }
 }
 
+// ---------------------------------------------------------------------------
+// The whole mode-space step (Sec. 4) of one chain per CTA, n_steps per launch,
+// on the CUDA cores (the FP64 path): the state stays in shared memory between
+// steps, so a small batch (one chain) pays no launch per step.  Per step:
+//   thread n (bead):  u_n = sum_p chi_{n,p} R_p (Eq. e5, all three axes from one
+//                     pass over chiT[p][n]), v_n = u_n (1/|u_n| - (1 - 2nu)),
+//                     v_0 = 0 (Eq. e11); threads c < 3M/4 draw Philox call c of
+//                     the step (four bead normals, Eq. b5)
+//   thread p (mode):  DeltaH_p = sum_n chi_{n,p} v_n, Z_p = sum_n phi_{n,p} z_n
+//                     (Eqs. e11, c4), then R_p += -dm_p R_p + h_p DeltaH_p + w_p Z_p
+//                     and the shear term g_p R^y_p on x (Eqs. d3, d6, f2, btum);
+//                     p = 0 moves the FP64 centre of mass.
+// Tables: chiT [p][n], chi [n][p], phi [n][p] (global, read through L1).  Shared
+// memory: R, v, z as [3][M] each.  A chain advances only while step < stop.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_chain_steps(T* __restrict__ Rg, double* __restrict__ com, int64_t* __restrict__ step,
+              const int64_t* __restrict__ stop, const uint32_t* __restrict__ job,
+              const double* __restrict__ shear, const T* __restrict__ chiT, const T* __restrict__ chi,
+              const T* __restrict__ phi, const T* __restrict__ dm, const T* __restrict__ h,
+              const T* __restrict__ w, const T* __restrict__ g, int C, int M, T c12nu, double w0_cm,
+              double dtau, uint32_t seed, int n_steps, int* __restrict__ bad)
+{
+    extern __shared__ unsigned char chain_smem[];
+    T* sR = reinterpret_cast<T*>(chain_smem);     // [3][M]
+    T* sv = sR + 3 * M;                           // [3][M]
+    T* sz = sv + 3 * M;                           // [3][M]
+    __shared__ double s_cm[3];
+    const int c = blockIdx.x;
+    if (c >= C) return;
+    T* Rc = Rg + (size_t)c * 3 * M;
+    for (int i = threadIdx.x; i < 3 * M; i += blockDim.x) sR[i] = Rc[i];
+    if (threadIdx.x < 3) s_cm[threadIdx.x] = com[3 * c + threadIdx.x];
+    const uint32_t jb = job[c];
+    const double sh = shear[c];
+    const T shT = (T)sh;
+    const int64_t st0 = step[c];
+    const int64_t lim = stop ? stop[c] : INT64_MAX;
+    const int n_calls = (3 * M + 3) >> 2;
+    bool fin = true;
+    __syncthreads();
+    int s = 0;
+    for (; s < n_steps && st0 + s < lim; ++s) {
+        // bond vectors, bond forces, bead normals
+        for (int n = threadIdx.x; n < M; n += blockDim.x) {
+            T u0 = T(0), u1 = T(0), u2 = T(0);
+            for (int p = 1; p < M; ++p) {
+                const T x = chiT[(size_t)p * M + n];
+                u0 = fma(x, sR[p], u0);
+                u1 = fma(x, sR[M + p], u1);
+                u2 = fma(x, sR[2 * M + p], u2);
+            }
+            const T uu[3] = {u0, u1, u2};
+            T vv[3];
+            residual_v<T>(uu, n >= 1, c12nu, vv);
+            sv[n] = vv[0]; sv[M + n] = vv[1]; sv[2 * M + n] = vv[2];
+        }
+        for (int k = threadIdx.x; k < n_calls; k += blockDim.x) {
+            T gq[4];
+            Normals<T>::draw4(seed, jb, st0 + s, (uint32_t)k, 0u, gq);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int q = 4 * k + e;
+                if (q < 3 * M) sz[(q % 3) * M + q / 3] = gq[e];
+            }
+        }
+        __syncthreads();
+        // forward transform and update, all three axes of mode p
+        for (int p = threadIdx.x; p < M; p += blockDim.x) {
+            T d0 = T(0), d1 = T(0), d2 = T(0), z0 = T(0), z1 = T(0), z2 = T(0);
+            for (int n = 0; n < M; ++n) {
+                const T x = chi[(size_t)n * M + p], f = phi[(size_t)n * M + p];
+                d0 = fma(x, sv[n], d0);
+                d1 = fma(x, sv[M + n], d1);
+                d2 = fma(x, sv[2 * M + n], d2);
+                z0 = fma(f, sz[n], z0);
+                z1 = fma(f, sz[M + n], z1);
+                z2 = fma(f, sz[2 * M + n], z2);
+            }
+            if (p == 0) {
+                // centre of mass (zeta_0 = 0, Eq. d6 limit; w0_cm = w_0 / sqrt(M)), shear on x
+                const double ycm = s_cm[1];
+                s_cm[0] += w0_cm * (double)z0 + sh * dtau * ycm;
+                s_cm[1] += w0_cm * (double)z1;
+                s_cm[2] += w0_cm * (double)z2;
+            } else {
+                const T r0 = sR[p], r1 = sR[M + p], r2 = sR[2 * M + p];
+                const T dd = dm[p], hh = h[p], ww = w[p];
+                T o0 = r0 + fma(-dd, r0, fma(hh, d0, ww * z0));
+                const T o1 = r1 + fma(-dd, r1, fma(hh, d1, ww * z1));
+                const T o2 = r2 + fma(-dd, r2, fma(hh, d2, ww * z2));
+                if (shT != T(0)) o0 += shT * g[p] * r1;
+                fin = fin && isfinite(o0) && isfinite(o1) && isfinite(o2);
+                sR[p] = o0; sR[M + p] = o1; sR[2 * M + p] = o2;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < 3 * M; i += blockDim.x) Rc[i] = (i % M == 0) ? T(0) : sR[i];
+    if (threadIdx.x < 3) com[3 * c + threadIdx.x] = s_cm[threadIdx.x];
+    if (threadIdx.x == 0) step[c] = st0 + s;
+    if (!fin) atomicOr(bad, 1);
+}
+
 // step[c] += 1 for chains still below their stop step (after k_mode_update).
 __global__ void k_advance_steps(int64_t* __restrict__ step, const int64_t* __restrict__ stop, int C)
 {

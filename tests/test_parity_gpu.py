@@ -372,6 +372,42 @@ def test_bf16_fused_step_against_the_oracle(M, C):
         fused.probe(sfp.SFP_PROBE_DH)
 
 
+def test_fp64_one_kernel_per_chain_against_the_oracle():
+    """SFP_FP64 on SFP_PATH_FUSED: one CUDA-core kernel per chunk of steps, a CTA
+    per chain with its state in shared memory.  Mixed lengths (3, 67 and the
+    paper's four), mixed shear: 150 steps in one call equal 150 calls of one
+    step bit for bit, match the oracle to 1e-9 and the staged FP64 kernels to
+    1e-11; probes refuse the fused step."""
+    lengths = [3, 64, 67, 128, 256, 512, 64]
+    dt = {3: 5.0, 64: 10.0, 67: 10.0, 128: 50.0, 256: 100.0, 512: 100.0}
+    rates = [0.0, 1.54e8, 0.0, 5e7, 0.0, 1e8, 0.0]
+    chains = [{"n_beads": M, "dtau": dt[M], "shear_rate_per_s": r, "job_id": 300 + i}
+              for i, (M, r) in enumerate(zip(lengths, rates))]
+    starts_ = [O.Model(M, dtau=dt[M]).equilibrium_start(4, 300 + i) for i, M in enumerate(lengths)]
+    out = []
+    for path, split in ((sfp.SFP_PATH_FUSED, False), (sfp.SFP_PATH_FUSED, True), (sfp.SFP_PATH_STAGED, False)):
+        b = sfp.Batch(chains, seed=4, precision=sfp.SFP_FP64)
+        b.set_path(path)
+        b.set_modes(starts_)
+        if split:
+            for _ in range(150):
+                b.step(1)
+        else:
+            b.step(150)
+        out.append(b.modes())
+        assert np.all(b.observe(sfp.SFP_OBS_STEP) == 150)
+        if path == sfp.SFP_PATH_FUSED:
+            with pytest.raises(sfp.SfpError):
+                b.probe(sfp.SFP_PROBE_DH)
+        b.close()
+    for i, M in enumerate(lengths):
+        assert np.array_equal(out[0][i], out[1][i]), i
+        ref = O.Model(M, dtau=dt[M]).run_modes(starts_[i][None], 4, [300 + i], 0, 150, shear=shear_tau(rates[i]))
+        assert rel_err(out[0][i][None], ref)[0] < 1e-9, (i, rel_err(out[0][i][None], ref)[0])
+        assert rel_err(out[0][i][None], out[2][i][None])[0] < 1e-11, i
+        assert abs(out[0][i][0, 0] - ref[0, 0, 0]) < 1e-9 * math.sqrt(M)
+
+
 @pytest.mark.parametrize("M,C", [(256, 50), (512, 12), (100, 7)])
 def test_bf16_two_pass_against_the_oracle(M, C):
     """SFP_MIXED_BF16_2: two passes (A_lo B_hi + A_hi B_hi), the tables rounded

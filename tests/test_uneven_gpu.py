@@ -1,6 +1,7 @@
-"""Uneven-length batches (64/128/256/512 bp, Table 1 steps): groups on their
-own streams, CUDA-graph replay of step chunks, and the chains-per-tile
-autotuner.  None of them may change a trajectory."""
+"""Uneven-length batches (64/128/256/512 bp, Table 1 steps): the grouped
+launch of all four length groups in clusters of two CTAs (or one launch per
+group on its own stream), CUDA-graph replay of step chunks, and the
+chains-per-tile autotuner.  None of them may change a trajectory."""
 import numpy as np
 import pytest
 
@@ -26,8 +27,9 @@ def mixed(C, seed=3):
              "shear_rate_per_s": 0.0 if i % 3 else 5e7} for i, M in enumerate(lengths)]
 
 
-def run(chains, steps, graph=False, autotune=False):
-    b = sfp.Batch(chains, seed=7)
+def run(chains, steps, graph=False, autotune=False, grouped=True, precision=sfp.SFP_FP32):
+    b = sfp.Batch(chains, seed=7, precision=precision)
+    b.set_grouped(grouped)
     b.init_equilibrium(0)
     tiles = None
     if autotune:
@@ -54,10 +56,29 @@ def test_graph_replay_and_autotune_leave_trajectories_unchanged():
         assert all(np.array_equal(x, y) for x, y in zip(a[0], b[0]))
         assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
     assert np.all(ref[2] == 200)
-    # a replay counts the kernels it runs: every group is fused (512 bp on clusters
-    # of two CTAs), so a chunk is one launch per group with or without graphs
+    # a replay counts the kernels it runs: all four length groups are one
+    # grouped launch (clusters of two CTAs), so a chunk is one launch with or
+    # without graphs
     assert gr[3] == ref[3]
     assert len(tiles) == 4 and all(4 <= t <= 40 and t % 4 == 0 for t in tiles)
+
+
+@pytest.mark.parametrize("precision", [sfp.SFP_FP32, sfp.SFP_MIXED_BF16, sfp.SFP_MIXED_BF16_2],
+                         ids=["tf32x3", "bf16x3", "bf16x2"])
+def test_grouped_launch_equals_one_launch_per_group(precision):
+    """The grouped launch (clusters of two CTAs: a 512-bp tile per cluster, or two
+    tiles of the other lengths) computes each tile exactly as the launch of its
+    own group does: the same trajectories bit for bit, with and without graph
+    replay, and one launch instead of four per chunk of steps."""
+    chains = mixed(700, seed=5)
+    (grp, _) = run(chains, 200, grouped=True, precision=precision)
+    (sep, _) = run(chains, 200, grouped=False, precision=precision)
+    (grg, _) = run(chains, 200, grouped=True, graph=True, precision=precision)
+    for other in (sep, grg):
+        assert all(np.array_equal(x, y) for x, y in zip(grp[0], other[0]))
+        assert np.array_equal(grp[1], other[1]) and np.array_equal(grp[2], other[2])
+    assert np.all(grp[2] == 200)
+    assert sep[3] - grp[3] == 3 * 3        # three calls, three launches fewer each
 
 
 def test_concurrent_groups_match_the_oracle():
