@@ -3,7 +3,7 @@
 Workload: 4096 independent 256-bp dsDNA chains, FP32 state, dt = 15.9 ps
 (dtau ~ 100, Table 2), equilibrium-sampled starts, zero shear, per-chain
 Philox streams.  A bench "step" is one Langevin step of the whole batch
-(inverse transform, force + noise, forward transform, mode update).  The K
+(inverse transform, bond force, bead noise, forward transform, mode update).  The K
 timed steps run as sfp_step calls of --steps-per-call steps (20; one fused
 launch each) with the L2 flushed before every call; the one-step-per-call
 figure is reported beside it.
@@ -223,9 +223,12 @@ def run_native(args, rank, world, local):
     if precision == sfp.SFP_FP32_SIMT:
         path = sfp.SFP_PATH_STAGED
 
-    def timed_steps(prec, pth, steps, warmup, with_clocks, per_call=1):
+    def timed_steps(prec, pth, steps, warmup, with_clocks, per_call=1, stages=True):
         """`steps` timed Langevin steps as sfp_step calls of `per_call` steps,
-        the L2 flushed before every call; returns per-call times (ms)."""
+        the L2 flushed before every call; returns per-call times (ms).  With
+        `stages`, per-stage CUDA events are recorded inside the calls (which runs
+        the staged path's noise kernel in line instead of beside the inverse
+        transform); without, the kernel times come from a second, untimed pass."""
         b = sfp.Batch(chains, seed=1, precision=prec, stream=stream)
         b.set_path(pth)
         b.init_equilibrium(0)
@@ -241,7 +244,7 @@ def run_native(args, rank, world, local):
             dist.barrier()
         torch.cuda.synchronize()
         clk = ClockSampler(local) if with_clocks else None
-        b.stage_timing(True)                  # per-stage CUDA events on the batch's stream
+        b.stage_timing(stages)                # per-stage CUDA events on the batch's stream
         for (e0, e1), n in zip(ev, calls):
             flush.zero_()                     # L2 flushed between timed calls
             e0.record(stream)
@@ -252,6 +255,11 @@ def run_native(args, rank, world, local):
         if world > 1:
             dist.barrier()
         launches = b.info()["launches"] - launches0
+        if not stages:
+            b.stage_timing(True)
+            for n in calls:
+                flush.zero_()
+                b.step(n)
         kern = b.stage_times()
         b.stage_timing(False)
         ms = [a.elapsed_time(c) for a, c in ev]
@@ -302,9 +310,15 @@ def run_native(args, rank, world, local):
         n_o = min(args.steps, 100)
 
         def leg(prec, pth, per_call, what):
-            _, ms_l, _, _, k_l = timed_steps(prec, pth, n_o, 3, False, per_call)
-            return {"value": beads * n_o / (sum(ms_l) * 1e-3), "unit": UNIT, "ms_per_step": float(sum(ms_l) / n_o),
-                    "steps_per_call": per_call, "kernels_us": k_l, "path": what}
+            staged_path = pth == sfp.SFP_PATH_STAGED
+            _, ms_l, _, _, k_l = timed_steps(prec, pth, n_o, 3, False, per_call, stages=not staged_path)
+            out = {"value": beads * n_o / (sum(ms_l) * 1e-3), "unit": UNIT, "ms_per_step": float(sum(ms_l) / n_o),
+                   "steps_per_call": per_call, "kernels_us": k_l, "path": what}
+            if staged_path:
+                out["kernels_us_note"] = ("per-kernel times from a second pass with stage events, the noise "
+                                          "kernel in line; the timed pass runs it beside the inverse transform")
+                out["hbm"] = staged_hbm(k_l, pk)
+            return out
 
         plain = leg(sfp.SFP_FP32_SIMT, sfp.SFP_PATH_STAGED, spc, "plain FP32 CUDA-core path")
         if path == sfp.SFP_PATH_FUSED:
@@ -502,6 +516,23 @@ def roofline(kern, pk, how, precision, path, sfp):
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
 
 
+def staged_hbm(kern, pk):
+    """HBM roofline of the staged step's streaming kernels from their live times:
+    bond force 12 B read + 12 B written per bead, bead noise 12 B written (bound
+    by its Philox arithmetic, listed for completeness), mode update 36 B read +
+    12 B written."""
+    beads = C_CHAINS * M_BEADS
+    peak = pk.get("hbm_gbs", 6800.0)
+    out = {"peak_gbs": peak}
+    for name, key, per_bead in (("k_force", "force_us", 24), ("k_noise", "noise_us", 12),
+                                ("k_mode_update", "update_us", 48)):
+        us = kern.get(key)
+        if us:
+            gbs = per_bead * beads / (us * 1e-6) / 1e9
+            out[name] = {"us": us, "algorithmic_bytes": per_bead * beads, "achieved_gbs": gbs, "frac": gbs / peak}
+    return out
+
+
 def end_to_end(sfp, b, torch, steps):
     """Per step: H2D of the FP64 mode state from pinned host memory (sfp_set_modes),
     one sfp_step, D2H of the FP64 mode state (sfp_observe); wall-clock timed."""
@@ -563,7 +594,7 @@ def tf32_peak(torch) -> float:
 
 def config1_leg(sfp, torch):
     """One 64-bp chain, FP64 on the GPU, dt = 1.59 ps (dtau 10), 2e4 steps from an
-    equilibrium start (CUDA-graph replay of the staged FP64 kernels); beside it the
+    equilibrium start (one kernel per chain running the steps of a call); beside it the
     default bead-position Euler scheme of the same chain at dtau = 0.1 (Sec. 3A)."""
     out = {"workload": "1 chain x 64 bp, FP64, dt 1.59 ps (dtau 10), 2e4 steps, equilibrium start"}
     for name, dtau, integ, n in (("mode_space", 10.0, sfp.SFP_INTEGRATOR_MODES, 20000),

@@ -305,15 +305,17 @@ int sfp_load(sfp_batch *b, const void *host_buf, size_t bytes);
 int sfp_info(const sfp_batch *b, int64_t out[4]);
 
 /* Stage timing.  While enabled, every sfp_step records CUDA events on the
- * batch's stream between its stage launches (inverse transform, force and
- * noise, forward transform, mode update).  Enabling clears the totals.
- * sfp_stage_times synchronises the stream and writes the summed device time
- * in microseconds of [inverse, force+noise, forward, update, whole step]
- * over *n_group_steps recorded group-steps (one per length group per step).
- * A fused step (SFP_PATH_FUSED) is one kernel: its whole time is counted in
- * the first entry and in the whole-step entry. */
+ * batch's stream between its stage launches (inverse transform, bond force,
+ * bead noise, forward transform, mode update); the noise kernel then runs in
+ * line on the batch's stream instead of beside the inverse transform on a
+ * stream of its own, and the length groups one after another.  Enabling clears
+ * the totals.  sfp_stage_times synchronises the stream and writes the summed
+ * device time in microseconds of [inverse, force, noise, forward, update,
+ * whole step] over *n_group_steps recorded group-steps (one per length group
+ * per step).  A fused step (SFP_PATH_FUSED) is one kernel: its whole time is
+ * counted in the first entry and in the whole-step entry. */
 int sfp_stage_timing(sfp_batch *b, int32_t enable);
-int sfp_stage_times(sfp_batch *b, double out_us[5], int64_t *n_group_steps);
+int sfp_stage_times(sfp_batch *b, double out_us[6], int64_t *n_group_steps);
 
 /* Free every device buffer of the batch (synchronises its stream). NULL is a no-op. */
 int sfp_destroy(sfp_batch *b);

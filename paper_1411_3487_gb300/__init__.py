@@ -221,11 +221,11 @@ class Batch:
 
     def stage_times(self) -> dict:
         """Average device time per group-step of each stage, in microseconds."""
-        out = (ct.c_double * 5)()
+        out = (ct.c_double * 6)()
         n = ct.c_int64()
         _lib.check(_lib.load().sfp_stage_times(self._h, out, ct.byref(n)))
         k = max(1, n.value)
-        names = ("inverse_us", "force_noise_us", "forward_us", "update_us", "step_us")
+        names = ("inverse_us", "force_us", "noise_us", "forward_us", "update_us", "step_us")
         d = {nm: out[i] / k for i, nm in enumerate(names)}
         d["group_steps"] = n.value
         return d

@@ -158,6 +158,10 @@ void rod_tables(int M, double nu, std::vector<double>* l0, std::vector<double>* 
 
 int sfp::report(int code, const char* msg) { return fail(code, "%s", msg); }
 
+// Stage timing: events 0..kLastMark of one group-step, around the stages
+// inverse, force, noise, forward, update (a fused step records 0 and kLastMark).
+constexpr int kMarks = 6, kLastMark = kMarks - 1;
+
 struct Group {
     int M = 0;
     double dtau = 0.0;
@@ -191,6 +195,8 @@ struct Group {
     bool last_fused = false;      // the most recent step of this group ran fused
     cudaStream_t gs = nullptr;    // this group's stream (batches of several groups)
     cudaEvent_t join = nullptr;
+    cudaStream_t ns = nullptr;    // the staged step's noise kernel, beside the inverse transform
+    cudaEvent_t nfork = nullptr, njoin = nullptr;
     // observable sampling (allocated by the first sfp_set_sampling)
     double* obs_tab = nullptr;    // [3][M] rows: phi_N - phi_0, chi_m, phi_m' (p >= 1)
     double* acc_shape = nullptr;  // [C][4]
@@ -234,11 +240,11 @@ struct sfp_batch {
     int* bad = nullptr;
     // stage timing
     bool timing = false;
-    std::vector<cudaEvent_t> events;   // pool, 5 per recorded group-step
-    std::vector<char> ev_fused;        // per recorded group-step: events 0 and 4 only
+    std::vector<cudaEvent_t> events;   // pool, kMarks per recorded group-step
+    std::vector<char> ev_fused;        // per recorded group-step: events 0 and kLastMark only
     std::vector<int64_t> ev_steps;     // per recorded group-step: steps it covered
     size_t ev_used = 0;
-    double stage_us[5] = {0, 0, 0, 0, 0};
+    double stage_us[kMarks] = {0, 0, 0, 0, 0, 0};   // inverse, force, noise, forward, update, step
     int64_t timed_group_steps = 0;
     // observable sampling
     int32_t sample_every = 0;      // 0 = off
@@ -325,18 +331,26 @@ int stall_test()
     return v && v[0] == '1' ? 1 : 0;
 }
 
-// Launch the staged bond force + noise kernel: one thread per chain and quad
-// of beads (float4 rows when M % 4 == 0).
+// Launch the staged bond force kernel: one thread per chain and quad of bonds
+// (float4 rows when M % 4 == 0).
 template <typename T>
-cudaError_t launch_force_noise(cudaStream_t st, const T* u, T* v, T* z, int C, int M, T c12nu, uint32_t seed,
-                               const uint32_t* job, const int64_t* step)
+cudaError_t launch_force(cudaStream_t st, const T* u, T* v, int C, int M, T c12nu)
 {
-    constexpr int QPT = 1;   // quads per thread (two were measured slower: 14.5 against 12.6 us at 4096 x 256)
-    const unsigned grid = nblk((int64_t)C * (((M + 3) / 4 + QPT - 1) / QPT), 128);
+    const unsigned grid = nblk((int64_t)C * ((M + 3) / 4), 256);
     if (sizeof(T) == 4 && M % 4 == 0)
-        sfp::k_force_noise<T, true, QPT><<<grid, 128, 0, st>>>(u, v, z, C, M, c12nu, seed, job, step);
+        sfp::k_force<T, true><<<grid, 256, 0, st>>>(u, v, C, M, c12nu);
     else
-        sfp::k_force_noise<T, false, QPT><<<grid, 128, 0, st>>>(u, v, z, C, M, c12nu, seed, job, step);
+        sfp::k_force<T, false><<<grid, 256, 0, st>>>(u, v, C, M, c12nu);
+    return cudaGetLastError();
+}
+
+// Launch the bead noise kernel: one thread per chain and Philox call.
+template <typename T>
+cudaError_t launch_noise(cudaStream_t st, T* z, int C, int M, uint32_t seed, const uint32_t* job,
+                         const int64_t* step)
+{
+    const unsigned grid = nblk((int64_t)C * ((3 * M + 3) / 4), 256);
+    sfp::k_noise<T><<<grid, 256, 0, st>>>(z, C, M, seed, job, step);
     return cudaGetLastError();
 }
 
@@ -370,8 +384,8 @@ cudaError_t launch_mode_update(cudaStream_t st, T* R, const T* DH, const T* ZM, 
 int mark(sfp_batch* b, int k, bool fused = false, int64_t steps = 1)
 {
     if (!b->timing) return SFP_OK;
-    if (k == 4) {
-        const size_t gs = b->ev_used / 5;
+    if (k == kLastMark) {
+        const size_t gs = b->ev_used / kMarks;
         if (b->ev_fused.size() <= gs) b->ev_fused.resize(gs + 1);
         if (b->ev_steps.size() <= gs) b->ev_steps.resize(gs + 1);
         b->ev_fused[gs] = fused;
@@ -384,7 +398,7 @@ int mark(sfp_batch* b, int k, bool fused = false, int64_t steps = 1)
         b->events.push_back(e);
     }
     CUDA_TRY(cudaEventRecord(b->events[idx], b->cur));
-    if (k == 4) b->ev_used += 5;
+    if (k == kLastMark) b->ev_used += kMarks;
     return SFP_OK;
 }
 
@@ -393,21 +407,21 @@ int harvest(sfp_batch* b)
 {
     if (b->ev_used == 0) return SFP_OK;
     CUDA_TRY(cudaStreamSynchronize(b->stream));
-    for (size_t i = 0; i < b->ev_used; i += 5) {
-        const bool fused = i / 5 < b->ev_fused.size() && b->ev_fused[i / 5];
+    for (size_t i = 0; i < b->ev_used; i += kMarks) {
+        const bool fused = i / kMarks < b->ev_fused.size() && b->ev_fused[i / kMarks];
         float ms = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&ms, b->events[i], b->events[i + 4]));
-        b->stage_us[4] += 1e3 * ms;
+        CUDA_TRY(cudaEventElapsedTime(&ms, b->events[i], b->events[i + kLastMark]));
+        b->stage_us[kLastMark] += 1e3 * ms;
         if (fused) {
             b->stage_us[0] += 1e3 * ms;
         } else {
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < kLastMark; ++k) {
                 float mk = 0.f;
                 CUDA_TRY(cudaEventElapsedTime(&mk, b->events[i + k], b->events[i + k + 1]));
                 b->stage_us[k] += 1e3 * mk;
             }
         }
-        b->timed_group_steps += (i / 5 < b->ev_steps.size()) ? b->ev_steps[i / 5] : 1;
+        b->timed_group_steps += (i / kMarks < b->ev_steps.size()) ? b->ev_steps[i / kMarks] : 1;
     }
     b->ev_used = 0;
     return SFP_OK;
@@ -446,7 +460,7 @@ int step_group_fused(sfp_batch* b, Group& g, int64_t n_steps)
     if ((rc = sfp::fused_step(g.fused, a, b->cur))) return rc;
     b->launches++;
     g.last_fused = true;
-    return mark(b, 4, true, n_steps);
+    return mark(b, kLastMark, true, n_steps);
 }
 
 // Groups on the fused step (at most one each of 64, 128, 256 and 512 beads)
@@ -498,7 +512,7 @@ int step_group_chain(sfp_batch* b, Group& g, int64_t n_steps)
     CUDA_TRY(cudaGetLastError());
     b->launches++;
     g.last_fused = true;   // no stage arrays to probe
-    return mark(b, 4, true, n_steps);
+    return mark(b, kLastMark, true, n_steps);
 }
 
 template <typename T>
@@ -513,26 +527,40 @@ int step_group(sfp_batch* b, Group& g)
     T* yz = (T*)g.yz;
     int rc;
     if ((rc = mark(b, 0))) return rc;
+    // a3: the bead noise depends on the step counters alone, so it runs on a
+    // stream of its own beside a1 and a2 (serially while stages are timed)
+    const bool side = !b->timing;
+    if (side) {
+        CUDA_TRY(cudaEventRecord(g.nfork, b->cur));
+        CUDA_TRY(cudaStreamWaitEvent(g.ns, g.nfork, 0));
+        CUDA_TRY(launch_noise<T>(g.ns, fz + n, C, M, b->seed, g.job, g.step));
+        CUDA_TRY(cudaEventRecord(g.njoin, g.ns));
+        b->launches++;
+    }
     // a1: modes -> bond vectors u = chi R  (Eqs. c1, e5; the centre of mass drops out)
     if (g.tc) rc = sfp::tc_transform(g.tc, 0, b->cur);
     else rc = launch_gemm<T>(b, R, (const T*)g.chi, r, 3 * C, M, M);
     if (rc) return rc;
     if (g.tc) b->launches++;
     if ((rc = mark(b, 1))) return rc;
-    // a2 + a3: residual bond force v (Eq. e11) and bead noise
-    {
-        const T c12 = (T)(1.0 - 2.0 * b->dv.nu);
-        CUDA_TRY(launch_force_noise<T>(b->cur, r, fz, fz + n, C, M, c12, b->seed, g.job, g.step));
+    // a2: residual bond force v (Eq. e11)
+    CUDA_TRY(launch_force<T>(b->cur, r, fz, C, M, (T)(1.0 - 2.0 * b->dv.nu)));
+    b->launches++;
+    if ((rc = mark(b, 2))) return rc;
+    if (side) {
+        CUDA_TRY(cudaStreamWaitEvent(b->cur, g.njoin, 0));
+    } else {
+        CUDA_TRY(launch_noise<T>(b->cur, fz + n, C, M, b->seed, g.job, g.step));
         b->launches++;
     }
-    if ((rc = mark(b, 2))) return rc;
+    if ((rc = mark(b, 3))) return rc;
     // a4: DeltaH = chi^T v (Eq. e11), Z = phi^T z (Eq. c4): the forward transform
     if (g.tc) rc = sfp::tc_transform(g.tc, 1, b->cur);
     else if (!(rc = launch_gemm<T>(b, fz, (const T*)g.chiT, yz, 3 * C, M, M)))
         rc = launch_gemm<T>(b, fz + n, (const T*)g.phiT, yz + n, 3 * C, M, M);
     if (rc) return rc;
     if (g.tc) b->launches++;
-    if ((rc = mark(b, 3))) return rc;
+    if ((rc = mark(b, 4))) return rc;
     // a5: mode update (Eqs. d3, d6, f2, btum)
     CUDA_TRY(launch_mode_update<T>(b->cur, R, yz, yz + n, g.com, g.step, (const T*)g.dm, (const T*)g.h,
                                    (const T*)g.w, (const T*)g.g, g.shear, C, M, g.tab.w0, g.dtau, b->bad,
@@ -543,7 +571,7 @@ int step_group(sfp_batch* b, Group& g)
         b->launches++;
         CUDA_TRY(cudaGetLastError());
     }
-    return mark(b, 4);
+    return mark(b, kLastMark);
 }
 
 // One sample of observables i-iii, the mode power and the centre-of-mass
@@ -609,7 +637,7 @@ int step_group_euler(sfp_batch* b, Group& g, int64_t n_steps)
     }
     if ((rc = launch_gemm<T>(b, (const T*)g.r, (const T*)g.psiT, (T*)g.R, 3 * C, M, M))) return rc;
     g.last_fused = true;   // no stage arrays to probe
-    return mark(b, 4, true, n_steps);
+    return mark(b, kLastMark, true, n_steps);
 }
 
 constexpr int64_t kMaxFusedSteps = 1024;   // steps per fused launch
@@ -814,8 +842,12 @@ int destroy_impl(sfp_batch* b)
         if (g.gs) cudaStreamSynchronize(g.gs);
         if (g.tc) sfp::tc_destroy(g.tc);
         if (g.fused) sfp::fused_destroy(g.fused);
+        if (g.ns) cudaStreamSynchronize(g.ns);
         if (g.gs) cudaStreamDestroy(g.gs);
         if (g.join) cudaEventDestroy(g.join);
+        if (g.ns) cudaStreamDestroy(g.ns);
+        if (g.nfork) cudaEventDestroy(g.nfork);
+        if (g.njoin) cudaEventDestroy(g.njoin);
     }
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
@@ -1083,7 +1115,11 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
         cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
         for (auto& g : b->groups) {
-            if (e != cudaSuccess || b->groups.size() < 2) break;
+            if (e != cudaSuccess) break;
+            e = cudaStreamCreateWithFlags(&g.ns, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.nfork, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.njoin, cudaEventDisableTiming);
+            if (e != cudaSuccess || b->groups.size() < 2) continue;
             e = cudaStreamCreateWithFlags(&g.gs, cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming);
         }
@@ -1464,12 +1500,12 @@ int sfp_stage_timing(sfp_batch* b, int32_t enable)
     return SFP_OK;
 }
 
-int sfp_stage_times(sfp_batch* b, double out_us[5], int64_t* n_group_steps)
+int sfp_stage_times(sfp_batch* b, double out_us[6], int64_t* n_group_steps)
 {
     if (!b || !out_us) return fail(SFP_EINVAL, "NULL argument");
     int rc = harvest(b);
     if (rc) return rc;
-    for (int k = 0; k < 5; ++k) out_us[k] = b->stage_us[k];
+    for (int k = 0; k < kMarks; ++k) out_us[k] = b->stage_us[k];
     if (n_group_steps) *n_group_steps = b->timed_group_steps;
     return SFP_OK;
 }
@@ -1786,7 +1822,8 @@ int sfp_step_noalloc(const sfp_params* params, const sfp_chain_desc* chain, int3
     int* bad = (int*)(base + o_bad);   // written by the update kernel, not reported here
     for (int64_t s = 0; s < n_steps; ++s) {
         CUDA_TRY(gemm_on<float>(st, modes_dev, chi, r, 3 * C, M, M));
-        CUDA_TRY(launch_force_noise<float>(st, r, fz, fz + n, C, M, c12, (uint32_t)seed, job, step));
+        CUDA_TRY(launch_force<float>(st, r, fz, C, M, c12));
+        CUDA_TRY(launch_noise<float>(st, fz + n, C, M, (uint32_t)seed, job, step));
         CUDA_TRY(gemm_on<float>(st, fz, chiT, yz, 3 * C, M, M));
         CUDA_TRY(gemm_on<float>(st, fz + n, phiT, yz + n, 3 * C, M, M));
         CUDA_TRY(launch_mode_update<float>(st, modes_dev, yz, yz + n, com_dev, step, dm, h, w, g, shear, C, M, w0,

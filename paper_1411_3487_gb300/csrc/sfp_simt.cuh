@@ -70,15 +70,15 @@ k_gemm_nt(const T* __restrict__ In, const T* __restrict__ B, T* __restrict__ Out
 }
 
 // ---------------------------------------------------------------------------
-// Residual bond force + bead noise (Eqs. e4, e5, e11, b5), from bond vectors:
+// Residual bond force (Eqs. e4, e5, e11), from bond vectors:
 //   u_n = sum_p chi_{n,p} R_p (given, n >= 1; slot 0 holds 0),
 //   v_n = u_n (1/|u_n| - (1 - 2nu)) for n >= 1, v_0 = 0,
 // so that DeltaH_p = sum_n chi_{n,p} v_n (Eq. e11) is the forward transform of
-// v with the table chi^T; z = the bead normals of (seed, job, step, tag 0).
-// The bond form needs no neighbour: each bond's force is its own.
-// One thread per chain and quad of beads 4t .. 4t+3 (the three Philox calls
-// of those beads' twelve normals); threads of a warp take consecutive quads,
-// so each axis row moves as one coalesced run of float4 (VEC: M % 4 == 0).
+// v with the table chi^T.  The bond form needs no neighbour: each bond's force
+// is its own, and the kernel is a stream of 12 B read and 12 B written per
+// bond.  One thread per chain and quad of bonds 4t .. 4t+3; threads of a warp
+// take consecutive quads, so each axis row moves as one coalesced run of
+// float4 (VEC: M % 4 == 0).
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void residual_v(const T u[3], bool ok, T c12nu, T v[3])
@@ -89,12 +89,15 @@ __device__ __forceinline__ void residual_v(const T u[3], bool ok, T c12nu, T v[3
     for (int a = 0; a < 3; ++a) v[a] = u[a] * s;
 }
 
-// One quad: beads n0 .. n0 + 3 of the chain whose arrays start at base.
 template <typename T, bool VEC>
-__device__ __forceinline__ void force_noise_quad(const T* __restrict__ ub, T* __restrict__ vb, T* __restrict__ z,
-                                                 size_t base, int n0, int M, T c12nu, uint32_t seed, uint32_t job,
-                                                 int64_t step)
+__global__ void __launch_bounds__(256)
+k_force(const T* __restrict__ ub, T* __restrict__ vb, int C, int M, T c12nu)
 {
+    const int Q = (M + 3) >> 2;                    // bond quads per chain
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)C * Q) return;
+    const int c = (int)(t / Q), n0 = 4 * (int)(t - (int64_t)c * Q);
+    const size_t base = (size_t)c * 3 * M;
     T u[3][4];
     if constexpr (VEC) {
 #pragma unroll
@@ -108,8 +111,6 @@ __device__ __forceinline__ void force_noise_quad(const T* __restrict__ ub, T* __
 #pragma unroll
             for (int i = 0; i < 4; ++i) u[a][i] = n0 + i < M ? ub[base + (size_t)a * M + n0 + i] : T(0);
     }
-    T g[3][4];
-    bead_quad_normals<T>(seed, job, step, (uint32_t)(n0 >> 2), 0u, g);
     T v[3][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -121,43 +122,42 @@ __device__ __forceinline__ void force_noise_quad(const T* __restrict__ ub, T* __
     }
     if constexpr (VEC) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
+        for (int a = 0; a < 3; ++a)
             *reinterpret_cast<float4*>(vb + base + (size_t)a * M + n0) = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
-            *reinterpret_cast<float4*>(z + base + (size_t)a * M + n0) = make_float4(g[a][0], g[a][1], g[a][2], g[a][3]);
-        }
     } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if (n0 + i < M) {
-                    vb[base + (size_t)a * M + n0 + i] = v[a][i];
-                    z[base + (size_t)a * M + n0 + i] = g[a][i];
-                }
+                if (n0 + i < M) vb[base + (size_t)a * M + n0 + i] = v[a][i];
     }
 }
 
-// QPT consecutive quads per thread (their Philox calls are independent, so
-// they interleave); the last group of a chain may hold fewer.
-template <typename T, bool VEC, int QPT>
-__global__ void __launch_bounds__(128)
-k_force_noise(const T* __restrict__ ub, T* __restrict__ vb, T* __restrict__ z,
-              int C, int M, T c12nu, uint32_t seed, const uint32_t* __restrict__ job,
-              const int64_t* __restrict__ step)
+// ---------------------------------------------------------------------------
+// Bead noise (Eq. b5): z = the bead normals of (seed, job, step, tag 0); normal
+// k = 3 n + alpha of a chain and step is value k % 4 of Philox call k / 4.
+// One thread per chain and Philox call: its four normals land on two or three
+// neighbouring beads, so the threads of a warp write ~43 consecutive beads of
+// each axis row.  Bound by the Philox / Box-Muller arithmetic, not by its
+// 12 B per bead; it does not depend on the state, so the staged step runs it
+// beside the inverse transform.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_noise(T* __restrict__ z, int C, int M, uint32_t seed, const uint32_t* __restrict__ job,
+        const int64_t* __restrict__ step)
 {
-    const int Q = (M + 3) >> 2;                    // bead quads per chain
-    const int G = (Q + QPT - 1) / QPT;             // groups of QPT quads per chain
+    const int K = (3 * M + 3) >> 2;                // Philox calls per chain and step
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)C * G) return;
-    const int c = (int)(t / G), q0 = (int)(t - (int64_t)c * G) * QPT;
-    const size_t base = (size_t)c * 3 * M;
-    const uint32_t jb = job[c];
-    const int64_t st = step[c];
-    if (q0 + QPT <= Q) {
+    if (t >= (int64_t)C * K) return;
+    const int c = (int)(t / K), call = (int)(t - (int64_t)c * K);
+    T g[4];
+    Normals<T>::draw4(seed, job[c], step[c], (uint32_t)call, 0u, g);
+    T* zc = z + (size_t)c * 3 * M;
 #pragma unroll
-        for (int j = 0; j < QPT; ++j) force_noise_quad<T, VEC>(ub, vb, z, base, 4 * (q0 + j), M, c12nu, seed, jb, st);
-    } else {
-        for (int q = q0; q < Q; ++q) force_noise_quad<T, VEC>(ub, vb, z, base, 4 * q, M, c12nu, seed, jb, st);
+    for (int e = 0; e < 4; ++e) {
+        const int k = 4 * call + e, n = k / 3;
+        if (n < M) zc[(size_t)(k - 3 * n) * M + n] = g[e];
     }
 }
 
@@ -207,43 +207,56 @@ k_mode_update(T* __restrict__ R, const T* __restrict__ DH, const T* __restrict__
 {
     const int p0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
     if (p0 >= M) return;
-    T d[V], hh[V], ww[V], gg[V];
-    load_v<T, V>(dm + p0, d);
-    load_v<T, V>(h + p0, hh);
-    load_v<T, V>(w + p0, ww);
-    load_v<T, V>(g + p0, gg);
     for (int c = blockIdx.y * blockDim.y + threadIdx.y; c < C; c += gridDim.y * blockDim.y) {
-        if (stop && step[c] >= stop[c]) continue;
+        // every load of the chain first (one memory round trip), the stop test after
         const size_t b = (size_t)c * 3 * M + p0;
-        const double sh = shear[c];
-        const T shT = (T)sh;                 // one conversion per chain
-        T r[3][V], y[3][V], zz[3][V];
+        T r[3][V], y[3][V], zz[3][V], d[V], hh[V], ww[V], gg[V];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             load_v<T, V>(R + b + (size_t)a * M, r[a]);
             load_v<T, V>(DH + b + (size_t)a * M, y[a]);
             load_v<T, V>(ZM + b + (size_t)a * M, zz[a]);
         }
+        load_v<T, V>(dm + p0, d);
+        load_v<T, V>(h + p0, hh);
+        load_v<T, V>(w + p0, ww);
+        load_v<T, V>(g + p0, gg);
+        const double sh = shear[c];
+        const bool run = !stop || step[c] < stop[c];
+        double cm[3] = {0.0, 0.0, 0.0};
+        if (p0 == 0) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) cm[a] = com[3 * c + a];
+        }
+        if (!run) continue;
+        // the FP64 shear rate is converted only for sheared chains (an integer test
+        // of its bits: +0 and -0 mean no shear)
+        const bool sheared = (__double_as_longlong(sh) << 1) != 0;
         T o[3][V];
         bool fin = true;
 #pragma unroll
         for (int i = 0; i < V; ++i) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) o[a][i] = r[a][i] + fma(-d[i], r[a][i], fma(hh[i], y[a][i], ww[i] * zz[a][i]));
-            if (shT != T(0)) o[0][i] += shT * gg[i] * r[1][i];
 #pragma unroll
             for (int a = 0; a < 3; ++a) fin = fin && isfinite(o[a][i]);
+        }
+        if (sheared) {
+            const T shT = (T)sh;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                o[0][i] += shT * gg[i] * r[1][i];
+                fin = fin && isfinite(o[0][i]);
+            }
         }
         if (p0 == 0) {
             // p = 0: the centre of mass in FP64 (zeta_0 = 0, Eq. d6 limit w_0;
             // w0_cm = w_0 / sqrt(M))
-            const double ycm = com[3 * c + 1];
+            com[3 * c] = cm[0] + w0_cm * (double)zz[0][0] + sh * dtau * cm[1];
+            com[3 * c + 1] = cm[1] + w0_cm * (double)zz[1][0];
+            com[3 * c + 2] = cm[2] + w0_cm * (double)zz[2][0];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                com[3 * c + a] += w0_cm * (double)zz[a][0];
-                o[a][0] = r[a][0];
-            }
-            com[3 * c] += sh * dtau * ycm;
+            for (int a = 0; a < 3; ++a) o[a][0] = r[a][0];
             if (!stop) step[c] += 1;
         }
         if (!fin) atomicOr(bad, 1);
