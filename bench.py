@@ -370,6 +370,15 @@ def run_native(args, rank, world, local):
                 big[name]["kernel"] = "k_fused_pair<%s>" % ({sfp.SFP_MIXED_BF16: "bf16", sfp.SFP_MIXED_BF16_2: "bf16, two passes"}.get(prec, "tf32"))
                 big[name]["roofline_tensor_frac"] = (passes * 18 * 512 * 16384 * 512 / (1e-3 * t_ms / n)) / 1e12 / (
                     pk["bf16_tflops"] if bf else pk.get("tf32_tflops") or pk["bf16_tflops"] * 1.1 / 2.25)
+            elif prec == sfp.SFP_MIXED_BF16:
+                # per-kernel times of the staged step at this size (stage events, noise in line)
+                bb.stage_timing(True)
+                for _ in range(calls):
+                    flush.zero_()
+                    bb.step(20)
+                big[name]["kernels_us"] = bb.stage_times()
+                bb.stage_timing(False)
+                big[name]["hbm"] = staged_hbm(big[name]["kernels_us"], pk, 16384 * 512)
             bb.modes()      # raises if a kernel reported an error
             bb.close()
         del flush
@@ -516,12 +525,12 @@ def roofline(kern, pk, how, precision, path, sfp):
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
 
 
-def staged_hbm(kern, pk):
+def staged_hbm(kern, pk, beads=None):
     """HBM roofline of the staged step's streaming kernels from their live times:
     bond force 12 B read + 12 B written per bead, bead noise 12 B written (bound
     by its Philox arithmetic, listed for completeness), mode update 36 B read +
     12 B written."""
-    beads = C_CHAINS * M_BEADS
+    beads = beads or C_CHAINS * M_BEADS
     peak = pk.get("hbm_gbs", 6800.0)
     out = {"peak_gbs": peak}
     for name, key, per_bead in (("k_force", "force_us", 24), ("k_noise", "noise_us", 12),
