@@ -302,6 +302,7 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
     constexpr int KB = NB / kKB;        // inverse K blocks = forward bead blocks
     constexpr int NBLK = 3 * KB;        // blocks of one step, in the order of sched_decode
     static_assert(KB % 2 == 0, "the block schedule pairs bead blocks");
+    static_assert(ST <= NBLK, "the last ST blocks of a step release every stage");
 
     uint8_t* stage0 = smem;
     uint8_t* misc = smem + ST * S::kStage;
@@ -485,16 +486,25 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
                     tma_load_2d(bl, &tmFL, &full[s], nb * kKB, noise ? NB : 0);
                 }
             }
-            // every stage is free once the forward MMAs are done: reload the R tile
-            // (KB column blocks of [128 rows][32]) there for the epilogue
-            if (ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag)) {
-                for (int k = 0; k < KB; ++k) {
+            // reload the R tile (KB column blocks of [128 rows][32]) into the stage
+            // memory for the epilogue: column block k as soon as every stage its
+            // bytes overlap has seen the last MMA of this step (the last ST blocks
+            // release the stages in turn), not only after the last MMA of all
+            unsigned freed = 0;
+            int k = 0;
+            for (int j = NBLK - ST; j < NBLK && ok; ++j) {
+                const int gl = sp * NBLK + j, sl = gl % ST;
+                if (!mbar_wait(&empty[sl], (gl / ST) & 1, a.err, abort_flag)) { ok = false; break; }
+                freed |= 1u << sl;
+                for (; k < KB; ++k) {
+                    const int s_lo = k * S::kRT / S::kStage, s_hi = ((k + 1) * S::kRT - 1) / S::kStage;
+                    bool all = true;
+                    for (int t = s_lo; t <= s_hi; ++t) all = all && ((freed >> t) & 1u);
+                    if (!all) break;
                     mbar_expect_tx(&r_blk[k], rblock);
                     for (int q = 0; q < 4; ++q)
                         tma_load_2d(stage0 + k * S::kRT + q * kQuarter, &tmR, &r_blk[k], k * kKB, 3 * (c0 + q * cpq));
                 }
-            } else {
-                ok = false;
             }
           }
           // the MMAs' commits of the last block of each stage have arrived, so
