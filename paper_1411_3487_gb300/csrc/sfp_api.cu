@@ -195,6 +195,9 @@ struct Group {
     bool last_fused = false;      // the most recent step of this group ran fused
     cudaStream_t gs = nullptr;    // this group's stream (batches of several groups)
     cudaEvent_t join = nullptr;
+    double* znoise = nullptr;     // FP64 cluster path: bead normals of znoise_steps steps [s][C][3][M]
+    int znoise_steps = 0;
+    int chain_g = -1;             // FP64 path: CTAs per chain (16, 8, or 0: one CTA per chain); -1 not chosen yet
     cudaStream_t ns = nullptr;    // the staged step's noise kernel, beside the inverse transform
     cudaEvent_t nfork = nullptr, njoin = nullptr;
     // observable sampling (allocated by the first sfp_set_sampling)
@@ -495,6 +498,66 @@ bool one_launch(const sfp_batch* b, const Group& g)
 
 // n_steps FP64 steps of a group in one launch of k_chain_steps (a CTA per chain,
 // state in shared memory between steps); recorded as one fused stage.
+// The most bytes of pre-drawn bead normals the FP64 cluster path keeps.
+constexpr size_t kNoiseStepBytes = (size_t)32 << 20;
+
+// Launch k_chain_cluster<G> (clusters of G CTAs, one per chain) for k steps.
+template <int G>
+cudaError_t launch_chain_cluster(sfp_batch* b, Group& g, size_t smem, double c12, double w0cm, int k)
+{
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(sfp::k_chain_cluster<G>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(G * g.C));
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = b->cur;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = G;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sfp::k_chain_cluster<G>, (double*)g.R, g.com, g.step,
+                              (const int64_t*)(g.limited ? g.stop : nullptr), (const double*)g.shear,
+                              (const double*)g.chiT, (const double*)g.chi, (const double*)g.phi_d,
+                              (const double*)g.dm, (const double*)g.h, (const double*)g.w, (const double*)g.g, g.C,
+                              g.M, c12, w0cm, g.dtau, k, (const double*)g.znoise, b->bad);
+}
+
+// CTAs per chain for the FP64 cluster path: 16 (a non-portable cluster size)
+// when the GPU can place such clusters for this shape, else 8; 0 when the
+// batch has too many chains for one cluster each.
+int chain_cluster_size(const Group& g, size_t smem, int sms)
+{
+    if ((int64_t)g.C * 16 <= sms &&
+        cudaFuncSetAttribute(sfp::k_chain_cluster<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess &&
+        (smem <= 48 * 1024 || cudaFuncSetAttribute(sfp::k_chain_cluster<16>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                                  cudaSuccess)) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(16u * (unsigned)g.C);
+        cfg.blockDim = dim3(128);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 16;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, sfp::k_chain_cluster<16>, &cfg) == cudaSuccess && n >= 1) return 16;
+        cudaGetLastError();
+    }
+    return (int64_t)g.C * 8 <= sms ? 8 : 0;
+}
+
 int step_group_chain(sfp_batch* b, Group& g, int64_t n_steps)
 {
     int rc;
@@ -503,14 +566,48 @@ int step_group_chain(sfp_batch* b, Group& g, int64_t n_steps)
     if (smem > 48 * 1024)
         CUDA_TRY(cudaFuncSetAttribute(sfp::k_chain_steps<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-    const int threads = std::min(256, (g.M + 31) / 32 * 32);
-    sfp::k_chain_steps<double><<<g.C, threads, smem, b->cur>>>(
-        (double*)g.R, g.com, g.step, g.limited ? g.stop : nullptr, g.job, g.shear, (const double*)g.chiT,
-        (const double*)g.chi, g.phi_d, (const double*)g.dm, (const double*)g.h, (const double*)g.w,
-        (const double*)g.g, g.C, g.M, 1.0 - 2.0 * b->dv.nu, g.tab.w0 / std::sqrt((double)g.M), g.dtau, b->seed,
-        (int)n_steps, b->bad);
+    const double c12 = 1.0 - 2.0 * b->dv.nu, w0cm = g.tab.w0 / std::sqrt((double)g.M);
+    int dev = 0, sms = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // few chains: a cluster of CTAs per chain, so that each chain uses several SMs;
+    // the bead normals of up to kNoiseStepBytes of steps are drawn beforehand in
+    // one kernel (the buffer is allocated on first use, outside stream capture)
+    if (g.chain_g < 0) g.chain_g = chain_cluster_size(g, smem, sms);
+    const int G = g.chain_g;
+    bool cluster = G > 0;
+    if (cluster && !g.znoise) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CUDA_TRY(cudaStreamIsCapturing(b->cur, &cs));
+        if (cs == cudaStreamCaptureStatusNone) {
+            const size_t per_step = (size_t)g.C * 3 * g.M * sizeof(double);
+            g.znoise_steps = (int)std::max<size_t>(1, std::min<size_t>(1024, kNoiseStepBytes / per_step));
+            if ((rc = dalloc_t(b, &g.znoise, per_step * g.znoise_steps))) return rc;
+        } else {
+            cluster = false;
+        }
+    }
+    if (cluster) {
+        for (int64_t done = 0; done < n_steps;) {
+            const int k = (int)std::min<int64_t>(g.znoise_steps, n_steps - done);
+            const int K = (3 * g.M + 3) / 4;
+            sfp::k_noise_steps<<<nblk((int64_t)k * g.C * K, 256), 256, 0, b->cur>>>(g.znoise, g.C, g.M, b->seed,
+                                                                                   g.job, g.step, k);
+            CUDA_TRY(cudaGetLastError());
+            CUDA_TRY(G == 16 ? launch_chain_cluster<16>(b, g, smem, c12, w0cm, k)
+                             : launch_chain_cluster<8>(b, g, smem, c12, w0cm, k));
+            b->launches += 2;
+            done += k;
+        }
+    } else {
+        const int threads = std::min(256, (g.M + 31) / 32 * 32);
+        sfp::k_chain_steps<double><<<g.C, threads, smem, b->cur>>>(
+            (double*)g.R, g.com, g.step, g.limited ? g.stop : nullptr, g.job, g.shear, (const double*)g.chiT,
+            (const double*)g.chi, g.phi_d, (const double*)g.dm, (const double*)g.h, (const double*)g.w,
+            (const double*)g.g, g.C, g.M, c12, w0cm, g.dtau, b->seed, (int)n_steps, b->bad);
+        b->launches++;
+    }
     CUDA_TRY(cudaGetLastError());
-    b->launches++;
     g.last_fused = true;   // no stage arrays to probe
     return mark(b, kLastMark, true, n_steps);
 }
@@ -1102,6 +1199,20 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
             rc = sfp::fused_create(&g.fused, M, g.C, g.tab.chi.data(), g.tab.phi.data(), g.tab.h.data(), w.data(),
                                    (float*)g.R, b->stream, bf16, two);
             if (rc) { destroy_impl(b); return rc; }
+        }
+        if (precision == SFP_FP64 && M <= kChainMaxBeads) {
+            // the FP64 chain path: a cluster of CTAs per chain for few chains, with
+            // its buffer of pre-drawn normals allocated here, outside any capture
+            int dev = 0, sms = 0;
+            e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) { destroy_impl(b); return fail(SFP_ECUDA, "create: %s", cudaGetErrorString(e)); }
+            g.chain_g = chain_cluster_size(g, (size_t)9 * M * sizeof(double), sms);
+            if (g.chain_g > 0) {
+                const size_t per_step = (size_t)g.C * 3 * M * sizeof(double);
+                g.znoise_steps = (int)std::max<size_t>(1, std::min<size_t>(1024, kNoiseStepBytes / per_step));
+                if ((rc = dalloc_t(b, &g.znoise, per_step * g.znoise_steps))) { destroy_impl(b); return rc; }
+            }
         }
         b->held += sfp::tc_bytes(g.tc) + sfp::fused_bytes(g.fused);
         if (b->budget && b->held > b->budget) {

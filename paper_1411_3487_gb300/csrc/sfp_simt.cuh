@@ -370,6 +370,191 @@ k_chain_steps(T* __restrict__ Rg, double* __restrict__ com, int64_t* __restrict_
     if (!fin) atomicOr(bad, 1);
 }
 
+// ---------------------------------------------------------------------------
+// The same FP64 step for a few chains, each on a cluster of G CTAs, so that a
+// chain uses the FP64 units of G SMs: CTA r of a chain's cluster owns bonds
+// and modes r S .. r S + S - 1 (S = ceil(M / G)) and keeps full copies of R,
+// v and z in its shared memory; each owner writes its slice into every CTA of
+// the cluster (distributed shared memory).  Per step:
+//   owner r:  u_n, v_n of its bonds (Eqs. e5, e11), written to every CTA;
+//             every CTA copies the step's bead normals (Eq. b5), drawn for
+//             all the steps of the launch beforehand by k_noise_steps, from
+//             zpre[s] into its shared memory;
+//   cluster barrier;
+//   owner r:  DeltaH_p, Z_p of its modes (Eqs. e11, c4), the update of R_p
+//             (Eqs. d3, d6, f2, btum; rank 0 the FP64 centre of mass), R_p
+//             written to every CTA;
+//   cluster barrier.
+// Q threads share the sums of one bond or mode (Q a power of 2 within a warp),
+// and the groups are dealt round-robin over the four warps: GB300 issues FP64
+// arithmetic at a small fraction of the FP32 rate on each SM sub-partition, so
+// the work must reach all four of them.  The FP64 Box-Muller of a Philox call
+// is a long dependent chain there (~5 us), so the normals come from a separate
+// kernel that draws every call of every step at once.  Every CTA
+// of a cluster runs the same number of steps (one chain), so the hardware
+// cluster barriers always meet.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_cta_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// *p in the shared memory of CTA `rank` of the cluster (p: this CTA's own copy).
+__device__ __forceinline__ void st_peer(const double* p, uint32_t rank, double v)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(r), "d"(v) : "memory");
+}
+
+template <int G>
+__global__ void __launch_bounds__(128)
+k_chain_cluster(double* __restrict__ Rg, double* __restrict__ com, int64_t* __restrict__ step,
+                const int64_t* __restrict__ stop, const double* __restrict__ shear, const double* __restrict__ chiT,
+                const double* __restrict__ chi, const double* __restrict__ phi, const double* __restrict__ dm,
+                const double* __restrict__ h, const double* __restrict__ w, const double* __restrict__ g, int C,
+                int M, double c12nu, double w0_cm, double dtau, int n_steps, const double* __restrict__ zpre,
+                int* __restrict__ bad)
+{
+    extern __shared__ unsigned char chain_smem[];
+    double* sR = reinterpret_cast<double*>(chain_smem);   // [3][M]
+    double* sv = sR + 3 * M;                              // [3][M]
+    double* sz = sv + 3 * M;                              // [3][M]
+    __shared__ double s_cm[3];
+    const uint32_t rank = cluster_cta_rank();
+    const int c = blockIdx.x / G;                         // the cluster's chain (c < C: grid = G C)
+    const int S = (M + G - 1) / G;
+    const int lo = min(M, (int)rank * S), hi = min(M, lo + S), nown = hi - lo;
+    int Q = 1;
+    while (Q < 32 && 2 * Q * max(nown, 1) <= (int)blockDim.x) Q *= 2;
+    const int nwarp = (int)blockDim.x / 32, wid = (int)threadIdx.x / 32, lane = (int)threadIdx.x % 32;
+    const int grp = (lane / Q) * nwarp + wid, j = lane % Q, nG = (int)blockDim.x / Q;
+    // every thread runs the same passes over the owned bonds / modes (groups past
+    // nown compute zeros), so the shuffles always see full warps
+    const int passes = (nown + nG - 1) / nG;
+    double* Rc = Rg + (size_t)c * 3 * M;
+    for (int i = threadIdx.x; i < 3 * M; i += blockDim.x) sR[i] = Rc[i];
+    if (threadIdx.x < 3) s_cm[threadIdx.x] = com[3 * c + threadIdx.x];
+    const double sh = shear[c];
+    const int64_t st0 = step[c];
+    const int64_t lim = stop ? stop[c] : INT64_MAX;
+    bool fin = true;
+    // every CTA of the cluster runs (and has loaded R) before any remote write
+    cluster_barrier();
+    int s = 0;
+    for (; s < n_steps && st0 + s < lim; ++s) {
+        const double* zs = zpre + ((size_t)s * C + c) * 3 * M;
+        for (int i = threadIdx.x; i < 3 * M; i += blockDim.x) sz[i] = zs[i];
+        for (int pass = 0; pass < passes; ++pass) {
+            const int gi = pass * nG + grp;
+            const bool act = gi < nown;
+            const int n = act ? lo + gi : 0;
+            double u0 = 0.0, u1 = 0.0, u2 = 0.0;
+            for (int p = 1 + j; act && p < M; p += Q) {
+                const double x = chiT[(size_t)p * M + n];
+                u0 = fma(x, sR[p], u0);
+                u1 = fma(x, sR[M + p], u1);
+                u2 = fma(x, sR[2 * M + p], u2);
+            }
+            for (int o = Q / 2; o > 0; o >>= 1) {
+                u0 += __shfl_xor_sync(0xffffffffu, u0, o);
+                u1 += __shfl_xor_sync(0xffffffffu, u1, o);
+                u2 += __shfl_xor_sync(0xffffffffu, u2, o);
+            }
+            const double uu[3] = {u0, u1, u2};
+            double vv[3];
+            residual_v<double>(uu, n >= 1, c12nu, vv);
+            for (int r = j; act && r < G; r += Q)
+                for (int a = 0; a < 3; ++a) st_peer(&sv[a * M + n], (uint32_t)r, vv[a]);
+        }
+        cluster_barrier();
+        for (int pass = 0; pass < passes; ++pass) {
+            const int gi = pass * nG + grp;
+            const bool act = gi < nown;
+            const int p = act ? lo + gi : 0;
+            double d0 = 0.0, d1 = 0.0, d2 = 0.0, z0 = 0.0, z1 = 0.0, z2 = 0.0;
+            for (int n = j; act && n < M; n += Q) {
+                const double x = chi[(size_t)n * M + p], f = phi[(size_t)n * M + p];
+                d0 = fma(x, sv[n], d0);
+                d1 = fma(x, sv[M + n], d1);
+                d2 = fma(x, sv[2 * M + n], d2);
+                z0 = fma(f, sz[n], z0);
+                z1 = fma(f, sz[M + n], z1);
+                z2 = fma(f, sz[2 * M + n], z2);
+            }
+            for (int o = Q / 2; o > 0; o >>= 1) {
+                d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+                d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+                d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+                z0 += __shfl_xor_sync(0xffffffffu, z0, o);
+                z1 += __shfl_xor_sync(0xffffffffu, z1, o);
+                z2 += __shfl_xor_sync(0xffffffffu, z2, o);
+            }
+            if (!act) {
+                // a group past the owned modes: nothing to update
+            } else if (p == 0) {
+                // centre of mass (zeta_0 = 0, Eq. d6 limit; w0_cm = w_0 / sqrt(M)), shear on x
+                if (j == 0) {
+                    const double ycm = s_cm[1];
+                    s_cm[0] += w0_cm * z0 + sh * dtau * ycm;
+                    s_cm[1] += w0_cm * z1;
+                    s_cm[2] += w0_cm * z2;
+                }
+            } else {
+                const double r0 = sR[p], r1 = sR[M + p], r2 = sR[2 * M + p];
+                const double dd = dm[p], hh = h[p], ww = w[p];
+                double o0 = r0 + fma(-dd, r0, fma(hh, d0, ww * z0));
+                const double o1 = r1 + fma(-dd, r1, fma(hh, d1, ww * z1));
+                const double o2 = r2 + fma(-dd, r2, fma(hh, d2, ww * z2));
+                if (sh != 0.0) o0 += sh * g[p] * r1;
+                fin = fin && isfinite(o0) && isfinite(o1) && isfinite(o2);
+                for (int r = j; r < G; r += Q) {
+                    st_peer(&sR[p], (uint32_t)r, o0);
+                    st_peer(&sR[M + p], (uint32_t)r, o1);
+                    st_peer(&sR[2 * M + p], (uint32_t)r, o2);
+                }
+            }
+        }
+        cluster_barrier();
+    }
+    // each CTA writes back its own modes; rank 0 the centre of mass and the counter
+    for (int i = threadIdx.x; i < 3 * nown; i += blockDim.x) {
+        const int a = i / nown, p = lo + i % nown;
+        Rc[a * M + p] = p == 0 ? 0.0 : sR[a * M + p];
+    }
+    if (rank == 0 && threadIdx.x < 3) com[3 * c + threadIdx.x] = s_cm[threadIdx.x];
+    if (rank == 0 && threadIdx.x == 0) step[c] = st0 + s;
+    if (!fin) atomicOr(bad, 1);
+}
+
+// Bead normals of n_steps consecutive steps for the FP64 cluster path (Eq. b5):
+// z[s][c][3][M] = the normals of chain c at step step[c] + s, one thread per
+// (step, chain, Philox call).
+__global__ void __launch_bounds__(256)
+k_noise_steps(double* __restrict__ z, int C, int M, uint32_t seed, const uint32_t* __restrict__ job,
+              const int64_t* __restrict__ step, int n_steps)
+{
+    const int K = (3 * M + 3) >> 2;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_steps * C * K) return;
+    const int call = (int)(t % K);
+    const int64_t sc = t / K;
+    const int c = (int)(sc % C), s = (int)(sc / C);
+    double gq[4];
+    Normals<double>::draw4(seed, job[c], step[c] + s, (uint32_t)call, 0u, gq);
+    double* zc = z + ((size_t)s * C + c) * 3 * M;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int k = 4 * call + e, n = k / 3;
+        if (n < M) zc[(size_t)(k - 3 * n) * M + n] = gq[e];
+    }
+}
+
 // step[c] += 1 for chains still below their stop step (after k_mode_update).
 __global__ void k_advance_steps(int64_t* __restrict__ step, const int64_t* __restrict__ stop, int C)
 {
