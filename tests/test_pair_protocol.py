@@ -17,7 +17,9 @@ and in-order MMA commits, and checks on every run:
   * when both CTAs pass the final cluster barrier, no copy or commit is still
     in flight towards either of them.
 A negative control replaces the compute warps' release-counter waits by plain
-parity waits and must be caught.  The block order is the kernel's
+parity waits and must be caught.  In the single-CTA kernel the producer moves
+each stage's part of the epilogue's R tile in as soon as the last MMA of the
+step that reads that stage has retired.  The block order is the kernel's
 (inverse / noise blocks interleaved, then force / noise pairs; FILL noise
 blocks moved to the end of phase 1), modelled here at block granularity."""
 import random
@@ -169,12 +171,20 @@ class Pair:
                 if not own:
                     bar["ready", s].arrive()
                 yield None
-            yield self.parity(r, "inc_done", sp)
             if self.pair:
+                yield self.parity(r, "inc_done", sp)
                 yield self.parity(r, "both_done", sp)
-            for s in range(self.epi_stages):    # the epilogue's R tile fills the first stages
-                for reg in ("R", "A", "B"):
-                    self.put(r, s, reg, ("epilogue", sp), {"compute", "noise"})
+                for s in range(self.epi_stages):    # the epilogue's R tile fills the first stages
+                    for reg in ("R", "A", "B"):
+                        self.put(r, s, reg, ("epilogue", sp), {"compute", "noise"})
+            else:
+                # single CTA: each of the first stages takes its part of the R tile
+                # as soon as the last MMA of this step that reads it has retired
+                for s in range(self.epi_stages):
+                    last = max(b for b in range(sp * nblk, (sp + 1) * nblk) if b % st == s)
+                    yield self.parity(r, ("empty", s), last // st)
+                    for reg in ("R", "A", "B"):
+                        self.put(r, s, reg, ("epilogue", sp), {"compute", "noise"})
             self.events.append((r, lambda r=r: self.bar[r]["r_blk"].arrive(), "R reload"))
         if self.pair:
             total = self.steps * nblk
