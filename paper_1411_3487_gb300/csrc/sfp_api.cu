@@ -1221,6 +1221,45 @@ int sfp_create(const sfp_params* params, const sfp_chain_desc* chains, int32_t n
             return fail(SFP_ENOMEM, "HBM budget of %zu bytes exceeded (%zu needed)", hbm_budget_bytes, held);
         }
     }
+    // Lengths that share one grouped launch (at most one group each of 64, 128,
+    // 256 and 512 beads): chains per tile chosen for all of them together, not
+    // for each group as if it had the GPU to itself.  If tiles of 40 chains (the
+    // fewest MMAs per chain) take more than one wave of the SMs, 40 (the
+    // autotuner's choice on 8192 mixed chains); else the smallest tiles that
+    // still fit one wave.
+    {
+        std::vector<size_t> cand;
+        bool seen[4] = {false, false, false, false};
+        for (size_t i = 0; i < b->groups.size(); ++i) {
+            const Group& g = b->groups[i];
+            if (!g.fused) continue;
+            const int slot = g.M == 512 ? 0 : g.M == 256 ? 1 : g.M == 128 ? 2 : 3;
+            if (seen[slot]) continue;
+            seen[slot] = true;
+            cand.push_back(i);
+        }
+        int dev = 0, sms = 0;
+        if (cand.size() >= 2 && cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) {
+            auto ctas = [&](int cpt) {
+                int64_t n = 0;
+                for (size_t i : cand) {
+                    const Group& g = b->groups[i];
+                    n += (int64_t)((g.C + cpt - 1) / cpt) * (g.M == 512 ? 2 : 1);
+                }
+                return n;
+            };
+            int best = 40;
+            if (ctas(40) <= sms)
+                for (int cpt = 4; cpt <= 40; cpt += 4)
+                    if (ctas(cpt) <= sms) {
+                        best = cpt;
+                        break;
+                    }
+            for (size_t i : cand)
+                if ((rc = sfp::fused_set_tile(b->groups[i].fused, best))) { destroy_impl(b); return rc; }
+        }
+    }
     b->cur = b->stream;
     {
         cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
