@@ -63,10 +63,13 @@ def lib():
             L.orc_energy.argtypes = [ct.c_void_p, _D]
             L.orc_energy.restype = ct.c_double
             L.orc_mode_step_z.argtypes = [ct.c_void_p, _D, ct.c_double, ct.c_int, _D]
+            L.orc_mode_step_Zm.argtypes = [ct.c_void_p, _D, ct.c_double, ct.c_int, _D]
+            L.orc_mode_normals.argtypes = [ct.c_uint32, ct.c_uint32, ct.c_int64, ct.c_int, _D]
             L.orc_euler_step_z.argtypes = [ct.c_void_p, _D, ct.c_double, _D]
             L.orc_run_modes.argtypes = [ct.c_void_p, ct.c_int, ct.c_uint32, _U32,
                                         ct.c_int64, ct.c_int64, ct.c_double, ct.c_int,
                                         _D, ct.c_int]
+            L.orc_run_modes_mk.argtypes = L.orc_run_modes.argtypes
             L.orc_run_euler.argtypes = [ct.c_void_p, ct.c_int, ct.c_uint32, _U32,
                                         ct.c_int64, ct.c_int64, ct.c_double, _D, ct.c_int]
             L.orc_ground_bonds.argtypes = [ct.c_void_p, _D]
@@ -105,6 +108,13 @@ def bead_normals(seed: int, job: int, step: int, tag: int, M: int) -> np.ndarray
     z = np.zeros((3, M))
     lib().orc_bead_normals(seed, job, step, tag, M, _dp(z))
     return z
+
+
+def mode_normals(seed: int, job: int, step: int, M: int) -> np.ndarray:
+    """Mode-keyed noise Z[alpha][p] of one chain and step (Philox tag 2)."""
+    Z = np.zeros((3, M))
+    lib().orc_mode_normals(seed, job, step, M, _dp(Z))
+    return Z
 
 
 def threads() -> int:
@@ -164,6 +174,13 @@ class Model:
         lib().orc_mode_step_z(self._h, _dp(z), float(shear), int(bool(coupling)), _dp(R))
         return R
 
+    def mode_step_Zm(self, R, Z, shear: float = 0.0, coupling: bool = True):
+        """One mode step with the mode noise Z given directly."""
+        R = np.array(R, dtype=np.float64).reshape(3, self.M)
+        Z = np.ascontiguousarray(Z, dtype=np.float64).reshape(3, self.M)
+        lib().orc_mode_step_Zm(self._h, _dp(Z), float(shear), int(bool(coupling)), _dp(R))
+        return R
+
     def euler_step_z(self, r, z, shear: float = 0.0):
         r = np.array(r, dtype=np.float64).reshape(3, self.M)
         z = np.ascontiguousarray(z, dtype=np.float64).reshape(3, self.M)
@@ -171,14 +188,16 @@ class Model:
         return r
 
     def run_modes(self, R, seed: int, jobs, step0: int, nsteps: int, shear: float = 0.0,
-                  coupling: bool = True, nthreads: int = 0):
+                  coupling: bool = True, nthreads: int = 0, mode_noise: bool = False):
+        """nsteps mode-space steps of C chains; mode_noise: noise drawn per mode
+        (orc_run_modes_mk) instead of per bead."""
         R = np.array(R, dtype=np.float64)
         C = R.shape[0]
         R = R.reshape(C, 3, self.M).copy()
         j = np.ascontiguousarray(jobs, dtype=np.uint32)
         assert j.shape == (C,)
-        lib().orc_run_modes(self._h, C, seed, _up(j), step0, nsteps, float(shear),
-                            int(bool(coupling)), _dp(R), nthreads)
+        fn = lib().orc_run_modes_mk if mode_noise else lib().orc_run_modes
+        fn(self._h, C, seed, _up(j), step0, nsteps, float(shear), int(bool(coupling)), _dp(R), nthreads)
         return R
 
     def run_euler(self, r, seed: int, jobs, step0: int, nsteps: int, shear: float = 0.0,

@@ -119,6 +119,16 @@ void orc_bead_normals(uint32_t seed, uint32_t job, int64_t step, uint32_t tag,
     }
 }
 
+/* Z[alpha*M + p] ~ N(0,1): noise drawn per mode instead of per bead (the
+ * mode-keyed variant).  Projecting iid normals through the orthonormal phi
+ * (Eq. c4, Z = phi^T z) gives iid normals again, so drawing Z directly has the
+ * same distribution.  Normal k = 3p + alpha is value k mod 4 of Philox call
+ * k / 4 with tag 2 (the bead noise has tag 0, the start sampler tag 1). */
+void orc_mode_normals(uint32_t seed, uint32_t job, int64_t step, int M, double *Z)
+{
+    orc_bead_normals(seed, job, step, 2u, M, Z);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Model tables (Secs. 3A, 4, 4A, 4B)                                        */
 /* ------------------------------------------------------------------------ */
@@ -312,16 +322,27 @@ void orc_full_force(const orc_model *m, const double *r, double *F)
  *   R_p <- exp(-zeta_p dtau) R_p + h_p DeltaH_p + w_p Z_p   (Eqs. d3, d6, f2)
  *   R^x_p += shear * g_p * R^y_p(start of step)               (Eq. btum)
  * coupling = 0 drops DeltaH (the pure Ornstein-Uhlenbeck case of Eq. d3). */
+void orc_mode_step_Zm(const orc_model *m, const double *Z, double shear, int coupling, double *R);
+
 void orc_mode_step_z(const orc_model *m, const double *z, double shear, int coupling, double *R)
+{
+    const int M = m->M;
+    double *Z = (double *)malloc(sizeof(double) * 3 * (size_t)M);
+    orc_beads_to_modes(m, z, Z);
+    orc_mode_step_Zm(m, Z, shear, coupling, R);
+    free(Z);
+}
+
+/* The same step with the mode noise Z given (Z = phi^T z for bead noise z,
+ * or drawn per mode by orc_mode_normals). */
+void orc_mode_step_Zm(const orc_model *m, const double *Z, double shear, int coupling, double *R)
 {
     const int M = m->M;
     double *r = (double *)malloc(sizeof(double) * 3 * (size_t)M);
     double *dH = (double *)malloc(sizeof(double) * 3 * (size_t)M);
-    double *Z = (double *)malloc(sizeof(double) * 3 * (size_t)M);
     orc_modes_to_beads(m, R, r);
     if (coupling) orc_delta_H(m, r, dH);
     else memset(dH, 0, sizeof(double) * 3 * (size_t)M);
-    orc_beads_to_modes(m, z, Z);
     for (int p = 0; p < M; ++p) {
         const double Ry = R[M + p];
         for (int a = 0; a < 3; ++a) {
@@ -330,7 +351,7 @@ void orc_mode_step_z(const orc_model *m, const double *z, double shear, int coup
         }
         R[p] += shear * m->g[p] * Ry;
     }
-    free(r); free(dH); free(Z);
+    free(r); free(dH);
 }
 
 /* One Euler step of the bead-position scheme (Eqs. b3-b5, btum) with the
@@ -385,6 +406,27 @@ int orc_run_modes(const orc_model *m, int C, uint32_t seed, const uint32_t *jobs
             orc_mode_step_z(m, z, shear, coupling, Rc);
         }
         free(z);
+    }
+    return 0;
+}
+
+/* Same with mode-keyed noise: chain c draws Z of (seed, jobs[c], step0 + s,
+ * mode, tag 2) by orc_mode_normals and takes it as the mode noise directly. */
+int orc_run_modes_mk(const orc_model *m, int C, uint32_t seed, const uint32_t *jobs,
+                     int64_t step0, int64_t nsteps, double shear, int coupling,
+                     double *R, int nthreads)
+{
+    const int M = m->M;
+    set_threads(nthreads);
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < C; ++c) {
+        double *Z = (double *)malloc(sizeof(double) * 3 * (size_t)M);
+        double *Rc = R + (size_t)c * 3 * M;
+        for (int64_t s = 0; s < nsteps; ++s) {
+            orc_mode_normals(seed, jobs[c], step0 + s, M, Z);
+            orc_mode_step_Zm(m, Z, shear, coupling, Rc);
+        }
+        free(Z);
     }
     return 0;
 }

@@ -490,3 +490,57 @@ def test_stored_monte_carlo_reference_is_the_oracles():
     per = obs[:, :3] / obs[:, 3:4]
     mine = np.concatenate([per.mean(axis=0), per.std(axis=0, ddof=1) / math.sqrt(Cm)])
     assert np.allclose(mine, stored, rtol=1e-9, atol=0)
+
+
+# ---------------------------------------------------------------- mode-keyed noise (Eq. c4)
+
+def test_mode_normals_statistics_and_key():
+    """The mode-keyed noise: iid N(0,1) over modes, axes, steps and chains, and a
+    stream of its own (Philox tag 2), so it shares no value with the bead noise
+    of the same key and step."""
+    M = 256
+    Z = np.concatenate([O.mode_normals(1, j, s, M).ravel() for j in range(4) for s in range(40)])
+    assert abs(Z.mean()) < 4.5 / math.sqrt(Z.size)
+    assert abs(Z.var() - 1) < 4.5 * math.sqrt(2.0 / Z.size)
+    assert stats.kstest(Z, "norm").pvalue > 1e-4
+    assert np.array_equal(O.mode_normals(3, 5, 7, 64), O.bead_normals(3, 5, 7, 2, 64))
+    assert not np.intersect1d(O.mode_normals(3, 5, 7, 64).ravel(), O.bead_normals(3, 5, 7, 0, 64).ravel()).size
+
+
+def test_mode_keyed_step_is_the_bead_step_with_projected_noise():
+    """Eq. c4 makes the bead noise enter only through Z = phi^T z.  A step with
+    the mode noise Z given equals the bead-noise step with z = phi Z (phi
+    orthonormal, so phi^T phi Z = Z): the mode-keyed variant integrates the same
+    dynamics, with shear and coupling, on the same trajectory."""
+    for M in (5, 64):
+        m = O.Model(M, dtau=10.0)
+        R0 = m.equilibrium_start(2, 0)
+        Z = O.mode_normals(2, 0, 0, M)
+        z = m.modes_to_beads(Z)                 # phi Z, per axis (Eq. c1)
+        for shear, coupling in ((0.0, True), (0.3, True), (0.0, False)):
+            a = m.mode_step_Zm(R0, Z, shear=shear, coupling=coupling)
+            b = m.mode_step_z(R0, z, shear=shear, coupling=coupling)
+            assert np.abs(a - b).max() < 1e-12 * (1 + np.abs(b).max()), (M, shear, coupling)
+
+
+def test_mode_keyed_ou_variance_and_com_diffusion():
+    """With mode-keyed noise the OU law of Eqs. d3, d6 (DeltaH = 0) holds for
+    any step, and the centre of mass diffuses freely with D = T*/(N+1) (Sec. 7B),
+    as with bead noise."""
+    M, dtau, k, C = 8, 40.0, 3, 4000
+    m = O.Model(M, dtau=dtau)
+    R = m.run_modes(np.zeros((C, 3, M)), seed=7, jobs=np.arange(C), step0=0, nsteps=k, coupling=False,
+                    mode_noise=True)
+    z = closed_zeta(M)
+    ref = np.empty(M)
+    ref[0] = 2 * TSTAR * k * dtau
+    ref[1:] = TSTAR * (1 - np.exp(-2 * z[1:] * k * dtau)) / z[1:]
+    var = R.var(axis=(0, 1))
+    assert np.all(np.abs(var / ref - 1) < 4.5 * math.sqrt(2.0 / (3 * C))), var / ref
+    M, dtau, k, C = 16, 5.0, 6, 3000
+    m = O.Model(M, dtau=dtau)
+    R0 = np.stack([m.equilibrium_start(3, j) for j in range(C)])
+    R = m.run_modes(R0, seed=3, jobs=np.arange(C), step0=0, nsteps=k, mode_noise=True)
+    dcm = (R[:, :, 0] - R0[:, :, 0]) / math.sqrt(M)
+    msd = np.mean(np.sum(dcm ** 2, axis=1))
+    assert msd == pytest.approx(6 * TSTAR * k * dtau / M, rel=4.5 * math.sqrt(2.0 / (3 * C)))
