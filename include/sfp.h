@@ -257,6 +257,27 @@ int sfp_autotune(sfp_batch *b, int32_t trial_steps, int32_t *chains_per_tile);
 enum { SFP_INTEGRATOR_MODES = 0, SFP_INTEGRATOR_EULER = 1 };
 int sfp_set_integrator(sfp_batch *b, int32_t integrator);
 
+/* Noise keying of the mode-space step (Eq. c4: the bead noise enters the mode
+ * equations only through Z = phi^T z; phi is orthonormal, so the projection of
+ * iid normals is iid normal again).
+ *   SFP_NOISE_BEADS  (default) the bead normals z of (seed, job, step, tag 0)
+ *                    are drawn and projected, Z = phi^T z: the same noise as
+ *                    the bead-position Euler scheme, so the two integrators can
+ *                    be compared path by path.
+ *   SFP_NOISE_MODES  Z itself is drawn per mode, normal 3 p + alpha of Philox
+ *                    call (3 p + alpha) / 4 under tag 2: the same distribution,
+ *                    a different stream; the projection's contraction (a third
+ *                    of the forward transform) is skipped.  The fused step takes
+ *                    it at 64, 128 and 256 beads with three passes (the noise
+ *                    warps draw Z one step ahead into a buffer of two steps,
+ *                    8 C M bytes, allocated here and counted against the
+ *                    budget); 512-bead and SFP_MIXED_BF16_2 groups then run on
+ *                    the staged kernels, and the grouped launch is off.  The
+ *                    Euler integrator and sfp_step_noalloc always draw bead
+ *                    noise.  Host only; SFP_EINVAL for an unknown value. */
+enum { SFP_NOISE_BEADS = 0, SFP_NOISE_MODES = 1 };
+int sfp_set_noise(sfp_batch *b, int32_t keying);
+
 /* Observable sampling (Sec. 5B).  every_steps > 0 clears the accumulators of
  * SFP_OBS_ACCUM, SFP_OBS_MODE_POWER and SFP_OBS_COM_MSD, takes sample 0 of the
  * current state at once, and from then on one sample after every every_steps

@@ -17,7 +17,7 @@ from ._lib import (SFP_FP32, SFP_FP32_SIMT, SFP_FP64, SFP_MIXED_BF16, SFP_MIXED_
                    SFP_OBS_BOND_MSD, SFP_OBS_COM_MSD, SFP_OBS_E2E2_MEAN, SFP_OBS_E2E_MSD, SFP_OBS_MID_MSD,
                    SFP_OBS_MODE_POWER, SFP_OBS_MODE_VAR,
                    SFP_OBS_MODES, SFP_OBS_POSITIONS,
-                   SFP_INTEGRATOR_EULER, SFP_INTEGRATOR_MODES, SFP_OBS_SHAPE, SFP_OBS_STEP,
+                   SFP_INTEGRATOR_EULER, SFP_INTEGRATOR_MODES, SFP_NOISE_BEADS, SFP_NOISE_MODES, SFP_OBS_SHAPE, SFP_OBS_STEP,
                    SFP_PATH_FUSED, SFP_PATH_STAGED, SFP_PROBE_BONDS, SFP_PROBE_DH,
                    SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_ZMODE, SfpChainDesc, SfpError,
                    SfpParams)
@@ -147,8 +147,12 @@ class Batch:
         _lib.check(_lib.load().sfp_set_graph(self._h, int(bool(enable))))
 
     def set_grouped(self, enable: bool = True) -> None:
-        """One persistent launch for the 64/128/256-bead groups (default), or one launch per group."""
+        """One launch of clusters of two CTAs for the fused groups of all lengths (default), or one per group."""
         _lib.check(_lib.load().sfp_set_grouped(self._h, int(bool(enable))))
+
+    def set_noise(self, keying: int) -> None:
+        """SFP_NOISE_BEADS (default: bead noise projected, Eq. c4) or SFP_NOISE_MODES (Z drawn per mode)."""
+        _lib.check(_lib.load().sfp_set_noise(self._h, int(keying)))
 
     def autotune(self, trial_steps: int = 20) -> list:
         """Choose chains per tile of the fused groups by timing; returns them per group."""

@@ -22,6 +22,7 @@ SFP_OBS_ACCUM, SFP_OBS_MODE_POWER, SFP_OBS_COM_MSD = 5, 6, 7
 SFP_OBS_MID_MSD, SFP_OBS_E2E2_MEAN, SFP_OBS_MODE_VAR, SFP_OBS_E2E_MSD, SFP_OBS_BOND_MSD = 8, 9, 10, 11, 12
 SFP_PATH_FUSED, SFP_PATH_STAGED = 0, 1
 SFP_INTEGRATOR_MODES, SFP_INTEGRATOR_EULER = 0, 1
+SFP_NOISE_BEADS, SFP_NOISE_MODES = 0, 1
 SFP_PROBE_BONDS, SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_DH, SFP_PROBE_ZMODE = 0, 1, 2, 3, 4
 
 # Every entry point declared in include/sfp.h.
@@ -30,7 +31,7 @@ EXPORTS = (
     "sfp_set_positions", "sfp_set_step", "sfp_step", "sfp_observe", "sfp_probe", "sfp_save",
     "sfp_load", "sfp_info", "sfp_destroy", "sfp_last_error", "sfp_philox_words",
     "sfp_stage_timing", "sfp_stage_times", "sfp_step_noalloc", "sfp_set_sampling", "sfp_set_msd_lags",
-    "sfp_set_path", "sfp_set_integrator", "sfp_set_graph", "sfp_set_grouped", "sfp_autotune", "sfp_server_config_default", "sfp_server_create", "sfp_server_submit",
+    "sfp_set_path", "sfp_set_integrator", "sfp_set_graph", "sfp_set_grouped", "sfp_set_noise", "sfp_autotune", "sfp_server_config_default", "sfp_server_create", "sfp_server_submit",
     "sfp_server_poll", "sfp_server_result_modes", "sfp_server_wait_idle", "sfp_server_stats",
     "sfp_server_destroy", "sfp_server_last_error",
 )
@@ -108,6 +109,8 @@ def load(path: str | None = None):
         L.sfp_set_path.argtypes = [vp, i32]
         L.sfp_set_integrator.argtypes = [vp, i32]
         L.sfp_set_graph.argtypes = [vp, i32]
+        L.sfp_set_grouped.argtypes = [vp, i32]
+        L.sfp_set_noise.argtypes = [vp, i32]
         L.sfp_autotune.argtypes = [vp, i32, vp]
         L.sfp_server_config_default.argtypes = [ct.POINTER(SfpServerConfig)]
         L.sfp_server_create.argtypes = [ct.POINTER(SfpParams), ct.POINTER(SfpServerConfig), ct.POINTER(vp)]

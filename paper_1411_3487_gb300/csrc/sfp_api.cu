@@ -230,6 +230,7 @@ struct sfp_batch {
     cudaEvent_t fork = nullptr;
     bool use_graph = false;
     bool grouped = true;               // one launch for the fused groups of all lengths
+    int32_t noise = SFP_NOISE_BEADS;   // noise keying of the mode integrator
     cudaGraphExec_t graph = nullptr;
     int64_t graph_chunk = 0;
     int64_t graph_launches = 0;        // kernels in one replay
@@ -350,10 +351,10 @@ cudaError_t launch_force(cudaStream_t st, const T* u, T* v, int C, int M, T c12n
 // Launch the bead noise kernel: one thread per chain and Philox call.
 template <typename T>
 cudaError_t launch_noise(cudaStream_t st, T* z, int C, int M, uint32_t seed, const uint32_t* job,
-                         const int64_t* step)
+                         const int64_t* step, uint32_t tag = 0u)
 {
     const unsigned grid = nblk((int64_t)C * ((3 * M + 3) / 4), 256);
-    sfp::k_noise<T><<<grid, 256, 0, st>>>(z, C, M, seed, job, step);
+    sfp::k_noise<T><<<grid, 256, 0, st>>>(z, C, M, seed, job, step, tag);
     return cudaGetLastError();
 }
 
@@ -452,6 +453,8 @@ sfp::FusedArgs fused_args(const sfp_batch* b, const Group& g, int64_t n_steps)
     a.n_steps = (int)n_steps;
     a.cpt = sfp::fused_tile(g.fused);
     a.stall_test = stall_test();
+    a.zbuf = nullptr;   // the plan's mode-noise buffer and w table, filled in by the launch
+    a.w = nullptr;
     return a;
 }
 
@@ -472,7 +475,9 @@ int step_group_fused(sfp_batch* b, Group& g, int64_t n_steps)
 std::vector<size_t> grouped_set(const sfp_batch* b)
 {
     std::vector<size_t> out;
-    if (!b->grouped || b->timing || b->integrator != SFP_INTEGRATOR_MODES || b->path != SFP_PATH_FUSED) return out;
+    if (!b->grouped || b->timing || b->integrator != SFP_INTEGRATOR_MODES || b->path != SFP_PATH_FUSED ||
+        b->noise != SFP_NOISE_BEADS)
+        return out;
     bool seen[4] = {false, false, false, false};
     for (size_t i = 0; i < b->groups.size(); ++i) {
         const Group& g = b->groups[i];
@@ -490,10 +495,19 @@ std::vector<size_t> grouped_set(const sfp_batch* b)
 // SFP_PATH_FUSED (three [3][M] FP64 arrays in shared memory).
 constexpr int kChainMaxBeads = 2048;
 
+// The group takes the fused tensor-core step: a fused plan on SFP_PATH_FUSED,
+// and with mode-keyed noise a length the fused kernel draws it for.
+bool fused_ok(const sfp_batch* b, const Group& g)
+{
+    if (!g.fused || b->path != SFP_PATH_FUSED) return false;
+    return b->noise == SFP_NOISE_BEADS ||
+           (sfp::fused_mode_noise_supported(g.M) && b->precision != SFP_MIXED_BF16_2);
+}
+
 bool one_launch(const sfp_batch* b, const Group& g)
 {
     if (b->path != SFP_PATH_FUSED) return false;
-    return g.fused != nullptr || (b->precision == SFP_FP64 && g.M <= kChainMaxBeads);
+    return fused_ok(b, g) || (b->precision == SFP_FP64 && g.M <= kChainMaxBeads);
 }
 
 // n_steps FP64 steps of a group in one launch of k_chain_steps (a CTA per chain,
@@ -526,7 +540,8 @@ cudaError_t launch_chain_cluster(sfp_batch* b, Group& g, size_t smem, double c12
                               (const int64_t*)(g.limited ? g.stop : nullptr), (const double*)g.shear,
                               (const double*)g.chiT, (const double*)g.chi, (const double*)g.phi_d,
                               (const double*)g.dm, (const double*)g.h, (const double*)g.w, (const double*)g.g, g.C,
-                              g.M, c12, w0cm, g.dtau, k, (const double*)g.znoise, b->bad);
+                              g.M, c12, w0cm, g.dtau, k, (const double*)g.znoise, b->noise == SFP_NOISE_MODES ? 1 : 0,
+                              b->bad);
 }
 
 // CTAs per chain for the FP64 cluster path: 16 (a non-portable cluster size)
@@ -591,8 +606,8 @@ int step_group_chain(sfp_batch* b, Group& g, int64_t n_steps)
         for (int64_t done = 0; done < n_steps;) {
             const int k = (int)std::min<int64_t>(g.znoise_steps, n_steps - done);
             const int K = (3 * g.M + 3) / 4;
-            sfp::k_noise_steps<<<nblk((int64_t)k * g.C * K, 256), 256, 0, b->cur>>>(g.znoise, g.C, g.M, b->seed,
-                                                                                   g.job, g.step, k);
+            sfp::k_noise_steps<<<nblk((int64_t)k * g.C * K, 256), 256, 0, b->cur>>>(
+                g.znoise, g.C, g.M, b->seed, g.job, g.step, k, b->noise == SFP_NOISE_MODES ? 2u : 0u);
             CUDA_TRY(cudaGetLastError());
             CUDA_TRY(G == 16 ? launch_chain_cluster<16>(b, g, smem, c12, w0cm, k)
                              : launch_chain_cluster<8>(b, g, smem, c12, w0cm, k));
@@ -604,7 +619,8 @@ int step_group_chain(sfp_batch* b, Group& g, int64_t n_steps)
         sfp::k_chain_steps<double><<<g.C, threads, smem, b->cur>>>(
             (double*)g.R, g.com, g.step, g.limited ? g.stop : nullptr, g.job, g.shear, (const double*)g.chiT,
             (const double*)g.chi, g.phi_d, (const double*)g.dm, (const double*)g.h, (const double*)g.w,
-            (const double*)g.g, g.C, g.M, c12, w0cm, g.dtau, b->seed, (int)n_steps, b->bad);
+            (const double*)g.g, g.C, g.M, c12, w0cm, g.dtau, b->seed, (int)n_steps,
+            b->noise == SFP_NOISE_MODES ? 1 : 0, b->bad);
         b->launches++;
     }
     CUDA_TRY(cudaGetLastError());
@@ -627,10 +643,15 @@ int step_group(sfp_batch* b, Group& g)
     // a3: the bead noise depends on the step counters alone, so it runs on a
     // stream of its own beside a1 and a2 (serially while stages are timed)
     const bool side = !b->timing;
+    // mode-keyed noise: Z drawn straight into the mode-space buffer, and the
+    // forward transform forms DeltaH alone
+    const bool mk = b->noise == SFP_NOISE_MODES;
+    T* znoise = mk ? yz + n : fz + n;
+    const uint32_t ntag = mk ? 2u : 0u;
     if (side) {
         CUDA_TRY(cudaEventRecord(g.nfork, b->cur));
         CUDA_TRY(cudaStreamWaitEvent(g.ns, g.nfork, 0));
-        CUDA_TRY(launch_noise<T>(g.ns, fz + n, C, M, b->seed, g.job, g.step));
+        CUDA_TRY(launch_noise<T>(g.ns, znoise, C, M, b->seed, g.job, g.step, ntag));
         CUDA_TRY(cudaEventRecord(g.njoin, g.ns));
         b->launches++;
     }
@@ -647,13 +668,13 @@ int step_group(sfp_batch* b, Group& g)
     if (side) {
         CUDA_TRY(cudaStreamWaitEvent(b->cur, g.njoin, 0));
     } else {
-        CUDA_TRY(launch_noise<T>(b->cur, fz + n, C, M, b->seed, g.job, g.step));
+        CUDA_TRY(launch_noise<T>(b->cur, znoise, C, M, b->seed, g.job, g.step, ntag));
         b->launches++;
     }
     if ((rc = mark(b, 3))) return rc;
     // a4: DeltaH = chi^T v (Eq. e11), Z = phi^T z (Eq. c4): the forward transform
-    if (g.tc) rc = sfp::tc_transform(g.tc, 1, b->cur);
-    else if (!(rc = launch_gemm<T>(b, fz, (const T*)g.chiT, yz, 3 * C, M, M)))
+    if (g.tc) rc = sfp::tc_transform(g.tc, mk ? 2 : 1, b->cur);
+    else if (!(rc = launch_gemm<T>(b, fz, (const T*)g.chiT, yz, 3 * C, M, M)) && !mk)
         rc = launch_gemm<T>(b, fz + n, (const T*)g.phiT, yz + n, 3 * C, M, M);
     if (rc) return rc;
     if (g.tc) b->launches++;
@@ -781,7 +802,7 @@ int issue_chunk(sfp_batch* b, int64_t chunk, cudaStream_t base)
         if (b->integrator == SFP_INTEGRATOR_EULER) {
             rc = (b->precision == SFP_FP64) ? step_group_euler<double>(b, g, chunk)
                                             : step_group_euler<float>(b, g, chunk);
-        } else if (g.fused && b->path == SFP_PATH_FUSED) {
+        } else if (fused_ok(b, g)) {
             rc = step_group_fused(b, g, chunk);
         } else if (one_launch(b, g)) {
             rc = step_group_chain(b, g, chunk);
@@ -1669,6 +1690,27 @@ int sfp_set_path(sfp_batch* b, int32_t path)
     return SFP_OK;
 }
 
+int sfp_set_noise(sfp_batch* b, int32_t keying)
+{
+    if (!b) return fail(SFP_EINVAL, "batch is NULL");
+    if (keying != SFP_NOISE_BEADS && keying != SFP_NOISE_MODES) return fail(SFP_EINVAL, "unknown noise keying %d", keying);
+    if (keying == SFP_NOISE_MODES) {
+        for (auto& g : b->groups) {
+            if (!g.fused || !sfp::fused_mode_noise_supported(g.M) || b->precision == SFP_MIXED_BF16_2) continue;
+            const size_t before = sfp::fused_bytes(g.fused);
+            int rc = sfp::fused_set_mode_noise(g.fused, true);
+            if (rc) return fail(rc, "%s", sfp_last_error());
+            b->held += sfp::fused_bytes(g.fused) - before;
+        }
+    } else {
+        for (auto& g : b->groups)
+            if (g.fused) sfp::fused_set_mode_noise(g.fused, false);
+    }
+    if (b->noise != keying) drop_graph(b);
+    b->noise = keying;
+    return SFP_OK;
+}
+
 int sfp_set_grouped(sfp_batch* b, int32_t enable)
 {
     if (!b) return fail(SFP_EINVAL, "batch is NULL");
@@ -1695,7 +1737,7 @@ int sfp_autotune(sfp_batch* b, int32_t trial_steps, int32_t* chains_per_tile)
     if (b->path != SFP_PATH_FUSED || b->integrator != SFP_INTEGRATOR_MODES || b->timing) return SFP_OK;
     std::vector<size_t> fg;
     for (size_t i = 0; i < G; ++i)
-        if (b->groups[i].fused) fg.push_back(i);
+        if (fused_ok(b, b->groups[i])) fg.push_back(i);
     if (fg.empty()) return SFP_OK;
     int dev = 0, sms = 148;
     CUDA_TRY(cudaGetDevice(&dev));

@@ -118,7 +118,7 @@ struct FSmem {
     static constexpr int kStages = BF ? ((192 * 1024) / kStage < 4 ? (192 * 1024) / kStage : 4)
                                       : (NB == 256 ? 2 : NB == 128 ? 3 : 4);
     static constexpr int kRT = kRows * kKB * 4;           // an FP32 R block of the epilogue, 16 KB
-    static constexpr int kMisc = 4096;   // per-chain keys, steps, shear, stops; tables; barriers
+    static constexpr int kMisc = 5120;   // per-chain keys, steps, shear, stops; tables; barriers
     static constexpr int kBytes = kStages * kStage + kMisc + 1024;
     static_assert(kBytes <= 227 * 1024, "shared memory of one CTA");
     static_assert(kStages <= 4, "stage barriers");
@@ -196,6 +196,17 @@ __device__ __forceinline__ void sched_decode(int blk, int& kind, int& nb)   // k
     }
 }
 template <int KB> __device__ __forceinline__ int sched_inv(int k) { return 3 * (k >> 1) + ((k & 1) ? 2 : 0); }
+// With mode-keyed noise (MZ) a step has no noise blocks: I_0 .. I_{KB-1}, then F_0 .. F_{KB-1}.
+template <int KB, int FILL, bool MZ>
+__device__ __forceinline__ void sched_decode_any(int blk, int& kind, int& nb)
+{
+    if constexpr (MZ) {
+        kind = blk < KB ? 0 : 2;
+        nb = blk < KB ? blk : blk - KB;
+    } else {
+        sched_decode<KB, FILL>(blk, kind, nb);
+    }
+}
 template <int KB, int FILL> __device__ __forceinline__ int sched_noise(int j)
 {
     constexpr int H = KB / 2, P = FILL < H ? FILL : H;
@@ -231,17 +242,17 @@ __device__ __forceinline__ int noise_h0(int nw, int qn) { return (nw + kNoiseWar
 
 // One item: four normals of Philox call `call` of chain slot cl (zeros past the tile's chains).
 __device__ __forceinline__ void noise_item(float (&z)[4], int h, int jb, int sp, int lane, int Ct, uint32_t seed,
-                                           const uint32_t* s_job, const int64_t* s_step)
+                                           const uint32_t* s_job, const int64_t* s_step, uint32_t tag = 0u)
 {
     const int f = 32 * h + lane;
     const int cl = f / kCallsPerBlock, call = f - kCallsPerBlock * cl;
-    Normals<float>::draw4(seed, s_job[cl], s_step[cl] + sp, (uint32_t)(kCallsPerBlock * jb + call), 0u, z);
+    Normals<float>::draw4(seed, s_job[cl], s_step[cl] + sp, (uint32_t)(kCallsPerBlock * jb + call), tag, z);
     if (cl >= Ct) z[0] = z[1] = z[2] = z[3] = 0.f;
 }
 
 __device__ __forceinline__ void noise_draw(float (&zz)[kChunksPerWarp][4], int nw, int qn, int jb, int sp,
                                            int lane, int cpt, int Ct, uint32_t seed, const uint32_t* s_job,
-                                           const int64_t* s_step)
+                                           const int64_t* s_step, uint32_t tag = 0u)
 {
     static_assert(kChunksPerWarp == 3, "the draw below handles up to three chunks per warp");
     const int nch = cpt * kCallsPerBlock / 32;
@@ -249,11 +260,12 @@ __device__ __forceinline__ void noise_draw(float (&zz)[kChunksPerWarp][4], int n
     // The warp's first two chunks are drawn in one straight-line block, so that
     // their Philox rounds interleave; the branches are the same for the whole warp.
     if (h0 + kNoiseWarps < nch) {
-        noise_item(zz[0], h0, jb, sp, lane, Ct, seed, s_job, s_step);
-        noise_item(zz[1], h0 + kNoiseWarps, jb, sp, lane, Ct, seed, s_job, s_step);
-        if (h0 + 2 * kNoiseWarps < nch) noise_item(zz[2], h0 + 2 * kNoiseWarps, jb, sp, lane, Ct, seed, s_job, s_step);
+        noise_item(zz[0], h0, jb, sp, lane, Ct, seed, s_job, s_step, tag);
+        noise_item(zz[1], h0 + kNoiseWarps, jb, sp, lane, Ct, seed, s_job, s_step, tag);
+        if (h0 + 2 * kNoiseWarps < nch)
+            noise_item(zz[2], h0 + 2 * kNoiseWarps, jb, sp, lane, Ct, seed, s_job, s_step, tag);
     } else if (h0 < nch) {
-        noise_item(zz[0], h0, jb, sp, lane, Ct, seed, s_job, s_step);
+        noise_item(zz[0], h0, jb, sp, lane, Ct, seed, s_job, s_step, tag);
     }
 }
 
@@ -291,7 +303,7 @@ __device__ __forceinline__ void noise_put(uint8_t* ah, uint8_t* al, const float 
 // function returns (the producer waits for the MMAs' last commits), so a
 // persistent kernel may run another tile in the same shared memory.  Returns
 // false if a wait gave up.
-template <int NB, bool BF, bool TWO>
+template <int NB, bool BF, bool TWO, bool MZ = false>
 __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtensorMap& tmChiH,
                                            const CUtensorMap& tmChiL, const CUtensorMap& tmFH,
                                            const CUtensorMap& tmFL, const FusedArgs& a, int tile, uint8_t* smem,
@@ -300,7 +312,7 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
     using S = FSmem<NB, BF, BF>;        // BF16: a separate FP32 R staging area per stage
     constexpr int ST = S::kStages;
     constexpr int KB = NB / kKB;        // inverse K blocks = forward bead blocks
-    constexpr int NBLK = 3 * KB;        // blocks of one step, in the order of sched_decode
+    constexpr int NBLK = MZ ? 2 * KB : 3 * KB;   // blocks of one step, in the order of sched_decode (MZ: sched_mz)
     static_assert(KB % 2 == 0, "the block schedule pairs bead blocks");
     static_assert(ST <= NBLK, "the last ST blocks of a step release every stage");
 
@@ -314,6 +326,7 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
     float* s_g = (float*)(misc + 2240);
     uint64_t* bars = (uint64_t*)(misc + 3264);
     int* s_rowb = (int*)(misc + 3584);          // first A-operand row of each chain slot
+    float* s_w = (float*)(misc + 4096);         // MZ: w_p (Eq. d6; w_0 of the centre of mass), NB <= 256
     uint64_t* full = bars;              // TMA bytes landed                 (1 + tx)
     uint64_t* ready = bars + 4;         // A operand written by one group   (kReadyCount)
     uint64_t* empty = bars + 8;         // MMAs done with the stage         (commit)
@@ -325,6 +338,8 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
     int* s_freed = (int*)(flags + 2);   // last block whose stage the producer saw released
     uint64_t* r_blk = bars + 18;        // R column block k reloaded for the epilogue (1 + tx), k < KB
     uint64_t* never = bars + 26;        // nothing arrives here (the stall test)
+    uint64_t* z_ready = bars + 27;      // MZ: a step's Z written into buffer b = step & 1 (every noise warp)
+    uint64_t* z_free = bars + 29;       // MZ: buffer b read by the step's epilogue (every worker warp)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cpq = a.cpt >> 2;         // chains per TMEM lane quarter (rows 32 q + 3 k + axis)
@@ -343,6 +358,12 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
         for (int k = 0; k < KB; ++k) mbar_init(&r_blk[k], 1);
         mbar_init(epi_done, kComputeWarps + kNoiseWarps);
         mbar_init(never, 1);
+        if constexpr (MZ) {
+            for (int b2 = 0; b2 < 2; ++b2) {
+                mbar_init(&z_ready[b2], kNoiseWarps);
+                mbar_init(&z_free[b2], kComputeWarps + kNoiseWarps);
+            }
+        }
         *abort_flag = 0;
         *s_freed = -1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -355,6 +376,7 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
     for (int p = threadIdx.x; p < NB; p += kThreads) {
         s_dm[p] = a.dm[p];
         s_g[p] = a.g[p];
+        if constexpr (MZ) s_w[p] = a.w[p];
     }
     for (int i = threadIdx.x; i < kChains; i += kThreads) {
         const bool live = i < Ct;
@@ -385,6 +407,12 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
         const int cl = inrow ? cpq * q + kq : 0;
         const bool live = inrow && cl < Ct;
         ok = ok && mbar_wait(inc_done, sp & 1, a.err, abort_flag);
+        // MZ: the step's mode noise Z (written one step ahead by the noise warps)
+        const float* zrow = nullptr;
+        if constexpr (MZ) {
+            ok = ok && mbar_wait(&z_ready[sp & 1], (sp >> 1) & 1, a.err, abort_flag);
+            zrow = a.zbuf + ((size_t)(sp & 1) * a.C * 3 + (size_t)3 * (c0 + cl) + ax) * NB;
+        }
         fence_after();
         // a chain whose step counter has reached its stop step stays as it is
         const bool adv = live && s_step[cl] + sp < s_stop[cl];
@@ -396,7 +424,21 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
             for (int kin = 0; kin < kKB; kin += 16) {
                 const int p0 = kb * kKB + kin;
                 float d[16], r[16];
-                tmem_ld16(t_inc + ((uint32_t)(32 * q) << 16) + (uint32_t)p0, d);
+                if constexpr (MZ) {
+                    // D_inc = h_p DeltaH_p; the noise term w_p Z_p (Eq. d6) is added here in FP32
+                    float z[16];
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        const float4 x = live ? *reinterpret_cast<const float4*>(zrow + p0 + 4 * k4)
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                        z[4 * k4] = x.x; z[4 * k4 + 1] = x.y; z[4 * k4 + 2] = x.z; z[4 * k4 + 3] = x.w;
+                    }
+                    tmem_ld16(t_inc + ((uint32_t)(32 * q) << 16) + (uint32_t)p0, d);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) d[i] = fmaf(s_w[p0 + i], z[i], d[i]);
+                } else {
+                    tmem_ld16(t_inc + ((uint32_t)(32 * q) << 16) + (uint32_t)p0, d);
+                }
 #pragma unroll
                 for (int k4 = 0; k4 < 4; ++k4) {
                     const float4 x = *reinterpret_cast<const float4*>(blk + swz(row, kin + 4 * k4));
@@ -451,6 +493,9 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
         fence_before();
         __syncwarp();
         if (lane == 0 && ok) mbar_arrive(epi_done);
+        if constexpr (MZ) {
+            if (lane == 0 && ok) mbar_arrive(&z_free[sp & 1]);   // this warp is done with Z of step sp
+        }
     };
 
     if (warp == 0) {
@@ -470,7 +515,7 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
                 uint8_t* bh = st + S::kR + 2 * S::kA;
                 uint8_t* bl = bh + S::kB;
                 int kind, nb;
-                sched_decode<KB, BF ? 0 : 1>(blk, kind, nb);
+                sched_decode_any<KB, BF ? 0 : 1, MZ>(blk, kind, nb);
                 if (kind == 0) {
                     // inverse: the R tile (FP32, one box per lane quarter) and chi
                     mbar_expect_tx(&full[s], rblock + 2 * S::kB);
@@ -529,7 +574,7 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
                 const int s = gb % ST;
                 const uint32_t ph = (gb / ST) & 1;
                 int kind, nb;
-                sched_decode<KB, BF ? 0 : 1>(blk, kind, nb);
+                sched_decode_any<KB, BF ? 0 : 1, MZ>(blk, kind, nb);
                 ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
                 ok = ok && mbar_wait(&ready[s], ph, a.err, abort_flag);
                 if (ok) {
@@ -537,7 +582,8 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
                     const uint32_t st = smem_u32(stage0 + s * S::kStage);
                     const uint32_t a_hi = st + S::kR, a_lo = a_hi + S::kA, b_hi = a_lo + S::kA, b_lo = b_hi + S::kB;
                     const uint32_t d = kind == 0 ? t_u : t_inc;
-                    const bool first = blk <= 1;       // first inverse block, first noise block
+                    // first inverse block, first forward (noise, or force with MZ) block
+                    const bool first = MZ ? (blk == 0 || blk == KB) : blk <= 1;
                     if constexpr (BF) {
 #pragma unroll
                         for (int kk = 0; kk < kKB / 16; ++kk) {
@@ -562,12 +608,57 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
                 }
                 if (ok) {
                     mma_commit(&empty[s]);
-                    if (blk == sched_inv<KB>(KB - 1)) mma_commit(u_done);
+                    if (blk == (MZ ? KB - 1 : sched_inv<KB>(KB - 1))) mma_commit(u_done);
                 }
             }
             if (ok) mma_commit(inc_done);
             }
         }
+    } else if (MZ && warp >= 2 + kComputeWarps) {
+        // ---------------- noise warps, mode-keyed noise: the normals Z of step
+        // sp + 1 (Philox tag 2, normal 3 p + alpha of call (3 p + alpha) / 4,
+        // 32-mode blocks of 24 calls per chain) drawn during step sp into buffer
+        // (sp + 1) & 1 of a.zbuf ([2][3 C][M], FP32), then this warp's share of
+        // step sp's epilogue.  A buffer is written again only after the epilogue
+        // two steps back has read it (z_free).
+        const int nw = warp - 2 - kComputeWarps;
+        bool ok = true, finite = true;
+        double cm_unused[3];
+        const int eq = warp & 3, et = (warp - 2 - kComputeWarps) / 4;   // epilogue quarter, worker 2 + et
+        const int nch = a.cpt * kCallsPerBlock / 32;
+        const int h0 = noise_h0(nw, 0);
+        auto draw_step = [&](int sp) {
+            const int b2 = sp & 1;
+            if (sp >= 2) ok = ok && mbar_wait(&z_free[b2], ((sp >> 1) - 1) & 1, a.err, abort_flag);
+            float* zb = a.zbuf + (size_t)b2 * a.C * 3 * NB;
+#pragma unroll 1
+            for (int j = 0; j < KB; ++j) {
+                float zz[kChunksPerWarp][4];
+                noise_draw(zz, nw, 0, j, sp, lane, a.cpt, Ct, a.seed, s_job, s_step, 2u);
+#pragma unroll
+                for (int i = 0; i < kChunksPerWarp; ++i) {
+                    const int h = h0 + kNoiseWarps * i;
+                    if (h >= nch || !ok) continue;
+                    const int f = 32 * h + lane;
+                    const int cl = f / kCallsPerBlock, call = kCallsPerBlock * j + (f - kCallsPerBlock * cl);
+                    if (cl >= Ct) continue;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int k = 4 * call + e, pm = k / 3;
+                        zb[(size_t)(3 * (c0 + cl) + (k - 3 * pm)) * NB + pm] = zz[i][e];
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0 && ok) mbar_arrive(&z_ready[b2]);
+        };
+        draw_step(0);
+#pragma unroll 1
+        for (int sp = 0; sp < a.n_steps; ++sp) {
+            if (sp + 1 < a.n_steps) draw_step(sp + 1);
+            epilogue(sp, eq, 2 + et, 2 + kNoiseInQ[(eq + 2) & 3], ok, finite, cm_unused[0], cm_unused[1], cm_unused[2]);
+        }
+        if (!finite) atomicOr(a.err, 1);
     } else if (warp >= 2 + kComputeWarps) {
         // ---------------- noise warps: Philox normals of noise block j (Eq. b5),
         // drawn into registers (noise_draw), then written as hi / lo operands once
@@ -658,7 +749,7 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
         // (1) split the R tile of each inverse block into hi / lo operands
 #pragma unroll 1
         for (int nb = 0; nb < KB; ++nb) {
-            const int blk = g0 + sched_inv<KB>(nb), s = blk % ST;
+            const int blk = g0 + (MZ ? nb : sched_inv<KB>(nb)), s = blk % ST;
             const uint32_t ph = (blk / ST) & 1;
             // The stage's previous use may be a noise block these warps never
             // waited for, so a parity wait alone could be two phases ahead; the
@@ -733,7 +824,7 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
                 const float fac = __shfl_sync(0xffffffffu, rsqrtf(t) - a.c12nu, src0);
                 v[i] = (live && col + i >= 1) ? v[i] * fac : 0.f;
             }
-            const int blk = g0 + sched_force<KB, BF ? 0 : 1>(nb), s = blk % ST;
+            const int blk = g0 + (MZ ? KB + nb : sched_force<KB, BF ? 0 : 1>(nb)), s = blk % ST;
             const uint32_t ph = (blk / ST) & 1;
             ok = ok && mbar_wait(&empty[s], ph ^ 1, a.err, abort_flag);
             if (ok && inrow) {
@@ -813,7 +904,7 @@ __device__ __forceinline__ void tmem_free(uint32_t tmem)
 }
 
 // One tile per CTA (a launch of one length group).
-template <int NB, bool BF, bool TWO = false>
+template <int NB, bool BF, bool TWO = false, bool MZ = false>
 __global__ void __launch_bounds__(kThreads, 1)
 k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmChiH,
              const __grid_constant__ CUtensorMap tmChiL, const __grid_constant__ CUtensorMap tmFH,
@@ -824,7 +915,7 @@ k_fused_step(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CU
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     tmem_alloc<2 * NB>(&s_tmem);
     const uint32_t tmem = s_tmem;
-    fused_tile<NB, BF, TWO>(tmR, tmChiH, tmChiL, tmFH, tmFL, a, blockIdx.x, smem, tmem);
+    fused_tile<NB, BF, TWO, MZ>(tmR, tmChiH, tmChiL, tmFH, tmFL, a, blockIdx.x, smem, tmem);
     tmem_free<2 * NB>(tmem);
 }
 
@@ -1515,6 +1606,9 @@ struct FusedPlan {
     bool bf16 = false, two = false;
     void* tab[4] = {nullptr, nullptr, nullptr, nullptr};    // chi_hi, chi_lo, F_hi, F_lo (TF32 or BF16)
     float* R = nullptr;
+    float* w32 = nullptr;       // w_p with w_0 (FP32), for the mode-keyed epilogue
+    float* zbuf = nullptr;      // mode-keyed noise of two steps [2][C][3][M]
+    bool mz = false;            // mode-keyed noise on
     CUtensorMap tmR, tmChiH, tmChiL, tmFH, tmFL;
 };
 
@@ -1532,10 +1626,10 @@ static int grouped_smem(bool bf16)
                             FSmem<64, false, false>::kBytes});
 }
 
-template <int NB, bool BF, bool TWO = false>
+template <int NB, bool BF, bool TWO = false, bool MZ = false>
 static cudaError_t set_smem()
 {
-    return cudaFuncSetAttribute(k_fused_step<NB, BF, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_fused_step<NB, BF, TWO, MZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 FSmem<NB, BF, BF>::kBytes);
 }
 template <bool BF, bool TWO = false>
@@ -1637,6 +1731,19 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
     else
         e = M == 512 ? set_smem_pair<false>() : M == 256 ? set_smem<256, false>() :
             M == 128 ? set_smem<128, false>() : set_smem<64, false>();
+    if (e == cudaSuccess && !p->two && M <= 256)
+        e = bf16 ? (M == 256 ? set_smem<256, true, false, true>() : M == 128 ? set_smem<128, true, false, true>()
+                                                                          : set_smem<64, true, false, true>())
+                 : (M == 256 ? set_smem<256, false, false, true>() : M == 128 ? set_smem<128, false, false, true>()
+                                                                             : set_smem<64, false, false, true>());
+    if (e == cudaSuccess) {
+        // w_p with w_0 (the centre of mass) in FP32, for the mode-keyed epilogue
+        std::vector<float> wf(M);
+        for (int q = 0; q < M; ++q) wf[q] = (float)w[q];
+        e = cudaMalloc((void**)&p->w32, (size_t)M * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p->w32, wf.data(), (size_t)M * sizeof(float), cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    }
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(p->two ? k_fused_grouped<true, true> : bf16 ? k_fused_grouped<true, false>
                                                                              : k_fused_grouped<false, false>,
@@ -1653,13 +1760,20 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
 {
     if (args.cpt != p->cpt) return report(SFP_EINVAL, "fused step: chains per tile differ from the plan's");
     const dim3 grid((unsigned)((p->C + p->cpt - 1) / p->cpt));
+    FusedArgs a = args;
+    a.zbuf = p->zbuf;
+    a.w = p->w32;
+    if (p->mz && (p->two || p->M > 256)) return report(SFP_ENOTSUP, "mode-keyed noise: M <= 256, three passes");
 #define SFP_FUSED_LAUNCH(NBV, BFV)                                                                   \
-    if (p->two)                                                                                      \
+    if (p->mz)                                                                                       \
+        k_fused_step<NBV, BFV, false, true><<<grid, kThreads, FSmem<NBV, BFV, BFV>::kBytes, stream>>>( \
+            p->tmR, p->tmChiH, p->tmChiL, p->tmFH, p->tmFL, a);                                      \
+    else if (p->two)                                                                                 \
         k_fused_step<NBV, BFV, BFV><<<grid, kThreads, FSmem<NBV, BFV, BFV>::kBytes, stream>>>(         \
-            p->tmR, p->tmChiH, p->tmChiL, p->tmFH, p->tmFL, args);                                   \
+            p->tmR, p->tmChiH, p->tmChiL, p->tmFH, p->tmFL, a);                                      \
     else                                                                                             \
         k_fused_step<NBV, BFV><<<grid, kThreads, FSmem<NBV, BFV, BFV>::kBytes, stream>>>(              \
-            p->tmR, p->tmChiH, p->tmChiL, p->tmFH, p->tmFL, args)
+            p->tmR, p->tmChiH, p->tmChiL, p->tmFH, p->tmFL, a)
     cudaError_t e = cudaSuccess;
     switch (p->M * 2 + (p->bf16 ? 1 : 0)) {
         case 1024:
@@ -1743,7 +1857,12 @@ int fused_tile(const FusedPlan* p) { return p->cpt; }
 
 int fused_ctas_per_tile(const FusedPlan* p) { return p->M == 512 ? 2 : 1; }
 
-size_t fused_bytes(const FusedPlan* p) { return p ? (size_t)6 * p->M * p->M * (p->bf16 ? 2 : 4) : 0; }
+size_t fused_bytes(const FusedPlan* p)
+{
+    if (!p) return 0;
+    return (size_t)6 * p->M * p->M * (p->bf16 ? 2 : 4) + (size_t)p->M * sizeof(float) +
+           (p->zbuf ? (size_t)2 * p->C * 3 * p->M * sizeof(float) : 0);
+}
 
 int fused_set_tile(FusedPlan* p, int cpt)
 {
@@ -1757,11 +1876,27 @@ int fused_set_tile(FusedPlan* p, int cpt)
     return SFP_OK;
 }
 
+bool fused_mode_noise_supported(int M) { return M == 64 || M == 128 || M == 256; }
+
+int fused_set_mode_noise(FusedPlan* p, bool on)
+{
+    if (on && (!fused_mode_noise_supported(p->M) || p->two))
+        return report(SFP_ENOTSUP, "mode-keyed noise on the fused step: 64, 128 or 256 beads, three passes");
+    if (on && !p->zbuf) {
+        const size_t bytes = (size_t)2 * p->C * 3 * p->M * sizeof(float);
+        if (cudaMalloc((void**)&p->zbuf, bytes) != cudaSuccess) return report(SFP_ENOMEM, "mode-noise buffer allocation failed");
+    }
+    p->mz = on;
+    return SFP_OK;
+}
+
 void fused_destroy(FusedPlan* p)
 {
     if (!p) return;
     for (void* t : p->tab)
         if (t) cudaFree(t);
+    if (p->w32) cudaFree(p->w32);
+    if (p->zbuf) cudaFree(p->zbuf);
     delete p;
 }
 

@@ -28,6 +28,8 @@ struct FusedArgs {
     int n_steps;            // steps per launch (>= 1)
     int cpt;                // chains per tile (4..40, a multiple of 4), as in the plan (fused_tile)
     int stall_test;         // 1: the MMA thread first waits on a barrier nothing arrives at (tests the bounded waits)
+    float* zbuf;            // mode-keyed noise: Z of two steps [2][C][3][M] (set by fused_step from the plan)
+    const float* w;         // mode-keyed noise: w_p, w_0 of the centre of mass (set by fused_step)
 };
 
 // True when a group of M beads can take the fused step (M = 64, 128 or 256).
@@ -51,6 +53,10 @@ int fused_ctas_per_tile(const FusedPlan* plan);
 // Device bytes the plan's tables hold.
 size_t fused_bytes(const FusedPlan* plan);
 int fused_set_tile(FusedPlan* plan, int cpt);
+// Mode-keyed noise on (Z drawn per mode, Eq. c4 reading; M <= 256 only: the
+// 512-bead cluster kernel draws bead noise): allocates the plan's Z buffer.
+int fused_set_mode_noise(FusedPlan* plan, bool on);
+bool fused_mode_noise_supported(int M);
 // True for plans that the grouped launch takes (every fused plan).
 bool fused_groupable(const FusedPlan* plan);
 // One launch of clusters of two CTAs for up to four plans of different lengths

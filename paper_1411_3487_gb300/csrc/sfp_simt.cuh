@@ -136,6 +136,8 @@ k_force(const T* __restrict__ ub, T* __restrict__ vb, int C, int M, T c12nu)
 // ---------------------------------------------------------------------------
 // Bead noise (Eq. b5): z = the bead normals of (seed, job, step, tag 0); normal
 // k = 3 n + alpha of a chain and step is value k % 4 of Philox call k / 4.
+// With tag 2 the same kernel draws the mode-keyed noise Z (normal 3 p + alpha)
+// straight into the mode-space noise buffer.
 // One thread per chain and Philox call: its four normals land on two or three
 // neighbouring beads, so the threads of a warp write ~43 consecutive beads of
 // each axis row.  Bound by the Philox / Box-Muller arithmetic, not by its
@@ -145,14 +147,14 @@ k_force(const T* __restrict__ ub, T* __restrict__ vb, int C, int M, T c12nu)
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_noise(T* __restrict__ z, int C, int M, uint32_t seed, const uint32_t* __restrict__ job,
-        const int64_t* __restrict__ step)
+        const int64_t* __restrict__ step, uint32_t tag)
 {
     const int K = (3 * M + 3) >> 2;                // Philox calls per chain and step
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)C * K) return;
     const int c = (int)(t / K), call = (int)(t - (int64_t)c * K);
     T g[4];
-    Normals<T>::draw4(seed, job[c], step[c], (uint32_t)call, 0u, g);
+    Normals<T>::draw4(seed, job[c], step[c], (uint32_t)call, tag, g);
     T* zc = z + (size_t)c * 3 * M;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -287,7 +289,7 @@ k_chain_steps(T* __restrict__ Rg, double* __restrict__ com, int64_t* __restrict_
               const double* __restrict__ shear, const T* __restrict__ chiT, const T* __restrict__ chi,
               const T* __restrict__ phi, const T* __restrict__ dm, const T* __restrict__ h,
               const T* __restrict__ w, const T* __restrict__ g, int C, int M, T c12nu, double w0_cm,
-              double dtau, uint32_t seed, int n_steps, int* __restrict__ bad)
+              double dtau, uint32_t seed, int n_steps, int mode_noise, int* __restrict__ bad)
 {
     extern __shared__ unsigned char chain_smem[];
     T* sR = reinterpret_cast<T*>(chain_smem);     // [3][M]
@@ -325,7 +327,7 @@ k_chain_steps(T* __restrict__ Rg, double* __restrict__ com, int64_t* __restrict_
         }
         for (int k = threadIdx.x; k < n_calls; k += blockDim.x) {
             T gq[4];
-            Normals<T>::draw4(seed, jb, st0 + s, (uint32_t)k, 0u, gq);
+            Normals<T>::draw4(seed, jb, st0 + s, (uint32_t)k, mode_noise ? 2u : 0u, gq);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int q = 4 * k + e;
@@ -337,13 +339,22 @@ k_chain_steps(T* __restrict__ Rg, double* __restrict__ com, int64_t* __restrict_
         for (int p = threadIdx.x; p < M; p += blockDim.x) {
             T d0 = T(0), d1 = T(0), d2 = T(0), z0 = T(0), z1 = T(0), z2 = T(0);
             for (int n = 0; n < M; ++n) {
-                const T x = chi[(size_t)n * M + p], f = phi[(size_t)n * M + p];
+                const T x = chi[(size_t)n * M + p];
                 d0 = fma(x, sv[n], d0);
                 d1 = fma(x, sv[M + n], d1);
                 d2 = fma(x, sv[2 * M + n], d2);
-                z0 = fma(f, sz[n], z0);
-                z1 = fma(f, sz[M + n], z1);
-                z2 = fma(f, sz[2 * M + n], z2);
+                if (!mode_noise) {
+                    const T f = phi[(size_t)n * M + p];
+                    z0 = fma(f, sz[n], z0);
+                    z1 = fma(f, sz[M + n], z1);
+                    z2 = fma(f, sz[2 * M + n], z2);
+                }
+            }
+            if (mode_noise) {
+                // mode-keyed noise: the drawn normals are Z itself
+                z0 = sz[p];
+                z1 = sz[M + p];
+                z2 = sz[2 * M + p];
             }
             if (p == 0) {
                 // centre of mass (zeta_0 = 0, Eq. d6 limit; w0_cm = w_0 / sqrt(M)), shear on x
@@ -419,7 +430,7 @@ k_chain_cluster(double* __restrict__ Rg, double* __restrict__ com, int64_t* __re
                 const double* __restrict__ chi, const double* __restrict__ phi, const double* __restrict__ dm,
                 const double* __restrict__ h, const double* __restrict__ w, const double* __restrict__ g, int C,
                 int M, double c12nu, double w0_cm, double dtau, int n_steps, const double* __restrict__ zpre,
-                int* __restrict__ bad)
+                int mode_noise, int* __restrict__ bad)
 {
     extern __shared__ unsigned char chain_smem[];
     double* sR = reinterpret_cast<double*>(chain_smem);   // [3][M]
@@ -479,13 +490,22 @@ k_chain_cluster(double* __restrict__ Rg, double* __restrict__ com, int64_t* __re
             const int p = act ? lo + gi : 0;
             double d0 = 0.0, d1 = 0.0, d2 = 0.0, z0 = 0.0, z1 = 0.0, z2 = 0.0;
             for (int n = j; act && n < M; n += Q) {
-                const double x = chi[(size_t)n * M + p], f = phi[(size_t)n * M + p];
+                const double x = chi[(size_t)n * M + p];
                 d0 = fma(x, sv[n], d0);
                 d1 = fma(x, sv[M + n], d1);
                 d2 = fma(x, sv[2 * M + n], d2);
-                z0 = fma(f, sz[n], z0);
-                z1 = fma(f, sz[M + n], z1);
-                z2 = fma(f, sz[2 * M + n], z2);
+                if (!mode_noise) {
+                    const double f = phi[(size_t)n * M + p];
+                    z0 = fma(f, sz[n], z0);
+                    z1 = fma(f, sz[M + n], z1);
+                    z2 = fma(f, sz[2 * M + n], z2);
+                }
+            }
+            if (mode_noise && act && j == 0) {
+                // mode-keyed noise: Z_p itself (taken once per group)
+                z0 = sz[p];
+                z1 = sz[M + p];
+                z2 = sz[2 * M + p];
             }
             for (int o = Q / 2; o > 0; o >>= 1) {
                 d0 += __shfl_xor_sync(0xffffffffu, d0, o);
@@ -534,10 +554,10 @@ k_chain_cluster(double* __restrict__ Rg, double* __restrict__ com, int64_t* __re
 
 // Bead normals of n_steps consecutive steps for the FP64 cluster path (Eq. b5):
 // z[s][c][3][M] = the normals of chain c at step step[c] + s, one thread per
-// (step, chain, Philox call).
+// (step, chain, Philox call); tag 2: the mode-keyed noise Z instead.
 __global__ void __launch_bounds__(256)
 k_noise_steps(double* __restrict__ z, int C, int M, uint32_t seed, const uint32_t* __restrict__ job,
-              const int64_t* __restrict__ step, int n_steps)
+              const int64_t* __restrict__ step, int n_steps, uint32_t tag)
 {
     const int K = (3 * M + 3) >> 2;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -546,7 +566,7 @@ k_noise_steps(double* __restrict__ z, int C, int M, uint32_t seed, const uint32_
     const int64_t sc = t / K;
     const int c = (int)(sc % C), s = (int)(sc / C);
     double gq[4];
-    Normals<double>::draw4(seed, job[c], step[c] + s, (uint32_t)call, 0u, gq);
+    Normals<double>::draw4(seed, job[c], step[c] + s, (uint32_t)call, tag, gq);
     double* zc = z + ((size_t)s * C + c) * 3 * M;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {

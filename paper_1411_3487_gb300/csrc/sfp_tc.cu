@@ -471,10 +471,13 @@ int tc_create(TcPlan** out, int M, int rows, const double* chi, const double* ch
 int tc_transform(TcPlan* p, int which, cudaStream_t stream)
 {
     // inverse: one table over the rows of R; forward: the force half (chi^T) and
-    // the noise half (phi^T) of [v | z] as grid z = 0, 1
+    // the noise half (phi^T) of [v | z] as grid z = 0, 1; which = 2: the force
+    // half alone (mode-keyed noise, whose Z needs no projection)
+    if (which < 0 || which > 2) return report(SFP_EINVAL, "tc_transform: which must be 0, 1 or 2");
     const int J = p->rows;
-    const dim3 grid((J + kRows - 1) / kRows, p->M / p->NT, which == 0 ? 1 : 2);
-    const int b0 = which == 0 ? 0 : 1, b1 = which == 0 ? 0 : 2;
+    const dim3 grid((J + kRows - 1) / kRows, p->M / p->NT, which == 1 ? 2 : 1);
+    const int b0 = which == 0 ? 0 : 1, b1 = which == 0 ? 0 : which == 1 ? 2 : 1;
+    which = which == 0 ? 0 : 1;
 #define SFP_TC_LAUNCH(K, S)                                                                             \
     K<<<grid, kThreads, S::kBytes, stream>>>(p->mapA[which], p->mapBh[b0], p->mapBl[b0], p->mapBh[b1], \
                                             p->mapBl[b1], p->out[which], J, p->M, p->err)

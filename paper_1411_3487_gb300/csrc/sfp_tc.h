@@ -25,7 +25,7 @@ bool tc_supported(int M);
 int tc_create(TcPlan** out, int M, int rows, const double* chi, const double* chiT, const double* phiT,
               const float* R, float* r_out, const float* fz, float* yz_out, int* err, cudaStream_t stream,
               bool bf16 = false, bool two = false);
-// which = 0: inverse, 1: forward.
+// which: 0 inverse (u = chi R), 1 forward (DeltaH = chi^T v and Z = phi^T z), 2 the forward force half alone.
 int tc_transform(TcPlan* plan, int which, cudaStream_t stream);
 // Device bytes the plan's tables hold.
 size_t tc_bytes(const TcPlan* plan);
