@@ -223,7 +223,7 @@ def run_native(args, rank, world, local):
     if precision == sfp.SFP_FP32_SIMT:
         path = sfp.SFP_PATH_STAGED
 
-    def timed_steps(prec, pth, steps, warmup, with_clocks, per_call=1, stages=True):
+    def timed_steps(prec, pth, steps, warmup, with_clocks, per_call=1, stages=True, noise=None):
         """`steps` timed Langevin steps as sfp_step calls of `per_call` steps,
         the L2 flushed before every call; returns per-call times (ms).  With
         `stages`, per-stage CUDA events are recorded inside the calls (which runs
@@ -231,6 +231,8 @@ def run_native(args, rank, world, local):
         transform); without, the kernel times come from a second, untimed pass."""
         b = sfp.Batch(chains, seed=1, precision=prec, stream=stream)
         b.set_path(pth)
+        if noise is not None:
+            b.set_noise(noise)
         b.init_equilibrium(0)
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
         for _ in range(warmup):
@@ -304,14 +306,15 @@ def run_native(args, rank, world, local):
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = end_to_end(sfp, b, torch, min(args.steps, 50))
 
-    plain = staged = other = single = None
+    plain = staged = other = single = modes = None
     if not args.no_plain and precision != sfp.SFP_FP32_SIMT:
         b.close()
         n_o = min(args.steps, 100)
 
-        def leg(prec, pth, per_call, what):
+        def leg(prec, pth, per_call, what, noise=None):
             staged_path = pth == sfp.SFP_PATH_STAGED
-            _, ms_l, _, _, k_l = timed_steps(prec, pth, n_o, 3, False, per_call, stages=not staged_path)
+            _, ms_l, _, _, k_l = timed_steps(prec, pth, n_o, 3, False, per_call, stages=not staged_path,
+                                             noise=noise)
             out = {"value": beads * n_o / (sum(ms_l) * 1e-3), "unit": UNIT, "ms_per_step": float(sum(ms_l) / n_o),
                    "steps_per_call": per_call, "kernels_us": k_l, "path": what}
             if staged_path:
@@ -330,6 +333,18 @@ def run_native(args, rank, world, local):
             other = leg(o_prec, sfp.SFP_PATH_FUSED, spc, "fused step")
             other.update({"precision": PREC_NAME[o_prec], "dtype": DTYPE[o_prec],
                           "roofline": roofline(other["kernels_us"], pk, how, o_prec, sfp.SFP_PATH_FUSED, sfp)})
+            # the same fused step with mode-keyed noise (Z drawn per mode: no
+            # projection, a third fewer MMAs; a different noise stream)
+            modes = leg(precision, sfp.SFP_PATH_FUSED, spc, "fused step, mode-keyed noise (sfp_set_noise)",
+                        noise=sfp.SFP_NOISE_MODES)
+            us_m = modes["kernels_us"].get("inverse_us")
+            if us_m and precision in (sfp.SFP_MIXED_BF16, sfp.SFP_FP32):
+                peak_m = pk.get("bf16_tflops", 1900.0) if precision == sfp.SFP_MIXED_BF16 else (
+                    pk.get("tf32_tflops") or pk.get("bf16_tflops", 1900.0) * 1.1 / 2.25)
+                fl = 3 * 12.0 * M_BEADS * beads      # inverse 2M x 3 + forward force half 2M x 3, three passes
+                modes["roofline_tensor"] = {"achieved": fl / (us_m * 1e-6) / 1e12, "peak": peak_m,
+                                            "frac": fl / (us_m * 1e-6) / 1e12 / peak_m, "kernel_us": us_m,
+                                            "flops_per_bead_step": 3 * 12 * M_BEADS}
 
     # the mixed-precision workload, 16384 chains x 512 bp at dt 15.9 ps: the fused
     # step (a tile per cluster of two CTAs) with each split, the staged
@@ -418,7 +433,8 @@ def run_native(args, rank, world, local):
             "sim_ns_per_s_per_chain": DT_PS * 1e-3 * args.steps / (tot_ms * 1e-3),
             "roofline": roof, "kernels_us": kern, "cpu_baseline": cpu, "e2e": e2e,
             "sustained": sustained, "plain_path": plain, "staged_path": staged,
-            "other_split_fused": other, "single_step_calls": single, "mixed_precision_512bp": big,
+            "other_split_fused": other, "mode_keyed_noise": modes, "single_step_calls": single,
+            "mixed_precision_512bp": big,
             "serving": serving, "uneven": uneven, "config1_fp64": config1,
             "tf32_peak": {"value": pk.get("tf32_tflops"), "unit": "TFLOP/s",
                           "how": "torch.matmul FP32 with TF32 tensor cores, 8192^3, best of 10 (measured live)"},
