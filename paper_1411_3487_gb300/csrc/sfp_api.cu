@@ -177,7 +177,8 @@ struct Group {
     int64_t* stop = nullptr;      // [C] a chain advances only while step < stop
     bool limited = false;         // some stop < INT64_MAX (serving pools)
     double* rod = nullptr;        // [3N] ground-state bonds and Cholesky factor (slot starts)
-    int32_t* slot_idx = nullptr;  // [C] staging for slot starts / reads
+    int32_t* slot_idx = nullptr;  // [C] staging for slot starts
+    int32_t* read_idx = nullptr;  // [kGather] staging for slot reads (their own: reads may run beside starts)
     uint32_t* slot_job = nullptr;
     int64_t* slot_stop = nullptr;
     double* slot_shear = nullptr;
@@ -231,6 +232,7 @@ struct sfp_batch {
     bool use_graph = false;
     bool grouped = true;               // one launch for the fused groups of all lengths
     int32_t noise = SFP_NOISE_BEADS;   // noise keying of the mode integrator
+    int64_t active_limit = -1;         // serving pools: the fused step covers chains [0, limit) (-1: all)
     cudaGraphExec_t graph = nullptr;
     int64_t graph_chunk = 0;
     int64_t graph_launches = 0;        // kernels in one replay
@@ -445,7 +447,7 @@ sfp::FusedArgs fused_args(const sfp_batch* b, const Group& g, int64_t n_steps)
     a.dm = (const float*)g.dm;
     a.g = (const float*)g.g;
     a.err = b->bad;
-    a.C = g.C;
+    a.C = b->active_limit >= 0 ? (int)std::min<int64_t>(g.C, b->active_limit) : g.C;
     a.c12nu = (float)(1.0 - 2.0 * b->dv.nu);
     a.seed = b->seed;
     a.inv_sqrtM = 1.0 / std::sqrt((double)g.M);
@@ -2038,6 +2040,7 @@ int slot_buffers(sfp_batch* b, Group& g)
     int rc;
     const int N = g.M - 1;
     if ((rc = dalloc_t(b, &g.rod, (size_t)3 * N * 8)) || (rc = dalloc_t(b, &g.slot_idx, (size_t)g.C * 4)) ||
+        (rc = dalloc_t(b, &g.read_idx, (size_t)kGather * 4)) ||
         (rc = dalloc_t(b, &g.slot_job, (size_t)g.C * 4)) || (rc = dalloc_t(b, &g.slot_stop, (size_t)g.C * 8)) ||
         (rc = dalloc_t(b, &g.slot_shear, (size_t)g.C * 8)) ||
         (rc = dalloc_t(b, &g.gather, (size_t)kGather * (3 * g.M + 4) * 8)))
@@ -2105,13 +2108,15 @@ int sfp::internal_slots_start(sfp_batch* b, const int32_t* slots, const uint32_t
 }
 
 int sfp::internal_slots_read(sfp_batch* b, const int32_t* slots, int32_t n, double* modes, double* com_nm,
-                             int64_t* steps)
+                             int64_t* steps, cudaStream_t stream, cudaEvent_t after)
 {
     if (!b || b->groups.size() != 1) return fail(SFP_EINVAL, "serving pools hold one length group");
     Group& g = b->groups[0];
     int rc = slot_buffers(b, g);
     if (rc) return rc;
     const int M = g.M;
+    cudaStream_t st_r = stream ? stream : b->stream;
+    if (after) CUDA_TRY(cudaStreamWaitEvent(st_r, after, 0));
     for (int i0 = 0; i0 < n; i0 += kGather) {
         const int k = std::min(kGather, n - i0);
         for (int i = 0; i < k; ++i)
@@ -2119,25 +2124,33 @@ int sfp::internal_slots_read(sfp_batch* b, const int32_t* slots, int32_t n, doub
         double* out = g.gather;
         double* cm = out + (size_t)kGather * 3 * M;
         int64_t* st = (int64_t*)(cm + (size_t)kGather * 3);
-        CUDA_TRY(cudaMemcpyAsync(g.slot_idx, slots + i0, (size_t)k * 4, cudaMemcpyHostToDevice, b->stream));
+        CUDA_TRY(cudaMemcpyAsync(g.read_idx, slots + i0, (size_t)k * 4, cudaMemcpyHostToDevice, st_r));
         if (b->precision == SFP_FP64)
-            sfp::k_gather_slots<double><<<k, 128, 0, b->stream>>>((const double*)g.R, g.com, g.step, g.slot_idx, k, M, out, cm, st);
+            sfp::k_gather_slots<double><<<k, 128, 0, st_r>>>((const double*)g.R, g.com, g.step, g.read_idx, k, M, out, cm, st);
         else
-            sfp::k_gather_slots<float><<<k, 128, 0, b->stream>>>((const float*)g.R, g.com, g.step, g.slot_idx, k, M, out, cm, st);
+            sfp::k_gather_slots<float><<<k, 128, 0, st_r>>>((const float*)g.R, g.com, g.step, g.read_idx, k, M, out, cm, st);
         CUDA_TRY(cudaGetLastError());
-        if (modes) CUDA_TRY(cudaMemcpyAsync(modes + (size_t)i0 * 3 * M, out, (size_t)k * 3 * M * 8, cudaMemcpyDeviceToHost, b->stream));
+        if (modes) CUDA_TRY(cudaMemcpyAsync(modes + (size_t)i0 * 3 * M, out, (size_t)k * 3 * M * 8, cudaMemcpyDeviceToHost, st_r));
         std::vector<double> c3((size_t)k * 3);
-        CUDA_TRY(cudaMemcpyAsync(c3.data(), cm, c3.size() * 8, cudaMemcpyDeviceToHost, b->stream));
-        if (steps) CUDA_TRY(cudaMemcpyAsync(steps + i0, st, (size_t)k * 8, cudaMemcpyDeviceToHost, b->stream));
-        CUDA_TRY(cudaStreamSynchronize(b->stream));
+        CUDA_TRY(cudaMemcpyAsync(c3.data(), cm, c3.size() * 8, cudaMemcpyDeviceToHost, st_r));
+        if (steps) CUDA_TRY(cudaMemcpyAsync(steps + i0, st, (size_t)k * 8, cudaMemcpyDeviceToHost, st_r));
+        CUDA_TRY(cudaStreamSynchronize(st_r));
         if (com_nm)
             for (size_t i = 0; i < c3.size(); ++i) com_nm[(size_t)i0 * 3 + i] = c3[i] * b->dv.d_nm;
     }
     int bad = 0;
-    CUDA_TRY(cudaMemcpy(&bad, b->bad, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpyAsync(&bad, b->bad, sizeof(int), cudaMemcpyDeviceToHost, st_r));
+    CUDA_TRY(cudaStreamSynchronize(st_r));
     if (bad & 4) return fail(SFP_ECUDA, "a 512-bead fused step ran without its two-CTA cluster");
     if (bad & 2) return fail(SFP_ETIMEDOUT, "a tensor-core pipeline wait timed out");
     if (bad & 1) return fail(SFP_ENONFINITE, "a chain's state became non-finite");
+    return SFP_OK;
+}
+
+int sfp::internal_set_active(sfp_batch* b, int64_t n)
+{
+    if (!b) return fail(SFP_EINVAL, "batch is NULL");
+    b->active_limit = n;
     return SFP_OK;
 }
 

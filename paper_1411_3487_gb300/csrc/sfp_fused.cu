@@ -1759,7 +1759,8 @@ int fused_create(FusedPlan** out, int M, int C, const double* chi, const double*
 int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
 {
     if (args.cpt != p->cpt) return report(SFP_EINVAL, "fused step: chains per tile differ from the plan's");
-    const dim3 grid((unsigned)((p->C + p->cpt - 1) / p->cpt));
+    if (args.C < 1 || args.C > p->C) return report(SFP_EINVAL, "fused step: chain count outside the plan");
+    const dim3 grid((unsigned)((args.C + p->cpt - 1) / p->cpt));   // the first args.C chains
     FusedArgs a = args;
     a.zbuf = p->zbuf;
     a.w = p->w32;
@@ -1830,7 +1831,8 @@ int fused_step_grouped(FusedPlan* const* plans, const FusedArgs* args, int n, cu
         GroupSlot& g = P.g[slot];
         g.tmR = p->tmR; g.tmChiH = p->tmChiH; g.tmChiL = p->tmChiL; g.tmFH = p->tmFH; g.tmFL = p->tmFL;
         g.a = args[i];
-        g.tiles = (p->C + p->cpt - 1) / p->cpt;
+        if (args[i].C < 1 || args[i].C > p->C) return report(SFP_EINVAL, "grouped step: chain count outside the plan");
+        g.tiles = (args[i].C + p->cpt - 1) / p->cpt;
     }
     P.err = args[0].err;
     const int small = P.g[1].tiles + P.g[2].tiles + P.g[3].tiles;

@@ -13,6 +13,10 @@
 //           (per-slot stop step), so no job runs past its length.
 //   retire  finished slots are read back, their results queued for
 //           sfp_server_poll, and the slots reused by the next admissions.
+//           A slot that has reached its stop step no longer changes, so the
+//           jobs that finished in one round are read on a side stream of the
+//           pool while the next round's quanta already run: each pool's
+//           stream always has its next quantum queued.
 // Jobs that arrive while others run join the next quantum of the same launch:
 // their work overlaps on the device.  A job's noise is keyed by its own id
 // and step counter, so its result does not depend on the slot it ran in or on
@@ -47,6 +51,7 @@ struct Job {
     Pool* pool = nullptr;
     int slot = -1;
     int64_t remaining = 0;          // steps still to run (host mirror of the slot)
+    int64_t fin_round = -1;         // the round whose quantum ran the job's last step
     std::vector<double> modes;      // [3][M] after the run (kept if requested)
     double com_nm[3] = {0, 0, 0};
 };
@@ -54,11 +59,14 @@ struct Job {
 struct Pool {
     sfp_batch* b = nullptr;
     cudaStream_t stream = nullptr;  // the pool's own stream: pools of different shapes overlap
+    cudaStream_t rs = nullptr;      // reads of finished slots, beside the next quanta
+    cudaEvent_t ev[2] = {nullptr, nullptr};   // end of the pool's quantum of round r, in ev[r & 1]
     int M = 0;
     double dtau = 0.0;
     int cap = 0;
     std::vector<Job*> slot_job;     // nullptr = free slot
-    int active = 0;
+    int active = 0;                 // slots holding a job (running or waiting to be read)
+    int running = 0;                // slots whose job still has steps to run
     size_t bytes = 0;
     // slots admitted in this round, started together
     std::vector<int32_t> st_slot;
@@ -92,6 +100,7 @@ struct sfp_server {
     std::string worker_msg;
 
     // owned by the worker thread
+    int64_t round = 0;                 // quanta issued so far
     std::deque<Job*> pending;
     std::vector<std::unique_ptr<Pool>> pools;
     std::thread worker;
@@ -145,6 +154,16 @@ int make_pool(sfp_server* s, int M, double dtau, int cap, std::unique_ptr<Pool>*
     }
     std::unique_ptr<Pool> p(new Pool());
     p->stream = st;
+    if (cudaStreamCreateWithFlags(&p->rs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev[1], cudaEventDisableTiming) != cudaSuccess) {
+        if (p->rs) cudaStreamDestroy(p->rs);
+        for (cudaEvent_t e : p->ev)
+            if (e) cudaEventDestroy(e);
+        sfp_destroy(b);
+        cudaStreamDestroy(st);
+        return srv_fail(SFP_ECUDA, "pool stream creation failed");
+    }
     sfp::internal_shape(b, nullptr, nullptr, nullptr, &p->bytes);
     p->b = b;
     p->M = M;
@@ -159,10 +178,17 @@ int make_pool(sfp_server* s, int M, double dtau, int cap, std::unique_ptr<Pool>*
     return SFP_OK;
 }
 
+void release_pool(Pool& p)
+{
+    sfp_destroy(p.b);
+    cudaStreamDestroy(p.stream);
+    cudaStreamDestroy(p.rs);
+    for (cudaEvent_t e : p.ev) cudaEventDestroy(e);
+}
+
 void drop_pool(sfp_server* s, size_t i)
 {
-    sfp_destroy(s->pools[i]->b);
-    cudaStreamDestroy(s->pools[i]->stream);
+    release_pool(*s->pools[i]);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->held -= s->pools[i]->bytes;
@@ -245,6 +271,7 @@ int admit(sfp_server* s)
         }
         pool->slot_job[slot] = j;
         pool->active++;
+        pool->running++;
         j->pool = pool;
         j->slot = slot;
         j->remaining = j->desc.n_steps;
@@ -272,19 +299,24 @@ int admit(sfp_server* s)
 }
 
 // Read back and release the slots whose jobs have run all their steps.
-int retire(sfp_server* s)
+// Read back and hand out the jobs that ran their last step in a round up to
+// `upto`.  side: each pool reads on its side stream after the event of round
+// upto (the next round's quanta may run meanwhile), else after everything
+// queued on the pool's stream.
+int retire(sfp_server* s, int64_t upto, bool side)
 {
     for (auto& pp : s->pools) {
         Pool& p = *pp;
         std::vector<int32_t> fin;
         for (int c = 0; c < p.cap; ++c)
-            if (p.slot_job[c] && p.slot_job[c]->remaining <= 0) fin.push_back(c);
+            if (p.slot_job[c] && p.slot_job[c]->fin_round >= 0 && p.slot_job[c]->fin_round <= upto) fin.push_back(c);
         if (fin.empty()) continue;
         const int n = (int)fin.size();
         std::vector<double> modes(s->cfg.keep_results ? (size_t)n * 3 * p.M : 0), com((size_t)n * 3);
         std::vector<int64_t> steps(n);
         const int rc = sfp::internal_slots_read(p.b, fin.data(), n, s->cfg.keep_results ? modes.data() : nullptr,
-                                                com.data(), steps.data());
+                                                com.data(), steps.data(), side ? p.rs : nullptr,
+                                                side ? p.ev[upto & 1] : nullptr);
         const double t = s->now();
         std::lock_guard<std::mutex> lk(s->mu);
         for (int i = 0; i < n; ++i) {
@@ -329,29 +361,43 @@ void worker_main(sfp_server* s)
         }
         int rc = admit(s);
         if (!rc) {
-            // one quantum of every pool with active slots, each on its own stream
+            // one quantum of every pool with running slots, each on its own stream
             // (queued without waiting, so the shapes share the GPU), the pool
-            // with the most work (active slots x M^2) first
+            // with the most work (running slots x M^2) first; an event marks the
+            // end of each pool's quantum of this round
+            const int64_t r = s->round;
             std::vector<Pool*> order;
             for (auto& p : s->pools)
-                if (p->active > 0) order.push_back(p.get());
+                if (p->running > 0) order.push_back(p.get());
             std::stable_sort(order.begin(), order.end(), [](const Pool* x, const Pool* y) {
-                return (double)x->active * x->M * x->M > (double)y->active * y->M * y->M;
+                return (double)x->running * x->M * x->M > (double)y->running * y->M * y->M;
             });
-            bool any = false;
             for (Pool* p : order) {
-                any = true;
+                // the quantum covers the slots up to the highest running one
+                int top = 0;
+                for (int c = 0; c < p->cap; ++c)
+                    if (p->slot_job[c] && p->slot_job[c]->fin_round < 0) top = c + 1;
+                sfp::internal_set_active(p->b, top);
                 rc = sfp_step(p->b, s->cfg.quantum_steps);
+                if (!rc && cudaEventRecord(p->ev[r & 1], p->stream) != cudaSuccess) rc = SFP_ECUDA;
                 if (rc) {
                     srv_fail(rc, std::string("step failed: ") + sfp_last_error());
                     break;
                 }
+                for (Job* j : p->slot_job)
+                    if (j && j->fin_round < 0) {
+                        j->remaining -= s->cfg.quantum_steps;
+                        if (j->remaining <= 0) {
+                            j->fin_round = r;
+                            p->running--;
+                        }
+                    }
             }
-            if (!rc && any) {
-                for (auto& p : s->pools)
-                    for (Job* j : p->slot_job)
-                        if (j) j->remaining -= s->cfg.quantum_steps;
-                rc = retire(s);
+            if (!rc) {
+                // the jobs of the previous round are read while this round runs; with
+                // nothing queued this round, every finished job at once
+                rc = order.empty() ? retire(s, r, false) : retire(s, r - 1, true);
+                s->round++;
             }
         }
         if (rc) {
@@ -362,10 +408,7 @@ void worker_main(sfp_server* s)
             break;
         }
     }
-    for (auto& p : s->pools) {
-        sfp_destroy(p->b);
-        cudaStreamDestroy(p->stream);
-    }
+    for (auto& p : s->pools) release_pool(*p);
     s->pools.clear();
     std::lock_guard<std::mutex> lk(s->mu);
     s->held = 0;
