@@ -305,6 +305,8 @@ def run_native(args, rank, world, local):
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = end_to_end(sfp, b, torch, min(args.steps, 50))
+    e64 = end_to_end(sfp, b, torch, min(args.steps, 50), f32=False)
+    e2e["fp64_state"] = {k: e64[k] for k in ("value", "h2d_bytes_per_step", "d2h_bytes_per_step", "api")}
 
     plain = staged = other = single = modes = None
     if not args.no_plain and precision != sfp.SFP_FP32_SIMT:
@@ -558,30 +560,38 @@ def staged_hbm(kern, pk, beads=None):
     return out
 
 
-def end_to_end(sfp, b, torch, steps):
-    """Per step: H2D of the FP64 mode state from pinned host memory (sfp_set_modes),
-    one sfp_step, D2H of the FP64 mode state (sfp_observe); wall-clock timed."""
+def end_to_end(sfp, b, torch, steps, f32=True):
+    """Per step: H2D of the mode state from pinned host memory, one sfp_step,
+    D2H of the mode state; wall-clock timed.  f32: the state as FP32
+    (sfp_set_modes_f32 + SFP_OBS_MODES_F32, the precision the FP32 and mixed
+    paths hold it in), else FP64 (sfp_set_modes + SFP_OBS_MODES)."""
     n = 3 * C_CHAINS * M_BEADS
-    hin = torch.empty(n, dtype=torch.float64, pin_memory=True)
-    hout = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    dt_t, dt_n, width = (torch.float32, np.float32, 4) if f32 else (torch.float64, np.float64, 8)
+    hin = torch.empty(n, dtype=dt_t, pin_memory=True)
+    hout = torch.empty(n, dtype=dt_t, pin_memory=True)
     a_in, a_out = hin.numpy(), hout.numpy()
-    a_in[:] = b.modes().ravel()
-    import ctypes as ct
+    a_in[:] = b.modes().ravel().astype(dt_n)
     L = sfp._lib.load()
-    for _ in range(3):
-        sfp._lib.check(L.sfp_set_modes(b._h, a_in.ctypes.data, n))
+    set_modes = L.sfp_set_modes_f32 if f32 else L.sfp_set_modes
+    what = sfp.SFP_OBS_MODES_F32 if f32 else sfp.SFP_OBS_MODES
+
+    def one():
+        sfp._lib.check(set_modes(b._h, a_in.ctypes.data, n))
         sfp._lib.check(L.sfp_step(b._h, 1))
-        sfp._lib.check(L.sfp_observe(b._h, sfp.SFP_OBS_MODES, a_out.ctypes.data, n * 8))
+        sfp._lib.check(L.sfp_observe(b._h, what, a_out.ctypes.data, n * width))
+
+    for _ in range(3):
+        one()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        sfp._lib.check(L.sfp_set_modes(b._h, a_in.ctypes.data, n))
-        sfp._lib.check(L.sfp_step(b._h, 1))
-        sfp._lib.check(L.sfp_observe(b._h, sfp.SFP_OBS_MODES, a_out.ctypes.data, n * 8))
+        one()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    return {"value": C_CHAINS * M_BEADS * steps / dt, "unit": UNIT, "h2d_bytes_per_step": n * 8,
-            "d2h_bytes_per_step": n * 8, "steps": steps, "api": "sfp_set_modes + sfp_step + sfp_observe"}
+    api = "sfp_set_modes_f32 + sfp_step + sfp_observe(SFP_OBS_MODES_F32)" if f32 else \
+        "sfp_set_modes + sfp_step + sfp_observe(SFP_OBS_MODES)"
+    return {"value": C_CHAINS * M_BEADS * steps / dt, "unit": UNIT, "h2d_bytes_per_step": n * width,
+            "d2h_bytes_per_step": n * width, "steps": steps, "api": api}
 
 
 def bench_precision(sfp, args):

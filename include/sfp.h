@@ -140,6 +140,11 @@ int sfp_init_equilibrium(sfp_batch *b, int64_t burn_in_steps);
  * reads the caller's buffer from the GPU directly (no staging copy); the
  * same holds for SFP_OBS_MODES of sfp_observe. */
 int sfp_set_modes(sfp_batch *b, const double *host_modes, size_t n_doubles);
+/* sfp_set_modes from FP32 amplitudes (same layout and units, n_floats values):
+ * half the host traffic; the SFP_FP32 / mixed state is FP32 already, so only
+ * R_0 (the centre of mass, carried in FP64) is rounded.  SFP_EINVAL for a NULL
+ * argument or too few values. */
+int sfp_set_modes_f32(sfp_batch *b, const float *host_modes, size_t n_floats);
 int sfp_set_positions(sfp_batch *b, const double *host_pos_nm, size_t n_doubles);
 
 /* Set every chain's step counter (the Philox counter of its next step). */
@@ -157,6 +162,8 @@ int sfp_step(sfp_batch *b, int64_t n_steps);
 
 /* Observables, copied to host_out (synchronises the stream).
  *   SFP_OBS_MODES      FP64 packed [3][M_c], scaled units, R_0 = sqrt(M) r_cm
+ *   SFP_OBS_MODES_F32  the same rounded to FP32 (half the bytes; written
+ *                      directly like SFP_OBS_MODES into a page-locked buffer)
  *   SFP_OBS_POSITIONS  FP64 packed [3][M_c], absolute bead positions in nm
  *   SFP_OBS_COM        FP64 [C][3] centre of mass in nm
  *   SFP_OBS_STEP       int64 [C] step counters
@@ -198,7 +205,7 @@ int sfp_step(sfp_batch *b, int64_t n_steps);
 enum { SFP_OBS_MODES = 0, SFP_OBS_POSITIONS = 1, SFP_OBS_COM = 2, SFP_OBS_STEP = 3,
        SFP_OBS_SHAPE = 4, SFP_OBS_ACCUM = 5, SFP_OBS_MODE_POWER = 6, SFP_OBS_COM_MSD = 7,
        SFP_OBS_MID_MSD = 8, SFP_OBS_E2E2_MEAN = 9, SFP_OBS_MODE_VAR = 10, SFP_OBS_E2E_MSD = 11,
-       SFP_OBS_BOND_MSD = 12 };
+       SFP_OBS_BOND_MSD = 12, SFP_OBS_MODES_F32 = 13 };
 int sfp_observe(sfp_batch *b, int32_t what, void *host_out, size_t bytes);
 
 /* Kernel path of the step (SFP_FP32_SIMT ignores it).

@@ -16,7 +16,7 @@ from ._lib import (SFP_FP32, SFP_FP32_SIMT, SFP_FP64, SFP_MIXED_BF16, SFP_MIXED_
                    SFP_OBS_ACCUM, SFP_OBS_COM,
                    SFP_OBS_BOND_MSD, SFP_OBS_COM_MSD, SFP_OBS_E2E2_MEAN, SFP_OBS_E2E_MSD, SFP_OBS_MID_MSD,
                    SFP_OBS_MODE_POWER, SFP_OBS_MODE_VAR,
-                   SFP_OBS_MODES, SFP_OBS_POSITIONS,
+                   SFP_OBS_MODES, SFP_OBS_MODES_F32, SFP_OBS_POSITIONS,
                    SFP_INTEGRATOR_EULER, SFP_INTEGRATOR_MODES, SFP_NOISE_BEADS, SFP_NOISE_MODES, SFP_OBS_SHAPE, SFP_OBS_STEP,
                    SFP_PATH_FUSED, SFP_PATH_STAGED, SFP_PROBE_BONDS, SFP_PROBE_DH,
                    SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_ZMODE, SfpChainDesc, SfpError,
@@ -110,15 +110,24 @@ class Batch:
     def init_equilibrium(self, burn_in_steps: int = 0) -> None:
         _lib.check(_lib.load().sfp_init_equilibrium(self._h, burn_in_steps))
 
-    def _packed(self, a) -> np.ndarray:
+    def _packed(self, a, dtype=np.float64) -> np.ndarray:
         if isinstance(a, (list, tuple)):
-            a = np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in a])
-        a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+            a = np.concatenate([np.asarray(x, dtype=dtype).ravel() for x in a])
+        a = np.ascontiguousarray(a, dtype=dtype).ravel()
         if a.size != self.offsets[-1]:
-            raise ValueError(f"expected {self.offsets[-1]} doubles, got {a.size}")
+            raise ValueError(f"expected {self.offsets[-1]} values, got {a.size}")
         return a
 
     def set_modes(self, modes) -> None:
+        """Mode amplitudes, packed [3][M_c] per chain; a float32 array (or a list
+        of them) goes through sfp_set_modes_f32 (half the host traffic)."""
+        f32 = (isinstance(modes, np.ndarray) and modes.dtype == np.float32) or (
+            isinstance(modes, (list, tuple)) and len(modes) > 0 and all(
+                isinstance(x, np.ndarray) and x.dtype == np.float32 for x in modes))
+        if f32:
+            a = self._packed(modes, np.float32)
+            _lib.check(_lib.load().sfp_set_modes_f32(self._h, a.ctypes.data, a.size))
+            return
         a = self._packed(modes)
         _lib.check(_lib.load().sfp_set_modes(self._h, a.ctypes.data, a.size))
 
@@ -179,8 +188,8 @@ class Batch:
 
     def observe(self, what: int):
         L = _lib.load()
-        if what in (SFP_OBS_MODES, SFP_OBS_POSITIONS, SFP_OBS_MODE_POWER, SFP_OBS_MODE_VAR):
-            out = np.zeros(int(self.offsets[-1]))
+        if what in (SFP_OBS_MODES, SFP_OBS_MODES_F32, SFP_OBS_POSITIONS, SFP_OBS_MODE_POWER, SFP_OBS_MODE_VAR):
+            out = np.zeros(int(self.offsets[-1]), dtype=np.float32 if what == SFP_OBS_MODES_F32 else np.float64)
             _lib.check(L.sfp_observe(self._h, what, out.ctypes.data, out.nbytes))
             return self._unpack(out)
         if what == SFP_OBS_COM:

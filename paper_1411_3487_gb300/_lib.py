@@ -20,6 +20,7 @@ SFP_MIXED_BF16_2 = 3        # FP32 state, two-pass BF16 transforms (tables round
 SFP_OBS_MODES, SFP_OBS_POSITIONS, SFP_OBS_COM, SFP_OBS_STEP, SFP_OBS_SHAPE = 0, 1, 2, 3, 4
 SFP_OBS_ACCUM, SFP_OBS_MODE_POWER, SFP_OBS_COM_MSD = 5, 6, 7
 SFP_OBS_MID_MSD, SFP_OBS_E2E2_MEAN, SFP_OBS_MODE_VAR, SFP_OBS_E2E_MSD, SFP_OBS_BOND_MSD = 8, 9, 10, 11, 12
+SFP_OBS_MODES_F32 = 13
 SFP_PATH_FUSED, SFP_PATH_STAGED = 0, 1
 SFP_INTEGRATOR_MODES, SFP_INTEGRATOR_EULER = 0, 1
 SFP_NOISE_BEADS, SFP_NOISE_MODES = 0, 1
@@ -27,7 +28,7 @@ SFP_PROBE_BONDS, SFP_PROBE_FORCE, SFP_PROBE_NOISE, SFP_PROBE_DH, SFP_PROBE_ZMODE
 
 # Every entry point declared in include/sfp.h.
 EXPORTS = (
-    "sfp_params_dsdna", "sfp_derive", "sfp_create", "sfp_init_equilibrium", "sfp_set_modes",
+    "sfp_params_dsdna", "sfp_derive", "sfp_create", "sfp_init_equilibrium", "sfp_set_modes", "sfp_set_modes_f32",
     "sfp_set_positions", "sfp_set_step", "sfp_step", "sfp_observe", "sfp_probe", "sfp_save",
     "sfp_load", "sfp_info", "sfp_destroy", "sfp_last_error", "sfp_philox_words",
     "sfp_stage_timing", "sfp_stage_times", "sfp_step_noalloc", "sfp_set_sampling", "sfp_set_msd_lags",
@@ -92,6 +93,7 @@ def load(path: str | None = None):
                                  ct.POINTER(vp)]
         L.sfp_init_equilibrium.argtypes = [vp, i64]
         L.sfp_set_modes.argtypes = [vp, vp, sz]
+        L.sfp_set_modes_f32.argtypes = [vp, vp, sz]
         L.sfp_set_positions.argtypes = [vp, vp, sz]
         L.sfp_set_step.argtypes = [vp, i64]
         L.sfp_step.argtypes = [vp, i64]

@@ -890,15 +890,30 @@ int step_all(sfp_batch* b, int64_t n_steps)
     return SFP_OK;
 }
 
-// Modes (FP64, device, [C][3][M] incl. p = 0) -> state
-int load_modes_dev(sfp_batch* b, Group& g, const double* src)
+// Modes (S = double or float, device-readable, [C][3][M] incl. p = 0) -> state
+template <typename S>
+int load_modes_dev(sfp_batch* b, Group& g, const S* src)
 {
     const int64_t n = (int64_t)g.C * 3 * g.M;
     const double inv = 1.0 / std::sqrt((double)g.M);
     if (b->precision == SFP_FP64)
-        sfp::k_load_modes<double><<<nblk(n, 256), 256, 0, b->stream>>>(src, (double*)g.R, g.com, g.C, g.M, inv);
+        sfp::k_load_modes<S, double><<<nblk(n, 256), 256, 0, b->stream>>>(src, (double*)g.R, g.com, g.C, g.M, inv);
     else
-        sfp::k_load_modes<float><<<nblk(n, 256), 256, 0, b->stream>>>(src, (float*)g.R, g.com, g.C, g.M, inv);
+        sfp::k_load_modes<S, float><<<nblk(n, 256), 256, 0, b->stream>>>(src, (float*)g.R, g.com, g.C, g.M, inv);
+    CUDA_TRY(cudaGetLastError());
+    return SFP_OK;
+}
+
+// State -> modes (D = double or float, device-writable, [C][3][M], R_0 = sqrt(M) r_cm)
+template <typename D>
+int store_modes_dev(sfp_batch* b, Group& g, D* dst)
+{
+    const int64_t n = (int64_t)g.C * 3 * g.M;
+    const double sq = std::sqrt((double)g.M);
+    if (b->precision == SFP_FP64)
+        sfp::k_store_modes<double, D><<<nblk(n, 256), 256, 0, b->stream>>>((const double*)g.R, g.com, dst, g.C, g.M, sq);
+    else
+        sfp::k_store_modes<float, D><<<nblk(n, 256), 256, 0, b->stream>>>((const float*)g.R, g.com, dst, g.C, g.M, sq);
     CUDA_TRY(cudaGetLastError());
     return SFP_OK;
 }
@@ -929,19 +944,21 @@ const void* mapped_host(const void* p)
 }
 
 // Gather host packed [3][M_c] blocks of one group into a contiguous host array.
-void gather_group(const sfp_batch* b, const Group& g, const double* packed, std::vector<double>& out)
+template <typename E>
+void gather_group(const sfp_batch* b, const Group& g, const E* packed, std::vector<E>& out)
 {
     const size_t blk = (size_t)3 * g.M;
     out.resize((size_t)g.C * blk);
     for (int i = 0; i < g.C; ++i)
-        std::memcpy(out.data() + i * blk, packed + b->off[g.chains[i]], blk * sizeof(double));
+        std::memcpy(out.data() + i * blk, packed + b->off[g.chains[i]], blk * sizeof(E));
 }
 
-void scatter_group(const sfp_batch* b, const Group& g, const std::vector<double>& in, double* packed)
+template <typename E>
+void scatter_group(const sfp_batch* b, const Group& g, const std::vector<E>& in, E* packed)
 {
     const size_t blk = (size_t)3 * g.M;
     for (int i = 0; i < g.C; ++i)
-        std::memcpy(packed + b->off[g.chains[i]], in.data() + i * blk, blk * sizeof(double));
+        std::memcpy(packed + b->off[g.chains[i]], in.data() + i * blk, blk * sizeof(E));
 }
 
 // CoM-relative bead positions (FP64, scaled) of a group into g.stage2
@@ -1057,6 +1074,60 @@ cudaError_t gemm_on(cudaStream_t st, const T* In, const T* B, T* Out, int J, int
         sfp::k_gemm_nt<T, 64, 64, 8, 4, 4><<<grid, 256, 0, st>>>(In, B, Out, J, Nc, K);
     }
     return cudaGetLastError();
+}
+
+// sfp_set_modes body for host element type S (double or float).
+template <typename S>
+int set_modes_impl(sfp_batch* b, const S* host, size_t n)
+{
+    if (!b || !host) return fail(SFP_EINVAL, "NULL argument");
+    if (n < (size_t)(3 * b->total_beads)) return fail(SFP_EINVAL, "need %lld values", (long long)(3 * b->total_beads));
+    std::vector<S> tmp;
+    for (auto& g : b->groups) {
+        const S* dev = b->groups.size() == 1 ? (const S*)mapped_host(host) : nullptr;
+        if (dev) {   // one group, page-locked caller buffer: the kernel reads it directly
+            int rc = load_modes_dev(b, g, dev);
+            if (rc) return rc;
+            CUDA_TRY(cudaStreamSynchronize(b->stream));
+            continue;
+        }
+        S* stage = (S*)g.stage;   // [C][3][M] doubles: room for either type
+        if (b->groups.size() == 1) {   // packed order is the group order: copy straight from the caller
+            CUDA_TRY(cudaMemcpyAsync(stage, host, (size_t)g.C * 3 * g.M * sizeof(S), cudaMemcpyHostToDevice, b->stream));
+        } else {
+            gather_group(b, g, host, tmp);
+            CUDA_TRY(cudaMemcpyAsync(stage, tmp.data(), tmp.size() * sizeof(S), cudaMemcpyHostToDevice, b->stream));
+        }
+        int rc = load_modes_dev(b, g, (const S*)stage);
+        if (rc) return rc;
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+    }
+    b->probed = false;
+    return SFP_OK;
+}
+
+// SFP_OBS_MODES / SFP_OBS_MODES_F32 of one group into the caller's packed
+// array.  With one group and a page-locked caller buffer the kernel writes it
+// directly and returns without waiting (sfp_observe's error-word read waits for
+// the stream).
+template <typename D>
+int observe_modes(sfp_batch* b, Group& g, D* host_out, std::vector<D>& tmp)
+{
+    const int64_t n = (int64_t)g.C * 3 * g.M;
+    D* direct = b->groups.size() == 1 ? (D*)mapped_host(host_out) : nullptr;
+    D* dst = direct ? direct : (D*)g.stage;
+    int rc = store_modes_dev(b, g, dst);
+    if (rc || direct) return rc;
+    if (b->groups.size() == 1) {
+        CUDA_TRY(cudaMemcpyAsync(host_out, dst, n * sizeof(D), cudaMemcpyDeviceToHost, b->stream));
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+    } else {
+        tmp.resize(n);
+        CUDA_TRY(cudaMemcpyAsync(tmp.data(), dst, n * sizeof(D), cudaMemcpyDeviceToHost, b->stream));
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+        scatter_group(b, g, tmp, host_out);
+    }
+    return SFP_OK;
 }
 
 }  // namespace
@@ -1325,29 +1396,12 @@ int sfp_set_step(sfp_batch* b, int64_t step)
 
 int sfp_set_modes(sfp_batch* b, const double* host, size_t n_doubles)
 {
-    if (!b || !host) return fail(SFP_EINVAL, "NULL argument");
-    if (n_doubles < (size_t)(3 * b->total_beads)) return fail(SFP_EINVAL, "need %lld doubles", (long long)(3 * b->total_beads));
-    std::vector<double> tmp;
-    for (auto& g : b->groups) {
-        const double* dev = b->groups.size() == 1 ? (const double*)mapped_host(host) : nullptr;
-        if (dev) {   // one group, page-locked caller buffer: the kernel reads it directly
-            int rc = load_modes_dev(b, g, dev);
-            if (rc) return rc;
-            CUDA_TRY(cudaStreamSynchronize(b->stream));
-            continue;
-        }
-        if (b->groups.size() == 1) {   // packed order is the group order: copy straight from the caller
-            CUDA_TRY(cudaMemcpyAsync(g.stage, host, (size_t)g.C * 3 * g.M * 8, cudaMemcpyHostToDevice, b->stream));
-        } else {
-            gather_group(b, g, host, tmp);
-            CUDA_TRY(cudaMemcpyAsync(g.stage, tmp.data(), tmp.size() * 8, cudaMemcpyHostToDevice, b->stream));
-        }
-        int rc = load_modes_dev(b, g, g.stage);
-        if (rc) return rc;
-        CUDA_TRY(cudaStreamSynchronize(b->stream));
-    }
-    b->probed = false;
-    return SFP_OK;
+    return set_modes_impl(b, host, n_doubles);
+}
+
+int sfp_set_modes_f32(sfp_batch* b, const float* host, size_t n_floats)
+{
+    return set_modes_impl(b, host, n_floats);
 }
 
 int sfp_set_positions(sfp_batch* b, const double* host, size_t n_doubles)
@@ -1415,6 +1469,7 @@ int sfp_observe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
     size_t need = 0;
     switch (what) {
         case SFP_OBS_MODES: case SFP_OBS_POSITIONS: need = packed; break;
+        case SFP_OBS_MODES_F32: need = packed / 2; break;
         case SFP_OBS_COM: need = (size_t)b->C * 3 * 8; break;
         case SFP_OBS_STEP: need = (size_t)b->C * 8; break;
         case SFP_OBS_SHAPE: need = (size_t)b->C * 4 * 8; break;
@@ -1432,27 +1487,15 @@ int sfp_observe(sfp_batch* b, int32_t what, void* host_out, size_t bytes)
         return fail(SFP_EINVAL, "observable %d needs sfp_set_sampling first", what);
     if (bytes < need) return fail(SFP_EINVAL, "buffer too small: need %zu bytes", need);
     std::vector<double> tmp;
+    std::vector<float> tmp32;
     for (auto& g : b->groups) {
         const int64_t n = (int64_t)g.C * 3 * g.M;
         if (what == SFP_OBS_MODES) {
-            // one group, page-locked caller buffer: the kernel writes it directly
-            double* direct = b->groups.size() == 1 ? (double*)mapped_host(host_out) : nullptr;
-            double* dst = direct ? direct : g.stage;
-            if (b->precision == SFP_FP64)
-                sfp::k_store_modes<double><<<nblk(n, 256), 256, 0, b->stream>>>((const double*)g.R, g.com, dst, g.C, g.M, std::sqrt((double)g.M));
-            else
-                sfp::k_store_modes<float><<<nblk(n, 256), 256, 0, b->stream>>>((const float*)g.R, g.com, dst, g.C, g.M, std::sqrt((double)g.M));
-            CUDA_TRY(cudaGetLastError());
-            if (direct) continue;   // the error-word read below waits for the stream
-            if (b->groups.size() == 1) {
-                CUDA_TRY(cudaMemcpyAsync(host_out, g.stage, n * 8, cudaMemcpyDeviceToHost, b->stream));
-                CUDA_TRY(cudaStreamSynchronize(b->stream));
-            } else {
-                tmp.resize(n);
-                CUDA_TRY(cudaMemcpyAsync(tmp.data(), g.stage, n * 8, cudaMemcpyDeviceToHost, b->stream));
-                CUDA_TRY(cudaStreamSynchronize(b->stream));
-                scatter_group(b, g, tmp, (double*)host_out);
-            }
+            int rc = observe_modes(b, g, (double*)host_out, tmp);
+            if (rc) return rc;
+        } else if (what == SFP_OBS_MODES_F32) {
+            int rc = observe_modes(b, g, (float*)host_out, tmp32);
+            if (rc) return rc;
         } else if (what == SFP_OBS_POSITIONS || what == SFP_OBS_SHAPE) {
             int rc = positions_dev(b, g);
             if (rc) return rc;

@@ -730,9 +730,10 @@ __global__ void k_gather_slots(const T* __restrict__ R, const double* __restrict
 // ---------------------------------------------------------------------------
 // Small conversion kernels.
 // ---------------------------------------------------------------------------
-// modes (FP64, packed rows incl. p = 0) -> state R (T, p = 0 zeroed) + r_cm
-template <typename T>
-__global__ void k_load_modes(const double* __restrict__ src, T* __restrict__ R,
+// modes (S = FP64 or FP32, packed rows incl. p = 0) -> state R (T, p = 0
+// zeroed) + r_cm
+template <typename S, typename T>
+__global__ void k_load_modes(const S* __restrict__ src, T* __restrict__ R,
                              double* __restrict__ com, int C, int M, double inv_sqrtM)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -740,22 +741,22 @@ __global__ void k_load_modes(const double* __restrict__ src, T* __restrict__ R,
     const int p = (int)(t % M);
     const int64_t row = t / M;
     if (p == 0) {
-        com[row] = src[t] * inv_sqrtM;
+        com[row] = (double)src[t] * inv_sqrtM;
         R[t] = T(0);
     } else {
         R[t] = (T)src[t];
     }
 }
 
-// state -> modes (FP64, R_0 = sqrt(M) r_cm)
-template <typename T>
+// state -> modes (D = FP64 or FP32, R_0 = sqrt(M) r_cm)
+template <typename T, typename D>
 __global__ void k_store_modes(const T* __restrict__ R, const double* __restrict__ com,
-                              double* __restrict__ dst, int C, int M, double sqrtM)
+                              D* __restrict__ dst, int C, int M, double sqrtM)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)C * 3 * M) return;
     const int p = (int)(t % M);
-    dst[t] = (p == 0) ? com[t / M] * sqrtM : (double)R[t];
+    dst[t] = (p == 0) ? (D)(com[t / M] * sqrtM) : (D)R[t];
 }
 
 template <typename T>
