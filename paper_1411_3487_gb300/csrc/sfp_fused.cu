@@ -103,10 +103,15 @@ static_assert(2 + kComputeWarps == 10 && kComputeWarps == 8, "warp numbering of 
 // K block of 32: TF32 operands are FP32-sized with a 128-byte swizzle (the R
 // tile of an inverse block lands in A hi and is split in place); BF16
 // operands are 2 bytes with a 64-byte swizzle, and the FP32 R tile (16 KB)
-// either has a staging area R of its own (RS: the single-CTA kernel, three
-// stages at M = 256, measured faster) or lands in A hi + A lo, which the
-// compute warps read out in full before they write the hi and lo parts over
-// it (the 512-bead kernel, four stages instead of three).
+// either has a staging area R of its own (RS) or lands in A hi + A lo, which
+// the compute warps read out in full before they write the hi and lo parts
+// over it.  The single-CTA kernel stages R on its own at 64 and 128 beads
+// (four stages either way) and in place at 256 beads, where that gives four
+// stages of 48 KB instead of three of 64 KB (24.2 -> 23.1 us per step at
+// 4096 x 256 bp; with mode-keyed noise, whose steps have no noise blocks,
+// three stages stay faster: 24.0 against 24.5 us); the 512-bead kernel splits
+// in place.
+template <int NB, bool BF, bool MZ = false> constexpr bool kRS = BF && (NB != 256 || MZ);
 template <int NB, bool BF, bool RS>
 struct FSmem {
     static constexpr int kEl = BF ? 2 : 4;
@@ -309,7 +314,7 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
                                            const CUtensorMap& tmFL, const FusedArgs& a, int tile, uint8_t* smem,
                                            uint32_t tmem)
 {
-    using S = FSmem<NB, BF, BF>;        // BF16: a separate FP32 R staging area per stage
+    using S = FSmem<NB, BF, kRS<NB, BF, MZ>>;
     constexpr int ST = S::kStages;
     constexpr int KB = NB / kKB;        // inverse K blocks = forward bead blocks
     constexpr int NBLK = MZ ? 2 * KB : 3 * KB;   // blocks of one step, in the order of sched_decode (MZ: sched_mz)
@@ -745,7 +750,46 @@ __device__ __forceinline__ bool fused_tile(const CUtensorMap& tmR, const CUtenso
             // producer's release counter first (that use is consumed) makes it exact.
             ok = ok && count_wait(s_freed, blk, a.err, abort_flag);
             ok = ok && mbar_wait(&full[s], ph, a.err, abort_flag);
-            if (ok && BF) {
+            if (BF && !S::kR) {
+                // in place: every compute thread reads its values, the compute warps
+                // meet (all of them, whether or not a wait gave up), then the hi / lo
+                // parts go over the FP32 tile
+                uint8_t* base = stage0 + s * S::kStage;
+                float xv[kRows * 4 / kCompute][8];
+#pragma unroll
+                for (int e = 0; e < kRows * 4 / kCompute; ++e) {
+                    const int t = ct + kCompute * e;
+                    const int r = t >> 2, c = t & 3;
+                    if (ok && (r & 31) < 3 * cpq) {
+#pragma unroll
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            const float4 x = *reinterpret_cast<const float4*>(base + swz(r, 8 * c + 4 * h2));
+                            xv[e][4 * h2] = x.x; xv[e][4 * h2 + 1] = x.y; xv[e][4 * h2 + 2] = x.z; xv[e][4 * h2 + 3] = x.w;
+                        }
+                    }
+                }
+                __syncwarp();
+                asm volatile("bar.sync 1, %0;" ::"n"(kCompute) : "memory");
+#pragma unroll
+                for (int e = 0; e < kRows * 4 / kCompute; ++e) {
+                    const int t = ct + kCompute * e;
+                    const int r = t >> 2, c = t & 3;
+                    if (ok && (r & 31) < 3 * cpq) {
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const uint16_t h0 = bf16_rn(xv[e][2 * i]), h1 = bf16_rn(xv[e][2 * i + 1]);
+                            hw[i] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                            lw[i] = (uint32_t)bf16_rn(xv[e][2 * i] - bf16_f(h0)) |
+                                    ((uint32_t)bf16_rn(xv[e][2 * i + 1] - bf16_f(h1)) << 16);
+                        }
+                        const uint32_t o = swz_bf(r, 8 * c);
+                        *reinterpret_cast<uint4*>(base + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4*>(base + S::kA + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                }
+                if (ok) fence_proxy_async();
+            } else if (ok && BF) {
                 // row t/4, BF16 chunk t%4 (8 values) from the FP32 staging tile
                 const uint8_t* r32 = stage0 + s * S::kStage;
                 uint8_t* ah = stage0 + s * S::kStage + S::kR;
@@ -1605,7 +1649,7 @@ template <int NB, bool BF, bool TWO = false, bool MZ = false>
 static cudaError_t set_smem()
 {
     return cudaFuncSetAttribute(k_fused_step<NB, BF, TWO, MZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                FSmem<NB, BF, BF>::kBytes);
+                                FSmem<NB, BF, kRS<NB, BF, MZ>>::kBytes);
 }
 template <bool BF, bool TWO = false>
 static cudaError_t set_smem_pair()
@@ -1742,13 +1786,13 @@ int fused_step(FusedPlan* p, const FusedArgs& args, cudaStream_t stream)
     if (p->mz && (p->two || p->M > 256)) return report(SFP_ENOTSUP, "mode-keyed noise: M <= 256, three passes");
 #define SFP_FUSED_LAUNCH(NBV, BFV)                                                                   \
     if (p->mz)                                                                                       \
-        k_fused_step<NBV, BFV, false, true><<<grid, kThreads, FSmem<NBV, BFV, BFV>::kBytes, stream>>>( \
+        k_fused_step<NBV, BFV, false, true><<<grid, kThreads, FSmem<NBV, BFV, kRS<NBV, BFV, true>>::kBytes, stream>>>( \
             p->tmR, p->tmChiH, p->tmChiL, p->tmFH, p->tmFL, a);                                      \
     else if (p->two)                                                                                 \
-        k_fused_step<NBV, BFV, BFV><<<grid, kThreads, FSmem<NBV, BFV, BFV>::kBytes, stream>>>(         \
+        k_fused_step<NBV, BFV, BFV><<<grid, kThreads, FSmem<NBV, BFV, kRS<NBV, BFV>>::kBytes, stream>>>(         \
             p->tmR, p->tmChiH, p->tmChiL, p->tmFH, p->tmFL, a);                                      \
     else                                                                                             \
-        k_fused_step<NBV, BFV><<<grid, kThreads, FSmem<NBV, BFV, BFV>::kBytes, stream>>>(              \
+        k_fused_step<NBV, BFV><<<grid, kThreads, FSmem<NBV, BFV, kRS<NBV, BFV>>::kBytes, stream>>>(              \
             p->tmR, p->tmChiH, p->tmChiL, p->tmFH, p->tmFL, a)
     cudaError_t e = cudaSuccess;
     switch (p->M * 2 + (p->bf16 ? 1 : 0)) {
